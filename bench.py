@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark: solves of the heat-equation KKT system to a 1e-8 relative residual on GB300.
+
+One step = one full solve (x_0 = 0) of the 256 x 256, Nt = 1024, N_D = 64 FP64 problem
+(nu = 1, omega = 1e-4, seeded random low-mode sine-series target): flexible GMRES(30) with the
+block preconditioner whose Schur block is the two-level time-DD inverse, every step of it in
+the library's CUDA kernels. Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--omega W]
+
+Multi-GPU: one process per GPU (torchrun); every rank solves its own replica (the path has no
+exchange step on one instance here), the timing is the max over ranks, value = solves of all
+ranks / time. --impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload, on rank 0 only.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "KKT solve time to 1e-8 rel. residual; precond applies/s; HBM GB/s vs peak"
+TOL = 1e-8
+MAXIT = 420
+# Roofline denominators: HBM from the measured copy (MEASURED_PEAKS.json when present, else the
+# recipe's fallback); FP64 from the unit count: 2 DFMA per SM per clock x 152 SMs x 2070 MHz.
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+def workload_for(omega: float) -> workloads.Workload:
+    w = workloads.CFG_GPU
+    return workloads.Workload(w.name, nx=w.nx, ny=w.ny, Nt=w.Nt, n_sub=w.n_sub, nu=w.nu, omega=omega,
+                              target=w.target, seed=w.seed)
+
+
+def describe(w: workloads.Workload) -> dict:
+    return {"workload": f"plain FP64 KKT solve nx=ny={w.nx} Nt={w.Nt} N_D={w.n_sub} nu={w.nu} omega={w.omega:g}",
+            "nx": w.nx, "ny": w.ny, "Nt": w.Nt, "n_sub": w.n_sub, "nu": w.nu, "omega": w.omega,
+            "unknowns": 3 * w.V, "tol": TOL, "restart": 30, "coarse": "exact two-level, multiplicative",
+            "l2": "inputs larger than L2 (KKT vector 1.6 GB, Krylov basis ~66 GB)"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------------------------
+
+def oracle_iteration_sample(w: workloads.Workload, krylov_dim: int) -> tuple[float, str]:
+    """Seconds of one FGMRES iteration of the FP64 oracle on the full workload, from a sample.
+
+    Timed pieces, each scaled to the full iteration by the share it processed:
+    RASQ sweeps of 4 of the N_D subdomains (x N_D/4), the per-mode coarse solve of the first
+    4096 modes (x N/4096), S-hat x and K x on a 64-slice time window of the same grid and dt
+    (x Nt/64), and the Gram-Schmidt work (2 passes of dots and updates against krylov_dim
+    full vectors, timed in full).
+    """
+    from oracle import problem, schwarz
+    from oracle.problem import HeatKKT
+
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    pre = schwarz.schur_preconditioner(p, w.n_sub, coarse_solver="per-mode")
+    r = workloads.random_vector(p.V, 1)
+    t = {}
+    subs = pre.subs
+    t0 = time.perf_counter()
+    pre.subs = subs[:4]
+    pre.rasq(r)
+    pre.subs = subs
+    t["rasq"] = (time.perf_counter() - t0) * (w.n_sub / 4)
+    lim = min(4096, p.N)
+    t0 = time.perf_counter()
+    pre.coarse_per_mode(r, mode_limit=lim)
+    t["coarse"] = (time.perf_counter() - t0) * (p.N / lim)
+    win = 64
+    pw = HeatKKT(nx=w.nx, ny=w.ny, Nt=win, T=p.dt * win, nu=w.nu, omega=w.omega)
+    prew = schwarz.schur_preconditioner(pw, 4, variant="one-level")
+    rw = workloads.random_vector(pw.V, 2)
+    t0 = time.perf_counter()
+    prew.schur_apply(rw)
+    t["schur"] = (time.perf_counter() - t0) * (w.Nt / win)
+    xw = workloads.random_vector(3 * pw.V, 3)
+    t0 = time.perf_counter()
+    problem.kkt_apply_blockwise(pw, xw)
+    t["matvec"] = (time.perf_counter() - t0) * (w.Nt / win)
+    vecs = [workloads.random_vector(3 * p.V, 10 + k) for k in range(2)]
+    t0 = time.perf_counter()
+    for _ in range(2 * krylov_dim):
+        np.dot(vecs[0], vecs[1])
+        vecs[1] -= 1e-3 * vecs[0]
+    t["orth"] = (time.perf_counter() - t0) * 2
+    sample = (f"one FGMRES iteration of the FP64 oracle at full size, sampled: RASQ on 4/{w.n_sub} subdomains, "
+              f"coarse solve on {lim}/{p.N} modes, S-hat and K on a {win}/{w.Nt}-slice window, "
+              f"CGS2 against {krylov_dim} vectors; scaled to the whole iteration")
+    return sum(t.values()), sample
+
+
+def cpu_threads() -> int:
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload_for(args.omega)
+    iters = args.ref_iterations
+    kdim = (iters % 30) // 2 + 1 if iters else 15
+    per = []
+    for step in range(args.warmup + args.steps):
+        s, sample = oracle_iteration_sample(w, kdim)
+        if step >= args.warmup:
+            per.append(s * iters)
+    solve_s = statistics.median(per)
+    value = 1.0 / solve_s
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": describe(w), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": sample + f"; x {iters} iterations (the GPU solve's count)"},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def roofline(kkt_mod, prof: dict, w: workloads.Workload, peaks: dict, peak_kind: str, iters: int,
+             steps: int) -> dict:
+    """Roofline of the kernel class with the largest device time in the timed region.
+
+    Algorithmic work per launch (V = N Nt unknowns per block):
+      dst      2.5 (n-1) log2(2n) FLOP per grid line (one real DST-I of n-1 points; a 2D pass
+               transforms Nt (n-1) lines); FP64-ALU bound on GB300
+      multidot, update, axpy: 2 FLOP per vector element and basis vector (FP64 FMA)
+      matvec   48 V bytes (3 blocks in, 3 out)
+      sweep    16 V bytes (read rhat, write yhat) + coarse pairs
+      coarse   8 V bytes (read rhat)
+    """
+    n = w.nx
+    ms = {k: v["ms"] for k, v in prof.items()}
+    top = max(ms, key=ms.get)
+    launches = max(prof[top]["timed"], 1)
+    avg_s = ms[top] / launches / 1e3
+    V = w.V
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    if top == "dst":
+        flops = (n - 1) * w.Nt * 2.5 * (n - 1) * np.log2(2 * n)
+        ach = flops / avg_s / 1e12
+        return {"kernel": "dst_tile_kernel", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)",
+                "per_launch_ms": avg_s * 1e3}
+    if top in ("multidot", "update", "axpy"):
+        # average basis vectors per launch over the run: total FMAs / launches
+        flops_total = 0.0
+        # one Arnoldi step j touches j+1 vectors in each pass; sum over the cycle (restart 30)
+        per_cycle = sum(j + 1 for j in range(min(iters, 30)))
+        passes = prof[top]["timed"] / max(steps, 1)
+        vec_per_launch = (per_cycle * max(1, iters // 30 + (1 if iters % 30 else 0))) / max(passes, 1)
+        flops_total = 2.0 * 3 * V * vec_per_launch
+        ach = flops_total / avg_s / 1e12
+        return {"kernel": f"{top}_kernel", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)",
+                "per_launch_ms": avg_s * 1e3}
+    bytes_per = {"matvec": 48 * V, "sweep": 16 * V, "coarse": 8 * V, "reduce": 8 * 3 * V}.get(top, 16 * V)
+    ach = bytes_per / avg_s / 1e9
+    return {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": None, "peak_source": f"{peak_kind} HBM copy", "per_launch_ms": avg_s * 1e3}
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2305_04421_gb300.kkt as kkt
+
+    w = workload_for(args.omega)
+    dev = torch.device("cuda", local)
+    solver = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
+    ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
+    f = solver.build_rhs(ut)
+    x = torch.zeros_like(f)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    iters = []
+    for _ in range(args.warmup):
+        x.zero_()
+        res = solver.solve(f, x, tol=TOL, maxit=MAXIT)
+        iters.append(res.iterations)
+    sampler = ClockSampler(local)
+    sampler.start()
+    kkt.kkt_profile_read(reset=True)
+    kkt.kkt_profile_enable(True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = []
+    for _ in range(args.steps):
+        x.zero_()
+        results.append(solver.solve(f, x, tol=TOL, maxit=MAXIT))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    kkt.kkt_profile_enable(False)
+    prof = kkt.kkt_profile_read(reset=True)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ok = all(r.status == kkt.KKT_OK and r.rel_residual <= TOL for r in results)
+    its = results[-1].iterations
+    value = world * args.steps / (ms / 1e3)
+    launches = sum(v["launches"] for v in prof.values())
+    applies = sum(r.iterations for r in results)
+    # end to end through the C ABI with host buffers: H2D of f and x0, D2H of x inside the timed region
+    f_host = f.cpu().pin_memory()
+    x_host = torch.zeros(f.numel(), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x_host.zero_()
+        r = solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = f.numel() * 8
+    peaks, peak_kind = measured_peaks()
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": describe(w),
+            "iterations": its, "converged": ok, "rel_residual": results[-1].rel_residual,
+            "precond_applies_per_s": world * applies / (ms / 1e3),
+            "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
+                    "d2h_bytes_per_step": nbytes},
+            "gpu_launches": launches,
+            "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
+            "kernel_launches": {k: v["launches"] for k, v in prof.items()},
+            "clocks": clocks}
+    line["roofline"] = roofline(kkt, prof, w, peaks, peak_kind, its, args.steps)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s, sample = oracle_iteration_sample(w, min(its, 30) // 2 + 1)
+        line["cpu_baseline"] = {"value": 1.0 / (s * its), "unit": "solves/s", "cores": cpu_threads(),
+                                "kind": "oracle", "sample": sample + f"; x {its} iterations"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    solver.close()
+    return 0 if ok else 1
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--omega", type=float, default=1e-4)
+    ap.add_argument("--ref-iterations", type=int, default=32,
+                    help="iterations the reference arm scales its per-iteration sample by")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,208 @@
+/*
+ * kkt.h - C ABI of the GB300 solver for the heat-equation-constrained KKT system of
+ * Cyr, "A 2-Level Domain Decomposition Preconditioner for KKT Systems with Heat-Equation
+ * Constraints" (arXiv 2305.04421).
+ *
+ * Problem (Section 1, Eq 1; discretised in Section 2, Eqs 2-5): minimise
+ *   1/2 int ||u - u~||^2 dt + omega/2 int ||z||^2 dt  subject to  u_t - nu Lap u = z,
+ * on (0,Lx) x (0,Ly) with u = 0 on the boundary, u(0) = u_0, 5-point finite differences on
+ * nx x ny intervals, backward Euler with Nt steps of dt = T/Nt. The optimality system is
+ *   K (u, z, w) = (f_u, f_z, f),  K = [[M_u, 0, J^T], [0, omega M_z, L^T], [J, L, 0]]   (Eq 5)
+ * with M_u = M_z = h I, h = dt dx dy, J block lower bidiagonal (diagonal I + dt nu A,
+ * sub-diagonal -I) and L = -dt I.
+ *
+ * Vector layout (every double* below): a KKT vector is three blocks u | z | w, each of
+ * V = Nt * (ny-1) * (nx-1) doubles ordered [n][j][i], n = 1..Nt the time node, j the y index,
+ * i the x index (fastest). A "block" argument is one such V-vector.
+ *
+ * Pointers: unless an entry point says otherwise, vector pointers are DEVICE pointers (for
+ * instance from torch CUDA tensors), contiguous, 8-byte aligned, owned by the caller; the
+ * library never keeps them after the call returns. Input and output must not overlap unless
+ * stated. `stream` is a cudaStream_t (NULL = the legacy default stream); the
+ * asynchronous entry points only enqueue work on it.
+ *
+ * Errors: every int-returning entry point returns KKT_OK (0) on success, KKT_NOT_CONVERGED (1)
+ * when a solve stopped at maxit, and a negative KKT_ERR_* code on failure; kkt_last_error()
+ * then returns a message for the calling thread. A handle is not thread-safe: use one handle
+ * per host thread and stream.
+ */
+#ifndef KKT_H
+#define KKT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum kkt_status {
+  KKT_OK = 0,
+  KKT_NOT_CONVERGED = 1,
+  KKT_ERR_INVALID_ARG = -1,
+  KKT_ERR_OOM = -2,
+  KKT_ERR_CUDA = -3,
+  KKT_ERR_NONFINITE = -4,
+  KKT_ERR_TIMEOUT = -5,
+  KKT_ERR_BREAKDOWN = -6,
+  KKT_ERR_UNSUPPORTED = -7
+};
+
+/* Arithmetic of the spatial transforms and time sweeps inside the preconditioner. */
+enum kkt_precision {
+  KKT_PREC_FP64 = 0,   /* FP64 everywhere */
+  KKT_PREC_BF16 = 1,   /* DST GEMMs on tcgen05 tensor cores, BF16 in, FP32 accumulate; FP32 sweeps */
+  KKT_PREC_TF32 = 2    /* as BF16 with TF32 operands */
+};
+
+/* Coarse level of the Schur-complement preconditioner (Section 3, Eqs 14-15). */
+enum kkt_coarse {
+  KKT_COARSE_EXACT = 0,    /* Nicolaides coarse space, exact coarse solve: the two-level method */
+  KKT_COARSE_NONE = 1,     /* one-level RASQ (Eq 13) */
+  KKT_COARSE_LEARNED = 2   /* learned correction on the lowest modes, exact solve elsewhere */
+};
+
+/* How the coarse correction is composed with RASQ (Eq 15). */
+enum kkt_variant {
+  KKT_MULTIPLICATIVE = 0,  /* x0 = R0^T S0^-1 R0 r ; y = x0 + S_RASQ^-1 (r - S-hat x0) */
+  KKT_ADDITIVE = 1         /* y = R0^T S0^-1 R0 r + S_RASQ^-1 r */
+};
+
+/* Owner of the time node shared by neighbouring subdomains (boolean partition of unity D_s). */
+enum kkt_pou {
+  KKT_POU_LEFT = 0,   /* the subdomain whose last step ends on the node */
+  KKT_POU_RIGHT = 1   /* the subdomain whose first step starts from the node */
+};
+
+typedef struct kkt_options {
+  int precision;    /* enum kkt_precision, default KKT_PREC_FP64 */
+  int coarse;       /* enum kkt_coarse, default KKT_COARSE_EXACT */
+  int variant;      /* enum kkt_variant, default KKT_MULTIPLICATIVE */
+  int pou;          /* enum kkt_pou, default KKT_POU_LEFT */
+  int restart;      /* FGMRES restart length, 1..32, default 30 */
+  int jhat_sign;    /* -1 (default): Jhat = J - omega^-1/2 L; +1: the sign printed in Eq 7 */
+  double Lx, Ly;    /* domain (0,Lx) x (0,Ly), default 1, 1 */
+} kkt_options;
+
+typedef struct kkt_info {
+  int nx, ny, Nt, n_sub;
+  long long N;          /* (nx-1)(ny-1) spatial unknowns per time node */
+  long long V;          /* N * Nt, unknowns per block */
+  double dx, dy, dt, h; /* h = dt dx dy */
+  long long workspace_bytes;  /* device memory the handle holds now */
+} kkt_info;
+
+#define KKT_HISTORY_MAX 1024
+typedef struct kkt_stats {
+  int iterations;          /* Arnoldi steps taken (one preconditioner apply + one matvec each) */
+  int restarts;            /* completed restart cycles */
+  int precond_applies;
+  int status;              /* same value the solve returned */
+  double rel_residual;     /* ||f - K x||_2 / ||f||_2 recomputed from x at exit */
+  double time_ms;          /* wall time of the solve, host clock */
+  int history_len;
+  double history[KKT_HISTORY_MAX];   /* Arnoldi residual estimate / ||f|| per iteration */
+} kkt_stats;
+
+typedef struct kkt_handle kkt_handle;
+
+/* Message of the last failure on this host thread ("" if none). */
+const char* kkt_last_error(void);
+/* Fixed text for a status code. */
+const char* kkt_status_string(int status);
+/* Fill *opt with the defaults listed in kkt_options. */
+int kkt_default_options(kkt_options* opt);
+
+/*
+ * Create a solver for one KKT instance on the current CUDA device (Section 2).
+ * nx, ny >= 2 grid intervals (powers of two use the fast sine transform, any other size a
+ * direct O(n^2) one); Nt >= 2 time steps on (0, T]; nu > 0 conductivity; omega > 0
+ * regularisation weight; n_sub time subdomains, 1 <= n_sub and Nt / n_sub >= 2 (each
+ * subdomain must span two steps for the linear coarse function of Eq 14). Nt need not be a
+ * multiple of n_sub: subdomain s covers steps floor((s-1)Nt/n_sub)+1 .. floor(s Nt/n_sub).
+ * Returns NULL on failure (kkt_last_error() says why). Allocates the preconditioner's
+ * workspace; the Krylov basis is allocated at the first kkt_solve.
+ */
+kkt_handle* kkt_create(int nx, int ny, int Nt, double T, double nu, double omega, int n_sub);
+/* Release the handle and all device memory it holds. NULL is accepted. */
+void kkt_destroy(kkt_handle* h);
+/* Replace the options; takes effect at the next call. Validates every field. */
+int kkt_set_options(kkt_handle* h, const kkt_options* opt);
+int kkt_get_options(const kkt_handle* h, kkt_options* opt);
+int kkt_get_info(const kkt_handle* h, kkt_info* info);
+
+/*
+ * f = (f_u, f_z, f) of Eq 5 for a target u_target (a block, [n][j][i], values at t_n = n dt)
+ * and an initial state u0 ([j][i], N doubles; NULL means 0): f_u = h u~, f_z = 0, and f is
+ * u0 in its first time slice, 0 elsewhere. Pointers may be host or device memory
+ * (detected per pointer); host buffers are copied synchronously.
+ */
+int kkt_build_rhs(kkt_handle* h, const double* u_target, const double* u0, double* f, void* stream);
+
+/* y = K x (Eq 5), x and y full KKT vectors (3V). Fused single pass; asynchronous. */
+int kkt_matvec(kkt_handle* h, const double* x, double* y, void* stream);
+
+/*
+ * y = P^{-1} r for the block preconditioner of Eq 7: y_u = r_u / h, y_z = r_z / (omega h),
+ * y_w = S-hat_2level^{-1} r_w (Eqs 13-15 with the options' coarse/variant/pou). Full KKT
+ * vectors; asynchronous; uses the handle's workspace, so calls on one handle must not overlap.
+ */
+int kkt_precond_apply(kkt_handle* h, const double* r, double* y, void* stream);
+
+/*
+ * Solve K x = f with right-preconditioned flexible GMRES(restart) (Section 4), stopping when
+ * ||f - K x||_2 / ||f||_2 <= tol (checked on the recomputed residual) or after maxit
+ * iterations. x holds the initial guess on entry and the solution on exit. f and x may be
+ * host or device memory (detected per pointer; host data is staged through the handle).
+ * Synchronises `stream`. Returns KKT_OK, KKT_NOT_CONVERGED (x = last iterate), or an error
+ * (KKT_ERR_NONFINITE if f or an iterate is not finite, KKT_ERR_BREAKDOWN on a zero
+ * Hessenberg pivot before convergence). stats may be NULL.
+ */
+int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit,
+              kkt_stats* stats, void* stream);
+
+/* ---- single steps of the path (device pointers, asynchronous) ------------------------- */
+
+/* out = Q in for every time slice: the orthonormal 2D DST-I along x then y (Q^2 = I), which
+ * diagonalises the 5-point Laplacian of Eq 2. Blocks in [n][j][i]; in == out is allowed. */
+int kkt_dst2d(kkt_handle* h, const double* in, double* out, void* stream);
+
+/* y = S-hat x = Jhat M_u^{-1} Jhat^T x (Eq 7), blocks. */
+int kkt_schur_apply(kkt_handle* h, const double* x, double* y, void* stream);
+
+/* y = S-hat_2level^{-1} r (Eqs 13-15, per the options), blocks: the w-block of P^{-1}. */
+int kkt_schur_precond_apply(kkt_handle* h, const double* r, double* y, void* stream);
+
+/* x0 = R_0^T S_0^{-1} R_0 r, the coarse correction alone (Eq 14 and the operator after it),
+ * blocks. Needs coarse = KKT_COARSE_EXACT. */
+int kkt_coarse_apply(kkt_handle* h, const double* r, double* x0, void* stream);
+
+/* ---- instrumentation ------------------------------------------------------------------ */
+
+/* Kernel classes counted and timed by the library (process-wide, all handles). */
+enum kkt_kernel_class {
+  KKT_K_DST = 0,       /* 2D sine transform passes (rows or columns) */
+  KKT_K_COARSE = 1,    /* coarse restriction + block-tridiagonal coarse solve */
+  KKT_K_SWEEP = 2,     /* per-subdomain forward/backward sweeps (+ coarse prolongation) */
+  KKT_K_MATVEC = 3,    /* KKT matvec and other stencil passes */
+  KKT_K_MULTIDOT = 4,  /* Gram-Schmidt multi-dot */
+  KKT_K_UPDATE = 5,    /* Gram-Schmidt update + norm */
+  KKT_K_AXPY = 6,      /* solution update and elementwise passes */
+  KKT_K_REDUCE = 7,    /* reduction finalisation and norms */
+  KKT_K_COUNT = 8
+};
+
+typedef struct kkt_kernel_stats {
+  long long launches[KKT_K_COUNT];  /* kernels launched, always counted */
+  double ms[KKT_K_COUNT];           /* summed device time (CUDA events), only while timing is on */
+  long long timed[KKT_K_COUNT];     /* launches that were timed */
+} kkt_kernel_stats;
+
+/* Turn per-launch CUDA-event timing on (1) or off (0); each timed launch records two events on
+ * its stream. Process-wide; not thread-safe against concurrent solves. */
+int kkt_profile_enable(int on);
+/* Copy the counters (synchronising on the pending timing events) and, if reset != 0, zero them. */
+int kkt_profile_read(kkt_kernel_stats* out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KKT_H */

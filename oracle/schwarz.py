@@ -124,7 +124,8 @@ class SchurPreconditioner:
     """
 
     def __init__(self, Bhat, Nt: int, n_sub: int, h: float, *, pou: str = "left",
-                 variant: str = "multiplicative", build_coarse: bool = True):
+                 variant: str = "multiplicative", build_coarse: bool = True, mode_diagonal=None,
+                 mode_transform=None):
         self.Bhat = sp.csr_matrix(Bhat, dtype=np.float64)
         self.N = self.Bhat.shape[0]
         self.Nt = Nt
@@ -138,7 +139,12 @@ class SchurPreconditioner:
         self._S = None
         self._Z = None
         self._S0_lu = None
-        if build_coarse and variant != "one-level":
+        # Optional per-mode coarse solve (for grids where the sparse coarse LU does not fit):
+        # mode_diagonal[q] is Bhat's eigenvalue on mode q and mode_transform(X) applies the
+        # orthonormal, involutory transform that diagonalises Bhat to each row X[t] (length N).
+        self.mode_diagonal = None if mode_diagonal is None else np.asarray(mode_diagonal, np.float64).ravel()
+        self.mode_transform = mode_transform
+        if build_coarse and variant not in ("one-level", "ras") and self.mode_diagonal is None:
             self._build_coarse()
 
     # ----- S-hat = Jhat M_u^{-1} Jhat^T (Eq 7) ---------------------------------------------
@@ -265,9 +271,40 @@ class SchurPreconditioner:
 
     def coarse(self, r):
         """R_0^T S_0^{-1} R_0 r."""
+        if self.mode_diagonal is not None:
+            return self.coarse_per_mode(r)
         if self._S0_lu is None:
             self._build_coarse()
         return self.Z @ self._S0_lu.solve(self.Z.T @ r)
+
+    def coarse_per_mode(self, r, chunk: int = 1024, mode_limit: int | None = None):
+        """R_0^T S_0^{-1} R_0 r with S_0 solved mode by mode.
+
+        Z = Z_t kron I_N commutes with the spatial transform Q, and Q Bhat Q = diag(mu), so
+        S_0 = (I kron Q) blockdiag_q(Z_t^T T(mu_q) Z_t / h) (I kron Q), where
+        T(mu) = Jhat Jhat^T for the scalar diagonal mu: mu^2 I + D - mu E, D = diag(0, 1, .., 1)
+        and E the time shift in both directions. Each mode's 2 N_D x 2 N_D system is solved
+        densely (numpy.linalg.solve), in batches of modes.
+        """
+        Zt = self.coarse_time_basis().toarray()
+        Nt = self.Nt
+        D = np.ones(Nt)
+        D[0] = 0.0
+        E = np.eye(Nt, k=1) + np.eye(Nt, k=-1)
+        G1 = Zt.T @ Zt
+        G2 = Zt.T @ (D[:, None] * Zt)
+        G3 = Zt.T @ E @ Zt
+        R = r.reshape(Nt, self.N)
+        c = Zt.T @ R                                   # R_0 r: [2 N_D][N]
+        chat = self.mode_transform(c)                  # into the sine basis, row by row
+        out = np.zeros_like(chat)
+        mu = self.mode_diagonal
+        for q0 in range(0, self.N if mode_limit is None else min(mode_limit, self.N), chunk):
+            m = mu[q0:q0 + chunk]
+            S0 = (m[:, None, None] ** 2 * G1[None] + G2[None] - m[:, None, None] * G3[None]) / self.h
+            out[:, q0:q0 + chunk] = np.linalg.solve(S0, chat[:, q0:q0 + chunk].T[:, :, None])[:, :, 0].T
+        x = self.mode_transform(out)
+        return (Zt @ x).ravel()
 
     # ----- two-level composition (Eq 15) ---------------------------------------------------
     def apply(self, r):
@@ -284,8 +321,23 @@ class SchurPreconditioner:
         raise ValueError(self.variant)
 
 
-def schur_preconditioner(p: HeatKKT, n_sub: int, *, jhat_sign: int = -1, **kw) -> SchurPreconditioner:
-    """The approximate Schur inverse of the physical problem (Bhat from jhat_diagonal_block)."""
+def schur_preconditioner(p: HeatKKT, n_sub: int, *, jhat_sign: int = -1, coarse_solver: str = "sparse-lu",
+                         **kw) -> SchurPreconditioner:
+    """The approximate Schur inverse of the physical problem (Bhat from jhat_diagonal_block).
+
+    coarse_solver="sparse-lu" factors Z^T S-hat Z as a sparse matrix (the literal definition);
+    "per-mode" solves it in the sine basis (see SchurPreconditioner.coarse_per_mode), which a
+    test checks against the sparse factorisation.
+    """
+    if coarse_solver == "per-mode":
+        from . import spectral
+
+        mu = spectral.jhat_mode_diagonal(p, jhat_sign)
+
+        def transform(X):
+            return spectral.dst2(X, p).reshape(X.shape[0], -1)
+
+        kw = dict(kw, mode_diagonal=mu, mode_transform=transform)
     return SchurPreconditioner(jhat_diagonal_block(p, jhat_sign), p.Nt, n_sub, p.h, **kw)
 
 

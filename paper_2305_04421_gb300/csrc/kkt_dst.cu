@@ -1,0 +1,254 @@
+// Orthonormal DST-I of every grid line of a space-time block: the spatial transform that
+// diagonalises the 5-point Laplacian of Eq 2, so that each implicit step of the sweeps in
+// Eq 13 becomes a division per sine mode (the paper solves the implicit operator in space
+// "with a direct solve", Section 4).
+//
+// For n = 2^p intervals a line of n-1 points is transformed with a real FFT of length n,
+// itself a complex FFT of length n/2 (radix-2, decimation in time, in shared memory):
+//   y_0 = 0, y_j = sin(j pi/n)(x_j + x_{n-j}) + (x_j - x_{n-j})/2,   j = 1..n-1
+//   Y_k = sum_j y_j exp(-2 pi i j k / n) = R_k - i I_k
+//   S_2k = I_k,  S_2k+1 = S_2k-1 + R_k  (S_1 = R_0 / 2),   S_k = sum_j x_j sin(pi j k / n)
+// (the odd-symmetric DST-I folded onto a half-length real transform; the odd outputs are a
+// prefix sum, computed with a warp scan). Other n use the direct O(n^2) sum.
+//
+// Work layout: a CTA stages a tile of `tile_lines` lines in shared memory with coalesced
+// loads (rows: one contiguous run; columns: 32 consecutive columns per grid row), each of
+// its 8 warps transforms whole lines, and the tile is stored back the same way.
+// Every output element is written by exactly one thread; in == out is allowed.
+#include <cmath>
+
+#include "kkt_internal.cuh"
+
+namespace kkt {
+namespace {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+
+struct DstLaunch {
+  const double* in;
+  double* out;
+  int n, logn, M, ldt, tile_lines;
+  int mode;                 // 0: lines are rows (along x), 1: lines are columns (along y)
+  long long total_lines;    // rows mode: number of rows in the block
+  int cols;                 // columns mode: columns per slice (the row length Mx)
+  long long slice;          // columns mode: elements per slice
+  int tiles_per_slice;      // columns mode
+  double scale;             // 1 / sqrt(2 n)
+  const double* pre;
+  const double2* tw;
+  const double2* post;
+  const double* sintab;
+};
+
+__device__ __forceinline__ int bit_reverse(int v, int bits) {
+  return bits > 0 ? static_cast<int>(__brev(static_cast<unsigned>(v)) >> (32 - bits)) : 0;
+}
+
+// One warp, one line x[0..n-2] (x[j-1] holds the j-th point), in place. buf: n/2 double2.
+__device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int lane) {
+  const int n = L.n, P = n >> 1, logp = L.logn - 1;
+  for (int j = lane; j < n; j += 32) {
+    double yj = 0.0;
+    if (j > 0) {
+      const double a = x[j - 1], b = x[n - j - 1];
+      yj = fma(L.pre[j <= P ? j : n - j], a + b, 0.5 * (a - b));
+    }
+    reinterpret_cast<double*>(buf + bit_reverse(j >> 1, logp))[j & 1] = yj;
+  }
+  __syncwarp();
+  for (int s = 1; s <= logp; ++s) {
+    const int half = 1 << (s - 1);
+    for (int b = lane; b < (P >> 1); b += 32) {
+      const int k = b & (half - 1);
+      const int i0 = ((b >> (s - 1)) << s) + k;
+      const int i1 = i0 + half;
+      const double2 w = L.tw[k << (logp - s)];
+      const double2 u = buf[i0], v = buf[i1];
+      const double tr = fma(v.x, w.x, -v.y * w.y);
+      const double ti = fma(v.x, w.y, v.y * w.x);
+      buf[i0] = make_double2(u.x + tr, u.y + ti);
+      buf[i1] = make_double2(u.x - tr, u.y - ti);
+    }
+    __syncwarp();
+  }
+  // Unpack Y_k (times 2) from the half-length FFT; even outputs directly, odd ones by a scan.
+  const int chunk = P >= 32 ? P / 32 : 1;
+  const int k0 = lane * chunk;
+  const bool active = k0 < P;
+  const double c = L.scale;
+  double total = 0.0;
+  if (active) {
+    for (int t = 0; t < chunk; ++t) {
+      const int k = k0 + t;
+      const double2 zk = buf[k];
+      const double2 zc = buf[(P - k) & (P - 1)];
+      const double er = zk.x + zc.x, ei = zk.y - zc.y;     // Z_k + conj(Z_{P-k})
+      const double orr = zk.y + zc.y, oi = zc.x - zk.x;    // (Z_k - conj(Z_{P-k})) / i
+      const double2 w = L.post[k];                         // exp(-2 pi i k / n)
+      const double yr = fma(w.x, orr, fma(-w.y, oi, er));
+      const double yi = fma(w.x, oi, fma(w.y, orr, ei));
+      if (k > 0) x[2 * k - 1] = -c * yi;                   // S_2k = I_k = -Im Y_k
+      total += (k == 0) ? 0.5 * yr : yr;                   // R_0 / 2 + R_1 + ... + R_k
+      x[2 * k] = total;
+    }
+  }
+  double incl = total;
+  for (int o = 1; o < 32; o <<= 1) {
+    const double v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const double prev = __shfl_up_sync(0xffffffffu, incl, 1);
+  const double excl = lane == 0 ? 0.0 : prev;
+  if (active)
+    for (int t = 0; t < chunk; ++t) x[2 * (k0 + t)] = c * (x[2 * (k0 + t)] + excl);
+  __syncwarp();
+}
+
+// Direct transform for n that is not a power of two: S_k = sum_j x_j sin(pi j k / n).
+__device__ void dst_line_direct(double* x, double* tmp, const DstLaunch& L, int lane) {
+  const int n = L.n, M = L.M, n2 = 2 * n;
+  for (int k = lane + 1; k <= M; k += 32) {
+    double acc = 0.0;
+    int idx = 0;                       // (j k) mod 2n, advanced incrementally
+    for (int j = 1; j <= M; ++j) {
+      idx += k;
+      if (idx >= n2) idx -= n2;
+      acc = fma(x[j - 1], L.sintab[idx], acc);
+    }
+    tmp[k - 1] = acc;
+  }
+  __syncwarp();
+  for (int k = lane; k < M; k += 32) x[k] = tmp[k];
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kThreads) dst_tile_kernel(DstLaunch L) {
+  extern __shared__ double smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* tile = smem;
+  const int tile_words = (L.tile_lines * L.ldt + 1) & ~1;
+  double2* fbuf = reinterpret_cast<double2*>(smem + tile_words) + warp * (L.n >> 1);
+
+  long long base = 0;
+  int nl = 0;
+  if (L.mode == 0) {
+    const long long first = static_cast<long long>(blockIdx.x) * L.tile_lines;
+    { const long long rem = L.total_lines - first; nl = static_cast<int>(rem < L.tile_lines ? rem : L.tile_lines); }
+    base = first * L.M;
+    for (int l = warp; l < nl; l += kWarps)
+      for (int e = lane; e < L.M; e += 32) tile[l * L.ldt + e] = L.in[base + static_cast<long long>(l) * L.M + e];
+  } else {
+    const long long sl = blockIdx.x / L.tiles_per_slice;
+    const int col0 = (blockIdx.x % L.tiles_per_slice) * L.tile_lines;
+    nl = min(L.tile_lines, L.cols - col0);
+    base = sl * L.slice + col0;
+    for (int e = warp; e < L.M; e += kWarps)
+      for (int l = lane; l < nl; l += 32) tile[l * L.ldt + e] = L.in[base + static_cast<long long>(e) * L.cols + l];
+  }
+  __syncthreads();
+  for (int l = warp; l < nl; l += kWarps) {
+    if (L.logn >= 2)
+      dst_line_fft(tile + l * L.ldt, fbuf, L, lane);
+    else
+      dst_line_direct(tile + l * L.ldt, reinterpret_cast<double*>(fbuf), L, lane);
+  }
+  __syncthreads();
+  if (L.mode == 0) {
+    for (int l = warp; l < nl; l += kWarps)
+      for (int e = lane; e < L.M; e += 32) L.out[base + static_cast<long long>(l) * L.M + e] = tile[l * L.ldt + e];
+  } else {
+    for (int e = warp; e < L.M; e += kWarps)
+      for (int l = lane; l < nl; l += 32) L.out[base + static_cast<long long>(e) * L.cols + l] = tile[l * L.ldt + e];
+  }
+}
+
+int tile_lines_for(int n) { return n > 512 ? 16 : 32; }
+
+size_t smem_bytes(int n) {
+  const int M = n - 1;
+  const int ldt = M | 1;
+  const int tl = tile_lines_for(n);
+  const size_t tile_words = (static_cast<size_t>(tl) * ldt + 1) & ~static_cast<size_t>(1);
+  return (tile_words + static_cast<size_t>(kWarps) * n) * sizeof(double);
+}
+
+int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long long total_lines,
+                 int cols, long long slice, long long nslices, cudaStream_t st) {
+  DstLaunch L;
+  L.in = in;
+  L.out = out;
+  L.n = p.n;
+  L.logn = p.logn;
+  L.M = p.n - 1;
+  L.ldt = L.M | 1;
+  L.tile_lines = tile_lines_for(p.n);
+  L.mode = mode;
+  L.total_lines = total_lines;
+  L.cols = cols;
+  L.slice = slice;
+  L.tiles_per_slice = (cols + L.tile_lines - 1) / L.tile_lines;
+  L.scale = 1.0 / std::sqrt(2.0 * p.n);
+  L.pre = p.d_pre;
+  L.tw = p.d_tw;
+  L.post = p.d_post;
+  L.sintab = p.d_sin;
+  const size_t sm = smem_bytes(p.n);
+  KKT_CUDA_TRY(cudaFuncSetAttribute(dst_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(sm)));
+  long long grid = mode == 0 ? (total_lines + L.tile_lines - 1) / L.tile_lines
+                             : nslices * L.tiles_per_slice;
+  if (grid <= 0) return KKT_OK;
+  if (grid > 2147483647LL) return set_error(KKT_ERR_UNSUPPORTED, "DST grid too large");
+  ProfScope ps(KKT_K_DST, st);
+  dst_tile_kernel<<<static_cast<unsigned>(grid), kThreads, sm, st>>>(L);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+}  // namespace
+
+int dst_plan_create(DstPlan& p, int n) {
+  if (n < 2 || n > 1024) return set_error(KKT_ERR_UNSUPPORTED, "grid intervals per direction must be in [2, 1024]");
+  p.n = n;
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  p.logn = ((1 << lg) == n && n >= 4) ? lg : -1;
+  const double pi = 3.14159265358979323846;
+  std::vector<double> pre(n / 2 + 1), sintab(2 * n);
+  std::vector<double2> tw(std::max(n / 4, 1)), post(n / 2 + 1);
+  for (int j = 0; j <= n / 2; ++j) pre[j] = std::sin(j * pi / n);
+  for (int k = 0; k < static_cast<int>(tw.size()); ++k)
+    tw[k] = make_double2(std::cos(2 * pi * k / (n / 2)), -std::sin(2 * pi * k / (n / 2)));
+  for (int k = 0; k <= n / 2; ++k) post[k] = make_double2(std::cos(2 * pi * k / n), -std::sin(2 * pi * k / n));
+  const double sc = std::sqrt(2.0 / n);
+  for (int m = 0; m < 2 * n; ++m) sintab[m] = sc * std::sin(m * pi / n);
+  KKT_CUDA_TRY(cudaMalloc(&p.d_pre, pre.size() * sizeof(double)));
+  KKT_CUDA_TRY(cudaMalloc(&p.d_tw, tw.size() * sizeof(double2)));
+  KKT_CUDA_TRY(cudaMalloc(&p.d_post, post.size() * sizeof(double2)));
+  KKT_CUDA_TRY(cudaMalloc(&p.d_sin, sintab.size() * sizeof(double)));
+  KKT_CUDA_TRY(cudaMemcpy(p.d_pre, pre.data(), pre.size() * sizeof(double), cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(p.d_tw, tw.data(), tw.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(p.d_post, post.data(), post.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(p.d_sin, sintab.data(), sintab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return KKT_OK;
+}
+
+void dst_plan_destroy(DstPlan& p) {
+  cudaFree(p.d_pre);
+  cudaFree(p.d_tw);
+  cudaFree(p.d_post);
+  cudaFree(p.d_sin);
+  p = DstPlan();
+}
+
+int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st) {
+  const Geometry& g = h->g;
+  // rows: Nt * My lines of Mx contiguous points (transform along x)
+  KKT_TRY(launch_lines(h->dst_x, in, out, 0, static_cast<long long>(g.Nt) * g.My, g.Mx, 0, 0, st));
+  // columns: per slice, Mx lines of My points with stride Mx (transform along y)
+  KKT_TRY(launch_lines(h->dst_y, out, out, 1, 0, g.Mx, g.N, g.Nt, st));
+  return KKT_OK;
+}
+
+}  // namespace kkt

@@ -1,0 +1,151 @@
+// Internal declarations shared by the CUDA translation units of the KKT solver library.
+// The public C ABI is include/kkt.h; nothing here is exported.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "kkt.h"
+
+namespace kkt {
+
+// Records a message for kkt_last_error() and returns `status`.
+int set_error(int status, const std::string& msg);
+
+#define KKT_CUDA_TRY(expr)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (expr);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return ::kkt::set_error(KKT_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define KKT_TRY(expr)                 \
+  do {                                \
+    int s_ = (expr);                  \
+    if (s_ < 0) return s_;            \
+  } while (0)
+
+// Tables of one orthonormal DST-I of length n-1 (n intervals), resident on the device.
+struct DstPlan {
+  int n = 0;          // intervals; the transform has n-1 points
+  int logn = 0;       // log2(n) when n is a power of two, else -1 (direct transform)
+  double* d_pre = nullptr;    // sin(j pi / n), j = 0..n/2 (pre-processing weights)
+  double2* d_tw = nullptr;    // exp(-2 pi i k / (n/2)), k = 0..n/4-1 (FFT twiddles)
+  double2* d_post = nullptr;  // exp(-2 pi i k / n), k = 0..n/2 (real-FFT unpacking)
+  double* d_sin = nullptr;    // direct transform: sqrt(2/n) sin(pi m / n), m = 0..2n-1
+};
+
+// Time decomposition of Section 3 and the data of the Nicolaides coarse space (Eq 14).
+struct TimeDecomp {
+  int n_sub = 0;
+  int max_len = 0;                    // max nodes of a subdomain (last - first + 1)
+  std::vector<int> first, last;       // per subdomain: first/last time node (1-based)
+  std::vector<int> ofirst, olast;     // per subdomain: owned node range (D_s)
+  std::vector<int> owner;             // per node n (index n-1): owning subdomain (0-based)
+  std::vector<double> phi;            // per node: the linear coarse function of its owner
+  // per subdomain, 2x2 symmetric moment matrices (xx, xy, yy) of (1, phi) over owned nodes:
+  // P0 = sum phi~ phi~^T, P1 = same over nodes >= 2, P2 = sum over owned neighbour pairs of
+  // (phi~_n phi~_{n+1}^T + phi~_{n+1} phi~_n^T); the coarse block is (mu^2 P0 + P1 - mu P2)/h
+  std::vector<double> P0, P1, P2;
+};
+
+// Device copy of TimeDecomp (one allocation).
+struct DeviceDecomp {
+  int n_sub = 0, max_len = 0, Nt = 0;
+  int* first = nullptr;
+  int* last = nullptr;
+  int* ofirst = nullptr;
+  int* olast = nullptr;
+  int* owner = nullptr;
+  double* phi = nullptr;
+  double* moments = nullptr;   // [s][9]: P0 (3), P1 (3), P2 (3)
+  void* base = nullptr;
+};
+
+struct Geometry {
+  int nx, ny, Nt, n_sub, Mx, My;
+  long long N, V;
+  double T, nu, omega, Lx, Ly, dx, dy, dt, h;
+  double a;        // diagonal shift of Jhat's block: 1 - jhat_sign * dt / sqrt(omega)
+  double dtnu, cx, cy;   // dt nu, dt nu / dx^2, dt nu / dy^2
+};
+
+}  // namespace kkt
+
+struct kkt_handle {
+  kkt::Geometry g;
+  kkt_options opt;
+  int device = 0;
+  kkt::DstPlan dst_x, dst_y;
+  kkt::TimeDecomp td;
+  kkt::DeviceDecomp dd;
+  double* d_lx = nullptr;      // lambda_x[k], k = 1..Mx (eigenvalues of the x second difference)
+  double* d_ly = nullptr;
+  // preconditioner workspace
+  double* spec = nullptr;      // V doubles: spectral coefficients [n][l][k]
+  double* spec2 = nullptr;     // V doubles
+  double* coarse_c = nullptr;  // [n_sub][2][N] coarse coefficients
+  double* coarse_w = nullptr;  // [n_sub][5][N] block-Thomas factors
+  double* vscratch = nullptr;  // sweep storage when a subdomain is too long for shared memory
+  int sweep_block = 128;
+  size_t sweep_smem = 0;
+  // Krylov workspace (allocated at the first solve)
+  int kry_restart = 0;
+  double* kV = nullptr;        // (restart+1) full vectors (3V each)
+  double* kZw = nullptr;       // restart w-blocks (V each)
+  double* kx = nullptr;        // staging for host x / f (3V each)
+  double* kf = nullptr;
+  double* red = nullptr;       // reduction partials
+  double* red_out = nullptr;   // reduction results (device)
+  double* h_red = nullptr;     // pinned host copy of reduction results
+  double* dcoef = nullptr;     // device coefficient arrays for multi-axpy
+  size_t bytes = 0;
+};
+
+namespace kkt {
+
+// ---- instrumentation: counts every launch, times it with CUDA events when enabled -------
+void prof_begin(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st);
+struct ProfScope {
+  int cls;
+  cudaStream_t st;
+  ProfScope(int c, cudaStream_t s) : cls(c), st(s) { prof_begin(c, s); }
+  ~ProfScope() { prof_end(cls, st); }
+};
+
+// ---- kernels launched from the C ABI (each defined in its own translation unit) ---------
+int dst_plan_create(DstPlan& p, int n);
+void dst_plan_destroy(DstPlan& p);
+// orthonormal 2D DST-I of every slice: rows (along x) then columns (along y)
+int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st);
+
+int launch_matvec(const kkt_handle* h, const double* u, double su, const double* z, double sz,
+                  const double* w, double sw, double* y, cudaStream_t st);
+int launch_build_rhs(const kkt_handle* h, const double* ut, const double* u0, double* f, cudaStream_t st);
+int launch_scale(const double* x, double s, double* y, long long n, cudaStream_t st);
+int launch_jhat_time(const kkt_handle* h, const double* in, double* out, int dir, double scale,
+                     cudaStream_t st);
+
+// Schur preconditioner in spectral space: in -> out, both [n][l][k] blocks (may alias)
+int spectral_schur_precond(const kkt_handle* h, const double* rhat, double* yhat, double in_scale,
+                           cudaStream_t st);
+int spectral_coarse_only(const kkt_handle* h, const double* rhat, double* xhat, cudaStream_t st);
+
+// Krylov primitives (deterministic two-stage reductions; results in h->red_out on device)
+int krylov_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w,
+                    long long n, cudaStream_t st);   // red_out[k] = <V_k, w>, red_out[count] = <w,w>
+int krylov_update_norm(kkt_handle* h, const double* V, long long stride, int count,
+                       const double* coef_dev, double* w, long long n, cudaStream_t st);  // w -= sum c_k V_k; red_out[0] = <w,w>
+int krylov_axpy_multi(const double* V, long long stride, int count, const double* coef_dev,
+                      double* x, long long n, cudaStream_t st);  // x += sum c_k V_k
+int krylov_norm2(kkt_handle* h, const double* x, long long n, cudaStream_t st);  // red_out[0]
+int krylov_partial_capacity();
+// out = alpha * x + beta * y (elementwise; out may alias x or y)
+int launch_axpby(double alpha, const double* x, double beta, const double* y, double* out, long long n,
+                 cudaStream_t st);
+
+}  // namespace kkt

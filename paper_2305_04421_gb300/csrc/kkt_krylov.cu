@@ -1,0 +1,238 @@
+// Streaming FP64 kernels of the FGMRES Arnoldi process (Section 4: right-preconditioned GMRES):
+// the multi-dot <V_k, w> of classical Gram-Schmidt, the fused multi-axpy w -= sum c_k V_k with
+// the norm of the result, and the solution update x += sum c_k V_k.
+//
+// Reductions are deterministic: a fixed grid of blocks each reduces its grid-stride share
+// (warp shuffles, then shared memory) into one partial per block, and a second kernel sums
+// the partials of each output in a fixed order. Results land in h->red_out on the device.
+#include "kkt_internal.cuh"
+
+namespace kkt {
+namespace {
+
+constexpr int kRedThreads = 256;
+constexpr int kMaxVec = 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sums `val` over the block; valid in thread 0
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < (blockDim.x >> 5) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) multidot_kernel(const double* __restrict__ V, long long stride,
+                                                               const double* __restrict__ w, long long n,
+                                                               double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc[NV + 1];
+#pragma unroll
+  for (int k = 0; k <= NV; ++k) acc[k] = 0.0;
+  const long long gs = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += gs) {
+    const double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = fma(V[k * stride + i], wi, acc[k]);
+    acc[NV] = fma(wi, wi, acc[NV]);
+  }
+#pragma unroll
+  for (int k = 0; k <= NV; ++k) {
+    const double t = block_sum(acc[k], sh);
+    if (threadIdx.x == 0) part[static_cast<long long>(blockIdx.x) * (NV + 1) + k] = t;
+  }
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) update_norm_kernel(const double* __restrict__ V, long long stride,
+                                                                  const double* __restrict__ coef, double* __restrict__ w,
+                                                                  long long n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double c[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) c[k] = coef[k];
+  double acc = 0.0;
+  const long long gs = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += gs) {
+    double wi = w[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) wi = fma(-c[k], V[k * stride + i], wi);
+    w[i] = wi;
+    acc = fma(wi, wi, acc);
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) axpy_multi_kernel(const double* __restrict__ V, long long stride,
+                                                                 const double* __restrict__ coef, double* __restrict__ x,
+                                                                 long long n) {
+  double c[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) c[k] = coef[k];
+  const long long gs = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += gs) {
+    double xi = x[i];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) xi = fma(c[k], V[k * stride + i], xi);
+    x[i] = xi;
+  }
+}
+
+__global__ void norm_kernel(const double* __restrict__ x, long long n, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const long long gs = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long i = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += gs)
+    acc = fma(x[i], x[i], acc);
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// out[k] = sum_b part[b * width + k], one warp per output, fixed order
+__global__ void finalize_kernel(const double* __restrict__ part, int nblocks, int width, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += 32) acc += part[static_cast<long long>(b) * width + k];
+  acc = warp_sum(acc);
+  if (threadIdx.x == 0) out[k] = acc;
+}
+
+int grid_blocks() {
+  static int blocks = 0;
+  if (!blocks) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    blocks = (sms > 0 ? sms : 132) * 4;
+  }
+  return blocks;
+}
+
+template <template <int> class Dispatch, typename... Args>
+int dispatch_nv(int count, Args... args) {
+  switch (count) {
+#define KKT_NV_CASE(k) \
+  case k:              \
+    return Dispatch<k>::run(args...);
+    KKT_NV_CASE(1) KKT_NV_CASE(2) KKT_NV_CASE(3) KKT_NV_CASE(4) KKT_NV_CASE(5) KKT_NV_CASE(6)
+    KKT_NV_CASE(7) KKT_NV_CASE(8) KKT_NV_CASE(9) KKT_NV_CASE(10) KKT_NV_CASE(11) KKT_NV_CASE(12)
+    KKT_NV_CASE(13) KKT_NV_CASE(14) KKT_NV_CASE(15) KKT_NV_CASE(16) KKT_NV_CASE(17) KKT_NV_CASE(18)
+    KKT_NV_CASE(19) KKT_NV_CASE(20) KKT_NV_CASE(21) KKT_NV_CASE(22) KKT_NV_CASE(23) KKT_NV_CASE(24)
+    KKT_NV_CASE(25) KKT_NV_CASE(26) KKT_NV_CASE(27) KKT_NV_CASE(28) KKT_NV_CASE(29) KKT_NV_CASE(30)
+    KKT_NV_CASE(31) KKT_NV_CASE(32)
+#undef KKT_NV_CASE
+    default:
+      return set_error(KKT_ERR_INVALID_ARG, "Krylov kernel vector count out of range");
+  }
+}
+
+template <int NV>
+struct MultidotRun {
+  static int run(const double* V, long long stride, const double* w, long long n, double* part, int nb,
+                 cudaStream_t st) {
+    ProfScope ps(KKT_K_MULTIDOT, st);
+    multidot_kernel<NV><<<nb, kRedThreads, 0, st>>>(V, stride, w, n, part);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
+};
+
+template <int NV>
+struct UpdateRun {
+  static int run(const double* V, long long stride, const double* coef, double* w, long long n, double* part,
+                 int nb, cudaStream_t st) {
+    ProfScope ps(KKT_K_UPDATE, st);
+    update_norm_kernel<NV><<<nb, kRedThreads, 0, st>>>(V, stride, coef, w, n, part);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
+};
+
+template <int NV>
+struct AxpyRun {
+  static int run(const double* V, long long stride, const double* coef, double* x, long long n, int nb,
+                 cudaStream_t st) {
+    ProfScope ps(KKT_K_AXPY, st);
+    axpy_multi_kernel<NV><<<nb, kRedThreads, 0, st>>>(V, stride, coef, x, n);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
+};
+
+}  // namespace
+
+int krylov_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w, long long n,
+                    cudaStream_t st) {
+  const int nb = grid_blocks();
+  int done = 0;
+  // groups of up to 32 vectors; each group writes count_g + 1 partial columns (last = <w,w>)
+  while (done < count) {
+    const int cg = std::min(kMaxVec, count - done);
+    KKT_TRY(dispatch_nv<MultidotRun>(cg, V + done * stride, stride, static_cast<const double*>(w), n, h->red, nb, st));
+    {
+      ProfScope ps(KKT_K_REDUCE, st);
+      finalize_kernel<<<cg + 1, 32, 0, st>>>(h->red, nb, cg + 1, h->red_out + done);
+    }
+    KKT_CUDA_TRY(cudaGetLastError());
+    done += cg;
+  }
+  return KKT_OK;
+}
+
+int krylov_update_norm(kkt_handle* h, const double* V, long long stride, int count, const double* coef_dev,
+                       double* w, long long n, cudaStream_t st) {
+  const int nb = grid_blocks();
+  if (count > kMaxVec) return set_error(KKT_ERR_INVALID_ARG, "too many basis vectors");
+  KKT_TRY(dispatch_nv<UpdateRun>(count, V, stride, coef_dev, w, n, h->red, nb, st));
+  {
+    ProfScope ps(KKT_K_REDUCE, st);
+    finalize_kernel<<<1, 32, 0, st>>>(h->red, nb, 1, h->red_out);
+  }
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int krylov_axpy_multi(const double* V, long long stride, int count, const double* coef_dev, double* x,
+                      long long n, cudaStream_t st) {
+  const int nb = grid_blocks();
+  int done = 0;
+  while (done < count) {
+    const int cg = std::min(kMaxVec, count - done);
+    KKT_TRY(dispatch_nv<AxpyRun>(cg, V + done * stride, stride, coef_dev + done, x, n, nb, st));
+    done += cg;
+  }
+  return KKT_OK;
+}
+
+int krylov_norm2(kkt_handle* h, const double* x, long long n, cudaStream_t st) {
+  const int nb = grid_blocks();
+  {
+    ProfScope ps(KKT_K_REDUCE, st);
+    norm_kernel<<<nb, kRedThreads, 0, st>>>(x, n, h->red);
+  }
+  KKT_CUDA_TRY(cudaGetLastError());
+  {
+    ProfScope ps(KKT_K_REDUCE, st);
+    finalize_kernel<<<1, 32, 0, st>>>(h->red, nb, 1, h->red_out);
+  }
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int krylov_partial_capacity() { return grid_blocks() * (kMaxVec + 1); }
+
+}  // namespace kkt

@@ -1,0 +1,155 @@
+// Stencil kernels on the space-time grid: the KKT matvec of Eq 5, the right-hand side,
+// the time-coupled Jhat / Jhat^T products (Eq 7) and a scaling pass.
+//
+// K (u, z, w) per time node n (Eqs 2-5), with B0 = I + dt nu A and the 5-point A of Eq 2:
+//   y_u^n = h u^n + B0 w^n - w^{n+1}          (w^{Nt+1} = 0)
+//   y_z^n = omega h z^n - dt w^n
+//   y_w^n = B0 u^n - u^{n-1} - dt z^n         (u^0 = 0; the initial state lives in f)
+// One thread per grid point computes all three outputs; every input value is read from
+// global memory, neighbours hit L1/L2.
+#include "kkt_internal.cuh"
+
+namespace kkt {
+namespace {
+
+struct Stencil {
+  int Mx, My, Nt;
+  long long N, V;
+  double c0, cx, cy;   // B v = c0 v - cx (v_w + v_e) - cy (v_s + v_n)
+};
+
+__device__ __forceinline__ double apply_b(const double* __restrict__ v, long long idx, int i, int j,
+                                          const Stencil& s) {
+  const double c = v[idx];
+  const double we = (i > 0 ? v[idx - 1] : 0.0) + (i + 1 < s.Mx ? v[idx + 1] : 0.0);
+  const double sn = (j > 0 ? v[idx - s.Mx] : 0.0) + (j + 1 < s.My ? v[idx + s.Mx] : 0.0);
+  return fma(s.c0, c, -fma(s.cx, we, s.cy * sn));
+}
+
+__global__ void matvec_kernel(const double* __restrict__ u, double su, const double* __restrict__ z,
+                              double sz, const double* __restrict__ w, double sw, double* __restrict__ y,
+                              Stencil s, double h, double omh, double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = blockIdx.z;
+  if (i >= s.Mx || j >= s.My) return;
+  const long long idx = static_cast<long long>(n) * s.N + static_cast<long long>(j) * s.Mx + i;
+  const double bw = apply_b(w, idx, i, j, s) * sw;
+  const double wn = (n + 1 < s.Nt ? w[idx + s.N] : 0.0) * sw;
+  const double bu = apply_b(u, idx, i, j, s) * su;
+  const double up = (n > 0 ? u[idx - s.N] : 0.0) * su;
+  const double zc = z[idx] * sz;
+  const double wc = w[idx] * sw;
+  y[idx] = fma(h * su, u[idx], bw - wn);
+  y[s.V + idx] = fma(omh, zc, -dt * wc);
+  y[2 * s.V + idx] = fma(-dt, zc, bu - up);
+}
+
+// out_n = scale * (B in_n - in_{n+dir}), dir = +1: Jhat^T, dir = -1: Jhat (zero outside 1..Nt)
+__global__ void jhat_time_kernel(const double* __restrict__ in, double* __restrict__ out, Stencil s,
+                                 int dir, double scale) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = blockIdx.z;
+  if (i >= s.Mx || j >= s.My) return;
+  const long long idx = static_cast<long long>(n) * s.N + static_cast<long long>(j) * s.Mx + i;
+  const int nn = n + dir;
+  const double nb = (nn >= 0 && nn < s.Nt) ? in[idx + dir * s.N] : 0.0;
+  out[idx] = scale * (apply_b(in, idx, i, j, s) - nb);
+}
+
+__global__ void rhs_kernel(const double* __restrict__ ut, const double* __restrict__ u0, double* __restrict__ f,
+                           long long V, long long N, double h) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= V) return;
+  f[t] = h * ut[t];
+  f[V + t] = 0.0;
+  f[2 * V + t] = (t < N && u0) ? u0[t] : 0.0;
+}
+
+__global__ void scale_kernel(const double* __restrict__ x, double s, double* __restrict__ y, long long n) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long st = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long k = t; k < n; k += st) y[k] = s * x[k];
+}
+
+__global__ void axpby_kernel(double alpha, const double* __restrict__ x, double beta, const double* __restrict__ y,
+                             double* __restrict__ out, long long n) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long st = static_cast<long long>(gridDim.x) * blockDim.x;
+  for (long long k = t; k < n; k += st) out[k] = fma(alpha, x[k], beta * y[k]);
+}
+
+Stencil make_stencil(const Geometry& g, double shift) {
+  Stencil s;
+  s.Mx = g.Mx;
+  s.My = g.My;
+  s.Nt = g.Nt;
+  s.N = g.N;
+  s.V = g.V;
+  s.cx = g.cx;
+  s.cy = g.cy;
+  s.c0 = shift + 2.0 * g.cx + 2.0 * g.cy;
+  return s;
+}
+
+}  // namespace
+
+int launch_matvec(const kkt_handle* h, const double* u, double su, const double* z, double sz,
+                  const double* w, double sw, double* y, cudaStream_t st) {
+  const Geometry& g = h->g;
+  const Stencil s = make_stencil(g, 1.0);   // B0 = I + dt nu A
+  dim3 tb(32, 8);
+  dim3 grid((g.Mx + 31) / 32, (g.My + 7) / 8, g.Nt);
+  ProfScope ps(KKT_K_MATVEC, st);
+  matvec_kernel<<<grid, tb, 0, st>>>(u, su, z, sz, w, sw, y, s, g.h, g.omega * g.h, g.dt);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int launch_jhat_time(const kkt_handle* h, const double* in, double* out, int dir, double scale,
+                     cudaStream_t st) {
+  const Geometry& g = h->g;
+  const Stencil s = make_stencil(g, g.a);   // Bhat = a I + dt nu A
+  dim3 tb(32, 8);
+  dim3 grid((g.Mx + 31) / 32, (g.My + 7) / 8, g.Nt);
+  ProfScope ps(KKT_K_MATVEC, st);
+  jhat_time_kernel<<<grid, tb, 0, st>>>(in, out, s, dir, scale);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int launch_build_rhs(const kkt_handle* h, const double* ut, const double* u0, double* f, cudaStream_t st) {
+  const Geometry& g = h->g;
+  const int tb = 256;
+  const long long nb = (g.V + tb - 1) / tb;
+  ProfScope ps(KKT_K_AXPY, st);
+  rhs_kernel<<<static_cast<unsigned>(nb), tb, 0, st>>>(ut, u0, f, g.V, g.N, g.h);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int launch_scale(const double* x, double s, double* y, long long n, cudaStream_t st) {
+  if (n <= 0) return KKT_OK;
+  const int tb = 256;
+  long long nb = (n + tb - 1) / tb;
+  if (nb > 65535LL * 8) nb = 65535LL * 8;
+  ProfScope ps(KKT_K_AXPY, st);
+  scale_kernel<<<static_cast<unsigned>(nb), tb, 0, st>>>(x, s, y, n);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int launch_axpby(double alpha, const double* x, double beta, const double* y, double* out, long long n,
+                 cudaStream_t st) {
+  if (n <= 0) return KKT_OK;
+  const int tb = 256;
+  long long nb = (n + tb - 1) / tb;
+  if (nb > 65535LL * 8) nb = 65535LL * 8;
+  ProfScope ps(KKT_K_AXPY, st);
+  axpby_kernel<<<static_cast<unsigned>(nb), tb, 0, st>>>(alpha, x, beta, y, out, n);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+}  // namespace kkt

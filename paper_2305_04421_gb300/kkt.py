@@ -1,0 +1,301 @@
+"""Thin ctypes binding of the C ABI in include/kkt.h (argument marshalling only).
+
+Every function here forwards to ``libkkt.so``; all arithmetic of the method runs in the
+library's CUDA kernels. Device vectors are torch CUDA float64 tensors (contiguous, layout
+[u | z | w] x [n][j][i] as in the header); the stream defaults to torch's current stream.
+If the library is missing, loading raises: there is no fallback implementation.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libkkt.so")
+
+KKT_OK = 0
+KKT_NOT_CONVERGED = 1
+KKT_ERR_INVALID_ARG = -1
+KKT_ERR_OOM = -2
+KKT_ERR_CUDA = -3
+KKT_ERR_NONFINITE = -4
+KKT_ERR_TIMEOUT = -5
+KKT_ERR_BREAKDOWN = -6
+KKT_ERR_UNSUPPORTED = -7
+
+PREC = {"fp64": 0, "bf16": 1, "tf32": 2}
+COARSE = {"exact": 0, "none": 1, "learned": 2}
+VARIANT = {"multiplicative": 0, "additive": 1}
+POU = {"left": 0, "right": 1}
+HISTORY_MAX = 1024
+
+
+class KKTOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("coarse", ctypes.c_int), ("variant", ctypes.c_int),
+                ("pou", ctypes.c_int), ("restart", ctypes.c_int), ("jhat_sign", ctypes.c_int),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double)]
+
+
+class KKTInfo(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("Nt", ctypes.c_int), ("n_sub", ctypes.c_int),
+                ("N", ctypes.c_longlong), ("V", ctypes.c_longlong), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("dt", ctypes.c_double), ("h", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_longlong)]
+
+
+class KKTStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("precond_applies", ctypes.c_int),
+                ("status", ctypes.c_int), ("rel_residual", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("history_len", ctypes.c_int), ("history", ctypes.c_double * HISTORY_MAX)]
+
+
+KERNEL_CLASSES = ["dst", "coarse", "sweep", "matvec", "multidot", "update", "axpy", "reduce"]
+
+
+class KKTKernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * 8), ("ms", ctypes.c_double * 8), ("timed", ctypes.c_longlong * 8)]
+
+
+class KKTError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"kkt status {status}: {message}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+# (name, restype, argtypes) of every exported entry point
+SIGNATURES = [
+    ("kkt_last_error", ctypes.c_char_p, []),
+    ("kkt_status_string", ctypes.c_char_p, [_I]),
+    ("kkt_default_options", _I, [ctypes.POINTER(KKTOptions)]),
+    ("kkt_create", _P, [_I, _I, _I, _D, _D, _D, _I]),
+    ("kkt_destroy", None, [_P]),
+    ("kkt_set_options", _I, [_P, ctypes.POINTER(KKTOptions)]),
+    ("kkt_get_options", _I, [_P, ctypes.POINTER(KKTOptions)]),
+    ("kkt_get_info", _I, [_P, ctypes.POINTER(KKTInfo)]),
+    ("kkt_build_rhs", _I, [_P, _P, _P, _P, _P]),
+    ("kkt_matvec", _I, [_P, _P, _P, _P]),
+    ("kkt_precond_apply", _I, [_P, _P, _P, _P]),
+    ("kkt_solve", _I, [_P, _P, _P, _D, _I, ctypes.POINTER(KKTStats), _P]),
+    ("kkt_dst2d", _I, [_P, _P, _P, _P]),
+    ("kkt_schur_apply", _I, [_P, _P, _P, _P]),
+    ("kkt_schur_precond_apply", _I, [_P, _P, _P, _P]),
+    ("kkt_coarse_apply", _I, [_P, _P, _P, _P]),
+    ("kkt_profile_enable", _I, [_I]),
+    ("kkt_profile_read", _I, [ctypes.POINTER(KKTKernelStats), _I]),
+]
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libkkt.so (built by paper_2305_04421_gb300.build). Raises if it is absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"{p} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(p)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _check(status: int) -> int:
+    if status < 0:
+        lib = load_library()
+        raise KKTError(status, lib.kkt_last_error().decode())
+    return status
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("vectors must be contiguous float64 tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+# ---- same-named wrappers of the C entry points ----------------------------------------------
+
+def kkt_create(nx, ny, Nt, T, nu, omega, n_sub) -> int:
+    lib = load_library()
+    h = lib.kkt_create(nx, ny, Nt, T, nu, omega, n_sub)
+    if not h:
+        raise KKTError(KKT_ERR_INVALID_ARG, lib.kkt_last_error().decode())
+    return h
+
+
+def kkt_destroy(h) -> None:
+    load_library().kkt_destroy(h)
+
+
+def kkt_set_options(h, opt: KKTOptions) -> int:
+    return _check(load_library().kkt_set_options(h, ctypes.byref(opt)))
+
+
+def kkt_get_options(h) -> KKTOptions:
+    opt = KKTOptions()
+    _check(load_library().kkt_get_options(h, ctypes.byref(opt)))
+    return opt
+
+
+def kkt_get_info(h) -> KKTInfo:
+    info = KKTInfo()
+    _check(load_library().kkt_get_info(h, ctypes.byref(info)))
+    return info
+
+
+def kkt_build_rhs(h, u_target, u0, f, stream=None) -> int:
+    return _check(load_library().kkt_build_rhs(h, _ptr(u_target), _ptr(u0), _ptr(f), _stream(stream)))
+
+
+def kkt_matvec(h, x, y, stream=None) -> int:
+    return _check(load_library().kkt_matvec(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def kkt_precond_apply(h, r, y, stream=None) -> int:
+    return _check(load_library().kkt_precond_apply(h, _ptr(r), _ptr(y), _stream(stream)))
+
+
+def kkt_solve(h, f, x, tol, maxit, stats: KKTStats | None = None, stream=None) -> int:
+    st = stats if stats is not None else KKTStats()
+    return _check(load_library().kkt_solve(h, _ptr(f), _ptr(x), tol, maxit, ctypes.byref(st), _stream(stream)))
+
+
+def kkt_dst2d(h, x, y, stream=None) -> int:
+    return _check(load_library().kkt_dst2d(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def kkt_schur_apply(h, x, y, stream=None) -> int:
+    return _check(load_library().kkt_schur_apply(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def kkt_schur_precond_apply(h, r, y, stream=None) -> int:
+    return _check(load_library().kkt_schur_precond_apply(h, _ptr(r), _ptr(y), _stream(stream)))
+
+
+def kkt_coarse_apply(h, r, y, stream=None) -> int:
+    return _check(load_library().kkt_coarse_apply(h, _ptr(r), _ptr(y), _stream(stream)))
+
+
+def kkt_profile_enable(on: bool) -> int:
+    return _check(load_library().kkt_profile_enable(1 if on else 0))
+
+
+def kkt_profile_read(reset: bool = False) -> dict:
+    """Per kernel class: launches, timed launches and summed device milliseconds."""
+    st = KKTKernelStats()
+    _check(load_library().kkt_profile_read(ctypes.byref(st), 1 if reset else 0))
+    return {name: {"launches": st.launches[i], "timed": st.timed[i], "ms": st.ms[i]}
+            for i, name in enumerate(KERNEL_CLASSES)}
+
+
+# ---- convenience object ---------------------------------------------------------------------
+
+@dataclass
+class SolveResult:
+    x: torch.Tensor
+    status: int
+    iterations: int
+    restarts: int
+    rel_residual: float
+    time_ms: float
+    history: list
+
+
+class Solver:
+    """One KKT instance on the current CUDA device (owns a kkt_handle)."""
+
+    def __init__(self, nx, ny, Nt, T=1.0, nu=1.0, omega=1e-4, n_sub=1, *, precision="fp64",
+                 coarse="exact", variant="multiplicative", pou="left", restart=30, jhat_sign=-1,
+                 Lx=1.0, Ly=1.0):
+        self.h = kkt_create(nx, ny, Nt, T, nu, omega, n_sub)
+        self.set_options(precision=precision, coarse=coarse, variant=variant, pou=pou, restart=restart,
+                         jhat_sign=jhat_sign, Lx=Lx, Ly=Ly)
+        self.info = kkt_get_info(self.h)
+
+    def set_options(self, *, precision="fp64", coarse="exact", variant="multiplicative", pou="left",
+                    restart=30, jhat_sign=-1, Lx=1.0, Ly=1.0):
+        opt = KKTOptions(PREC[precision], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign, Lx, Ly)
+        kkt_set_options(self.h, opt)
+        self.info = kkt_get_info(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            kkt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def V(self) -> int:
+        return int(self.info.V)
+
+    def _out(self, like: torch.Tensor, n: int) -> torch.Tensor:
+        return torch.empty(n, dtype=torch.float64, device=like.device)
+
+    def build_rhs(self, u_target, u0=None, out=None, stream=None):
+        f = out if out is not None else torch.empty(3 * self.V, dtype=torch.float64, device=u_target.device)
+        kkt_build_rhs(self.h, u_target, u0, f, stream)
+        return f
+
+    def matvec(self, x, out=None, stream=None):
+        y = out if out is not None else self._out(x, 3 * self.V)
+        kkt_matvec(self.h, x, y, stream)
+        return y
+
+    def precond_apply(self, r, out=None, stream=None):
+        y = out if out is not None else self._out(r, 3 * self.V)
+        kkt_precond_apply(self.h, r, y, stream)
+        return y
+
+    def dst2d(self, x, out=None, stream=None):
+        y = out if out is not None else self._out(x, self.V)
+        kkt_dst2d(self.h, x, y, stream)
+        return y
+
+    def schur_apply(self, x, out=None, stream=None):
+        y = out if out is not None else self._out(x, self.V)
+        kkt_schur_apply(self.h, x, y, stream)
+        return y
+
+    def schur_precond_apply(self, r, out=None, stream=None):
+        y = out if out is not None else self._out(r, self.V)
+        kkt_schur_precond_apply(self.h, r, y, stream)
+        return y
+
+    def coarse_apply(self, r, out=None, stream=None):
+        y = out if out is not None else self._out(r, self.V)
+        kkt_coarse_apply(self.h, r, y, stream)
+        return y
+
+    def solve(self, f, x=None, tol=1e-8, maxit=420, stream=None) -> SolveResult:
+        if x is None:
+            x = torch.zeros_like(f)
+        st = KKTStats()
+        status = kkt_solve(self.h, f, x, tol, maxit, st, stream)
+        return SolveResult(x, status, st.iterations, st.restarts, st.rel_residual, st.time_ms,
+                           list(st.history[: st.history_len]))

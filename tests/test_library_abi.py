@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point of include/kkt.h
+(no GPU: no compute call is made)."""
+
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"^\s*(?:const char\*|int|void|kkt_handle\*)\s+(kkt_\w+)\s*\(", txt, re.M)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2305_04421_gb300 import build, kkt
+    build.build()
+    return kkt.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2305_04421_gb300 import kkt
+    bound = {n for n, _, _ in kkt.SIGNATURES}
+    assert set(_declared()) <= bound
+
+
+def test_status_strings_and_defaults(lib):
+    import ctypes
+    from paper_2305_04421_gb300 import kkt
+    assert lib.kkt_status_string(kkt.KKT_ERR_NONFINITE) == b"non-finite value"
+    opt = kkt.KKTOptions()
+    assert lib.kkt_default_options(ctypes.byref(opt)) == 0
+    assert (opt.precision, opt.coarse, opt.variant, opt.pou, opt.restart, opt.jhat_sign) == (0, 0, 0, 0, 30, -1)
+    assert (opt.Lx, opt.Ly) == (1.0, 1.0)
+
+
+def test_invalid_sizes_rejected_before_any_device_call(lib):
+    assert not lib.kkt_create(1, 8, 8, 1.0, 1.0, 1e-3, 2)
+    assert b"nx" in lib.kkt_last_error()
+    assert not lib.kkt_create(8, 8, 8, 1.0, 1.0, 1e-3, 5)
+    assert b"n_sub" in lib.kkt_last_error()
+    assert not lib.kkt_create(8, 8, 8, 1.0, 1.0, 0.0, 2)
+
+
+def test_product_package_does_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2305_04421_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                txt = open(os.path.join(dirpath, fn)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), fn

@@ -382,3 +382,15 @@ def test_ras_and_rasq_differ_only_through_the_first_node():
     np.testing.assert_allclose(diff[:N, :N], np.eye(N) / p.h, rtol=1e-12, atol=1e-9)
     np.testing.assert_allclose(diff[N:, :], 0, atol=1e-9)
     np.testing.assert_allclose(diff[:, N:], 0, atol=1e-9)
+
+
+@pytest.mark.parametrize("pou", ["left", "right"])
+def test_per_mode_coarse_solve_matches_sparse_factorisation(pou):
+    """The per-mode coarse solve (used where the sparse coarse LU does not fit) equals the
+    literal sparse R_0^T (Z^T S-hat Z)^{-1} R_0."""
+    p = HeatKKT(nx=8, ny=6, Nt=24, nu=0.9, omega=1e-3, Ly=1.5)
+    a = schwarz.schur_preconditioner(p, 4, pou=pou)
+    b = schwarz.schur_preconditioner(p, 4, pou=pou, coarse_solver="per-mode")
+    r = workloads.random_vector(p.V, 31)
+    np.testing.assert_allclose(b.coarse(r), a.coarse(r), rtol=1e-11, atol=1e-11 * np.abs(a.coarse(r)).max())
+    np.testing.assert_allclose(b.apply(r), a.apply(r), rtol=1e-10, atol=1e-10 * np.abs(a.apply(r)).max())
