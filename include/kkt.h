@@ -65,6 +65,16 @@ enum kkt_variant {
   KKT_ADDITIVE = 1         /* y = R0^T S0^-1 R0 r + S_RASQ^-1 r */
 };
 
+/* Norm of the residual that FGMRES minimises and tests against tol. */
+enum kkt_residual_norm {
+  /* Discrete L2(0,T;L2) norms: the u and z rows (gradients of the objective) in the dual
+   * norm, weight h^-1/2; the state-equation rows in the primal norm, weight h^1/2. */
+  KKT_NORM_L2 = 0,
+  /* Unweighted Euclidean norm over all three blocks. In FP64 its attainable relative value
+   * is limited to about machine epsilon times |J| / h (about 3e-7 at 256 x 256, Nt = 1024). */
+  KKT_NORM_EUCLIDEAN = 1
+};
+
 /* Owner of the time node shared by neighbouring subdomains (boolean partition of unity D_s). */
 enum kkt_pou {
   KKT_POU_LEFT = 0,   /* the subdomain whose last step ends on the node */
@@ -78,6 +88,7 @@ typedef struct kkt_options {
   int pou;          /* enum kkt_pou, default KKT_POU_LEFT */
   int restart;      /* FGMRES restart length, 1..32, default 30 */
   int jhat_sign;    /* -1 (default): Jhat = J - omega^-1/2 L; +1: the sign printed in Eq 7 */
+  int residual_norm;  /* enum kkt_residual_norm, default KKT_NORM_L2 */
   double Lx, Ly;    /* domain (0,Lx) x (0,Ly), default 1, 1 */
 } kkt_options;
 
@@ -95,7 +106,9 @@ typedef struct kkt_stats {
   int restarts;            /* completed restart cycles */
   int precond_applies;
   int status;              /* same value the solve returned */
-  double rel_residual;     /* ||f - K x||_2 / ||f||_2 recomputed from x at exit */
+  double rel_residual;     /* ||D (f - K x)||_2 / ||D f||_2 recomputed from x at exit, D the
+                              weights of the options' residual norm */
+  double rel_residual_euclid;  /* ||f - K x||_2 / ||f||_2 at exit (unweighted) */
   double time_ms;          /* wall time of the solve, host clock */
   int history_len;
   double history[KKT_HISTORY_MAX];   /* Arnoldi residual estimate / ||f|| per iteration */
@@ -147,9 +160,9 @@ int kkt_matvec(kkt_handle* h, const double* x, double* y, void* stream);
 int kkt_precond_apply(kkt_handle* h, const double* r, double* y, void* stream);
 
 /*
- * Solve K x = f with right-preconditioned flexible GMRES(restart) (Section 4), stopping when
- * ||f - K x||_2 / ||f||_2 <= tol (checked on the recomputed residual) or after maxit
- * iterations. x holds the initial guess on entry and the solution on exit. f and x may be
+ * Solve K x = f with right-preconditioned flexible GMRES(restart) (Section 4), minimising the
+ * residual in the options' norm and stopping when ||D (f - K x)|| / ||D f|| <= tol (checked on
+ * the recomputed residual) or after maxit iterations. x holds the initial guess on entry and the solution on exit. f and x may be
  * host or device memory (detected per pointer; host data is staged through the handle).
  * Synchronises `stream`. Returns KKT_OK, KKT_NOT_CONVERGED (x = last iterate), or an error
  * (KKT_ERR_NONFINITE if f or an iterate is not finite, KKT_ERR_BREAKDOWN on a zero

@@ -26,13 +26,23 @@ class KrylovResult:
     history: list = field(default_factory=list)   # relative residual estimate per iteration
 
 
-def fgmres(matvec, precond, f, x0=None, *, tol=1e-8, restart=30, maxit=420, fixed_iterations=None):
+def fgmres(matvec, precond, f, x0=None, *, tol=1e-8, restart=30, maxit=420, fixed_iterations=None,
+           row_scale=None):
     """Solve K x = f. ``matvec(x)`` = K x, ``precond(r)`` = P^{-1} r.
 
     ``fixed_iterations``: stop after exactly this many Arnoldi steps (a single cycle), whatever
     the residual; used to compare iterates of two implementations after the same k.
+    ``row_scale`` (a positive vector d): minimise and test ||d * (f - K x)|| / ||d * f|| instead
+    of the Euclidean residual, i.e. run FGMRES on (d K) x = d f with the preconditioner applied
+    to the unscaled residual, P^{-1}(r / d).
     """
     f = np.asarray(f, dtype=np.float64)
+    if row_scale is not None:
+        wts = np.asarray(row_scale, dtype=np.float64)
+        inner_mv, inner_pc = matvec, precond
+        matvec = lambda v: wts * inner_mv(v)        # noqa: E731
+        precond = lambda q: inner_pc(q / wts)       # noqa: E731
+        f = wts * f
     n = f.size
     x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64)
     fnorm = np.linalg.norm(f)

@@ -176,3 +176,16 @@ def kkt_apply_blockwise(p: HeatKKT, x: np.ndarray) -> np.ndarray:
             t = t - u[n - 1]
         yw[n] = t
     return np.concatenate([yu.ravel(), yz.ravel(), yw.ravel()])
+
+
+def l2_residual_weights(p: HeatKKT) -> np.ndarray:
+    """Row weights of the residual norm used to stop the solve.
+
+    The rows of Eq 5 are, per time node and grid point, a gradient of the discrete objective
+    (u and z rows: the residual is a functional, measured in the dual L2 norm, weight
+    h^{-1/2}) and the state equation (w rows: a function, measured in the space-time L2 norm
+    with the mass h, weight h^{1/2}). This is the discrete L2(0,T; L2(Omega)) norm pair; the
+    paper states only "relative residual".
+    """
+    V = p.V
+    return np.concatenate([np.full(V, p.h ** -0.5), np.full(V, p.h ** -0.5), np.full(V, p.h ** 0.5)])

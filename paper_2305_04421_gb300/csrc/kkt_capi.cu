@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -280,6 +281,7 @@ int kkt_default_options(kkt_options* opt) {
   opt->pou = KKT_POU_LEFT;
   opt->restart = 30;
   opt->jhat_sign = -1;
+  opt->residual_norm = KKT_NORM_L2;
   opt->Lx = 1.0;
   opt->Ly = 1.0;
   return KKT_OK;
@@ -368,6 +370,8 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
   if (opt->pou != KKT_POU_LEFT && opt->pou != KKT_POU_RIGHT) return set_error(KKT_ERR_INVALID_ARG, "pou out of range");
   if (opt->restart < 1 || opt->restart > 32) return set_error(KKT_ERR_INVALID_ARG, "restart must be in [1, 32]");
   if (opt->jhat_sign != -1 && opt->jhat_sign != 1) return set_error(KKT_ERR_INVALID_ARG, "jhat_sign must be -1 or +1");
+  if (opt->residual_norm != KKT_NORM_L2 && opt->residual_norm != KKT_NORM_EUCLIDEAN)
+    return set_error(KKT_ERR_INVALID_ARG, "residual_norm out of range");
   if (!finite_pos(opt->Lx) || !finite_pos(opt->Ly)) return set_error(KKT_ERR_INVALID_ARG, "Lx, Ly must be positive");
   // with the shared node given to the later subdomain, the first subdomain owns nodes
   // 1 .. b_1 - 1; its linear coarse function needs two of them
@@ -515,7 +519,11 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   auto Hs = [&](int i, int j) -> double& { return H[static_cast<size_t>(i) * m + j]; };
   kkt_stats local;
   std::memset(&local, 0, sizeof(local));
+  double fnorm_plain = 0.0;
+  std::function<double()> euclid_residual;
   auto finish = [&](int status, double rel) -> int {
+    if (status >= 0 && std::isfinite(rel) && fnorm_plain > 0.0 && euclid_residual)
+      local.rel_residual_euclid = euclid_residual();
     if (!dev_x) {
       cudaMemcpyAsync(x, dx, n3 * sizeof(double), cudaMemcpyDeviceToHost, st);
       cudaStreamSynchronize(st);
@@ -531,23 +539,47 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
     KKT_CUDA_TRY(cudaStreamSynchronize(st));
     return KKT_OK;
   };
-  // ||f||
-  KKT_TRY(krylov_norm2(h, df, n3, st));
-  KKT_TRY(fetch(1));
-  const double fnorm = std::sqrt(hr[0]);
+  // residual weights D = diag(du, dz, dw) of the options' norm
+  const bool l2 = h->opt.residual_norm == KKT_NORM_L2;
+  const double du = l2 ? 1.0 / std::sqrt(g.h) : 1.0, dz = du, dw = l2 ? std::sqrt(g.h) : 1.0;
+  const double dblk[3] = {du, dz, dw};
+  // squared block norms of a full vector -> weighted and unweighted totals
+  auto block_norms = [&](const double* v, double& weighted, double& plain) -> int {
+    double b[3];
+    for (int k = 0; k < 3; ++k) {
+      KKT_TRY(krylov_norm2(h, v + k * V, V, st));
+      KKT_TRY(fetch(1));
+      b[k] = hr[0];
+    }
+    weighted = du * du * b[0] + dz * dz * b[1] + dw * dw * b[2];
+    plain = b[0] + b[1] + b[2];
+    return KKT_OK;
+  };
+  double fw2 = 0.0, fp2 = 0.0;
+  KKT_TRY(block_norms(df, fw2, fp2));
+  const double fnorm = std::sqrt(fw2);
+  fnorm_plain = std::sqrt(fp2);
   if (!std::isfinite(fnorm)) return finish(set_error(KKT_ERR_NONFINITE, "right-hand side is not finite"), NAN);
   if (fnorm == 0.0) {
     KKT_CUDA_TRY(cudaMemsetAsync(dx, 0, n3 * sizeof(double), st));
     return finish(KKT_OK, 0.0);
   }
-  // r = f - K x  (into V_0)
+  // V_0 = D (f - K x), beta = ||V_0||
   auto residual = [&](double& beta) -> int {
-    KKT_TRY(launch_matvec(h, dx, 1.0, dx + V, 1.0, dx + 2 * V, 1.0, Vb, st));
-    KKT_TRY(launch_axpby(1.0, df, -1.0, Vb, Vb, n3, st));
+    KKT_TRY(launch_matvec(h, dx, 1.0, dx + V, 1.0, dx + 2 * V, 1.0, Vb, st, du, dz, dw));
+    for (int k = 0; k < 3; ++k) KKT_TRY(launch_axpby(dblk[k], df + k * V, -1.0, Vb + k * V, Vb + k * V, V, st));
     KKT_TRY(krylov_norm2(h, Vb, n3, st));
     KKT_TRY(fetch(1));
     beta = std::sqrt(hr[0]);
     return KKT_OK;
+  };
+  // unweighted relative residual of x, into the stats (uses V_1 as scratch)
+  euclid_residual = [&]() -> double {
+    double* R = Vb + n3;
+    if (launch_matvec(h, dx, 1.0, dx + V, 1.0, dx + 2 * V, 1.0, R, st) < 0) return NAN;
+    if (launch_axpby(1.0, df, -1.0, R, R, n3, st) < 0) return NAN;
+    if (krylov_norm2(h, R, n3, st) < 0 || fetch(1) < 0) return NAN;
+    return std::sqrt(hr[0]) / fnorm_plain;
   };
   double beta = 0.0;
   KKT_TRY(residual(beta));
@@ -565,10 +597,12 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
       double* Vj = Vb + static_cast<size_t>(j) * n3;
       double* W = Vb + static_cast<size_t>(j + 1) * n3;
       double* Zj = Zw + static_cast<size_t>(j) * V;
-      // z_j = P^{-1} v_j: u, z blocks are scalings (folded into the matvec), w block via S-hat_2level^{-1}
-      KKT_TRY(schur_precond_w(h, Vj + 2 * V, 1.0 / eta[j], Zj, st));
+      // z_j = P^{-1} D^{-1} v_j: the u, z blocks are scalings (folded into the matvec), the
+      // w block goes through S-hat_2level^{-1}; then W = D K z_j
+      KKT_TRY(schur_precond_w(h, Vj + 2 * V, 1.0 / (dw * eta[j]), Zj, st));
       local.precond_applies++;
-      KKT_TRY(launch_matvec(h, Vj, 1.0 / (g.h * eta[j]), Vj + V, 1.0 / (g.omega * g.h * eta[j]), Zj, 1.0, W, st));
+      KKT_TRY(launch_matvec(h, Vj, 1.0 / (g.h * du * eta[j]), Vj + V, 1.0 / (g.omega * g.h * dz * eta[j]), Zj, 1.0,
+                            W, st, du, dz, dw));
       // classical Gram-Schmidt with one conditional reorthogonalisation (||w'|| < ||w|| / sqrt 2)
       for (int k = 0; k <= j; ++k) Hs(k, j) = 0.0;
       double wnorm2 = 0.0;
@@ -619,8 +653,8 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
       yv[i] = Hs(i, i) != 0.0 ? s / Hs(i, i) : 0.0;
     }
     for (int k = 0; k < jused; ++k) {
-      hc[k] = yv[k] / (g.h * eta[k]);
-      hc[128 + k] = yv[k] / (g.omega * g.h * eta[k]);
+      hc[k] = yv[k] / (g.h * du * eta[k]);
+      hc[128 + k] = yv[k] / (g.omega * g.h * dz * eta[k]);
       hc[256 + k] = yv[k];
     }
     KKT_CUDA_TRY(cudaMemcpyAsync(h->dcoef, hc, 3 * 128 * sizeof(double), cudaMemcpyHostToDevice, st));

@@ -123,8 +123,10 @@ void dst_plan_destroy(DstPlan& p);
 // orthonormal 2D DST-I of every slice: rows (along x) then columns (along y)
 int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st);
 
+// y = diag(ou, oz, ow) K (su u, sz z, sw w)
 int launch_matvec(const kkt_handle* h, const double* u, double su, const double* z, double sz,
-                  const double* w, double sw, double* y, cudaStream_t st);
+                  const double* w, double sw, double* y, cudaStream_t st, double ou = 1.0, double oz = 1.0,
+                  double ow = 1.0);
 int launch_build_rhs(const kkt_handle* h, const double* ut, const double* u0, double* f, cudaStream_t st);
 int launch_scale(const double* x, double s, double* y, long long n, cudaStream_t st);
 int launch_jhat_time(const kkt_handle* h, const double* in, double* out, int dir, double scale,

@@ -31,13 +31,14 @@ PREC = {"fp64": 0, "bf16": 1, "tf32": 2}
 COARSE = {"exact": 0, "none": 1, "learned": 2}
 VARIANT = {"multiplicative": 0, "additive": 1}
 POU = {"left": 0, "right": 1}
+NORM = {"l2": 0, "euclidean": 1}
 HISTORY_MAX = 1024
 
 
 class KKTOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coarse", ctypes.c_int), ("variant", ctypes.c_int),
                 ("pou", ctypes.c_int), ("restart", ctypes.c_int), ("jhat_sign", ctypes.c_int),
-                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double)]
+                ("residual_norm", ctypes.c_int), ("Lx", ctypes.c_double), ("Ly", ctypes.c_double)]
 
 
 class KKTInfo(ctypes.Structure):
@@ -49,7 +50,8 @@ class KKTInfo(ctypes.Structure):
 
 class KKTStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("restarts", ctypes.c_int), ("precond_applies", ctypes.c_int),
-                ("status", ctypes.c_int), ("rel_residual", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("status", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("rel_residual_euclid", ctypes.c_double), ("time_ms", ctypes.c_double),
                 ("history_len", ctypes.c_int), ("history", ctypes.c_double * HISTORY_MAX)]
 
 
@@ -218,6 +220,7 @@ class SolveResult:
     iterations: int
     restarts: int
     rel_residual: float
+    rel_residual_euclid: float
     time_ms: float
     history: list
 
@@ -227,15 +230,16 @@ class Solver:
 
     def __init__(self, nx, ny, Nt, T=1.0, nu=1.0, omega=1e-4, n_sub=1, *, precision="fp64",
                  coarse="exact", variant="multiplicative", pou="left", restart=30, jhat_sign=-1,
-                 Lx=1.0, Ly=1.0):
+                 residual_norm="l2", Lx=1.0, Ly=1.0):
         self.h = kkt_create(nx, ny, Nt, T, nu, omega, n_sub)
         self.set_options(precision=precision, coarse=coarse, variant=variant, pou=pou, restart=restart,
-                         jhat_sign=jhat_sign, Lx=Lx, Ly=Ly)
+                         jhat_sign=jhat_sign, residual_norm=residual_norm, Lx=Lx, Ly=Ly)
         self.info = kkt_get_info(self.h)
 
     def set_options(self, *, precision="fp64", coarse="exact", variant="multiplicative", pou="left",
-                    restart=30, jhat_sign=-1, Lx=1.0, Ly=1.0):
-        opt = KKTOptions(PREC[precision], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign, Lx, Ly)
+                    restart=30, jhat_sign=-1, residual_norm="l2", Lx=1.0, Ly=1.0):
+        opt = KKTOptions(PREC[precision], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
+                         NORM[residual_norm], Lx, Ly)
         kkt_set_options(self.h, opt)
         self.info = kkt_get_info(self.h)
 
@@ -297,5 +301,5 @@ class Solver:
             x = torch.zeros_like(f)
         st = KKTStats()
         status = kkt_solve(self.h, f, x, tol, maxit, st, stream)
-        return SolveResult(x, status, st.iterations, st.restarts, st.rel_residual, st.time_ms,
+        return SolveResult(x, status, st.iterations, st.restarts, st.rel_residual, st.rel_residual_euclid, st.time_ms,
                            list(st.history[: st.history_len]))

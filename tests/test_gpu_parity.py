@@ -6,13 +6,14 @@ span several DST tiles and a ragged tail (31 x 31 lines in 32-line tiles, 255 co
 tiles), odd and even sizes, non-power-of-two grids (direct transform), Nt not divisible by
 N_D, both D_s readings and every composition variant.
 
-Solves are compared where the comparison is well conditioned. The relative residual of the
-exact solution of the 32 x 32, Nt = 64 problem is already 6.7e-10 in FP64, so no solver
-reaches a residual of 1e-12; and an FGMRES iterate after a fixed k at a stagnating step moves
-by 1e-6 when the preconditioner output is perturbed by 1e-14 (measured with the oracle), so
-iterates of two FP64 implementations cannot agree to 1e-10. The tests therefore compare
-residual histories, and the iterate after 60 steps (which has converged to the exact
-solution to 1e-15 in the oracle) against the exact per-mode solve.
+Solves are compared where the comparison is well conditioned. An FGMRES iterate after a fixed
+k at a stagnating step moves by 1e-6 when the preconditioner output is perturbed by 1e-14
+(measured with the oracle), so iterates of two FP64 implementations cannot agree to 1e-10
+there; the tests compare residual histories, and converged solutions against the exact
+per-mode solve. The default residual norm is the discrete L2 pair (u, z rows weighted
+h^-1/2, state rows h^1/2), in which the exact solution's relative residual is 1e-14; in the
+unweighted Euclidean norm it is already 6.7e-10 at 32 x 32, Nt = 64, so Euclidean solves are
+compared at 1e-8 only.
 """
 
 import numpy as np
@@ -163,26 +164,33 @@ def test_build_rhs_matches_oracle_device_and_host(kkt):
     assert rel(f_host.numpy(), want) < 1e-15
 
 
-def test_solve_small_configuration_matches_oracle_and_exact(kkt):
+@pytest.mark.parametrize("norm", ["l2", "euclidean"])
+def test_solve_small_configuration_matches_oracle_and_exact(kkt, norm):
     """The 32 x 32, Nt = 64, N_D = 4 problem to 1e-8: GPU FGMRES reaches the tolerance in the
-    oracle's iteration count, and after 60 iterations its iterate equals the per-mode exact
-    solve within 1e-10."""
+    oracle's iteration count (same residual norm); in the L2 norm a 1e-12 solve equals the
+    per-mode exact solve within 1e-10, in the Euclidean norm the iterate after 60 steps does."""
     w = workloads.CFG_SMALL
     p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
     f = problem.assemble_rhs(p, workloads.make_target(w), workloads.make_u0(w))
-    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, residual_norm=norm)
+    d = problem.l2_residual_weights(p) if norm == "l2" else np.ones(3 * p.V)
     res = s.solve(dev(f), tol=1e-8, maxit=420)
     assert res.status == kkt.KKT_OK and res.rel_residual <= 1e-8
     K = problem.assemble_K(p)
     x = host(res.x)
-    assert np.linalg.norm(f - K @ x) / np.linalg.norm(f) <= 1.01e-8
+    assert np.linalg.norm(d * (f - K @ x)) / np.linalg.norm(d * f) <= 1.01e-8
+    np.testing.assert_allclose(res.rel_residual_euclid, np.linalg.norm(f - K @ x) / np.linalg.norm(f), rtol=1e-6)
     pre = schwarz.schur_preconditioner(p, w.n_sub)
     ref = krylov.fgmres(lambda v: K @ v, lambda r: schwarz.block_preconditioner_apply(p, pre, r), f,
-                        tol=1e-8, restart=30, maxit=420)
+                        tol=1e-8, restart=30, maxit=420, row_scale=d)
     assert abs(res.iterations - ref.iterations) <= 1
-    tight = s.solve(dev(f), tol=1e-14, maxit=60)
     exact = spectral.kkt_exact_solve(p, f)
-    assert tight.status == kkt.KKT_NOT_CONVERGED and tight.iterations == 60
+    if norm == "l2":
+        tight = s.solve(dev(f), tol=1e-12, maxit=420)
+        assert tight.status == kkt.KKT_OK
+    else:
+        tight = s.solve(dev(f), tol=1e-14, maxit=60)
+        assert tight.status == kkt.KKT_NOT_CONVERGED and tight.iterations == 60
     assert rel(host(tight.x), exact) < TOL
 
 
@@ -197,12 +205,14 @@ def test_fixed_iteration_residuals_match_oracle(kkt, k):
     res = s.solve(dev(f), tol=1e-300, maxit=k)
     assert res.status == kkt.KKT_NOT_CONVERGED and res.iterations == k
     K = problem.assemble_K(p)
+    d = problem.l2_residual_weights(p)
     pre = schwarz.schur_preconditioner(p, w.n_sub)
     ref = krylov.fgmres(lambda v: K @ v, lambda r: schwarz.block_preconditioner_apply(p, pre, r), f,
-                        fixed_iterations=k)
-    np.testing.assert_allclose(res.history, ref.history, rtol=1e-7)
+                        fixed_iterations=k, row_scale=d)
+    np.testing.assert_allclose(res.history, ref.history, rtol=1e-7, atol=1e-13)
     x = host(res.x)
-    np.testing.assert_allclose(np.linalg.norm(f - K @ x) / np.linalg.norm(f), ref.rel_residual, rtol=1e-6)
+    np.testing.assert_allclose(np.linalg.norm(d * (f - K @ x)) / np.linalg.norm(d * f), ref.rel_residual,
+                               rtol=1e-6, atol=1e-13)
     if k == 1:
         assert rel(x, ref.x) < TOL       # one step: x = y_1 z_1, well conditioned
 
@@ -214,8 +224,8 @@ def test_solve_with_host_buffers_and_initial_guess(kkt):
     s = kkt.Solver(16, 16, 24, 1.0, 1.0, 1e-3, 3)
     exact = spectral.kkt_exact_solve(p, f)
     x = torch.zeros(3 * p.V, dtype=torch.float64)          # host tensor
-    res = s.solve(torch.from_numpy(f), x, tol=1e-14, maxit=60)
-    assert res.iterations == 60
+    res = s.solve(torch.from_numpy(f), x, tol=1e-12, maxit=300)
+    assert res.status == kkt.KKT_OK
     assert rel(x.numpy(), exact) < TOL
     # starting from the solution: converged at once
     res2 = s.solve(dev(f), dev(exact), tol=1e-8, maxit=10)

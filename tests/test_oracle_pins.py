@@ -394,3 +394,22 @@ def test_per_mode_coarse_solve_matches_sparse_factorisation(pou):
     r = workloads.random_vector(p.V, 31)
     np.testing.assert_allclose(b.coarse(r), a.coarse(r), rtol=1e-11, atol=1e-11 * np.abs(a.coarse(r)).max())
     np.testing.assert_allclose(b.apply(r), a.apply(r), rtol=1e-10, atol=1e-10 * np.abs(a.apply(r)).max())
+
+
+def test_weighted_residual_norm_reaches_the_exact_solution():
+    """In the L2-weighted norm the exact solution's relative residual is at rounding level and a
+    1e-12 FGMRES solve is within 1e-10 of it; the Euclidean residual of the exact solution is
+    already far above 1e-12 (the w rows carry O(1) coefficients against an O(h) right side)."""
+    w = workloads.CFG_SMALL
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    f = problem.assemble_rhs(p, workloads.make_target(w), workloads.make_u0(w))
+    K = problem.assemble_K(p)
+    d = problem.l2_residual_weights(p)
+    xe = spectral.kkt_exact_solve(p, f)
+    assert np.linalg.norm(d * (f - K @ xe)) / np.linalg.norm(d * f) < 1e-13
+    assert np.linalg.norm(f - K @ xe) / np.linalg.norm(f) > 1e-11
+    pre = schwarz.schur_preconditioner(p, w.n_sub)
+    res = krylov.fgmres(lambda v: K @ v, lambda r: schwarz.block_preconditioner_apply(p, pre, r), f,
+                        tol=1e-12, restart=30, maxit=200, row_scale=d)
+    assert res.converged
+    assert np.linalg.norm(res.x - xe) <= 1e-10 * np.linalg.norm(xe)
