@@ -187,6 +187,13 @@ int kkt_schur_precond_apply(kkt_handle* h, const double* r, double* y, void* str
  * blocks. Needs coarse = KKT_COARSE_EXACT. */
 int kkt_coarse_apply(kkt_handle* h, const double* r, double* x0, void* stream);
 
+/* out[k] = <V_k, w> for k < count and out[count] = <w, w>, with V_k = V + k * stride; the
+ * classical Gram-Schmidt multi-dot of the FGMRES Arnoldi step (Section 4). V, w and out are
+ * device pointers (out: count + 1 doubles); 1 <= count <= 32, n >= 1, stride >= n. FP64,
+ * deterministic (fixed grid, two-stage reduction through the handle's scratch). Asynchronous. */
+int kkt_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w, long long n,
+                 double* out, void* stream);
+
 /* ---- instrumentation ------------------------------------------------------------------ */
 
 /* Kernel classes counted and timed by the library (process-wide, all handles). */

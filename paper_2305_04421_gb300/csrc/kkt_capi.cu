@@ -326,6 +326,8 @@ kkt_handle* kkt_create(int nx, int ny, int Nt, double T, double nu, double omega
   if (st >= 0) st = dev_alloc(h, &h->spec2, g.V);
   if (st >= 0) st = dev_alloc(h, &h->coarse_c, 2 * static_cast<size_t>(n_sub) * g.N);
   if (st >= 0) st = dev_alloc(h, &h->coarse_w, 5 * static_cast<size_t>(n_sub) * g.N);
+  if (st >= 0) st = dev_alloc(h, &h->red, static_cast<size_t>(krylov_partial_capacity()));
+  if (st >= 0) st = dev_alloc(h, &h->red_out, 128);
   if (st < 0) {
     const std::string msg = kkt::g_last_error;
     kkt_destroy(h);
@@ -484,6 +486,15 @@ int kkt_coarse_apply(kkt_handle* h, const double* r, double* x0, void* stream) {
   KKT_TRY(dst2d(h, r, h->spec, st));
   KKT_TRY(spectral_coarse_only(h, h->spec, h->spec2, st));
   return dst2d(h, h->spec2, x0, st);
+}
+
+int kkt_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w, long long n,
+                 double* out, void* stream) {
+  KKT_TRY(check_handle(h));
+  KKT_TRY(check_ptrs({V, w, out}));
+  if (count < 1 || count > 32) return set_error(KKT_ERR_INVALID_ARG, "count must be in [1, 32]");
+  if (n < 1 || stride < n) return set_error(KKT_ERR_INVALID_ARG, "need n >= 1 and stride >= n");
+  return krylov_multidot(h, V, stride, count, w, n, as_stream(stream), out);
 }
 
 int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, kkt_stats* stats, void* stream) {

@@ -139,7 +139,7 @@ int spectral_coarse_only(const kkt_handle* h, const double* rhat, double* xhat, 
 
 // Krylov primitives (deterministic two-stage reductions; results in h->red_out on device)
 int krylov_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w,
-                    long long n, cudaStream_t st);   // red_out[k] = <V_k, w>, red_out[count] = <w,w>
+                    long long n, cudaStream_t st, double* out = nullptr);   // out (default red_out)[k] = <V_k, w>, [count] = <w,w>
 int krylov_update_norm(kkt_handle* h, const double* V, long long stride, int count,
                        const double* coef_dev, double* w, long long n, cudaStream_t st);  // w -= sum c_k V_k; red_out[0] = <w,w>
 int krylov_axpy_multi(const double* V, long long stride, int count, const double* coef_dev,

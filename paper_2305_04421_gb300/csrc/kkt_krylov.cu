@@ -176,8 +176,9 @@ struct AxpyRun {
 }  // namespace
 
 int krylov_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w, long long n,
-                    cudaStream_t st) {
+                    cudaStream_t st, double* out) {
   const int nb = grid_blocks();
+  if (!out) out = h->red_out;
   int done = 0;
   // groups of up to 32 vectors; each group writes count_g + 1 partial columns (last = <w,w>)
   while (done < count) {
@@ -185,7 +186,7 @@ int krylov_multidot(kkt_handle* h, const double* V, long long stride, int count,
     KKT_TRY(dispatch_nv<MultidotRun>(cg, V + done * stride, stride, static_cast<const double*>(w), n, h->red, nb, st));
     {
       ProfScope ps(KKT_K_REDUCE, st);
-      finalize_kernel<<<cg + 1, 32, 0, st>>>(h->red, nb, cg + 1, h->red_out + done);
+      finalize_kernel<<<cg + 1, 32, 0, st>>>(h->red, nb, cg + 1, out + done);
     }
     KKT_CUDA_TRY(cudaGetLastError());
     done += cg;
