@@ -194,6 +194,24 @@ int kkt_coarse_apply(kkt_handle* h, const double* r, double* x0, void* stream);
 int kkt_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w, long long n,
                  double* out, void* stream);
 
+/*
+ * kkt_multidot without any device allocation: the paper has no counterpart; this entry point
+ * serves callers that cannot call cudaMalloc, such as a host application whose device memory
+ * is owned by another allocator (a framework's caching pool, a fixed arena reserved at start-up)
+ * or a loop that must not allocate. The caller passes V, w and out as for kkt_multidot (no
+ * handle). The per-block partial sums live in a file-scope device array of 270,336 bytes (1024
+ * blocks x 33 columns of doubles) that every GPU loading this library holds until the process
+ * exits; hence count is limited to 32 and larger counts are rejected with KKT_ERR_INVALID_ARG.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture. All calls share the
+ * array and it keeps the last call's contents; each call writes every slot it reads before
+ * reading it, so no clearing is needed, but calls that overlap on the GPU (on different
+ * streams, or from different threads) race on the array and must be serialised by the caller.
+ * Calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+int kkt_multidot_noalloc(const double* V, long long stride, int count, const double* w, long long n,
+                         double* out, void* stream);
+
 /* ---- instrumentation ------------------------------------------------------------------ */
 
 /* Kernel classes counted and timed by the library (process-wide, all handles). */

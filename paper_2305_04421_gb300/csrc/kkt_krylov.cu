@@ -5,6 +5,8 @@
 // Reductions are deterministic: a fixed grid of blocks each reduces its grid-stride share
 // (warp shuffles, then shared memory) into one partial per block, and a second kernel sums
 // the partials of each output in a fixed order. Results land in h->red_out on the device.
+#include <mutex>
+
 #include "kkt_internal.cuh"
 
 namespace kkt {
@@ -236,4 +238,90 @@ int krylov_norm2(kkt_handle* h, const double* x, long long n, cudaStream_t st) {
 
 int krylov_partial_capacity() { return grid_blocks() * (kMaxVec + 1); }
 
+// ---- multi-dot without device allocation ------------------------------------------------
+//
+// Some callers cannot call cudaMalloc: a host application whose device memory is owned by
+// another allocator (a framework's caching pool or a fixed arena sized at start-up), or a
+// loop that must not allocate at all. kkt_multidot_noalloc serves them: the caller passes
+// the inputs and the output, and the per-block partial sums live in the file-scope array
+// below, which every GPU that loads this library holds until the process exits.
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 1024;
+constexpr int kNoAllocMaxCount = 32;
+constexpr int kNoAllocWords = kNoAllocMaxBlocks * (kNoAllocMaxCount + 1);   // 270,336 bytes
+
+static __device__ __align__(256) double g_noalloc_partials[kNoAllocWords];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_partials on the current device. The array's name in host code
+// is only a host-side stand-in, so the address is fetched with cudaGetSymbolAddress, once per
+// device, with that device current.
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  KKT_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(KKT_ERR_UNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess || !p)
+      return set_error(KKT_ERR_CUDA, std::string("cudaGetSymbolAddress of the multi-dot scratch: ") +
+                                         cudaGetErrorString(e));
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return KKT_OK;
+}
+
+template <int NV>
+struct MultidotNoAllocRun {
+  static int run(const double* V, long long stride, const double* w, long long n, double* part, int nb,
+                 cudaStream_t st) {
+    multidot_kernel<NV><<<nb, kRedThreads, 0, st>>>(V, stride, w, n, part);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
+};
+
+bool device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 }  // namespace kkt
+
+extern "C" int kkt_multidot_noalloc(const double* V, long long stride, int count, const double* w, long long n,
+                                    double* out, void* stream) {
+  using namespace kkt;
+  if (!V || !w || !out) return set_error(KKT_ERR_INVALID_ARG, "null pointer");
+  if (count < 1 || count > kNoAllocMaxCount)
+    return set_error(KKT_ERR_INVALID_ARG, "count must be in [1, 32]: the no-allocation scratch holds partial sums "
+                                          "for at most 32 vectors");
+  if (n < 1 || stride < n) return set_error(KKT_ERR_INVALID_ARG, "need n >= 1 and stride >= n");
+  for (const void* p : {static_cast<const void*>(V), static_cast<const void*>(w), static_cast<const void*>(out)}) {
+    if (reinterpret_cast<uintptr_t>(p) % 8) return set_error(KKT_ERR_INVALID_ARG, "pointer not 8-byte aligned");
+    if (!device_pointer(p)) return set_error(KKT_ERR_INVALID_ARG, "pointer is not device memory");
+  }
+  double* part = nullptr;
+  KKT_TRY(noalloc_scratch(&part));
+  const int nb = std::min(grid_blocks(), kNoAllocMaxBlocks);
+  if (static_cast<long long>(nb) * (count + 1) > kNoAllocWords)
+    return set_error(KKT_ERR_INVALID_ARG, "multi-dot partials exceed the no-allocation scratch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // every partial slot the finalisation reads (blocks < nb, columns <= count) is written by
+  // this call's multi-dot launch first, so nothing left by an earlier call is read
+  KKT_TRY(dispatch_nv<MultidotNoAllocRun>(count, V, stride, w, n, part, nb, st));
+  finalize_kernel<<<count + 1, 32, 0, st>>>(part, nb, count + 1, out);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}

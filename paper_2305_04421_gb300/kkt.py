@@ -91,6 +91,7 @@ SIGNATURES = [
     ("kkt_schur_precond_apply", _I, [_P, _P, _P, _P]),
     ("kkt_coarse_apply", _I, [_P, _P, _P, _P]),
     ("kkt_multidot", _I, [_P, _P, ctypes.c_longlong, _I, _P, ctypes.c_longlong, _P, _P]),
+    ("kkt_multidot_noalloc", _I, [_P, ctypes.c_longlong, _I, _P, ctypes.c_longlong, _P, _P]),
     ("kkt_profile_enable", _I, [_I]),
     ("kkt_profile_read", _I, [ctypes.POINTER(KKTKernelStats), _I]),
 ]
@@ -203,6 +204,13 @@ def kkt_coarse_apply(h, r, y, stream=None) -> int:
 def kkt_multidot(h, V, stride, count, w, n, out, stream=None) -> int:
     """out[k] = <V_k, w> (k < count), out[count] = <w, w>; V a contiguous float64 device tensor."""
     return _check(load_library().kkt_multidot(h, _ptr(V), stride, count, _ptr(w), n, _ptr(out), _stream(stream)))
+
+
+def kkt_multidot_noalloc(V, stride, count, w, n, out, stream=None) -> int:
+    """kkt_multidot without a handle or any device allocation (scratch in a static device array);
+    for callers that cannot allocate device memory. Calls must not overlap on the GPU."""
+    return _check(load_library().kkt_multidot_noalloc(_ptr(V), stride, count, _ptr(w), n, _ptr(out),
+                                                      _stream(stream)))
 
 
 def kkt_profile_enable(on: bool) -> int:
