@@ -171,25 +171,41 @@ int configure(kkt_handle* h) {
   KKT_CUDA_TRY(cudaMemcpy(h->d_ly, ly.data(), g.My * sizeof(double), cudaMemcpyHostToDevice));
   build_decomp(g.Nt, g.n_sub, o.pou, h->td);
   KKT_TRY(upload_decomp(h));
-  // sweep storage: shared memory when a subdomain's nodes fit, else a global scratch
-  const size_t limit = 200 * 1024;
-  h->sweep_block = 0;
-  for (int tb : {128, 64, 32}) {
-    if (static_cast<size_t>(h->td.max_len) * tb * sizeof(double) <= limit) {
-      h->sweep_block = tb;
-      break;
-    }
+  // reduced-precision forms: tensor-core transform plan over the padded mode grid
+  const bool mixed = o.precision != KKT_PREC_FP64;
+  const int bf16 = o.precision == KKT_PREC_BF16;
+  if (h->tc.q && (!mixed || h->tc.bf16 != bf16)) {
+    h->bytes -= h->tc.bytes;
+    tc_plan_destroy(h->tc);
   }
-  if (h->sweep_block) {
-    h->sweep_smem = static_cast<size_t>(h->td.max_len) * h->sweep_block * sizeof(double);
-    if (h->vscratch) {
-      cudaFree(h->vscratch);
-      h->vscratch = nullptr;
+  long long modes = g.N;
+  if (mixed) {
+    if (!h->tc.q) {
+      KKT_TRY(tc_plan_create(h->tc, g.nx, g.Nt, bf16));
+      h->bytes += h->tc.bytes;
     }
-  } else {
-    h->sweep_block = 128;
-    h->sweep_smem = 0;
-    KKT_TRY(dev_alloc(h, &h->vscratch, static_cast<size_t>(g.n_sub) * h->td.max_len * g.N));
+    const int P = h->tc.P;
+    std::vector<double> lxp(P, 0.0), lyp(P, 0.0);
+    std::copy(lx.begin(), lx.end(), lxp.begin());
+    std::copy(ly.begin(), ly.end(), lyp.begin());
+    if (!h->d_lx_pad) KKT_TRY(dev_alloc(h, &h->d_lx_pad, P));
+    if (!h->d_ly_pad) KKT_TRY(dev_alloc(h, &h->d_ly_pad, P));
+    KKT_CUDA_TRY(cudaMemcpy(h->d_lx_pad, lxp.data(), P * sizeof(double), cudaMemcpyHostToDevice));
+    KKT_CUDA_TRY(cudaMemcpy(h->d_ly_pad, lyp.data(), P * sizeof(double), cudaMemcpyHostToDevice));
+    modes = std::max(modes, static_cast<long long>(P) * P);
+  }
+  if (modes > h->coarse_modes) {
+    KKT_TRY(dev_alloc(h, &h->coarse_c, 2 * static_cast<size_t>(g.n_sub) * modes));
+    KKT_TRY(dev_alloc(h, &h->coarse_w, 5 * static_cast<size_t>(g.n_sub) * modes));
+    h->coarse_modes = modes;
+  }
+  // sweep storage: shared memory when a subdomain's nodes fit (32 threads x max_len doubles
+  // within 200 KB), else a global scratch sized for every mode
+  if (static_cast<size_t>(h->td.max_len) * 32 * sizeof(double) > 200 * 1024) {
+    KKT_TRY(dev_alloc(h, &h->vscratch, static_cast<size_t>(g.n_sub) * h->td.max_len * modes));
+  } else if (h->vscratch) {
+    cudaFree(h->vscratch);
+    h->vscratch = nullptr;
   }
   return KKT_OK;
 }
@@ -227,11 +243,25 @@ int ensure_precision(const kkt_handle* h) {
   return KKT_OK;
 }
 
-// y_w = S-hat_2level^{-1} (scale * r_w): DST, spectral two-level solve, inverse DST
+// y_w = S-hat_2level^{-1} (scale * r_w): DST, spectral two-level solve, inverse DST.
+// FP64: the FFT-based transforms. BF16 / TF32: pack into padded slices, two tensor-core
+// transforms into FP32 coefficients, FP32 sweeps (FP64 coarse solve), two transforms back.
 int schur_precond_w(kkt_handle* h, const double* rw, double scale, double* yw, cudaStream_t st) {
-  KKT_TRY(dst2d(h, rw, h->spec, st));
-  KKT_TRY(spectral_schur_precond(h, h->spec, h->spec2, scale, st));
-  KKT_TRY(dst2d(h, h->spec2, yw, st));
+  if (h->opt.precision == KKT_PREC_FP64) {
+    KKT_TRY(dst2d(h, rw, h->spec, st));
+    KKT_TRY(spectral_schur_precond(h, h->spec, h->spec2, scale, st));
+    KKT_TRY(dst2d(h, h->spec2, yw, st));
+    return KKT_OK;
+  }
+  const TcPlan& t = h->tc;
+  const int mid = t.bf16 ? 0 : 1;
+  const int valid = h->g.nx - 1;
+  KKT_TRY(tc_pack(t, rw, scale, valid, st));
+  KKT_TRY(tc_gemm(t, 0, mid, t.x1, valid, st));        // along x: [n][j][i] -> [n][k][j]
+  KKT_TRY(tc_gemm(t, 1, 1, t.rhat, valid, st));        // along y: -> [n][l][k], FP32
+  KKT_TRY(spectral_schur_precond_mixed(h, t.rhat, t.yin, t.bf16, st));
+  KKT_TRY(tc_gemm(t, 2, mid, t.x0, valid, st));        // back along x: [n][l][k] -> [n][i][l]
+  KKT_TRY(tc_gemm(t, 0, 2, yw, valid, st));            // back along y: -> [n][j][i], FP64
   return KKT_OK;
 }
 
@@ -324,8 +354,6 @@ kkt_handle* kkt_create(int nx, int ny, int Nt, double T, double nu, double omega
   if (st >= 0) st = dst_plan_create(h->dst_y, ny);
   if (st >= 0) st = dev_alloc(h, &h->spec, g.V);
   if (st >= 0) st = dev_alloc(h, &h->spec2, g.V);
-  if (st >= 0) st = dev_alloc(h, &h->coarse_c, 2 * static_cast<size_t>(n_sub) * g.N);
-  if (st >= 0) st = dev_alloc(h, &h->coarse_w, 5 * static_cast<size_t>(n_sub) * g.N);
   if (st >= 0) st = dev_alloc(h, &h->red, static_cast<size_t>(krylov_partial_capacity()));
   if (st >= 0) st = dev_alloc(h, &h->red_out, 128);
   if (st < 0) {
@@ -341,6 +369,9 @@ void kkt_destroy(kkt_handle* h) {
   if (!h) return;
   dst_plan_destroy(h->dst_x);
   dst_plan_destroy(h->dst_y);
+  if (h->tc.q) tc_plan_destroy(h->tc);
+  cudaFree(h->d_lx_pad);
+  cudaFree(h->d_ly_pad);
   if (h->dd.base) cudaFree(h->dd.base);
   cudaFree(h->d_lx);
   cudaFree(h->d_ly);
@@ -379,7 +410,8 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
   // 1 .. b_1 - 1; its linear coarse function needs two of them
   if (opt->pou == KKT_POU_RIGHT && h->g.Nt / h->g.n_sub < 3)
     return set_error(KKT_ERR_INVALID_ARG, "pou=right needs Nt / n_sub >= 3");
-  if (opt->precision != KKT_PREC_FP64) return set_error(KKT_ERR_UNSUPPORTED, "reduced precision is not built in this library");
+  if (opt->precision != KKT_PREC_FP64 && h->g.nx != h->g.ny)
+    return set_error(KKT_ERR_UNSUPPORTED, "the tensor-core transforms need a square grid (nx == ny)");
   if (opt->coarse == KKT_COARSE_LEARNED) return set_error(KKT_ERR_UNSUPPORTED, "no learned coarse model attached");
   h->opt = *opt;
   return configure(h);
@@ -449,7 +481,6 @@ int kkt_matvec(kkt_handle* h, const double* x, double* y, void* stream) {
 int kkt_precond_apply(kkt_handle* h, const double* r, double* y, void* stream) {
   KKT_TRY(check_handle(h));
   KKT_TRY(check_ptrs({r, y}));
-  KKT_TRY(ensure_precision(h));
   cudaStream_t st = as_stream(stream);
   const Geometry& g = h->g;
   KKT_TRY(launch_scale(r, 1.0 / g.h, y, g.V, st));
@@ -460,7 +491,14 @@ int kkt_precond_apply(kkt_handle* h, const double* r, double* y, void* stream) {
 int kkt_dst2d(kkt_handle* h, const double* in, double* out, void* stream) {
   KKT_TRY(check_handle(h));
   KKT_TRY(check_ptrs({in, out}));
-  return dst2d(h, in, out, as_stream(stream));
+  cudaStream_t st = as_stream(stream);
+  if (h->opt.precision == KKT_PREC_FP64) return dst2d(h, in, out, st);
+  // reduced precision: the tensor-core transforms (operands rounded to BF16 / TF32, FP32 sums)
+  const TcPlan& t = h->tc;
+  const int valid = h->g.nx - 1;
+  KKT_TRY(tc_pack(t, in, 1.0, valid, st));
+  KKT_TRY(tc_gemm(t, 0, t.bf16 ? 0 : 1, t.x1, valid, st));
+  return tc_gemm(t, 1, 2, out, valid, st);
 }
 
 int kkt_schur_apply(kkt_handle* h, const double* x, double* y, void* stream) {
@@ -474,7 +512,6 @@ int kkt_schur_apply(kkt_handle* h, const double* x, double* y, void* stream) {
 int kkt_schur_precond_apply(kkt_handle* h, const double* r, double* y, void* stream) {
   KKT_TRY(check_handle(h));
   KKT_TRY(check_ptrs({r, y}));
-  KKT_TRY(ensure_precision(h));
   return schur_precond_w(h, r, 1.0, y, as_stream(stream));
 }
 
@@ -502,7 +539,6 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   if (!f || !x) return set_error(KKT_ERR_INVALID_ARG, "null pointer");
   if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(KKT_ERR_INVALID_ARG, "tol must be positive");
   if (maxit < 1) return set_error(KKT_ERR_INVALID_ARG, "maxit must be >= 1");
-  KKT_TRY(ensure_precision(h));
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = as_stream(stream);
   const Geometry& g = h->g;
@@ -535,6 +571,7 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   auto finish = [&](int status, double rel) -> int {
     if (status >= 0 && std::isfinite(rel) && fnorm_plain > 0.0 && euclid_residual)
       local.rel_residual_euclid = euclid_residual();
+    if (status >= 0 && h->opt.precision != KKT_PREC_FP64 && tc_check(h->tc, st) < 0) status = KKT_ERR_TIMEOUT;
     if (!dev_x) {
       cudaMemcpyAsync(x, dx, n3 * sizeof(double), cudaMemcpyDeviceToHost, st);
       cudaStreamSynchronize(st);

@@ -2,6 +2,7 @@
 // The public C ABI is include/kkt.h; nothing here is exported.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -65,6 +66,20 @@ struct DeviceDecomp {
   void* base = nullptr;
 };
 
+// Tensor-core transform plan of the reduced-precision forms (square grids): the DST matrix Q
+// and the slice stacks [Nt][P][P] the four transforms of an apply pass through.
+struct TcPlan {
+  int n = 0, P = 0, slices = 0, bf16 = 1, tile_n = 256;
+  void* q = nullptr;       // Q, P x P, BF16 or FP32
+  void* x0 = nullptr;      // packed input / third transform output
+  void* x1 = nullptr;      // first transform output
+  void* yin = nullptr;     // sweep output, input of the inverse transform
+  float* rhat = nullptr;   // spectral coefficients [n][l][k], FP32
+  int* err = nullptr;      // device flag: a pipeline wait timed out
+  CUtensorMap map_q, map_x0, map_x1, map_yin;
+  size_t bytes = 0;
+};
+
 struct Geometry {
   int nx, ny, Nt, n_sub, Mx, My;
   long long N, V;
@@ -84,14 +99,16 @@ struct kkt_handle {
   kkt::DeviceDecomp dd;
   double* d_lx = nullptr;      // lambda_x[k], k = 1..Mx (eigenvalues of the x second difference)
   double* d_ly = nullptr;
+  double* d_lx_pad = nullptr;  // the same, zero-padded to the tensor-core transform size
+  double* d_ly_pad = nullptr;
+  kkt::TcPlan tc;              // reduced-precision transforms (allocated when such a precision is set)
+  long long coarse_modes = 0;  // modes the coarse buffers are sized for
   // preconditioner workspace
   double* spec = nullptr;      // V doubles: spectral coefficients [n][l][k]
   double* spec2 = nullptr;     // V doubles
   double* coarse_c = nullptr;  // [n_sub][2][N] coarse coefficients
   double* coarse_w = nullptr;  // [n_sub][5][N] block-Thomas factors
   double* vscratch = nullptr;  // sweep storage when a subdomain is too long for shared memory
-  int sweep_block = 128;
-  size_t sweep_smem = 0;
   // Krylov workspace (allocated at the first solve)
   int kry_restart = 0;
   double* kV = nullptr;        // (restart+1) full vectors (3V each)
@@ -136,6 +153,17 @@ int launch_jhat_time(const kkt_handle* h, const double* in, double* out, int dir
 int spectral_schur_precond(const kkt_handle* h, const double* rhat, double* yhat, double in_scale,
                            cudaStream_t st);
 int spectral_coarse_only(const kkt_handle* h, const double* rhat, double* xhat, cudaStream_t st);
+// reduced-precision forms: FP32 spectral input (padded modes), output BF16 (bf16 != 0) or FP32
+int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, int bf16, cudaStream_t st);
+
+// tensor-core transforms (kkt_tc_gemm.cu)
+int tc_padded_size(int n);
+int tc_plan_create(TcPlan& t, int n, int slices, int bf16);
+void tc_plan_destroy(TcPlan& t);
+// which_in: 0 = x0, 1 = x1, 2 = yin; out_mode: 0 BF16 / 1 FP32 padded slices, 2 FP64 valid x valid
+int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, cudaStream_t st);
+int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStream_t st);   // -> x0
+int tc_check(const TcPlan& t, cudaStream_t st);
 
 // Krylov primitives (deterministic two-stage reductions; results in h->red_out on device)
 int krylov_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w,

@@ -15,14 +15,19 @@
 //                        node (Jhat_s^{-1}, the extra node of Q_s carries zero), g = h v, and
 //                        the backward sweep y_n = (g_n + y_{n+1}) / mu with zero terminal
 //                        state (Jhat_s^{-T}); owned nodes receive y (+ x_0).
-// The coarse time solve is FP64 in every form.
+// The coarse time solve is FP64 in every form. In the reduced-precision forms the spectral
+// coefficients arrive in FP32 (from the tensor-core transforms), the sweeps run in FP32 and
+// write the type the inverse transform reads (BF16 or FP32); the residual r - S-hat x_0 is
+// formed in FP64 before rounding.
+#include <cuda_bf16.h>
+
 #include "kkt_internal.cuh"
 
 namespace kkt {
 namespace {
 
 struct SpecParams {
-  int Mx, Nt, n_sub;
+  int Mx, Nt, n_sub;      // Mx: modes per spectral row (the padded size in the mixed forms)
   long long N;
   double a, dtnu, h;
   const double* lx;
@@ -44,7 +49,22 @@ __device__ __forceinline__ double mode_mu(const SpecParams& p, long long q) {
   return p.a + p.dtnu * (p.lx[k] + p.ly[l]);
 }
 
-__global__ void coarse_solve_kernel(const double* __restrict__ rhat, double in_scale, SpecParams p,
+template <typename TI>
+__device__ __forceinline__ double load_d(const TI* p) {
+  return static_cast<double>(__ldg(p));
+}
+
+template <typename TO>
+__device__ __forceinline__ TO store_cast(double v) {
+  return static_cast<TO>(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16>(double v) {
+  return __double2bfloat16(v);
+}
+
+template <typename TI>
+__global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale, SpecParams p,
                                     double* __restrict__ cc, double* __restrict__ cw) {
   const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= p.N) return;
@@ -57,7 +77,7 @@ __global__ void coarse_solve_kernel(const double* __restrict__ rhat, double in_s
     const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
 #pragma unroll 4
     for (int n = o1; n <= o2; ++n) {
-      const double r = __ldg(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
+      const double r = load_d(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
       c0 += r;
       c1 = fma(r, __ldg(p.phi + n - 1), c1);
     }
@@ -122,19 +142,22 @@ __device__ __forceinline__ double coarse_value(const SpecParams& p, int n, int s
   return c3[2 * o] + c3[2 * o + 1] * __ldg(p.phi + n - 1);
 }
 
-__global__ void sweep_kernel(const double* __restrict__ rhat, double in_scale, double* __restrict__ yhat,
-                             SpecParams p, const double* __restrict__ cc, double* __restrict__ vglobal,
+template <typename TI, typename TC, typename TO>
+__global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* __restrict__ yhat,
+                             SpecParams p, const double* __restrict__ cc, TC* __restrict__ vglobal,
                              int max_len) {
-  extern __shared__ double vs_smem[];
+  extern __shared__ __align__(16) unsigned char vs_raw[];
+  TC* vs_smem = reinterpret_cast<TC*>(vs_raw);
   const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int s = blockIdx.y;
   if (q >= p.N) return;
   const long long N = p.N;
   const double mu = mode_mu(p, q), mu2 = mu * mu;
-  const double inv_mu = 1.0 / mu;
+  const TC inv_mu = static_cast<TC>(1.0 / mu);
+  const TC hc = static_cast<TC>(p.h);
   const int first = __ldg(p.first + s), last = __ldg(p.last + s);
   const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
-  double* vs;
+  TC* vs;
   long long vstride;
   if (vglobal) {
     vs = vglobal + static_cast<long long>(s) * max_len * N + q;
@@ -159,9 +182,9 @@ __global__ void sweep_kernel(const double* __restrict__ rhat, double in_scale, d
     xm = coarse_value(p, first - 1, s, c3);
     xc = coarse_value(p, first, s, c3);
   }
-  double v = 0.0;
+  TC v = 0;
   for (int n = first; n <= last; ++n) {
-    double r = __ldg(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
+    double r = load_d(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
     if (p.two_level) {
       xp = coarse_value(p, n + 1, s, c3);
       if (p.multiplicative) {
@@ -171,17 +194,17 @@ __global__ void sweep_kernel(const double* __restrict__ rhat, double in_scale, d
       xm = xc;
       xc = xp;
     }
-    v = (r + v) * inv_mu;
+    v = (static_cast<TC>(r) + v) * inv_mu;
     vs[static_cast<long long>(n - first) * vstride] = v;
   }
   // backward sweep; keep owned nodes
-  double y = 0.0;
+  TC y = 0;
   for (int n = last; n >= first; --n) {
-    y = fma(p.h, vs[static_cast<long long>(n - first) * vstride], y) * inv_mu;
+    y = fma(hc, vs[static_cast<long long>(n - first) * vstride], y) * inv_mu;
     if (n >= o1 && n <= o2) {
-      double out = y;
+      double out = static_cast<double>(y);
       if (p.two_level) out += coarse_value(p, n, s, c3);
-      yhat[static_cast<long long>(n - 1) * N + q] = out;
+      yhat[static_cast<long long>(n - 1) * N + q] = store_cast<TO>(out);
     }
   }
 }
@@ -195,18 +218,18 @@ __global__ void prolong_kernel(SpecParams p, const double* __restrict__ cc, doub
       cc[(2LL * o) * p.N + q] + cc[(2LL * o + 1) * p.N + q] * __ldg(p.phi + n - 1);
 }
 
-SpecParams make_params(const kkt_handle* h) {
+SpecParams make_params(const kkt_handle* h, bool padded) {
   SpecParams p;
   const Geometry& g = h->g;
-  p.Mx = g.Mx;
+  p.Mx = padded ? h->tc.P : g.Mx;
   p.Nt = g.Nt;
   p.n_sub = g.n_sub;
-  p.N = g.N;
+  p.N = padded ? static_cast<long long>(h->tc.P) * h->tc.P : g.N;
   p.a = g.a;
   p.dtnu = g.dtnu;
   p.h = g.h;
-  p.lx = h->d_lx;
-  p.ly = h->d_ly;
+  p.lx = padded ? h->d_lx_pad : h->d_lx;
+  p.ly = padded ? h->d_ly_pad : h->d_ly;
   p.first = h->dd.first;
   p.last = h->dd.last;
   p.ofirst = h->dd.ofirst;
@@ -219,11 +242,45 @@ SpecParams make_params(const kkt_handle* h) {
   return p;
 }
 
-int launch_coarse(const kkt_handle* h, const SpecParams& p, const double* rhat, double in_scale, cudaStream_t st) {
+template <typename TI>
+int launch_coarse(const kkt_handle* h, const SpecParams& p, const TI* rhat, double in_scale, cudaStream_t st) {
   const int tb = 128;
   const long long nb = (p.N + tb - 1) / tb;
   ProfScope ps(KKT_K_COARSE, st);
-  coarse_solve_kernel<<<static_cast<unsigned>(nb), tb, 0, st>>>(rhat, in_scale, p, h->coarse_c, h->coarse_w);
+  coarse_solve_kernel<TI><<<static_cast<unsigned>(nb), tb, 0, st>>>(rhat, in_scale, p, h->coarse_c, h->coarse_w);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+template <typename TI, typename TC, typename TO>
+int launch_sweeps(const kkt_handle* h, const SpecParams& p, const TI* rhat, double in_scale, TO* yhat,
+                  cudaStream_t st) {
+  if (static_cast<const void*>(rhat) == static_cast<const void*>(yhat))
+    return set_error(KKT_ERR_INVALID_ARG, "spectral sweep needs distinct buffers");
+  if (p.two_level) KKT_TRY(launch_coarse<TI>(h, p, rhat, in_scale, st));
+  // sweep storage: shared memory when a subdomain's nodes fit, else the global scratch
+  const size_t limit = 200 * 1024;
+  int tb = 0;
+  for (int cand : {128, 64, 32})
+    if (static_cast<size_t>(h->td.max_len) * cand * sizeof(TC) <= limit) {
+      tb = cand;
+      break;
+    }
+  size_t smem = 0;
+  TC* vglob = nullptr;
+  if (tb) {
+    smem = static_cast<size_t>(h->td.max_len) * tb * sizeof(TC);
+  } else {
+    tb = 128;
+    vglob = reinterpret_cast<TC*>(h->vscratch);
+    if (!vglob) return set_error(KKT_ERR_INVALID_ARG, "sweep scratch missing");
+  }
+  dim3 grid(static_cast<unsigned>((p.N + tb - 1) / tb), static_cast<unsigned>(p.n_sub));
+  auto kern = sweep_kernel<TI, TC, TO>;
+  if (smem > 0)
+    KKT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  ProfScope ps(KKT_K_SWEEP, st);
+  kern<<<grid, tb, smem, st>>>(rhat, in_scale, yhat, p, h->coarse_c, vglob, h->td.max_len);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
@@ -232,24 +289,19 @@ int launch_coarse(const kkt_handle* h, const SpecParams& p, const double* rhat, 
 
 int spectral_schur_precond(const kkt_handle* h, const double* rhat, double* yhat, double in_scale,
                            cudaStream_t st) {
-  if (rhat == yhat) return set_error(KKT_ERR_INVALID_ARG, "spectral sweep needs distinct buffers");
-  SpecParams p = make_params(h);
-  if (p.two_level) KKT_TRY(launch_coarse(h, p, rhat, in_scale, st));
-  const int tb = h->sweep_block;
-  dim3 grid(static_cast<unsigned>((p.N + tb - 1) / tb), static_cast<unsigned>(p.n_sub));
-  if (h->sweep_smem > 0)
-    KKT_CUDA_TRY(cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(h->sweep_smem)));
-  ProfScope ps(KKT_K_SWEEP, st);
-  sweep_kernel<<<grid, tb, h->sweep_smem, st>>>(rhat, in_scale, yhat, p, h->coarse_c, h->vscratch,
-                                                h->td.max_len);
-  KKT_CUDA_TRY(cudaGetLastError());
-  return KKT_OK;
+  SpecParams p = make_params(h, false);
+  return launch_sweeps<double, double, double>(h, p, rhat, in_scale, yhat, st);
+}
+
+int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, int bf16, cudaStream_t st) {
+  SpecParams p = make_params(h, true);
+  if (bf16) return launch_sweeps<float, float, __nv_bfloat16>(h, p, rhat, 1.0, static_cast<__nv_bfloat16*>(yhat), st);
+  return launch_sweeps<float, float, float>(h, p, rhat, 1.0, static_cast<float*>(yhat), st);
 }
 
 int spectral_coarse_only(const kkt_handle* h, const double* rhat, double* xhat, cudaStream_t st) {
-  SpecParams p = make_params(h);
-  KKT_TRY(launch_coarse(h, p, rhat, 1.0, st));
+  SpecParams p = make_params(h, false);
+  KKT_TRY(launch_coarse<double>(h, p, rhat, 1.0, st));
   const int tb = 128;
   dim3 grid(static_cast<unsigned>((p.N + tb - 1) / tb), static_cast<unsigned>(p.Nt));
   ProfScope ps(KKT_K_SWEEP, st);

@@ -1,0 +1,446 @@
+// Sine transforms as dense GEMMs on the 5th-generation tensor cores (tcgen05), for the
+// reduced-precision forms of the preconditioner: every implicit spatial step of the sweeps
+// of Eq 13 is diagonalised by the 2D DST-I, here applied as products with the DST matrix Q.
+//
+// One kernel serves all four transforms of a preconditioner apply. Input A is a stack of S
+// slices, each P x P (rows x K, K contiguous), B is Q (P x P, symmetric, zero-padded past
+// n-1), and the output is stored TRANSPOSED per slice:
+//     O[s][c][r] = sum_k A[s][r][k] Q[k][c]
+// so the next transform again contracts along the contiguous axis, and the stores of the
+// epilogue are coalesced (32 consecutive r per warp).
+//
+// Per CTA: one 128 x TILE_N output tile. Warp 0 lane 0 streams A and B chunks of 128 bytes of
+// K through a 2-stage ring with TMA (128B swizzle) and mbarriers, warp 1 lane 0 issues
+// tcgen05.mma (M = 128, N = TILE_N, K = 16 for BF16 / 8 for TF32, FP32 accumulation in TMEM),
+// and after the last commit all four warps read the accumulator with tcgen05.ld (each warp
+// its 32-lane quarter) and store. Every mbarrier wait is bounded (about 2 s of clock); on a
+// timeout the kernel records an error flag, skips its remaining work, still waits (bounded)
+// for its own copies and MMAs, frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "kkt_internal.cuh"
+
+namespace kkt {
+namespace {
+
+constexpr int kTileM = 128;
+constexpr int kStages = 2;
+constexpr int kChunkBytes = 128;                      // K bytes per TMA box row (one swizzle span)
+constexpr long long kWaitCycles = 4000000000LL;       // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true on success, false after ~2 s.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128B swizzle, 8-row atoms 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = (addr & 0x3FFFFull) >> 4;       // start address, bits [0,14)
+  d |= 1ull << 16;                             // leading byte offset (unused for swizzled K-major)
+  d |= (1024ull >> 4) << 32;                   // stride byte offset: 8 rows x 128 B
+  d |= 1ull << 46;                             // descriptor version
+  d |= 2ull << 61;                             // swizzle: 128B
+  return d;
+}
+
+template <typename TIn>
+struct MmaKind;
+
+template <>
+struct MmaKind<__nv_bfloat16> {
+  static constexpr int kFormat = 1;            // BF16
+  static constexpr int kUmmaK = 16;            // 32 bytes of K per instruction
+  static __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+};
+
+template <>
+struct MmaKind<float> {
+  static constexpr int kFormat = 2;            // TF32
+  static constexpr int kUmmaK = 8;
+  static __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
+        ::"r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+};
+
+// Instruction descriptor: FP32 accumulator, A and B of the given format, both K-major.
+template <typename TIn, int N>
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4)                                              // D format: F32
+         | (static_cast<uint32_t>(MmaKind<TIn>::kFormat) << 7)   // A format
+         | (static_cast<uint32_t>(MmaKind<TIn>::kFormat) << 10)  // B format
+         | (static_cast<uint32_t>(N >> 3) << 17)                 // N / 8
+         | (static_cast<uint32_t>(kTileM >> 4) << 24);           // M / 16
+}
+
+struct TcParams {
+  int P;              // padded transform size (multiple of 128)
+  int slices;
+  int valid;          // output mode 2: rows/cols < valid are stored, into a valid x valid slice
+  void* out;
+  int* err;           // device error flag (set to 1 on a wait timeout)
+};
+
+enum OutMode { kOutBF16 = 0, kOutF32 = 1, kOutF64 = 2 };
+
+template <typename TIn, int TILE_N, int OUT>
+__global__ void __launch_bounds__(128, 1)
+    tc_dst_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int A_BYTES = kTileM * kChunkBytes;
+  constexpr int B_BYTES = TILE_N * kChunkBytes;
+  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int KCHUNK = kChunkBytes / static_cast<int>(sizeof(TIn));   // elements of K per chunk
+  constexpr int UMMA_K = MmaKind<TIn>::kUmmaK;
+  constexpr int K_STEPS = KCHUNK / UMMA_K;                               // 4 MMAs per chunk
+  constexpr uint32_t IDESC = instr_desc<TIn, TILE_N>();
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * STAGE);
+  uint64_t* empty = full + kStages;
+  uint64_t* done = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntile_c = p.P / TILE_N, ntile_r = p.P / kTileM;
+  const int tile = blockIdx.x;
+  const int s = tile / (ntile_c * ntile_r);
+  const int rem = tile - s * ntile_c * ntile_r;
+  const int rt = rem / ntile_c, ct = rem - rt * ntile_c;
+  const int nchunks = p.P / KCHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TILE_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  int issued = 0;       // chunks whose TMA copies were issued (producer thread)
+  if (warp == 0 && lane == 0) {
+    for (int c = 0; c < nchunks; ++c) {
+      const int st = c % kStages;
+      if (c >= kStages && !mbar_wait(empty + st, ((c / kStages) & 1) ^ 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* sa = smem + st * STAGE;
+      mbar_expect_tx(full + st, STAGE);
+      tma_load_2d(sa, &tmA, c * KCHUNK, s * p.P + rt * kTileM, full + st);
+      tma_load_2d(sa + A_BYTES, &tmB, c * KCHUNK, ct * TILE_N, full + st);
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    for (int c = 0; c < nchunks; ++c) {
+      const int st = c % kStages;
+      if (!mbar_wait(full + st, (c / kStages) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint8_t* sa = smem + st * STAGE;
+      const uint64_t da = smem_desc(sa), db = smem_desc(sa + A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < K_STEPS; ++kk) {
+        // advance 32 bytes of K inside the 128-byte swizzle row: +2 in the encoded address
+        MmaKind<TIn>::mma(tmem, da + 2ull * kk, db + 2ull * kk, IDESC, (c | kk) != 0);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(empty + st)) : "memory");
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 ::"r"(smem_u32(done)) : "memory");
+  }
+  __syncwarp();
+  // every thread: wait for the last MMA (the commit on `done` arrives after all issued MMAs)
+  const bool ok = mbar_wait(done, 0);
+  if (!ok) *abort_flag = 1;
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) atomicExch(p.err, 1);
+    // let the copies this CTA issued land before its shared memory is released
+    // (only the last kStages issued chunks can still be in flight: an older stage was refilled
+    // only after its MMAs, and so its copy, had completed)
+    if (warp == 0 && lane == 0) {
+      for (int c = issued > kStages ? issued - kStages : 0; c < issued; ++c)
+        mbar_wait(full + (c % kStages), (c / kStages) & 1);
+    }
+  } else {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int r = rt * kTileM + warp * 32 + lane;
+    const uint32_t tbase = tmem + (static_cast<uint32_t>(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < TILE_N; c0 += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(tbase + c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int t = 0; t < 16; ++t) {
+        const int c = ct * TILE_N + c0 + t;
+        const float val = __uint_as_float(v[t]);
+        if (OUT == kOutBF16) {
+          reinterpret_cast<__nv_bfloat16*>(p.out)[(static_cast<long long>(s) * p.P + c) * p.P + r] = __float2bfloat16_rn(val);
+        } else if (OUT == kOutF32) {
+          reinterpret_cast<float*>(p.out)[(static_cast<long long>(s) * p.P + c) * p.P + r] = val;
+        } else {
+          if (c < p.valid && r < p.valid)
+            reinterpret_cast<double*>(p.out)[(static_cast<long long>(s) * p.valid + c) * p.valid + r] = static_cast<double>(val);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE_N));
+}
+
+// out[s][j][i] (P x P, zero padded) = scale * in[s][j][i] (valid x valid), converted to TIn
+template <typename TIn>
+__global__ void pack_kernel(const double* __restrict__ in, double scale, TIn* __restrict__ out, int P, int valid,
+                            long long total) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int i = static_cast<int>(t % P);
+  const long long sj = t / P;
+  const int j = static_cast<int>(sj % P);
+  const long long s = sj / P;
+  double v = 0.0;
+  if (i < valid && j < valid) v = scale * in[(s * valid + j) * valid + i];
+  if constexpr (sizeof(TIn) == 2)
+    out[t] = __double2bfloat16(v);
+  else
+    out[t] = static_cast<float>(v);
+}
+
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int get_encode(EncodeFn* fn) {
+  static EncodeFn cached = nullptr;
+  if (!cached) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    KKT_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q));
+    if (!f || q != cudaDriverEntryPointSuccess) return set_error(KKT_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    cached = reinterpret_cast<EncodeFn>(f);
+  }
+  *fn = cached;
+  return KKT_OK;
+}
+
+// 2D tensor map over rows x P (K contiguous), box = (128 bytes of K) x box_rows, 128B swizzle.
+int make_map(CUtensorMap* map, const void* base, int elem_bytes, long long rows, int P, int box_rows) {
+  EncodeFn enc = nullptr;
+  KKT_TRY(get_encode(&enc));
+  const cuuint64_t dims[2] = {static_cast<cuuint64_t>(P), static_cast<cuuint64_t>(rows)};
+  const cuuint64_t strides[1] = {static_cast<cuuint64_t>(P) * elem_bytes};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kChunkBytes / elem_bytes), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                         const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(KKT_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(static_cast<int>(r)));
+  return KKT_OK;
+}
+
+template <typename TIn, int TILE_N, int OUT>
+int launch_gemm(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, cudaStream_t st) {
+  constexpr int STAGE = (kTileM + TILE_N) * kChunkBytes;
+  const size_t smem = 1024 + kStages * STAGE + 256;
+  auto kern = tc_dst_gemm_kernel<TIn, TILE_N, OUT>;
+  KKT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  const long long tiles = static_cast<long long>(p.slices) * (p.P / kTileM) * (p.P / TILE_N);
+  ProfScope ps(KKT_K_DST, st);
+  kern<<<static_cast<unsigned>(tiles), 128, smem, st>>>(a, b, p);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+}  // namespace
+
+// Round-to-nearest-even of a double to BF16 (8 significant bits), as a bit pattern.
+uint16_t bf16_bits_rne(double v) {
+  if (v == 0.0 || !std::isfinite(v)) {
+    const float f = static_cast<float>(v);
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return static_cast<uint16_t>(b >> 16);
+  }
+  int e = 0;
+  const double m = std::frexp(v, &e);                 // v = m 2^e, 0.5 <= |m| < 1
+  const double r = std::nearbyint(m * 256.0) / 256.0;  // 8 significant bits, ties to even
+  const float f = static_cast<float>(std::ldexp(r, e)); // exact in FP32
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  return static_cast<uint16_t>(b >> 16);
+}
+
+// Padded transform size used by the tensor-core path: n - 1 rounded up to a multiple of 128.
+int tc_padded_size(int n) { return ((n - 1 + 127) / 128) * 128; }
+
+int tc_plan_create(TcPlan& t, int n, int slices, int bf16) {
+  t = TcPlan();
+  t.n = n;
+  t.P = tc_padded_size(n);
+  t.slices = slices;
+  t.bf16 = bf16;
+  const int P = t.P, M = n - 1;
+  const int eb = bf16 ? 2 : 4;
+  t.tile_n = P % 256 == 0 ? 256 : 128;
+  const size_t plane = static_cast<size_t>(P) * P;
+  const size_t elems = plane * slices;
+  // Q: orthonormal DST-I matrix, zero padded
+  std::vector<double> q(plane, 0.0);
+  const double pi = 3.14159265358979323846, sc = std::sqrt(2.0 / n);
+  for (int j = 0; j < M; ++j)
+    for (int k = 0; k < M; ++k) q[static_cast<size_t>(j) * P + k] = sc * std::sin(pi * (j + 1.0) * (k + 1.0) / n);
+  std::vector<uint8_t> qh(plane * eb);
+  for (size_t e = 0; e < plane; ++e) {
+    if (bf16) {
+      const uint16_t v = bf16_bits_rne(q[e]);
+      std::memcpy(qh.data() + 2 * e, &v, 2);
+    } else {
+      const float v = static_cast<float>(q[e]);
+      std::memcpy(qh.data() + 4 * e, &v, 4);
+    }
+  }
+  KKT_CUDA_TRY(cudaMalloc(&t.q, plane * eb));
+  KKT_CUDA_TRY(cudaMemcpy(t.q, qh.data(), plane * eb, cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMalloc(&t.x0, elems * eb));
+  KKT_CUDA_TRY(cudaMalloc(&t.x1, elems * eb));
+  KKT_CUDA_TRY(cudaMalloc(&t.yin, elems * eb));
+  KKT_CUDA_TRY(cudaMalloc(&t.rhat, elems * sizeof(float)));
+  KKT_CUDA_TRY(cudaMalloc(&t.err, sizeof(int)));
+  KKT_CUDA_TRY(cudaMemset(t.err, 0, sizeof(int)));
+  t.bytes = plane * eb + 3 * elems * eb + elems * sizeof(float) + sizeof(int);
+  const long long rows = static_cast<long long>(slices) * P;
+  KKT_TRY(make_map(&t.map_q, t.q, eb, P, P, t.tile_n));
+  KKT_TRY(make_map(&t.map_x0, t.x0, eb, rows, P, kTileM));
+  KKT_TRY(make_map(&t.map_x1, t.x1, eb, rows, P, kTileM));
+  KKT_TRY(make_map(&t.map_yin, t.yin, eb, rows, P, kTileM));
+  return KKT_OK;
+}
+
+void tc_plan_destroy(TcPlan& t) {
+  cudaFree(t.q);
+  cudaFree(t.x0);
+  cudaFree(t.x1);
+  cudaFree(t.yin);
+  cudaFree(t.rhat);
+  cudaFree(t.err);
+  t = TcPlan();
+}
+
+// One transform pass: out = per-slice transpose of (in-map rows) x Q.
+int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, cudaStream_t st) {
+  const CUtensorMap& a = which_in == 0 ? t.map_x0 : (which_in == 1 ? t.map_x1 : t.map_yin);
+  TcParams p;
+  p.P = t.P;
+  p.slices = t.slices;
+  p.valid = valid;
+  p.out = out;
+  p.err = t.err;
+#define KKT_TC_CASE(TIN, TN, OM)                                         \
+  if (t.tile_n == TN && out_mode == OM) return launch_gemm<TIN, TN, OM>(a, t.map_q, p, st);
+  if (t.bf16) {
+    KKT_TC_CASE(__nv_bfloat16, 256, kOutBF16)
+    KKT_TC_CASE(__nv_bfloat16, 256, kOutF32)
+    KKT_TC_CASE(__nv_bfloat16, 256, kOutF64)
+    KKT_TC_CASE(__nv_bfloat16, 128, kOutBF16)
+    KKT_TC_CASE(__nv_bfloat16, 128, kOutF32)
+    KKT_TC_CASE(__nv_bfloat16, 128, kOutF64)
+  } else {
+    KKT_TC_CASE(float, 256, kOutF32)
+    KKT_TC_CASE(float, 256, kOutF64)
+    KKT_TC_CASE(float, 128, kOutF32)
+    KKT_TC_CASE(float, 128, kOutF64)
+  }
+#undef KKT_TC_CASE
+  return set_error(KKT_ERR_UNSUPPORTED, "tensor-core transform: unsupported output mode");
+}
+
+int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStream_t st) {
+  const long long total = static_cast<long long>(t.slices) * t.P * t.P;
+  const int tb = 256;
+  const long long nb = (total + tb - 1) / tb;
+  ProfScope ps(KKT_K_AXPY, st);
+  if (t.bf16)
+    pack_kernel<__nv_bfloat16><<<static_cast<unsigned>(nb), tb, 0, st>>>(in, scale, static_cast<__nv_bfloat16*>(t.x0), t.P, valid, total);
+  else
+    pack_kernel<float><<<static_cast<unsigned>(nb), tb, 0, st>>>(in, scale, static_cast<float*>(t.x0), t.P, valid, total);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int tc_check(const TcPlan& t, cudaStream_t st) {
+  int e = 0;
+  KKT_CUDA_TRY(cudaMemcpyAsync(&e, t.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KKT_CUDA_TRY(cudaStreamSynchronize(st));
+  if (e) return set_error(KKT_ERR_TIMEOUT, "a tensor-core transform timed out waiting on its pipeline");
+  return KKT_OK;
+}
+
+}  // namespace kkt

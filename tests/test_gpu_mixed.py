@@ -1,0 +1,122 @@
+"""Reduced-precision forms: DST transforms on tcgen05 tensor cores (BF16 or TF32 operands, FP32
+accumulation), FP32 sweeps, FP64 coarse solve and FP64 FGMRES.
+
+Errors against FP64, per result (norm-wise relative):
+* BF16 transform vs an exact NumPy emulation of the same rounding (BF16 input, BF16 Q, BF16
+  intermediate, FP64 sums): <= 1e-4 (FP32 accumulation order and rare BF16 tie flips of the
+  intermediate); vs the FP64 transform: <= 2e-2 (about 2^-9 per rounding).
+* TF32 transform vs the FP64 transform: <= 5e-3.
+* preconditioner apply vs the FP64 oracle: <= 5e-2 (BF16), <= 1e-2 (TF32).
+* solves: the same 1e-8 weighted relative residual as FP64, checked against the exact solution.
+"""
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import problem, schwarz, spectral
+from oracle.problem import HeatKKT
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def kkt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_04421_gb300.kkt as k
+    k.load_library()
+    return k
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def bf16(x):
+    """Round-to-nearest-even to 8 significant bits (BF16), computed exactly in FP64."""
+    m, e = np.frexp(np.asarray(x, dtype=np.float64))
+    return np.ldexp(np.rint(m * 256.0) / 256.0, e)
+
+
+def dst_matrix(n):
+    j = np.arange(1, n)
+    return np.sqrt(2.0 / n) * np.sin(np.pi * np.outer(j, j) / n)
+
+
+@pytest.mark.parametrize("n,Nt", [(16, 3), (128, 5), (200, 2), (256, 4)])
+def test_bf16_tensor_core_transform_matches_emulation(kkt, n, Nt):
+    p = HeatKKT(nx=n, ny=n, Nt=Nt)
+    s = kkt.Solver(n, n, Nt, 1.0, 1.0, 1e-3, 1, precision="bf16")
+    x = workloads.random_vector(p.V, 40 + n).reshape(Nt, n - 1, n - 1)
+    got = host(s.dst2d(dev(x.ravel()))).reshape(Nt, n - 1, n - 1)       # [t][l][k]
+    Q = bf16(dst_matrix(n))
+    xb = bf16(x)
+    y1 = bf16(np.einsum("tji,ik->tkj", xb, Q))     # along x, BF16 intermediate [t][k][j]
+    want = np.einsum("tkj,jl->tlk", y1, Q)         # along y -> [t][l][k]
+    assert rel(got, want) < 1e-4
+    exact = spectral.dst2(x, p)
+    assert rel(got, exact) < 2e-2
+
+
+@pytest.mark.parametrize("n,Nt", [(16, 3), (130, 2), (256, 4)])
+def test_tf32_tensor_core_transform_close_to_fp64(kkt, n, Nt):
+    p = HeatKKT(nx=n, ny=n, Nt=Nt)
+    s = kkt.Solver(n, n, Nt, 1.0, 1.0, 1e-3, 1, precision="tf32")
+    x = workloads.random_vector(p.V, 50 + n)
+    got = host(s.dst2d(dev(x)))
+    assert rel(got, spectral.dst2(x, p).ravel()) < 5e-3
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 5e-2), ("tf32", 1e-2)])
+@pytest.mark.parametrize("variant,coarse", [("multiplicative", "exact"), ("multiplicative", "none")])
+def test_mixed_schur_preconditioner_error_vs_fp64_oracle(kkt, prec, tol, variant, coarse):
+    w = workloads.CFG_SMALL
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=prec, variant=variant, coarse=coarse)
+    pre = schwarz.schur_preconditioner(p, w.n_sub, variant="one-level" if coarse == "none" else variant)
+    r = workloads.random_vector(p.V, 61)
+    err = rel(host(s.schur_precond_apply(dev(r))), pre.apply(r))
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("prec", ["bf16", "tf32"])
+def test_mixed_solve_reaches_tolerance_and_exact_solution(kkt, prec):
+    w = workloads.CFG_SMALL
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    f = problem.assemble_rhs(p, workloads.make_target(w), workloads.make_u0(w))
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=prec)
+    res = s.solve(dev(f), tol=1e-8, maxit=420)
+    assert res.status == kkt.KKT_OK and res.rel_residual <= 1e-8
+    K = problem.assemble_K(p)
+    d = problem.l2_residual_weights(p)
+    x = host(res.x)
+    assert np.linalg.norm(d * (f - K @ x)) / np.linalg.norm(d * f) <= 1.01e-8
+    assert rel(x, spectral.kkt_exact_solve(p, f)) < 1e-6
+    tight = s.solve(dev(f), tol=1e-12, maxit=420)
+    assert tight.status == kkt.KKT_OK
+    assert rel(host(tight.x), spectral.kkt_exact_solve(p, f)) < 1e-10
+
+
+def test_mixed_preconditioner_full_grid_vs_fp64_gpu(kkt):
+    """512 x 512 grid (the mixed workload's spatial size), a short time axis: the BF16 and TF32
+    applies against the FP64 apply on the same GPU."""
+    n, Nt, nd = 512, 16, 4
+    r = torch.randn((n - 1) ** 2 * Nt, dtype=torch.float64, device="cuda",
+                    generator=torch.Generator("cuda").manual_seed(3))
+    ref = kkt.Solver(n, n, Nt, 1.0, 0.1, 1e-4, nd).schur_precond_apply(r)
+    for prec, tol in (("bf16", 5e-2), ("tf32", 1e-2)):
+        got = kkt.Solver(n, n, Nt, 1.0, 0.1, 1e-4, nd, precision=prec).schur_precond_apply(r)
+        err = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+        assert err < tol, (prec, err)
