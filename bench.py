@@ -203,49 +203,129 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------------
 
-def roofline(kkt_mod, prof: dict, w: workloads.Workload, peaks: dict, peak_kind: str, iters: int,
-             steps: int) -> dict:
+def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -> dict:
     """Roofline of the kernel class with the largest device time in the timed region.
 
-    Algorithmic work per launch (V = N Nt unknowns per block):
-      dst      2.5 (n-1) log2(2n) FLOP per grid line (one real DST-I of n-1 points; a 2D pass
-               transforms Nt (n-1) lines); FP64-ALU bound on GB300
-      multidot, update, axpy: 2 FLOP per vector element and basis vector (FP64 FMA)
-      matvec   48 V bytes (3 blocks in, 3 out)
-      sweep    16 V bytes (read rhat, write yhat) + coarse pairs
-      coarse   8 V bytes (read rhat)
+    The library sums, for every timed launch, the algorithmic FLOPs and bytes of that launch
+    (what the method must compute and move; formulas at each launch site). The binding roof is
+    the larger of FLOPs / compute peak and bytes / HBM peak; achieved = work / measured time.
+    Compute peaks: FP64 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived from unit counts); BF16 the
+    measured dense GEMM burst; TF32 the BF16 figure x 1.1/2.25 (nominal dense ratio).
     """
-    n = w.nx
-    ms = {k: v["ms"] for k, v in prof.items()}
-    top = max(ms, key=ms.get)
-    launches = max(prof[top]["timed"], 1)
-    avg_s = ms[top] / launches / 1e3
-    V = w.V
+    top = max(prof, key=lambda k: prof[k]["ms"])
+    e = prof[top]
+    sec = e["ms"] / 1e3
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    if top == "dst":
-        flops = (n - 1) * w.Nt * 2.5 * (n - 1) * np.log2(2 * n)
-        ach = flops / avg_s / 1e12
-        return {"kernel": "dst_tile_kernel", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)",
-                "per_launch_ms": avg_s * 1e3}
-    if top in ("multidot", "update", "axpy"):
-        # average basis vectors per launch over the run: total FMAs / launches
-        flops_total = 0.0
-        # one Arnoldi step j touches j+1 vectors in each pass; sum over the cycle (restart 30)
-        per_cycle = sum(j + 1 for j in range(min(iters, 30)))
-        passes = prof[top]["timed"] / max(steps, 1)
-        vec_per_launch = (per_cycle * max(1, iters // 30 + (1 if iters % 30 else 0))) / max(passes, 1)
-        flops_total = 2.0 * 3 * V * vec_per_launch
-        ach = flops_total / avg_s / 1e12
-        return {"kernel": f"{top}_kernel", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)",
-                "per_launch_ms": avg_s * 1e3}
-    bytes_per = {"matvec": 48 * V, "sweep": 16 * V, "coarse": 8 * V, "reduce": 8 * 3 * V}.get(top, 16 * V)
-    ach = bytes_per / avg_s / 1e9
-    return {"kernel": top, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": None, "peak_source": f"{peak_kind} HBM copy", "per_launch_ms": avg_s * 1e3}
+    if top == "dst" and precision in ("bf16", "tf32"):
+        bf = float(peaks.get("bf16_tflops", 1900.0))
+        alu_peak = bf if precision == "bf16" else bf * 1.1 / 2.25
+        alu_kind, alu_src = "tensor", f"{peak_kind} BF16 dense GEMM" + ("" if precision == "bf16" else " x 1.1/2.25 (TF32)")
+        kname = "tc_dst_gemm_kernel"
+    else:
+        alu_peak = FP64_PEAK_TFLOPS
+        alu_kind, alu_src = "alu", "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)"
+        kname = {"dst": "dst_tile_kernel", "multidot": "multidot_kernel", "update": "update_norm_kernel",
+                 "axpy": "axpy_multi_kernel", "matvec": "matvec_kernel", "sweep": "sweep_kernel",
+                 "coarse": "coarse_solve_kernel"}.get(top, top)
+    t_alu = e["flops"] / (alu_peak * 1e12)
+    t_mem = e["bytes"] / (hbm * 1e9)
+    per_launch = e["ms"] / max(e["timed"], 1)
+    if t_alu >= t_mem:
+        ach = e["flops"] / sec / 1e12
+        out = {"kernel": kname, "bound": alu_kind, "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+               "frac": ach / alu_peak, "peak_source": alu_src}
+    else:
+        ach = e["bytes"] / sec / 1e9
+        out = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+               "peak_source": f"{peak_kind} HBM copy"}
+    out.update({"traffic": None, "per_launch_ms": per_launch, "launches": e["timed"],
+                "algorithmic_flops_per_launch": e["flops"] / max(e["timed"], 1),
+                "algorithmic_bytes_per_launch": e["bytes"] / max(e["timed"], 1),
+                "hbm_gbs_algorithmic": e["bytes"] / sec / 1e9, "share_of_step": e["ms"] / sum(v["ms"] for v in prof.values())})
+    return out
+
+
+def time_applies(kkt_mod, solver, V: int, reps: int, dev) -> dict:
+    """Standalone P^-1 applies (kkt_precond_apply on a full KKT vector), CUDA events on the
+    launching stream. Algorithmic traffic 48 V bytes per apply (3 blocks in, 3 out)."""
+    import torch
+
+    r = torch.randn(3 * V, dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(7))
+    y = torch.empty_like(r)
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        solver.precond_apply(r, out=y)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        solver.precond_apply(r, out=y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    peaks, kind = measured_peaks()
+    gbs = 48.0 * V / (ms / 1e3) / 1e9
+    hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
+    del r, y
+    return {"ms": ms, "applies_per_s": 1e3 / ms, "algorithmic_bytes": 48 * V, "hbm_gbs": gbs,
+            "hbm_frac": gbs / hbm, "peak_gbs": hbm, "peak_source": f"{kind} HBM copy"}
+
+
+def time_solves(kkt_mod, solver, f, steps: int, warmup: int):
+    import torch
+
+    x = torch.zeros_like(f)
+    for _ in range(warmup):
+        x.zero_()
+        solver.solve(f, x, tol=TOL, maxit=MAXIT)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res = None
+    for _ in range(steps):
+        x.zero_()
+        res = solver.solve(f, x, tol=TOL, maxit=MAXIT)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, res, x
+
+
+def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
+    """Time to a 1e-8 (weighted) solve of the 512 x 512, Nt = 512, N_D = 64 mixed workload in
+    each arithmetic form on this GPU, plus its standalone preconditioner apply."""
+    import torch
+
+    w = workloads.CFG_MIXED
+    ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
+    out = {"workload": f"nx=ny={w.nx} Nt={w.Nt} N_D={w.n_sub} nu={w.nu} omega={w.omega:g}, sine-series target"}
+    ref_x = None
+    for prec in ("fp64", "bf16", "tf32"):
+        s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=prec)
+        f = s.build_rhs(ut)
+        ms, res, x = time_solves(kkt_mod, s, f, steps, warmup)
+        kkt_mod.kkt_profile_read(reset=True)
+        kkt_mod.kkt_profile_enable(True)
+        apply_stats = time_applies(kkt_mod, s, s.V, 5, dev)
+        kkt_mod.kkt_profile_enable(False)
+        prof = kkt_mod.kkt_profile_read(reset=True)
+        peaks, kind = measured_peaks()
+        apply_stats["dominant_kernel_roofline"] = roofline(prof, peaks, kind, prec)
+        apply_stats["kernel_ms_per_apply"] = {k: round(v["ms"] / 8, 4) for k, v in prof.items() if v["ms"] > 0}
+        entry = {"solve_ms": ms, "iterations": res.iterations, "rel_residual": res.rel_residual,
+                 "converged": res.status == kkt_mod.KKT_OK, "precond_apply": apply_stats}
+        if prec == "fp64":
+            ref_x = x.clone()
+        else:
+            entry["solution_rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(x - ref_x) / torch.linalg.vector_norm(ref_x))
+        out[prec] = entry
+        del f, x
+        s.close()
+        torch.cuda.empty_cache()
+    out["speedup_vs_fp64"] = {p: out["fp64"]["solve_ms"] / out[p]["solve_ms"] for p in ("bf16", "tf32")}
+    return out
 
 
 def run_ours(args):
@@ -270,11 +350,9 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    iters = []
     for _ in range(args.warmup):
         x.zero_()
-        res = solver.solve(f, x, tol=TOL, maxit=MAXIT)
-        iters.append(res.iterations)
+        solver.solve(f, x, tol=TOL, maxit=MAXIT)
     sampler = ClockSampler(local)
     sampler.start()
     kkt.kkt_profile_read(reset=True)
@@ -313,7 +391,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         x_host.zero_()
-        r = solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT)
+        solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     if world > 1:
@@ -322,19 +400,25 @@ def run_ours(args):
         e2e_s = float(t.item())
     nbytes = f.numel() * 8
     peaks, peak_kind = measured_peaks()
+    apply_stats = time_applies(kkt, solver, w.V, 10, dev)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": describe(w),
             "iterations": its, "converged": ok, "rel_residual": results[-1].rel_residual,
             "rel_residual_euclid": results[-1].rel_residual_euclid,
-            "precond_applies_per_s": world * applies / (ms / 1e3),
+            "precond_applies_per_s": apply_stats["applies_per_s"], "precond_apply": apply_stats,
             "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
                     "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches,
             "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "kernel_launches": {k: v["launches"] for k, v in prof.items()},
             "clocks": clocks}
-    line["roofline"] = roofline(kkt, prof, w, peaks, peak_kind, its, args.steps)
+    line["roofline"] = roofline(prof, peaks, peak_kind)
+    solver.close()
+    del f, x, f_host, x_host
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_forms:
+        line["forms"] = measure_forms(kkt, dev, steps=2, warmup=1)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s, sample = oracle_iteration_sample(w, min(its, 30) // 2 + 1)
         line["cpu_baseline"] = {"value": 1.0 / (s * its), "unit": "solves/s", "cores": cpu_threads(),
@@ -343,7 +427,6 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
-    solver.close()
     return 0 if ok else 1
 
 
@@ -357,6 +440,8 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=32,
                     help="iterations the reference arm scales its per-iteration sample by")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP64/BF16/TF32 time-to-solution comparison on the 512 x 512 workload")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

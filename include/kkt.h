@@ -234,6 +234,8 @@ typedef struct kkt_kernel_stats {
   long long launches[KKT_K_COUNT];  /* kernels launched, always counted */
   double ms[KKT_K_COUNT];           /* summed device time (CUDA events), only while timing is on */
   long long timed[KKT_K_COUNT];     /* launches that were timed */
+  double flops[KKT_K_COUNT];        /* algorithmic floating-point operations of the timed launches */
+  double bytes[KKT_K_COUNT];        /* algorithmic device-memory bytes of the timed launches */
 } kkt_kernel_stats;
 
 /* Turn per-launch CUDA-event timing on (1) or off (0); each timed launch records two events on

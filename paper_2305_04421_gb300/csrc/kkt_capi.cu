@@ -196,9 +196,20 @@ int configure(kkt_handle* h) {
   }
   if (modes > h->coarse_modes) {
     KKT_TRY(dev_alloc(h, &h->coarse_c, 2 * static_cast<size_t>(g.n_sub) * modes));
-    KKT_TRY(dev_alloc(h, &h->coarse_w, 5 * static_cast<size_t>(g.n_sub) * modes));
+    KKT_TRY(dev_alloc(h, &h->coarse_w, 2 * static_cast<size_t>(g.n_sub) * modes));
     h->coarse_modes = modes;
   }
+  // block-Thomas factors of the coarse operator, per mode (FP64), recomputed for these options
+  if (!h->coarse_f) KKT_TRY(dev_alloc(h, &h->coarse_f, 3 * static_cast<size_t>(g.n_sub) * g.N));
+  KKT_TRY(spectral_coarse_factor(h, false, h->coarse_f, nullptr));
+  if (mixed) {
+    KKT_TRY(dev_alloc(h, &h->coarse_f_pad, 3 * static_cast<size_t>(g.n_sub) * h->tc.P * h->tc.P));
+    KKT_TRY(spectral_coarse_factor(h, true, h->coarse_f_pad, nullptr));
+  } else if (h->coarse_f_pad) {
+    cudaFree(h->coarse_f_pad);
+    h->coarse_f_pad = nullptr;
+  }
+  KKT_CUDA_TRY(cudaDeviceSynchronize());
   // sweep storage: shared memory when a subdomain's nodes fit (32 threads x max_len doubles
   // within 200 KB), else a global scratch sized for every mode
   if (static_cast<size_t>(h->td.max_len) * 32 * sizeof(double) > 200 * 1024) {
@@ -379,6 +390,8 @@ void kkt_destroy(kkt_handle* h) {
   cudaFree(h->spec2);
   cudaFree(h->coarse_c);
   cudaFree(h->coarse_w);
+  cudaFree(h->coarse_f);
+  cudaFree(h->coarse_f_pad);
   cudaFree(h->vscratch);
   cudaFree(h->kV);
   cudaFree(h->kZw);

@@ -200,7 +200,9 @@ int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long
                              : nslices * L.tiles_per_slice;
   if (grid <= 0) return KKT_OK;
   if (grid > 2147483647LL) return set_error(KKT_ERR_UNSUPPORTED, "DST grid too large");
-  ProfScope ps(KKT_K_DST, st);
+  // one real DST-I of M points by FFT: 2.5 M log2(2n) flops; each point read and written once
+  const double lines = mode == 0 ? static_cast<double>(total_lines) : static_cast<double>(nslices) * cols;
+  ProfScope ps(KKT_K_DST, st, lines * 2.5 * L.M * std::log2(2.0 * p.n), lines * L.M * 16.0);
   dst_tile_kernel<<<static_cast<unsigned>(grid), kThreads, sm, st>>>(L);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;

@@ -107,7 +107,9 @@ struct kkt_handle {
   double* spec = nullptr;      // V doubles: spectral coefficients [n][l][k]
   double* spec2 = nullptr;     // V doubles
   double* coarse_c = nullptr;  // [n_sub][2][N] coarse coefficients
-  double* coarse_w = nullptr;  // [n_sub][5][N] block-Thomas factors
+  double* coarse_w = nullptr;  // [n_sub][2][modes] eliminated coarse right-hand sides
+  double* coarse_f = nullptr;  // [n_sub][3][N] block-Thomas factors D_s^{-1} (per configuration)
+  double* coarse_f_pad = nullptr;  // the same over the padded modes of the mixed forms
   double* vscratch = nullptr;  // sweep storage when a subdomain is too long for shared memory
   // Krylov workspace (allocated at the first solve)
   int kry_restart = 0;
@@ -125,13 +127,18 @@ struct kkt_handle {
 namespace kkt {
 
 // ---- instrumentation: counts every launch, times it with CUDA events when enabled -------
+// flops / bytes: the launch's algorithmic work (what the method must compute and move), summed
+// for the timed launches so that achieved rates can be read against a roofline.
 void prof_begin(int cls, cudaStream_t st);
-void prof_end(int cls, cudaStream_t st);
+void prof_end(int cls, cudaStream_t st, double flops, double bytes);
 struct ProfScope {
   int cls;
   cudaStream_t st;
-  ProfScope(int c, cudaStream_t s) : cls(c), st(s) { prof_begin(c, s); }
-  ~ProfScope() { prof_end(cls, st); }
+  double flops, bytes;
+  ProfScope(int c, cudaStream_t s, double f = 0.0, double b = 0.0) : cls(c), st(s), flops(f), bytes(b) {
+    prof_begin(c, s);
+  }
+  ~ProfScope() { prof_end(cls, st, flops, bytes); }
 };
 
 // ---- kernels launched from the C ABI (each defined in its own translation unit) ---------
@@ -153,6 +160,8 @@ int launch_jhat_time(const kkt_handle* h, const double* in, double* out, int dir
 int spectral_schur_precond(const kkt_handle* h, const double* rhat, double* yhat, double in_scale,
                            cudaStream_t st);
 int spectral_coarse_only(const kkt_handle* h, const double* rhat, double* xhat, cudaStream_t st);
+// per-mode block-Thomas factors of the coarse operator (depend on mu and the decomposition only)
+int spectral_coarse_factor(const kkt_handle* h, bool padded, double* cf, cudaStream_t st);
 // reduced-precision forms: FP32 spectral input (padded modes), output BF16 (bf16 != 0) or FP32
 int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, int bf16, cudaStream_t st);
 

@@ -131,7 +131,8 @@ int launch_matvec(const kkt_handle* h, const double* u, double su, const double*
   c.wz = ow * g.dt * sz;
   dim3 tb(32, 8);
   dim3 grid((g.Mx + 31) / 32, (g.My + 7) / 8, g.Nt);
-  ProfScope ps(KKT_K_MATVEC, st);
+  // 16 FP64 instructions (12 FMA) per point: 28 flops; 3 blocks in, 3 out
+  ProfScope ps(KKT_K_MATVEC, st, 28.0 * g.V, 48.0 * g.V);
   matvec_kernel<<<grid, tb, 0, st>>>(u, z, w, y, s, c);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;

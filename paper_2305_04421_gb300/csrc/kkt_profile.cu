@@ -11,6 +11,7 @@ namespace {
 struct Pending {
   cudaEvent_t a, b;
   int cls;
+  double flops, bytes;
 };
 
 std::mutex g_mu;
@@ -18,6 +19,8 @@ bool g_on = false;
 long long g_launches[KKT_K_COUNT] = {};
 double g_ms[KKT_K_COUNT] = {};
 long long g_timed[KKT_K_COUNT] = {};
+double g_flops[KKT_K_COUNT] = {};
+double g_bytes[KKT_K_COUNT] = {};
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_pool;
 thread_local cudaEvent_t t_open = nullptr;
@@ -40,6 +43,8 @@ void drain_locked() {
     if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
       g_ms[p.cls] += ms;
       g_timed[p.cls] += 1;
+      g_flops[p.cls] += p.flops;
+      g_bytes[p.cls] += p.bytes;
     }
     g_pool.push_back(p.a);
     g_pool.push_back(p.b);
@@ -57,12 +62,12 @@ void prof_begin(int cls, cudaStream_t st) {
   cudaEventRecord(t_open, st);
 }
 
-void prof_end(int cls, cudaStream_t st) {
+void prof_end(int cls, cudaStream_t st, double flops, double bytes) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on || !t_open) return;
   cudaEvent_t b = take_event();
   cudaEventRecord(b, st);
-  g_pending.push_back({t_open, b, cls});
+  g_pending.push_back({t_open, b, cls, flops, bytes});
   t_open = nullptr;
   if (g_pending.size() > 4096) drain_locked();
 }
@@ -85,10 +90,14 @@ int kkt_profile_read(kkt_kernel_stats* out, int reset) {
     out->launches[c] = kkt::g_launches[c];
     out->ms[c] = kkt::g_ms[c];
     out->timed[c] = kkt::g_timed[c];
+    out->flops[c] = kkt::g_flops[c];
+    out->bytes[c] = kkt::g_bytes[c];
     if (reset) {
       kkt::g_launches[c] = 0;
       kkt::g_ms[c] = 0.0;
       kkt::g_timed[c] = 0;
+      kkt::g_flops[c] = 0.0;
+      kkt::g_bytes[c] = 0.0;
     }
   }
   return KKT_OK;

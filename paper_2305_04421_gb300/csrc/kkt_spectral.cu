@@ -29,7 +29,7 @@ namespace {
 struct SpecParams {
   int Mx, Nt, n_sub;      // Mx: modes per spectral row (the padded size in the mixed forms)
   long long N;
-  double a, dtnu, h;
+  double a, dtnu, h, inv_h;
   const double* lx;
   const double* ly;
   const int* first;
@@ -39,6 +39,7 @@ struct SpecParams {
   const int* owner;
   const double* phi;
   const double* mom;
+  const double* cf;    // coarse factors [s][3][N]: D_s^{-1} of the block-Thomas elimination
   int two_level;       // apply the coarse correction
   int multiplicative;  // subtract S-hat x_0 before the local solves
 };
@@ -63,15 +64,50 @@ __device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16>(double v) {
   return __double2bfloat16(v);
 }
 
-template <typename TI>
-__global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale, SpecParams p,
-                                    double* __restrict__ cc, double* __restrict__ cw) {
+// Block-Thomas factorisation of the per-mode coarse operator h S_0 = Z_t^T T(mu) Z_t, which
+// depends on mu and the decomposition only: run once per configuration. Diagonal blocks
+// G_s = mu^2 P0 + P1 - mu P2; the coupling between s-1 and s is E = -mu a b^T with
+// a = (1, phi_last(s-1)), b = (1, phi_first(s)); D_s = G_s - E^T D_{s-1}^{-1} E.
+__global__ void coarse_factor_kernel(SpecParams p, double* __restrict__ cf) {
   const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= p.N) return;
   const long long N = p.N;
   const double mu = mode_mu(p, q), mu2 = mu * mu;
-  double d00 = 0, d01 = 0, d11 = 0, y0 = 0, y1 = 0;   // previous D^{-1} and eliminated rhs
-  double a1_prev = 0.0;                              // phi at the last owned node of s-1
+  double d00 = 0, d01 = 0, d11 = 0, a1_prev = 0.0;
+  for (int s = 0; s < p.n_sub; ++s) {
+    const double* M = p.mom + 9 * s;
+    double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
+    double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
+    double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
+    if (s > 0) {
+      const double b1 = __ldg(p.phi + __ldg(p.ofirst + s) - 1);
+      const double t0 = d00 + d01 * a1_prev, t1 = d01 + d11 * a1_prev;   // D^{-1} a
+      const double f = mu2 * (t0 + t1 * a1_prev);
+      g00 -= f;
+      g01 -= f * b1;
+      g11 -= f * b1 * b1;
+    }
+    const double id = 1.0 / (g00 * g11 - g01 * g01);
+    d00 = g11 * id;
+    d01 = -g01 * id;
+    d11 = g00 * id;
+    double* F = cf + static_cast<long long>(s) * 3 * N + q;
+    F[0] = d00;
+    F[N] = d01;
+    F[2 * N] = d11;
+    a1_prev = __ldg(p.phi + __ldg(p.olast + s) - 1);
+  }
+}
+
+// R_0 r and the block-Thomas substitutions with the precomputed factors; c' = h x.
+template <typename TI>
+__global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale, SpecParams p,
+                                    double* __restrict__ cc, double* __restrict__ cy) {
+  const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= p.N) return;
+  const long long N = p.N;
+  const double mu = mode_mu(p, q);
+  double y0 = 0, y1 = 0, t0 = 0, t1 = 0;   // eliminated rhs of s-1 and D_{s-1}^{-1} a_{s-1}
   for (int s = 0; s < p.n_sub; ++s) {
     double c0 = 0.0, c1 = 0.0;
     const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
@@ -81,65 +117,50 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
       c0 += r;
       c1 = fma(r, __ldg(p.phi + n - 1), c1);
     }
-    const double* M = p.mom + 9 * s;
-    double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
-    double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
-    double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
     if (s > 0) {
+      // y_s = c_s - E^T D^{-1} y_{s-1} = c_s + mu b (a^T D^{-1} y_{s-1})
       const double b1 = __ldg(p.phi + o1 - 1);
-      // E = -mu a b^T, a = (1, a1_prev), b = (1, b1): D -= E^T Dinv E, y = c - E^T Dinv y_prev
-      const double t0 = d00 + d01 * a1_prev, t1 = d01 + d11 * a1_prev;   // Dinv a
-      const double aDa = t0 + t1 * a1_prev;
       const double aDy = t0 * y0 + t1 * y1;
-      const double f = mu2 * aDa;
-      g00 -= f;
-      g01 -= f * b1;
-      g11 -= f * b1 * b1;
       c0 += mu * aDy;
       c1 += mu * b1 * aDy;
     }
-    const double det = g00 * g11 - g01 * g01;
-    const double id = 1.0 / det;
-    d00 = g11 * id;
-    d01 = -g01 * id;
-    d11 = g00 * id;
     y0 = c0;
     y1 = c1;
-    double* W = cw + static_cast<long long>(s) * 5 * N + q;
-    W[0] = d00;
-    W[N] = d01;
-    W[2 * N] = d11;
-    W[3 * N] = y0;
-    W[4 * N] = y1;
-    a1_prev = __ldg(p.phi + o2 - 1);
+    cy[(2LL * s) * N + q] = y0;
+    cy[(2LL * s + 1) * N + q] = y1;
+    const double* F = p.cf + static_cast<long long>(s) * 3 * N + q;
+    const double d00 = F[0], d01 = F[N], d11 = F[2 * N];
+    const double a1 = __ldg(p.phi + o2 - 1);
+    t0 = d00 + d01 * a1;
+    t1 = d01 + d11 * a1;
   }
-  // back substitution; c' = h * x (S_0 = G/h)
-  double x0 = d00 * y0 + d01 * y1, x1 = d01 * y0 + d11 * y1;
-  {
-    const int s = p.n_sub - 1;
-    cc[(2LL * s) * N + q] = p.h * x0;
-    cc[(2LL * s + 1) * N + q] = p.h * x1;
-  }
-  for (int s = p.n_sub - 2; s >= 0; --s) {
-    const double* W = cw + static_cast<long long>(s) * 5 * N + q;
-    const double e00 = W[0], e01 = W[N], e11 = W[2 * N], r0 = W[3 * N], r1 = W[4 * N];
-    const double a1 = __ldg(p.phi + __ldg(p.olast + s) - 1);
-    const double b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
-    const double bx = x0 + b1 * x1;                      // b^T x_{s+1}
-    const double z0 = r0 + mu * bx, z1 = r1 + mu * a1 * bx;   // y - E x_{s+1}
-    x0 = e00 * z0 + e01 * z1;
-    x1 = e01 * z0 + e11 * z1;
+  // back substitution: x_s = D_s^{-1} (y_s - E_s x_{s+1}) = D_s^{-1} (y_s + mu a_s (b_{s+1}^T x_{s+1}))
+  double x0 = 0, x1 = 0;
+  for (int s = p.n_sub - 1; s >= 0; --s) {
+    const double* F = p.cf + static_cast<long long>(s) * 3 * N + q;
+    const double d00 = F[0], d01 = F[N], d11 = F[2 * N];
+    double z0 = cy[(2LL * s) * N + q], z1 = cy[(2LL * s + 1) * N + q];
+    if (s + 1 < p.n_sub) {
+      const double a1 = __ldg(p.phi + __ldg(p.olast + s) - 1);
+      const double b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
+      const double bx = x0 + b1 * x1;
+      z0 += mu * bx;
+      z1 += mu * a1 * bx;
+    }
+    x0 = d00 * z0 + d01 * z1;
+    x1 = d01 * z0 + d11 * z1;
     cc[(2LL * s) * N + q] = p.h * x0;
     cc[(2LL * s + 1) * N + q] = p.h * x1;
   }
 }
 
 // x_0 at node n (1-based), given the coarse pairs of the three subdomains around s.
-__device__ __forceinline__ double coarse_value(const SpecParams& p, int n, int s, const double* c3) {
-  if (n < 1 || n > p.Nt) return 0.0;
+template <typename TC>
+__device__ __forceinline__ TC coarse_value(const SpecParams& p, int n, int s, const TC* c3) {
+  if (n < 1 || n > p.Nt) return TC(0);
   const int o = __ldg(p.owner + n - 1) - s + 1;        // 0, 1, 2 for s-1, s, s+1
-  if (o < 0 || o > 2) return 0.0;                       // cannot happen when every m_s >= 2
-  return c3[2 * o] + c3[2 * o + 1] * __ldg(p.phi + n - 1);
+  if (o < 0 || o > 2) return TC(0);                     // cannot happen when every m_s >= 2
+  return c3[2 * o] + c3[2 * o + 1] * static_cast<TC>(__ldg(p.phi + n - 1));
 }
 
 template <typename TI, typename TC, typename TO>
@@ -152,9 +173,10 @@ __global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* _
   const int s = blockIdx.y;
   if (q >= p.N) return;
   const long long N = p.N;
-  const double mu = mode_mu(p, q), mu2 = mu * mu;
-  const TC inv_mu = static_cast<TC>(1.0 / mu);
-  const TC hc = static_cast<TC>(p.h);
+  const double mud = mode_mu(p, q);
+  const TC mu = static_cast<TC>(mud), mu2 = mu * mu;
+  const TC inv_mu = static_cast<TC>(1.0 / mud);
+  const TC hc = static_cast<TC>(p.h), inv_h = static_cast<TC>(p.inv_h), scale = static_cast<TC>(in_scale);
   const int first = __ldg(p.first + s), last = __ldg(p.last + s);
   const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
   TC* vs;
@@ -166,35 +188,36 @@ __global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* _
     vs = vs_smem + threadIdx.x;
     vstride = blockDim.x;
   }
-  double c3[6] = {0, 0, 0, 0, 0, 0};
+  TC c3[6] = {0, 0, 0, 0, 0, 0};
   if (p.two_level) {
     for (int o = 0; o < 3; ++o) {
       const int so = s - 1 + o;
       if (so >= 0 && so < p.n_sub) {
-        c3[2 * o] = cc[(2LL * so) * N + q];
-        c3[2 * o + 1] = cc[(2LL * so + 1) * N + q];
+        c3[2 * o] = static_cast<TC>(cc[(2LL * so) * N + q]);
+        c3[2 * o + 1] = static_cast<TC>(cc[(2LL * so + 1) * N + q]);
       }
     }
   }
   // forward sweep over the subdomain's nodes
-  double xm = 0.0, xc = 0.0, xp = 0.0;   // x_0 at n-1, n, n+1
+  TC xm = 0, xc = 0, xp = 0;   // x_0 at n-1, n, n+1
   if (p.two_level) {
-    xm = coarse_value(p, first - 1, s, c3);
-    xc = coarse_value(p, first, s, c3);
+    xm = coarse_value<TC>(p, first - 1, s, c3);
+    xc = coarse_value<TC>(p, first, s, c3);
   }
   TC v = 0;
   for (int n = first; n <= last; ++n) {
-    double r = load_d(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
+    TC r = static_cast<TC>(__ldg(rhat + static_cast<long long>(n - 1) * N + q)) * scale;
     if (p.two_level) {
-      xp = coarse_value(p, n + 1, s, c3);
+      xp = coarse_value<TC>(p, n + 1, s, c3);
       if (p.multiplicative) {
-        const double tx = (n >= 2 ? mu2 + 1.0 : mu2) * xc - mu * (xm + xp);
-        r -= tx / p.h;
+        // r - (T x_0)_n / h, T_nn = mu^2 (+1 from n >= 2), T_{n,n+-1} = -mu
+        const TC tx = (n >= 2 ? mu2 + TC(1) : mu2) * xc - mu * (xm + xp);
+        r = fma(-tx, inv_h, r);
       }
       xm = xc;
       xc = xp;
     }
-    v = (static_cast<TC>(r) + v) * inv_mu;
+    v = (r + v) * inv_mu;
     vs[static_cast<long long>(n - first) * vstride] = v;
   }
   // backward sweep; keep owned nodes
@@ -202,9 +225,9 @@ __global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* _
   for (int n = last; n >= first; --n) {
     y = fma(hc, vs[static_cast<long long>(n - first) * vstride], y) * inv_mu;
     if (n >= o1 && n <= o2) {
-      double out = static_cast<double>(y);
-      if (p.two_level) out += coarse_value(p, n, s, c3);
-      yhat[static_cast<long long>(n - 1) * N + q] = store_cast<TO>(out);
+      TC out = y;
+      if (p.two_level) out += coarse_value<TC>(p, n, s, c3);
+      yhat[static_cast<long long>(n - 1) * N + q] = store_cast<TO>(static_cast<double>(out));
     }
   }
 }
@@ -228,6 +251,8 @@ SpecParams make_params(const kkt_handle* h, bool padded) {
   p.a = g.a;
   p.dtnu = g.dtnu;
   p.h = g.h;
+  p.inv_h = 1.0 / g.h;
+  p.cf = padded ? h->coarse_f_pad : h->coarse_f;
   p.lx = padded ? h->d_lx_pad : h->d_lx;
   p.ly = padded ? h->d_ly_pad : h->d_ly;
   p.first = h->dd.first;
@@ -246,7 +271,10 @@ template <typename TI>
 int launch_coarse(const kkt_handle* h, const SpecParams& p, const TI* rhat, double in_scale, cudaStream_t st) {
   const int tb = 128;
   const long long nb = (p.N + tb - 1) / tb;
-  ProfScope ps(KKT_K_COARSE, st);
+  // restriction: 2 flops per node; substitutions: ~26 flops per subdomain; reads the coefficients
+  // once, the factors twice, writes and reads the eliminated right-hand sides
+  const double V = static_cast<double>(p.N) * p.Nt;
+  ProfScope ps(KKT_K_COARSE, st, 2.0 * V + 26.0 * p.n_sub * p.N, V * sizeof(TI) + 12.0 * 8.0 * p.n_sub * p.N);
   coarse_solve_kernel<TI><<<static_cast<unsigned>(nb), tb, 0, st>>>(rhat, in_scale, p, h->coarse_c, h->coarse_w);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
@@ -279,7 +307,9 @@ int launch_sweeps(const kkt_handle* h, const SpecParams& p, const TI* rhat, doub
   auto kern = sweep_kernel<TI, TC, TO>;
   if (smem > 0)
     KKT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-  ProfScope ps(KKT_K_SWEEP, st);
+  // per mode and subdomain node: residual update (8 flops) + forward and backward steps (4)
+  const double visits = static_cast<double>(p.N) * (p.Nt + p.n_sub);
+  ProfScope ps(KKT_K_SWEEP, st, 12.0 * visits, visits * sizeof(TI) + static_cast<double>(p.N) * p.Nt * sizeof(TO));
   kern<<<grid, tb, smem, st>>>(rhat, in_scale, yhat, p, h->coarse_c, vglob, h->td.max_len);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
@@ -297,6 +327,15 @@ int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* y
   SpecParams p = make_params(h, true);
   if (bf16) return launch_sweeps<float, float, __nv_bfloat16>(h, p, rhat, 1.0, static_cast<__nv_bfloat16*>(yhat), st);
   return launch_sweeps<float, float, float>(h, p, rhat, 1.0, static_cast<float*>(yhat), st);
+}
+
+int spectral_coarse_factor(const kkt_handle* h, bool padded, double* cf, cudaStream_t st) {
+  SpecParams p = make_params(h, padded);
+  const int tb = 128;
+  const long long nb = (p.N + tb - 1) / tb;
+  coarse_factor_kernel<<<static_cast<unsigned>(nb), tb, 0, st>>>(p, cf);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
 }
 
 int spectral_coarse_only(const kkt_handle* h, const double* rhat, double* xhat, cudaStream_t st) {

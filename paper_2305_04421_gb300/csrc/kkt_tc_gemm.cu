@@ -313,7 +313,11 @@ int launch_gemm(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, c
   auto kern = tc_dst_gemm_kernel<TIn, TILE_N, OUT>;
   KKT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   const long long tiles = static_cast<long long>(p.slices) * (p.P / kTileM) * (p.P / TILE_N);
-  ProfScope ps(KKT_K_DST, st);
+  // dense GEMM with Q per slice: 2 P^3 flops; operand in, result out
+  const double planes = static_cast<double>(p.slices) * p.P * p.P;
+  const double out_b = OUT == kOutBF16 ? 2.0 * planes
+                       : (OUT == kOutF32 ? 4.0 * planes : 8.0 * static_cast<double>(p.slices) * p.valid * p.valid);
+  ProfScope ps(KKT_K_DST, st, 2.0 * planes * p.P, planes * sizeof(TIn) + out_b);
   kern<<<static_cast<unsigned>(tiles), 128, smem, st>>>(a, b, p);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
@@ -426,7 +430,7 @@ int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStre
   const long long total = static_cast<long long>(t.slices) * t.P * t.P;
   const int tb = 256;
   const long long nb = (total + tb - 1) / tb;
-  ProfScope ps(KKT_K_AXPY, st);
+  ProfScope ps(KKT_K_AXPY, st, 0.0, 8.0 * t.slices * static_cast<double>(valid) * valid + (t.bf16 ? 2.0 : 4.0) * total);
   if (t.bf16)
     pack_kernel<__nv_bfloat16><<<static_cast<unsigned>(nb), tb, 0, st>>>(in, scale, static_cast<__nv_bfloat16*>(t.x0), t.P, valid, total);
   else

@@ -59,7 +59,8 @@ KERNEL_CLASSES = ["dst", "coarse", "sweep", "matvec", "multidot", "update", "axp
 
 
 class KKTKernelStats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong * 8), ("ms", ctypes.c_double * 8), ("timed", ctypes.c_longlong * 8)]
+    _fields_ = [("launches", ctypes.c_longlong * 8), ("ms", ctypes.c_double * 8), ("timed", ctypes.c_longlong * 8),
+                ("flops", ctypes.c_double * 8), ("bytes", ctypes.c_double * 8)]
 
 
 class KKTError(RuntimeError):
@@ -221,8 +222,8 @@ def kkt_profile_read(reset: bool = False) -> dict:
     """Per kernel class: launches, timed launches and summed device milliseconds."""
     st = KKTKernelStats()
     _check(load_library().kkt_profile_read(ctypes.byref(st), 1 if reset else 0))
-    return {name: {"launches": st.launches[i], "timed": st.timed[i], "ms": st.ms[i]}
-            for i, name in enumerate(KERNEL_CLASSES)}
+    return {name: {"launches": st.launches[i], "timed": st.timed[i], "ms": st.ms[i], "flops": st.flops[i],
+                   "bytes": st.bytes[i]} for i, name in enumerate(KERNEL_CLASSES)}
 
 
 # ---- convenience object ---------------------------------------------------------------------
