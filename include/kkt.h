@@ -215,6 +215,69 @@ int kkt_multidot(kkt_handle* h, const double* V, long long stride, int count, co
 int kkt_multidot_noalloc(const double* V, long long stride, int count, const double* w, long long n,
                          double* out, void* stream);
 
+/* ---- learned coarse correction (not in the paper) ---------------------------------------
+ * A two-hidden-layer ReLU network maps a low sine mode's coarse right-hand side R_0 r
+ * (normalised, 2 n_sub values) and the mode's features (log dt nu lambda, log dt/sqrt(omega))
+ * to the direction of its coarse correction S_0^{-1} R_0 r; an exact one-dimensional Galerkin
+ * step with the mode's coarse operator sets the magnitude, and a residual guard
+ * (||c - S_0 x|| <= ||c|| / 2) falls back to the exact coarse solve. Trained on the GPU on
+ * coarse solves generated by the method (restriction of seeded residual time series, exact
+ * block-Thomas solve) with Adam on the squared error to the unit target. Weights BF16 for
+ * inference, FP32 accumulation; FP32 master weights for training. */
+typedef struct kkt_mlp kkt_mlp;
+
+typedef struct kkt_mlp_config {
+  int nx;        /* grid intervals of the training geometry (its sine spectrum gives lambda) */
+  int Nt;        /* time steps */
+  int n_sub;     /* subdomains; network input 2 n_sub + 2, output 2 n_sub */
+  int modes;     /* learned modes per direction: k, l < modes */
+  int width;     /* hidden width */
+  int seed;      /* initialisation and sampling seed */
+  int samples;   /* training samples (rounded up to whole (nu, omega) draws of modes^2) */
+  int epochs;
+  int batch;
+  double T;
+  double nu_lo, nu_hi;        /* nu log-uniform on [nu_lo, nu_hi] */
+  double omega_lo, omega_hi;  /* omega log-uniform on [omega_lo, omega_hi] */
+  double lr;                  /* Adam step (x 0.3 for the last third of the epochs) */
+} kkt_mlp_config;
+
+typedef struct kkt_mlp_train_stats {
+  int samples, steps;
+  double final_train_loss, val_loss, val_cosine;   /* val: held-out tenth, BF16 weights */
+} kkt_mlp_train_stats;
+
+int kkt_mlp_default_config(kkt_mlp_config* cfg);
+kkt_mlp* kkt_mlp_create(const kkt_mlp_config* cfg);   /* NULL on failure */
+void kkt_mlp_destroy(kkt_mlp* m);
+/* Parameters as one FP32 array: W1 [width][2 n_sub + 2], b1, W2 [width][width], b2,
+ * W3 [2 n_sub][width], b3 (host memory). */
+int kkt_mlp_param_count(const kkt_mlp* m, long long* count);
+int kkt_mlp_get_config(const kkt_mlp* m, kkt_mlp_config* cfg);
+int kkt_mlp_set_params(kkt_mlp* m, const float* host, long long count);
+int kkt_mlp_get_params(const kkt_mlp* m, float* host, long long count);
+/* Y = net(X) for a batch (device FP32, rows of 2 n_sub + 2 / 2 n_sub); use_bf16 selects the
+ * BF16 weights. */
+int kkt_mlp_forward(kkt_mlp* m, const float* X, float* Y, int batch, int use_bf16, void* stream);
+/* loss = 1/(2 batch) sum ||net(X) - T||^2 (FP32 weights); grad (device, parameter layout) may be
+ * NULL; *loss is written after synchronising `stream` when loss != NULL. */
+int kkt_mlp_loss_grad(kkt_mlp* m, const float* X, const float* T, int batch, float* grad, double* loss,
+                      void* stream);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on the batch. */
+int kkt_mlp_adam_step(kkt_mlp* m, const float* X, const float* T, int batch, double lr, double* loss,
+                      void* stream);
+/* Generate the training set on the GPU and train (synchronises). */
+int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream);
+int kkt_mlp_save(const kkt_mlp* m, const char* path);
+kkt_mlp* kkt_mlp_load(const char* path);
+/* Use the network for coarse = KKT_COARSE_LEARNED on this handle (the handle does not own it;
+ * keep it alive). mode 0: learned directions with the guard; mode 1: no coarse correction on the
+ * learned modes (ablation: what the network adds). Needs 2 n_sub of the handle = the network's
+ * output and modes <= min(nx, ny) - 1. */
+int kkt_attach_mlp(kkt_handle* h, kkt_mlp* m, int mode);
+/* Learned-mode coarse corrections kept and replaced by the exact solve since the last call. */
+int kkt_learned_stats(kkt_handle* h, long long* kept, long long* fallback, int reset);
+
 /* ---- instrumentation ------------------------------------------------------------------ */
 
 /* Kernel classes counted and timed by the library (process-wide, all handles). */

@@ -267,9 +267,9 @@ int schur_precond_w(kkt_handle* h, const double* rw, double scale, double* yw, c
   const TcPlan& t = h->tc;
   const int mid = t.bf16 ? 0 : 1;
   const int valid = h->g.nx - 1;
-  KKT_TRY(tc_pack(t, rw, scale, valid, st));
-  KKT_TRY(tc_gemm(t, 0, mid, t.x1, valid, st));        // along x: [n][j][i] -> [n][k][j]
-  KKT_TRY(tc_gemm(t, 1, 1, t.rhat, valid, st));        // along y: -> [n][l][k], FP32
+  KKT_TRY(tc_pack(t, rw, scale, valid, st));                   // hi + lo parts
+  KKT_TRY(tc_gemm(t, 0, 3, t.x1, valid, st, true, t.x1_lo));    // along x: [n][j][i] -> [n][k][j]
+  KKT_TRY(tc_gemm(t, 1, 1, t.rhat, valid, st, true));           // along y: -> [n][l][k], FP32
   KKT_TRY(spectral_schur_precond_mixed(h, t.rhat, t.yin, t.bf16, st));
   KKT_TRY(tc_gemm(t, 2, mid, t.x0, valid, st));        // back along x: [n][l][k] -> [n][i][l]
   KKT_TRY(tc_gemm(t, 0, 2, yw, valid, st));            // back along y: -> [n][j][i], FP64
@@ -383,6 +383,10 @@ void kkt_destroy(kkt_handle* h) {
   if (h->tc.q) tc_plan_destroy(h->tc);
   cudaFree(h->d_lx_pad);
   cudaFree(h->d_ly_pad);
+  cudaFree(h->learn_c);
+  cudaFree(h->learn_feat);
+  cudaFree(h->learn_x);
+  cudaFree(h->learn_count);
   if (h->dd.base) cudaFree(h->dd.base);
   cudaFree(h->d_lx);
   cudaFree(h->d_ly);
@@ -425,7 +429,8 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
     return set_error(KKT_ERR_INVALID_ARG, "pou=right needs Nt / n_sub >= 3");
   if (opt->precision != KKT_PREC_FP64 && h->g.nx != h->g.ny)
     return set_error(KKT_ERR_UNSUPPORTED, "the tensor-core transforms need a square grid (nx == ny)");
-  if (opt->coarse == KKT_COARSE_LEARNED) return set_error(KKT_ERR_UNSUPPORTED, "no learned coarse model attached");
+  if (opt->coarse == KKT_COARSE_LEARNED && !h->mlp)
+    return set_error(KKT_ERR_INVALID_ARG, "coarse = learned needs a network attached with kkt_attach_mlp");
   h->opt = *opt;
   return configure(h);
 }
@@ -510,8 +515,8 @@ int kkt_dst2d(kkt_handle* h, const double* in, double* out, void* stream) {
   const TcPlan& t = h->tc;
   const int valid = h->g.nx - 1;
   KKT_TRY(tc_pack(t, in, 1.0, valid, st));
-  KKT_TRY(tc_gemm(t, 0, t.bf16 ? 0 : 1, t.x1, valid, st));
-  return tc_gemm(t, 1, 2, out, valid, st);
+  KKT_TRY(tc_gemm(t, 0, 3, t.x1, valid, st, true, t.x1_lo));
+  return tc_gemm(t, 1, 2, out, valid, st, true);
 }
 
 int kkt_schur_apply(kkt_handle* h, const double* x, double* y, void* stream) {
@@ -536,6 +541,51 @@ int kkt_coarse_apply(kkt_handle* h, const double* r, double* x0, void* stream) {
   KKT_TRY(dst2d(h, r, h->spec, st));
   KKT_TRY(spectral_coarse_only(h, h->spec, h->spec2, st));
   return dst2d(h, h->spec2, x0, st);
+}
+
+int kkt_attach_mlp(kkt_handle* h, kkt_mlp* m, int mode) {
+  KKT_TRY(check_handle(h));
+  if (!m) return set_error(KKT_ERR_INVALID_ARG, "null network");
+  if (mode != 0 && mode != 1) return set_error(KKT_ERR_INVALID_ARG, "mode must be 0 (learned) or 1 (none)");
+  int d_in = 0, width = 0, d_out = 0;
+  KKT_TRY(mlp_dims(m, &d_in, &width, &d_out));
+  const Geometry& g = h->g;
+  if (d_out != 2 * g.n_sub) return set_error(KKT_ERR_INVALID_ARG, "network output width != 2 n_sub of this problem");
+  const int K = kkt::mlp_config(m).modes;
+  if (K < 1 || K > std::min(g.Mx, g.My)) return set_error(KKT_ERR_INVALID_ARG, "learned modes exceed the grid");
+  const size_t nl = static_cast<size_t>(K) * K;
+  KKT_TRY(dev_alloc(h, &h->learn_c, nl * d_out));
+  KKT_TRY(dev_alloc(h, &h->learn_feat, nl * 2));
+  KKT_TRY(dev_alloc(h, &h->learn_x, nl * d_in));
+  KKT_TRY(dev_alloc(h, &h->learn_count, 2));
+  KKT_CUDA_TRY(cudaMemset(h->learn_count, 0, 2 * sizeof(long long)));
+  // features of the learned modes: log(dt nu lambda_kl), log(a - 1) = log(dt / sqrt(omega))
+  const double pi = 3.14159265358979323846;
+  std::vector<double> feat(nl * 2);
+  for (int l = 0; l < K; ++l)
+    for (int k = 0; k < K; ++k) {
+      const double sx = std::sin((k + 1) * pi / (2.0 * g.nx)), sy = std::sin((l + 1) * pi / (2.0 * g.ny));
+      const double lam = 4.0 / (g.dx * g.dx) * sx * sx + 4.0 / (g.dy * g.dy) * sy * sy;
+      feat[2 * (l * K + k)] = std::log(g.dtnu * lam);
+      feat[2 * (l * K + k) + 1] = std::log(g.dt / std::sqrt(g.omega));
+    }
+  KKT_CUDA_TRY(cudaMemcpy(h->learn_feat, feat.data(), feat.size() * sizeof(double), cudaMemcpyHostToDevice));
+  h->mlp = m;
+  h->mlp_mode = mode;
+  h->learn_k = K;
+  return KKT_OK;
+}
+
+int kkt_learned_stats(kkt_handle* h, long long* kept, long long* fallback, int reset) {
+  KKT_TRY(check_handle(h));
+  long long c[2] = {0, 0};
+  if (h->learn_count) {
+    KKT_CUDA_TRY(cudaMemcpy(c, h->learn_count, sizeof(c), cudaMemcpyDeviceToHost));
+    if (reset) KKT_CUDA_TRY(cudaMemset(h->learn_count, 0, sizeof(c)));
+  }
+  if (kept) *kept = c[0];
+  if (fallback) *fallback = c[1];
+  return KKT_OK;
 }
 
 int kkt_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w, long long n,

@@ -70,13 +70,16 @@ struct DeviceDecomp {
 // and the slice stacks [Nt][P][P] the four transforms of an apply pass through.
 struct TcPlan {
   int n = 0, P = 0, slices = 0, bf16 = 1, tile_n = 256;
-  void* q = nullptr;       // Q, P x P, BF16 or FP32
-  void* x0 = nullptr;      // packed input / third transform output
-  void* x1 = nullptr;      // first transform output
+  void* q = nullptr;       // Q, P x P, BF16 or FP32 (hi part)
+  void* q_lo = nullptr;    // Q - Q_hi in the same type
+  void* x0 = nullptr;      // packed input (hi part) / third transform output
+  void* x0_lo = nullptr;   // lo part of the packed input
+  void* x1 = nullptr;      // first transform output (hi part)
+  void* x1_lo = nullptr;   // its lo part
   void* yin = nullptr;     // sweep output, input of the inverse transform
   float* rhat = nullptr;   // spectral coefficients [n][l][k], FP32
   int* err = nullptr;      // device flag: a pipeline wait timed out
-  CUtensorMap map_q, map_x0, map_x1, map_yin;
+  CUtensorMap map_q, map_q_lo, map_x0, map_x0_lo, map_x1, map_x1_lo, map_yin;
   size_t bytes = 0;
 };
 
@@ -103,6 +106,14 @@ struct kkt_handle {
   double* d_ly_pad = nullptr;
   kkt::TcPlan tc;              // reduced-precision transforms (allocated when such a precision is set)
   long long coarse_modes = 0;  // modes the coarse buffers are sized for
+  // learned coarse correction
+  kkt_mlp* mlp = nullptr;      // not owned
+  int mlp_mode = 0;            // 0 learned, 1 no coarse on the learned modes
+  int learn_k = 0;             // learned modes per direction
+  double* learn_c = nullptr;   // [learn_k^2][2 n_sub] restricted right-hand sides
+  double* learn_feat = nullptr;  // [learn_k^2][2]
+  float* learn_x = nullptr;    // [learn_k^2][2 n_sub + 2] network input
+  long long* learn_count = nullptr;  // device: kept, fallback
   // preconditioner workspace
   double* spec = nullptr;      // V doubles: spectral coefficients [n][l][k]
   double* spec2 = nullptr;     // V doubles
@@ -160,6 +171,14 @@ int launch_jhat_time(const kkt_handle* h, const double* in, double* out, int dir
 int spectral_schur_precond(const kkt_handle* h, const double* rhat, double* yhat, double in_scale,
                            cudaStream_t st);
 int spectral_coarse_only(const kkt_handle* h, const double* rhat, double* xhat, cudaStream_t st);
+// learned coarse correction: y (network output, [learn_k^2][2 n_sub] FP32) -> cc of the learned modes
+int spectral_learned_apply(const kkt_handle* h, bool padded, const float* y, cudaStream_t st);
+// network pieces used by the preconditioner (kkt_mlp.cu)
+int mlp_forward(kkt_mlp* m, const float* X, int B, int use_bf16, cudaStream_t st);
+const float* mlp_output(const kkt_mlp* m);
+int mlp_dims(const kkt_mlp* m, int* d_in, int* width, int* d_out);
+int mlp_make_input(const double* c, const double* feat, long long S, int nc, float* X, cudaStream_t st);
+const kkt_mlp_config& mlp_config(const kkt_mlp* m);
 // per-mode block-Thomas factors of the coarse operator (depend on mu and the decomposition only)
 int spectral_coarse_factor(const kkt_handle* h, bool padded, double* cf, cudaStream_t st);
 // reduced-precision forms: FP32 spectral input (padded modes), output BF16 (bf16 != 0) or FP32
@@ -169,8 +188,10 @@ int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* y
 int tc_padded_size(int n);
 int tc_plan_create(TcPlan& t, int n, int slices, int bf16);
 void tc_plan_destroy(TcPlan& t);
-// which_in: 0 = x0, 1 = x1, 2 = yin; out_mode: 0 BF16 / 1 FP32 padded slices, 2 FP64 valid x valid
-int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, cudaStream_t st);
+// which_in: 0 = x0, 1 = x1, 2 = yin; out_mode: 0 BF16 / 1 FP32 padded slices, 2 FP64 valid x
+// valid, 3 hi + lo pair (out, out_lo); split: the input and Q as hi + lo parts (3 products)
+int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, cudaStream_t st, bool split = false,
+            void* out_lo = nullptr);
 int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStream_t st);   // -> x0
 int tc_check(const TcPlan& t, cudaStream_t st);
 

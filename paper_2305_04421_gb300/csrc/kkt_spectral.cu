@@ -40,6 +40,8 @@ struct SpecParams {
   const double* phi;
   const double* mom;
   const double* cf;    // coarse factors [s][3][N]: D_s^{-1} of the block-Thomas elimination
+  int learn_k;         // modes k, l < learn_k also write their R_0 r to learn_c
+  double* learn_c;
   int two_level;       // apply the coarse correction
   int multiplicative;  // subtract S-hat x_0 before the local solves
 };
@@ -108,6 +110,11 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
   const long long N = p.N;
   const double mu = mode_mu(p, q);
   double y0 = 0, y1 = 0, t0 = 0, t1 = 0;   // eliminated rhs of s-1 and D_{s-1}^{-1} a_{s-1}
+  int learned = -1;                          // index among the learned modes, if any
+  if (p.learn_k > 0) {
+    const long long l = q / p.Mx, k = q - l * p.Mx;
+    if (k < p.learn_k && l < p.learn_k) learned = static_cast<int>(l * p.learn_k + k);
+  }
   for (int s = 0; s < p.n_sub; ++s) {
     double c0 = 0.0, c1 = 0.0;
     const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
@@ -116,6 +123,10 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
       const double r = load_d(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
       c0 += r;
       c1 = fma(r, __ldg(p.phi + n - 1), c1);
+    }
+    if (learned >= 0) {
+      p.learn_c[(learned * p.n_sub + s) * 2LL] = c0;
+      p.learn_c[(learned * p.n_sub + s) * 2LL + 1] = c1;
     }
     if (s > 0) {
       // y_s = c_s - E^T D^{-1} y_{s-1} = c_s + mu b (a^T D^{-1} y_{s-1})
@@ -152,6 +163,92 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
     cc[(2LL * s) * N + q] = p.h * x0;
     cc[(2LL * s + 1) * N + q] = p.h * x1;
   }
+}
+
+// Learned modes: d = network output (a direction), x = alpha d with the Galerkin
+// alpha = d^T c / d^T G d in the mode's coarse operator G = h S_0 (block tridiagonal, 2x2
+// blocks), kept when ||c - G x|| <= ||c|| / 2, else the exact c' already in cc stays. mode 1
+// zeroes the coarse correction of the learned modes instead.
+__global__ void learned_apply_kernel(SpecParams p, const float* __restrict__ y, int mode, double* __restrict__ cc,
+                                     long long* __restrict__ counts) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int K = p.learn_k;
+  if (i >= K * K) return;
+  const int k = i % K, l = i / K;
+  const long long q = static_cast<long long>(l) * p.Mx + k, N = p.N;
+  if (mode == 1) {
+    for (int s = 0; s < p.n_sub; ++s) {
+      cc[(2LL * s) * N + q] = 0.0;
+      cc[(2LL * s + 1) * N + q] = 0.0;
+    }
+    return;
+  }
+  const double mu = mode_mu(p, q), mu2 = mu * mu;
+  const float* d = y + static_cast<long long>(i) * 2 * p.n_sub;
+  const double* c = p.learn_c + static_cast<long long>(i) * 2 * p.n_sub;
+  // G d, d^T G d, d^T c, ||c||^2 in one pass over the subdomains
+  double dGd = 0, dc = 0, cc2 = 0;
+  for (int s = 0; s < p.n_sub; ++s) {
+    const double* M = p.mom + 9 * s;
+    const double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
+    const double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
+    const double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
+    const double d0 = d[2 * s], d1 = d[2 * s + 1];
+    double e0 = g00 * d0 + g01 * d1, e1 = g01 * d0 + g11 * d1;
+    if (s + 1 < p.n_sub) {   // E_s d_{s+1}, E_s = -mu a_s b_{s+1}^T
+      const double a1 = __ldg(p.phi + __ldg(p.olast + s) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
+      const double bd = d[2 * s + 2] + b1 * d[2 * s + 3];
+      e0 -= mu * bd;
+      e1 -= mu * a1 * bd;
+    }
+    if (s > 0) {             // E_{s-1}^T d_{s-1} = -mu b_s (a_{s-1}^T d_{s-1})
+      const double a1 = __ldg(p.phi + __ldg(p.olast + s - 1) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s) - 1);
+      const double ad = d[2 * s - 2] + a1 * d[2 * s - 1];
+      e0 -= mu * ad;
+      e1 -= mu * b1 * ad;
+    }
+    dGd += d0 * e0 + d1 * e1;
+    dc += d0 * c[2 * s] + d1 * c[2 * s + 1];
+    cc2 += c[2 * s] * c[2 * s] + c[2 * s + 1] * c[2 * s + 1];
+  }
+  if (!(dGd > 0.0)) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
+    return;
+  }
+  const double alpha = dc / dGd;
+  // residual ||c - alpha G d||^2 = ||c||^2 - 2 alpha d^T G c... computed directly
+  double res2 = 0;
+  for (int s = 0; s < p.n_sub; ++s) {
+    const double* M = p.mom + 9 * s;
+    const double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
+    const double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
+    const double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
+    const double d0 = d[2 * s], d1 = d[2 * s + 1];
+    double e0 = g00 * d0 + g01 * d1, e1 = g01 * d0 + g11 * d1;
+    if (s + 1 < p.n_sub) {
+      const double a1 = __ldg(p.phi + __ldg(p.olast + s) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
+      const double bd = d[2 * s + 2] + b1 * d[2 * s + 3];
+      e0 -= mu * bd;
+      e1 -= mu * a1 * bd;
+    }
+    if (s > 0) {
+      const double a1 = __ldg(p.phi + __ldg(p.olast + s - 1) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s) - 1);
+      const double ad = d[2 * s - 2] + a1 * d[2 * s - 1];
+      e0 -= mu * ad;
+      e1 -= mu * b1 * ad;
+    }
+    const double r0 = c[2 * s] - alpha * e0, r1 = c[2 * s + 1] - alpha * e1;
+    res2 += r0 * r0 + r1 * r1;
+  }
+  if (res2 > 0.25 * cc2) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
+    return;
+  }
+  for (int s = 0; s < p.n_sub; ++s) {
+    cc[(2LL * s) * N + q] = p.h * alpha * d[2 * s];
+    cc[(2LL * s + 1) * N + q] = p.h * alpha * d[2 * s + 1];
+  }
+  atomicAdd(reinterpret_cast<unsigned long long*>(counts), 1ull);
 }
 
 // x_0 at node n (1-based), given the coarse pairs of the three subdomains around s.
@@ -262,7 +359,9 @@ SpecParams make_params(const kkt_handle* h, bool padded) {
   p.owner = h->dd.owner;
   p.phi = h->dd.phi;
   p.mom = h->dd.moments;
-  p.two_level = h->opt.coarse == KKT_COARSE_EXACT;
+  p.two_level = h->opt.coarse != KKT_COARSE_NONE;
+  p.learn_k = (h->opt.coarse == KKT_COARSE_LEARNED && h->mlp) ? h->learn_k : 0;
+  p.learn_c = h->learn_c;
   p.multiplicative = h->opt.variant == KKT_MULTIPLICATIVE;
   return p;
 }
@@ -282,10 +381,17 @@ int launch_coarse(const kkt_handle* h, const SpecParams& p, const TI* rhat, doub
 
 template <typename TI, typename TC, typename TO>
 int launch_sweeps(const kkt_handle* h, const SpecParams& p, const TI* rhat, double in_scale, TO* yhat,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool padded) {
   if (static_cast<const void*>(rhat) == static_cast<const void*>(yhat))
     return set_error(KKT_ERR_INVALID_ARG, "spectral sweep needs distinct buffers");
   if (p.two_level) KKT_TRY(launch_coarse<TI>(h, p, rhat, in_scale, st));
+  if (p.learn_k > 0) {
+    // learned coarse directions for the lowest modes, then the Galerkin step and the guard
+    const long long nl = static_cast<long long>(p.learn_k) * p.learn_k;
+    KKT_TRY(mlp_make_input(h->learn_c, h->learn_feat, nl, 2 * p.n_sub, h->learn_x, st));
+    KKT_TRY(mlp_forward(h->mlp, h->learn_x, static_cast<int>(nl), 1, st));
+    KKT_TRY(spectral_learned_apply(h, padded, mlp_output(h->mlp), st));
+  }
   // sweep storage: shared memory when a subdomain's nodes fit, else the global scratch
   const size_t limit = 200 * 1024;
   int tb = 0;
@@ -320,13 +426,24 @@ int launch_sweeps(const kkt_handle* h, const SpecParams& p, const TI* rhat, doub
 int spectral_schur_precond(const kkt_handle* h, const double* rhat, double* yhat, double in_scale,
                            cudaStream_t st) {
   SpecParams p = make_params(h, false);
-  return launch_sweeps<double, double, double>(h, p, rhat, in_scale, yhat, st);
+  return launch_sweeps<double, double, double>(h, p, rhat, in_scale, yhat, st, false);
 }
 
 int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, int bf16, cudaStream_t st) {
   SpecParams p = make_params(h, true);
-  if (bf16) return launch_sweeps<float, float, __nv_bfloat16>(h, p, rhat, 1.0, static_cast<__nv_bfloat16*>(yhat), st);
-  return launch_sweeps<float, float, float>(h, p, rhat, 1.0, static_cast<float*>(yhat), st);
+  if (bf16)
+    return launch_sweeps<float, float, __nv_bfloat16>(h, p, rhat, 1.0, static_cast<__nv_bfloat16*>(yhat), st, true);
+  return launch_sweeps<float, float, float>(h, p, rhat, 1.0, static_cast<float*>(yhat), st, true);
+}
+
+int spectral_learned_apply(const kkt_handle* h, bool padded, const float* y, cudaStream_t st) {
+  SpecParams p = make_params(h, padded);
+  const int n = p.learn_k * p.learn_k;
+  if (n == 0) return KKT_OK;
+  ProfScope ps(KKT_K_COARSE, st, 40.0 * n * p.n_sub, 40.0 * n * p.n_sub);
+  learned_apply_kernel<<<(n + 127) / 128, 128, 0, st>>>(p, y, h->mlp_mode, h->coarse_c, h->learn_count);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
 }
 
 int spectral_coarse_factor(const kkt_handle* h, bool padded, double* cf, cudaStream_t st) {

@@ -9,6 +9,14 @@
 // so the next transform again contracts along the contiguous axis, and the stores of the
 // epilogue are coalesced (32 consecutive r per warp).
 //
+// Split operands (forward transforms): A = A_hi + A_lo and Q = Q_hi + Q_lo, each part in the
+// operand type, and the tile accumulates A_hi Q_hi + A_hi Q_lo + A_lo Q_hi in the same TMEM
+// accumulator (the lo x lo term, about 2^-16 (BF16) or 2^-22 (TF32) of the product, is
+// dropped). The forward transform's rounding error is spread evenly over all modes and the
+// sweeps then amplify the low modes by up to (mu_max / mu_min)^2, so the forward transforms
+// need this extra accuracy; the inverse transforms do not (their error is relative to their
+// own output) and use single operands.
+//
 // Per CTA: one 128 x TILE_N output tile. Warp 0 lane 0 streams A and B chunks of 128 bytes of
 // K through a 2-stage ring with TMA (128B swizzle) and mbarriers, warp 1 lane 0 issues
 // tcgen05.mma (M = 128, N = TILE_N, K = 16 for BF16 / 8 for TF32, FP32 accumulation in TMEM),
@@ -122,19 +130,54 @@ struct TcParams {
   int slices;
   int valid;          // output mode 2: rows/cols < valid are stored, into a valid x valid slice
   void* out;
+  void* out_lo;       // output mode 3: the lo part
   int* err;           // device error flag (set to 1 on a wait timeout)
 };
 
-enum OutMode { kOutBF16 = 0, kOutF32 = 1, kOutF64 = 2 };
+enum OutMode { kOutBF16 = 0, kOutF32 = 1, kOutF64 = 2, kOutSplit = 3 };
 
-template <typename TIn, int TILE_N, int OUT>
+// TF32 rounding of an FP32 value (10 explicit mantissa bits, ties away from zero)
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// hi + lo split of a value in the operand type
+template <typename TIn>
+struct Split;
+template <>
+struct Split<__nv_bfloat16> {
+  static __device__ __forceinline__ void make(float v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __float2bfloat16_rn(v);
+    lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+  }
+  static __device__ __forceinline__ void make_d(double v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+    hi = __double2bfloat16(v);
+    lo = __double2bfloat16(v - static_cast<double>(__bfloat162float(hi)));
+  }
+};
+template <>
+struct Split<float> {
+  static __device__ __forceinline__ void make(float v, float& hi, float& lo) {
+    hi = tf32_round(v);
+    lo = v - hi;
+  }
+  static __device__ __forceinline__ void make_d(double v, float& hi, float& lo) {
+    hi = tf32_round(static_cast<float>(v));
+    lo = static_cast<float>(v - static_cast<double>(hi));
+  }
+};
+
+template <typename TIn, int TILE_N, int OUT, bool SPLIT>
 __global__ void __launch_bounds__(128, 1)
-    tc_dst_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+    tc_dst_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                       const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo,
+                       TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int A_BYTES = kTileM * kChunkBytes;
   constexpr int B_BYTES = TILE_N * kChunkBytes;
-  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int PART = A_BYTES + B_BYTES;                 // one hi (or lo) pair of tiles
+  constexpr int STAGE = SPLIT ? 2 * PART : PART;
   constexpr int KCHUNK = kChunkBytes / static_cast<int>(sizeof(TIn));   // elements of K per chunk
   constexpr int UMMA_K = MmaKind<TIn>::kUmmaK;
   constexpr int K_STEPS = KCHUNK / UMMA_K;                               // 4 MMAs per chunk
@@ -185,6 +228,10 @@ __global__ void __launch_bounds__(128, 1)
       mbar_expect_tx(full + st, STAGE);
       tma_load_2d(sa, &tmA, c * KCHUNK, s * p.P + rt * kTileM, full + st);
       tma_load_2d(sa + A_BYTES, &tmB, c * KCHUNK, ct * TILE_N, full + st);
+      if (SPLIT) {
+        tma_load_2d(sa + PART, &tmAlo, c * KCHUNK, s * p.P + rt * kTileM, full + st);
+        tma_load_2d(sa + PART + A_BYTES, &tmBlo, c * KCHUNK, ct * TILE_N, full + st);
+      }
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
@@ -201,6 +248,14 @@ __global__ void __launch_bounds__(128, 1)
       for (int kk = 0; kk < K_STEPS; ++kk) {
         // advance 32 bytes of K inside the 128-byte swizzle row: +2 in the encoded address
         MmaKind<TIn>::mma(tmem, da + 2ull * kk, db + 2ull * kk, IDESC, (c | kk) != 0);
+      }
+      if (SPLIT) {
+        const uint64_t dal = smem_desc(sa + PART), dbl = smem_desc(sa + PART + A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < K_STEPS; ++kk) {
+          MmaKind<TIn>::mma(tmem, da + 2ull * kk, dbl + 2ull * kk, IDESC, 1u);    // A_hi Q_lo
+          MmaKind<TIn>::mma(tmem, dal + 2ull * kk, db + 2ull * kk, IDESC, 1u);    // A_lo Q_hi
+        }
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    ::"r"(smem_u32(empty + st)) : "memory");
@@ -241,6 +296,12 @@ __global__ void __launch_bounds__(128, 1)
         const float val = __uint_as_float(v[t]);
         if (OUT == kOutBF16) {
           reinterpret_cast<__nv_bfloat16*>(p.out)[(static_cast<long long>(s) * p.P + c) * p.P + r] = __float2bfloat16_rn(val);
+        } else if (OUT == kOutSplit) {
+          TIn hi, lo;
+          Split<TIn>::make(val, hi, lo);
+          const long long o = (static_cast<long long>(s) * p.P + c) * p.P + r;
+          reinterpret_cast<TIn*>(p.out)[o] = hi;
+          reinterpret_cast<TIn*>(p.out_lo)[o] = lo;
         } else if (OUT == kOutF32) {
           reinterpret_cast<float*>(p.out)[(static_cast<long long>(s) * p.P + c) * p.P + r] = val;
         } else {
@@ -255,10 +316,11 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE_N));
 }
 
-// out[s][j][i] (P x P, zero padded) = scale * in[s][j][i] (valid x valid), converted to TIn
+// out + out_lo (P x P per slice, zero padded) = scale * in[s][j][i] (valid x valid), split into
+// hi and lo parts of the operand type
 template <typename TIn>
-__global__ void pack_kernel(const double* __restrict__ in, double scale, TIn* __restrict__ out, int P, int valid,
-                            long long total) {
+__global__ void pack_kernel(const double* __restrict__ in, double scale, TIn* __restrict__ out,
+                            TIn* __restrict__ out_lo, int P, int valid, long long total) {
   const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= total) return;
   const int i = static_cast<int>(t % P);
@@ -267,10 +329,10 @@ __global__ void pack_kernel(const double* __restrict__ in, double scale, TIn* __
   const long long s = sj / P;
   double v = 0.0;
   if (i < valid && j < valid) v = scale * in[(s * valid + j) * valid + i];
-  if constexpr (sizeof(TIn) == 2)
-    out[t] = __double2bfloat16(v);
-  else
-    out[t] = static_cast<float>(v);
+  TIn hi, lo;
+  Split<TIn>::make_d(v, hi, lo);
+  out[t] = hi;
+  out_lo[t] = lo;
 }
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -306,19 +368,21 @@ int make_map(CUtensorMap* map, const void* base, int elem_bytes, long long rows,
   return KKT_OK;
 }
 
-template <typename TIn, int TILE_N, int OUT>
-int launch_gemm(const CUtensorMap& a, const CUtensorMap& b, const TcParams& p, cudaStream_t st) {
-  constexpr int STAGE = (kTileM + TILE_N) * kChunkBytes;
-  const size_t smem = 1024 + kStages * STAGE + 256;
-  auto kern = tc_dst_gemm_kernel<TIn, TILE_N, OUT>;
+template <typename TIn, int TILE_N, int OUT, bool SPLIT>
+int launch_gemm(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& alo, const CUtensorMap& blo,
+                const TcParams& p, cudaStream_t st) {
+  constexpr int PART = (kTileM + TILE_N) * kChunkBytes;
+  const size_t smem = 1024 + kStages * (SPLIT ? 2 * PART : PART) + 256;
+  auto kern = tc_dst_gemm_kernel<TIn, TILE_N, OUT, SPLIT>;
   KKT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   const long long tiles = static_cast<long long>(p.slices) * (p.P / kTileM) * (p.P / TILE_N);
-  // dense GEMM with Q per slice: 2 P^3 flops; operand in, result out
+  // dense GEMM with Q per slice: 2 P^3 flops (x3 for split operands); operands in, result out
   const double planes = static_cast<double>(p.slices) * p.P * p.P;
   const double out_b = OUT == kOutBF16 ? 2.0 * planes
-                       : (OUT == kOutF32 ? 4.0 * planes : 8.0 * static_cast<double>(p.slices) * p.valid * p.valid);
-  ProfScope ps(KKT_K_DST, st, 2.0 * planes * p.P, planes * sizeof(TIn) + out_b);
-  kern<<<static_cast<unsigned>(tiles), 128, smem, st>>>(a, b, p);
+                       : (OUT == kOutSplit ? 2.0 * sizeof(TIn) * planes
+                                           : (OUT == kOutF32 ? 4.0 * planes : 8.0 * static_cast<double>(p.slices) * p.valid * p.valid));
+  ProfScope ps(KKT_K_DST, st, (SPLIT ? 6.0 : 2.0) * planes * p.P, planes * sizeof(TIn) * (SPLIT ? 2 : 1) + out_b);
+  kern<<<static_cast<unsigned>(tiles), 128, smem, st>>>(a, b, alo, blo, p);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
@@ -345,6 +409,29 @@ uint16_t bf16_bits_rne(double v) {
 // Padded transform size used by the tensor-core path: n - 1 rounded up to a multiple of 128.
 int tc_padded_size(int n) { return ((n - 1 + 127) / 128) * 128; }
 
+// hi / lo parts of a double in the operand type, as raw bits
+void split_host(double v, int bf16, uint8_t* hi, uint8_t* lo) {
+  if (bf16) {
+    const uint16_t h = bf16_bits_rne(v);
+    uint32_t hb = static_cast<uint32_t>(h) << 16;
+    float hf;
+    std::memcpy(&hf, &hb, 4);
+    const uint16_t l = bf16_bits_rne(v - static_cast<double>(hf));
+    std::memcpy(hi, &h, 2);
+    std::memcpy(lo, &l, 2);
+  } else {
+    const float f = static_cast<float>(v);
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    b = (b + 0x1000u) & 0xFFFFE000u;
+    float hf;
+    std::memcpy(&hf, &b, 4);
+    const float lf = static_cast<float>(v - static_cast<double>(hf));
+    std::memcpy(hi, &hf, 4);
+    std::memcpy(lo, &lf, 4);
+  }
+}
+
 int tc_plan_create(TcPlan& t, int n, int slices, int bf16) {
   t = TcPlan();
   t.n = n;
@@ -361,67 +448,76 @@ int tc_plan_create(TcPlan& t, int n, int slices, int bf16) {
   const double pi = 3.14159265358979323846, sc = std::sqrt(2.0 / n);
   for (int j = 0; j < M; ++j)
     for (int k = 0; k < M; ++k) q[static_cast<size_t>(j) * P + k] = sc * std::sin(pi * (j + 1.0) * (k + 1.0) / n);
-  std::vector<uint8_t> qh(plane * eb);
-  for (size_t e = 0; e < plane; ++e) {
-    if (bf16) {
-      const uint16_t v = bf16_bits_rne(q[e]);
-      std::memcpy(qh.data() + 2 * e, &v, 2);
-    } else {
-      const float v = static_cast<float>(q[e]);
-      std::memcpy(qh.data() + 4 * e, &v, 4);
-    }
-  }
+  std::vector<uint8_t> qh(plane * eb), ql(plane * eb);
+  for (size_t e = 0; e < plane; ++e) split_host(q[e], bf16, qh.data() + eb * e, ql.data() + eb * e);
   KKT_CUDA_TRY(cudaMalloc(&t.q, plane * eb));
+  KKT_CUDA_TRY(cudaMalloc(&t.q_lo, plane * eb));
   KKT_CUDA_TRY(cudaMemcpy(t.q, qh.data(), plane * eb, cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(t.q_lo, ql.data(), plane * eb, cudaMemcpyHostToDevice));
   KKT_CUDA_TRY(cudaMalloc(&t.x0, elems * eb));
+  KKT_CUDA_TRY(cudaMalloc(&t.x0_lo, elems * eb));
   KKT_CUDA_TRY(cudaMalloc(&t.x1, elems * eb));
+  KKT_CUDA_TRY(cudaMalloc(&t.x1_lo, elems * eb));
   KKT_CUDA_TRY(cudaMalloc(&t.yin, elems * eb));
   KKT_CUDA_TRY(cudaMalloc(&t.rhat, elems * sizeof(float)));
   KKT_CUDA_TRY(cudaMalloc(&t.err, sizeof(int)));
   KKT_CUDA_TRY(cudaMemset(t.err, 0, sizeof(int)));
-  t.bytes = plane * eb + 3 * elems * eb + elems * sizeof(float) + sizeof(int);
+  t.bytes = 2 * plane * eb + 5 * elems * eb + elems * sizeof(float) + sizeof(int);
   const long long rows = static_cast<long long>(slices) * P;
   KKT_TRY(make_map(&t.map_q, t.q, eb, P, P, t.tile_n));
+  KKT_TRY(make_map(&t.map_q_lo, t.q_lo, eb, P, P, t.tile_n));
   KKT_TRY(make_map(&t.map_x0, t.x0, eb, rows, P, kTileM));
+  KKT_TRY(make_map(&t.map_x0_lo, t.x0_lo, eb, rows, P, kTileM));
   KKT_TRY(make_map(&t.map_x1, t.x1, eb, rows, P, kTileM));
+  KKT_TRY(make_map(&t.map_x1_lo, t.x1_lo, eb, rows, P, kTileM));
   KKT_TRY(make_map(&t.map_yin, t.yin, eb, rows, P, kTileM));
   return KKT_OK;
 }
 
 void tc_plan_destroy(TcPlan& t) {
   cudaFree(t.q);
+  cudaFree(t.q_lo);
   cudaFree(t.x0);
+  cudaFree(t.x0_lo);
   cudaFree(t.x1);
+  cudaFree(t.x1_lo);
   cudaFree(t.yin);
   cudaFree(t.rhat);
   cudaFree(t.err);
   t = TcPlan();
 }
 
-// One transform pass: out = per-slice transpose of (in-map rows) x Q.
-int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, cudaStream_t st) {
+// One transform pass: out = per-slice transpose of (in-map rows) x Q. split: use the lo parts of
+// the input (x0_lo / x1_lo) and of Q as well (forward transforms).
+int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, cudaStream_t st, bool split,
+            void* out_lo) {
   const CUtensorMap& a = which_in == 0 ? t.map_x0 : (which_in == 1 ? t.map_x1 : t.map_yin);
+  const CUtensorMap& alo = which_in == 0 ? t.map_x0_lo : t.map_x1_lo;
+  if (split && which_in == 2) return set_error(KKT_ERR_INVALID_ARG, "no lo part for the sweep output");
   TcParams p;
   p.P = t.P;
   p.slices = t.slices;
   p.valid = valid;
   p.out = out;
+  p.out_lo = out_lo;
   p.err = t.err;
-#define KKT_TC_CASE(TIN, TN, OM)                                         \
-  if (t.tile_n == TN && out_mode == OM) return launch_gemm<TIN, TN, OM>(a, t.map_q, p, st);
+#define KKT_TC_CASE(TIN, TN, OM, SP)                                                       \
+  if (t.tile_n == TN && out_mode == OM && split == SP)                                      \
+    return launch_gemm<TIN, TN, OM, SP>(a, t.map_q, alo, t.map_q_lo, p, st);
+#define KKT_TC_TYPE(TIN)                                                                   \
+  KKT_TC_CASE(TIN, 256, kOutF32, true) KKT_TC_CASE(TIN, 256, kOutSplit, true)              \
+  KKT_TC_CASE(TIN, 256, kOutF64, true) KKT_TC_CASE(TIN, 128, kOutF64, true)                 \
+  KKT_TC_CASE(TIN, 256, kOutBF16, false) KKT_TC_CASE(TIN, 256, kOutF32, false)             \
+  KKT_TC_CASE(TIN, 256, kOutF64, false)                                                     \
+  KKT_TC_CASE(TIN, 128, kOutF32, true) KKT_TC_CASE(TIN, 128, kOutSplit, true)              \
+  KKT_TC_CASE(TIN, 128, kOutBF16, false) KKT_TC_CASE(TIN, 128, kOutF32, false)             \
+  KKT_TC_CASE(TIN, 128, kOutF64, false)
   if (t.bf16) {
-    KKT_TC_CASE(__nv_bfloat16, 256, kOutBF16)
-    KKT_TC_CASE(__nv_bfloat16, 256, kOutF32)
-    KKT_TC_CASE(__nv_bfloat16, 256, kOutF64)
-    KKT_TC_CASE(__nv_bfloat16, 128, kOutBF16)
-    KKT_TC_CASE(__nv_bfloat16, 128, kOutF32)
-    KKT_TC_CASE(__nv_bfloat16, 128, kOutF64)
+    KKT_TC_TYPE(__nv_bfloat16)
   } else {
-    KKT_TC_CASE(float, 256, kOutF32)
-    KKT_TC_CASE(float, 256, kOutF64)
-    KKT_TC_CASE(float, 128, kOutF32)
-    KKT_TC_CASE(float, 128, kOutF64)
+    KKT_TC_TYPE(float)
   }
+#undef KKT_TC_TYPE
 #undef KKT_TC_CASE
   return set_error(KKT_ERR_UNSUPPORTED, "tensor-core transform: unsupported output mode");
 }
@@ -430,11 +526,13 @@ int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStre
   const long long total = static_cast<long long>(t.slices) * t.P * t.P;
   const int tb = 256;
   const long long nb = (total + tb - 1) / tb;
-  ProfScope ps(KKT_K_AXPY, st, 0.0, 8.0 * t.slices * static_cast<double>(valid) * valid + (t.bf16 ? 2.0 : 4.0) * total);
+  ProfScope ps(KKT_K_AXPY, st, 0.0, 8.0 * t.slices * static_cast<double>(valid) * valid + 2.0 * (t.bf16 ? 2.0 : 4.0) * total);
   if (t.bf16)
-    pack_kernel<__nv_bfloat16><<<static_cast<unsigned>(nb), tb, 0, st>>>(in, scale, static_cast<__nv_bfloat16*>(t.x0), t.P, valid, total);
+    pack_kernel<__nv_bfloat16><<<static_cast<unsigned>(nb), tb, 0, st>>>(
+        in, scale, static_cast<__nv_bfloat16*>(t.x0), static_cast<__nv_bfloat16*>(t.x0_lo), t.P, valid, total);
   else
-    pack_kernel<float><<<static_cast<unsigned>(nb), tb, 0, st>>>(in, scale, static_cast<float*>(t.x0), t.P, valid, total);
+    pack_kernel<float><<<static_cast<unsigned>(nb), tb, 0, st>>>(in, scale, static_cast<float*>(t.x0),
+                                                                 static_cast<float*>(t.x0_lo), t.P, valid, total);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }

@@ -63,6 +63,18 @@ class KKTKernelStats(ctypes.Structure):
                 ("flops", ctypes.c_double * 8), ("bytes", ctypes.c_double * 8)]
 
 
+class KKTMlpConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("Nt", ctypes.c_int), ("n_sub", ctypes.c_int), ("modes", ctypes.c_int),
+                ("width", ctypes.c_int), ("seed", ctypes.c_int), ("samples", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("batch", ctypes.c_int), ("T", ctypes.c_double), ("nu_lo", ctypes.c_double), ("nu_hi", ctypes.c_double),
+                ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double), ("lr", ctypes.c_double)]
+
+
+class KKTMlpTrainStats(ctypes.Structure):
+    _fields_ = [("samples", ctypes.c_int), ("steps", ctypes.c_int), ("final_train_loss", ctypes.c_double),
+                ("val_loss", ctypes.c_double), ("val_cosine", ctypes.c_double)]
+
+
 class KKTError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"kkt status {status}: {message}")
@@ -93,6 +105,21 @@ SIGNATURES = [
     ("kkt_coarse_apply", _I, [_P, _P, _P, _P]),
     ("kkt_multidot", _I, [_P, _P, ctypes.c_longlong, _I, _P, ctypes.c_longlong, _P, _P]),
     ("kkt_multidot_noalloc", _I, [_P, ctypes.c_longlong, _I, _P, ctypes.c_longlong, _P, _P]),
+    ("kkt_mlp_default_config", _I, [ctypes.POINTER(KKTMlpConfig)]),
+    ("kkt_mlp_create", _P, [ctypes.POINTER(KKTMlpConfig)]),
+    ("kkt_mlp_destroy", None, [_P]),
+    ("kkt_mlp_param_count", _I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
+    ("kkt_mlp_get_config", _I, [_P, ctypes.POINTER(KKTMlpConfig)]),
+    ("kkt_mlp_set_params", _I, [_P, _P, ctypes.c_longlong]),
+    ("kkt_mlp_get_params", _I, [_P, _P, ctypes.c_longlong]),
+    ("kkt_mlp_forward", _I, [_P, _P, _P, _I, _I, _P]),
+    ("kkt_mlp_loss_grad", _I, [_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    ("kkt_mlp_adam_step", _I, [_P, _P, _P, _I, _D, ctypes.POINTER(ctypes.c_double), _P]),
+    ("kkt_mlp_train", _I, [_P, ctypes.POINTER(KKTMlpTrainStats), _P]),
+    ("kkt_mlp_save", _I, [_P, ctypes.c_char_p]),
+    ("kkt_mlp_load", _P, [ctypes.c_char_p]),
+    ("kkt_attach_mlp", _I, [_P, _P, _I]),
+    ("kkt_learned_stats", _I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _I]),
     ("kkt_profile_enable", _I, [_I]),
     ("kkt_profile_read", _I, [ctypes.POINTER(KKTKernelStats), _I]),
 ]
@@ -226,6 +253,101 @@ def kkt_profile_read(reset: bool = False) -> dict:
                    "bytes": st.bytes[i]} for i, name in enumerate(KERNEL_CLASSES)}
 
 
+def _fptr(t):
+    if t is None:
+        return None
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError("network tensors must be contiguous float32")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def kkt_mlp_default_config() -> KKTMlpConfig:
+    c = KKTMlpConfig()
+    _check(load_library().kkt_mlp_default_config(ctypes.byref(c)))
+    return c
+
+
+class Mlp:
+    """The learned coarse correction's network (owns a kkt_mlp)."""
+
+    def __init__(self, cfg: KKTMlpConfig | None = None, *, handle=None, **overrides):
+        lib = load_library()
+        if handle is not None:
+            self.m = handle
+        else:
+            c = cfg if cfg is not None else kkt_mlp_default_config()
+            for k, v in overrides.items():
+                setattr(c, k, v)
+            self.m = lib.kkt_mlp_create(ctypes.byref(c))
+            if not self.m:
+                raise KKTError(KKT_ERR_INVALID_ARG, lib.kkt_last_error().decode())
+        self.cfg = KKTMlpConfig()
+        _check(lib.kkt_mlp_get_config(self.m, ctypes.byref(self.cfg)))
+        n = ctypes.c_longlong()
+        _check(lib.kkt_mlp_param_count(self.m, ctypes.byref(n)))
+        self.nparam = n.value
+
+    @classmethod
+    def load(cls, path: str) -> "Mlp":
+        lib = load_library()
+        m = lib.kkt_mlp_load(path.encode())
+        if not m:
+            raise KKTError(KKT_ERR_INVALID_ARG, lib.kkt_last_error().decode())
+        return cls(handle=m)
+
+    def save(self, path: str) -> None:
+        _check(load_library().kkt_mlp_save(self.m, path.encode()))
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(load_library().kkt_mlp_get_params(self.m, out.ctypes.data_as(ctypes.c_void_p), self.nparam))
+        return out
+
+    def set_params(self, arr) -> None:
+        import numpy as np
+        a = np.ascontiguousarray(arr, dtype=np.float32)
+        _check(load_library().kkt_mlp_set_params(self.m, a.ctypes.data_as(ctypes.c_void_p), a.size))
+
+    def forward(self, X, use_bf16=False, stream=None):
+        B = X.shape[0]
+        Y = torch.empty((B, self._d_out()), dtype=torch.float32, device=X.device)
+        _check(load_library().kkt_mlp_forward(self.m, _fptr(X), _fptr(Y), B, 1 if use_bf16 else 0, _stream(stream)))
+        return Y
+
+    def loss_grad(self, X, T, stream=None):
+        g = torch.empty(self.nparam, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_double()
+        _check(load_library().kkt_mlp_loss_grad(self.m, _fptr(X), _fptr(T), X.shape[0], _fptr(g), ctypes.byref(loss),
+                                                _stream(stream)))
+        return loss.value, g
+
+    def adam_step(self, X, T, lr, stream=None):
+        loss = ctypes.c_double()
+        _check(load_library().kkt_mlp_adam_step(self.m, _fptr(X), _fptr(T), X.shape[0], lr, ctypes.byref(loss),
+                                                _stream(stream)))
+        return loss.value
+
+    def train(self, stream=None) -> KKTMlpTrainStats:
+        st = KKTMlpTrainStats()
+        _check(load_library().kkt_mlp_train(self.m, ctypes.byref(st), _stream(stream)))
+        return st
+
+    def _d_out(self):
+        return 2 * self.cfg.n_sub
+
+    def close(self):
+        if getattr(self, "m", None):
+            load_library().kkt_mlp_destroy(self.m)
+            self.m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---- convenience object ---------------------------------------------------------------------
 
 @dataclass
@@ -310,6 +432,17 @@ class Solver:
         y = out if out is not None else self._out(r, self.V)
         kkt_coarse_apply(self.h, r, y, stream)
         return y
+
+    def attach_mlp(self, mlp: "Mlp", mode: str = "learned"):
+        """Use `mlp` for coarse='learned' (mode 'learned'), or no coarse correction on the learned
+        modes (mode 'none', the ablation); then switch the options to coarse='learned'."""
+        _check(load_library().kkt_attach_mlp(self.h, mlp.m, 0 if mode == "learned" else 1))
+        self._mlp = mlp
+
+    def learned_stats(self, reset=False):
+        kept, fb = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(load_library().kkt_learned_stats(self.h, ctypes.byref(kept), ctypes.byref(fb), 1 if reset else 0))
+        return kept.value, fb.value
 
     def solve(self, f, x=None, tol=1e-8, maxit=420, stream=None) -> SolveResult:
         if x is None:

@@ -413,3 +413,52 @@ def test_weighted_residual_norm_reaches_the_exact_solution():
                         tol=1e-12, restart=30, maxit=200, row_scale=d)
     assert res.converged
     assert np.linalg.norm(res.x - xe) <= 1e-10 * np.linalg.norm(xe)
+
+
+# ---------------------------------------------------------------------------------------
+# Learned coarse correction: the network reference (not in the paper)
+# ---------------------------------------------------------------------------------------
+
+def test_mlp_backward_matches_central_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(0)
+    params = mlp.init_params(6, 5, 4, seed=1)
+    for k in ("b1", "b2", "b3"):
+        params[k] = 0.1 * rng.standard_normal(params[k].shape)   # avoid kinks at zero
+    X = rng.standard_normal((7, 6))
+    T = rng.standard_normal((7, 4))
+    Y, cache = mlp.forward(params, X)
+    g = mlp.backward(params, cache, Y, T)
+    for k, P in params.items():
+        fd = np.zeros_like(P)
+        for idx in np.ndindex(P.shape):
+            old = P[idx]
+            P[idx] = old + 1e-6
+            lp = mlp.loss(mlp.forward(params, X)[0], T)
+            P[idx] = old - 1e-6
+            lm = mlp.loss(mlp.forward(params, X)[0], T)
+            P[idx] = old
+            fd[idx] = (lp - lm) / 2e-6
+        np.testing.assert_allclose(g[k], fd, rtol=1e-6, atol=1e-8)
+
+
+def test_adam_first_step_moves_each_parameter_by_lr():
+    """With zero moments, the bias-corrected first Adam step is lr * g / (|g| + eps)."""
+    from oracle import mlp
+    params = {"w": np.array([1.0, -2.0, 3.0])}
+    grads = {"w": np.array([0.5, -4.0, 1e-3])}
+    state = {}
+    mlp.adam_step(params, grads, state, t=1, lr=0.01)
+    g = np.array([0.5, -4.0, 1e-3])
+    np.testing.assert_allclose(params["w"], np.array([1.0, -2.0, 3.0]) - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_coarse_operator_inverse_reproduces_the_per_mode_coarse_solve():
+    """The network's target, (h S_0(mu))^{-1} c, equals the coarse correction of the scalar oracle."""
+    from oracle import mlp
+    mu, Nt, nd = 1.7, 24, 4
+    G = mlp.coarse_operator(mu, Nt, nd)
+    pre = schwarz.SchurPreconditioner(np.array([[mu]]), Nt, nd, 1.0)
+    r = workloads.random_vector(Nt, 5)
+    c = pre.Z.T @ r
+    np.testing.assert_allclose(pre.Z @ np.linalg.solve(G, c), pre.coarse(r), rtol=1e-12, atol=1e-12)
