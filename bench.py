@@ -302,8 +302,10 @@ def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
     out = {"workload": f"nx=ny={w.nx} Nt={w.Nt} N_D={w.n_sub} nu={w.nu} omega={w.omega:g}, sine-series target"}
     ref_x = None
-    for prec in ("fp64", "bf16", "tf32"):
-        s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=prec)
+    for form in ("fp64", "bf16", "tf32", "bf16_single", "tf32_single"):
+        prec = form.split("_")[0]
+        s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=prec,
+                           tc_split=not form.endswith("_single"))
         f = s.build_rhs(ut)
         ms, res, x = time_solves(kkt_mod, s, f, steps, warmup)
         kkt_mod.kkt_profile_read(reset=True)
@@ -320,11 +322,13 @@ def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
             ref_x = x.clone()
         else:
             entry["solution_rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(x - ref_x) / torch.linalg.vector_norm(ref_x))
-        out[prec] = entry
+            entry["transform_operands"] = "single BF16/TF32" if form.endswith("_single") else "hi + lo split (3 products)"
+        out[form] = entry
         del f, x
         s.close()
         torch.cuda.empty_cache()
-    out["speedup_vs_fp64"] = {p: out["fp64"]["solve_ms"] / out[p]["solve_ms"] for p in ("bf16", "tf32")}
+    out["speedup_vs_fp64"] = {p: out["fp64"]["solve_ms"] / out[p]["solve_ms"]
+                              for p in ("bf16", "tf32", "bf16_single", "tf32_single")}
     return out
 
 

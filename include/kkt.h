@@ -89,6 +89,8 @@ typedef struct kkt_options {
   int restart;      /* FGMRES restart length, 1..32, default 30 */
   int jhat_sign;    /* -1 (default): Jhat = J - omega^-1/2 L; +1: the sign printed in Eq 7 */
   int residual_norm;  /* enum kkt_residual_norm, default KKT_NORM_L2 */
+  int tc_split;     /* BF16 / TF32 only: 1 (default) every tensor-core transform uses hi + lo operands
+                       (three products, FP32 accumulation); 0 single operands */
   double Lx, Ly;    /* domain (0,Lx) x (0,Ly), default 1, 1 */
 } kkt_options;
 

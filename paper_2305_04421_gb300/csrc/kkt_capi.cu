@@ -265,14 +265,15 @@ int schur_precond_w(kkt_handle* h, const double* rw, double scale, double* yw, c
     return KKT_OK;
   }
   const TcPlan& t = h->tc;
-  const int mid = t.bf16 ? 0 : 1;
+  const bool sp = h->opt.tc_split != 0;
+  const int mid = sp ? 3 : (t.bf16 ? 0 : 1);
   const int valid = h->g.nx - 1;
-  KKT_TRY(tc_pack(t, rw, scale, valid, st));                   // hi + lo parts
-  KKT_TRY(tc_gemm(t, 0, 3, t.x1, valid, st, true, t.x1_lo));    // along x: [n][j][i] -> [n][k][j]
-  KKT_TRY(tc_gemm(t, 1, 1, t.rhat, valid, st, true));           // along y: -> [n][l][k], FP32
-  KKT_TRY(spectral_schur_precond_mixed(h, t.rhat, t.yin, t.bf16, st));
-  KKT_TRY(tc_gemm(t, 2, mid, t.x0, valid, st));        // back along x: [n][l][k] -> [n][i][l]
-  KKT_TRY(tc_gemm(t, 0, 2, yw, valid, st));            // back along y: -> [n][j][i], FP64
+  KKT_TRY(tc_pack(t, rw, scale, valid, st));                       // hi (+ lo) parts
+  KKT_TRY(tc_gemm(t, 0, mid, t.x1, valid, st, sp, t.x1_lo));        // along x: [n][j][i] -> [n][k][j]
+  KKT_TRY(tc_gemm(t, 1, 1, t.rhat, valid, st, sp));                 // along y: -> [n][l][k], FP32
+  KKT_TRY(spectral_schur_precond_mixed(h, t.rhat, t.yin, sp ? t.yin_lo : nullptr, t.bf16, st));
+  KKT_TRY(tc_gemm(t, 2, mid, t.x0, valid, st, sp, t.x0_lo));        // back along x: [n][l][k] -> [n][i][l]
+  KKT_TRY(tc_gemm(t, 0, 2, yw, valid, st, sp));                     // back along y: -> [n][j][i], FP64
   return KKT_OK;
 }
 
@@ -323,6 +324,7 @@ int kkt_default_options(kkt_options* opt) {
   opt->restart = 30;
   opt->jhat_sign = -1;
   opt->residual_norm = KKT_NORM_L2;
+  opt->tc_split = 1;
   opt->Lx = 1.0;
   opt->Ly = 1.0;
   return KKT_OK;
@@ -422,6 +424,7 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
   if (opt->jhat_sign != -1 && opt->jhat_sign != 1) return set_error(KKT_ERR_INVALID_ARG, "jhat_sign must be -1 or +1");
   if (opt->residual_norm != KKT_NORM_L2 && opt->residual_norm != KKT_NORM_EUCLIDEAN)
     return set_error(KKT_ERR_INVALID_ARG, "residual_norm out of range");
+  if (opt->tc_split != 0 && opt->tc_split != 1) return set_error(KKT_ERR_INVALID_ARG, "tc_split must be 0 or 1");
   if (!finite_pos(opt->Lx) || !finite_pos(opt->Ly)) return set_error(KKT_ERR_INVALID_ARG, "Lx, Ly must be positive");
   // with the shared node given to the later subdomain, the first subdomain owns nodes
   // 1 .. b_1 - 1; its linear coarse function needs two of them
@@ -514,9 +517,10 @@ int kkt_dst2d(kkt_handle* h, const double* in, double* out, void* stream) {
   // reduced precision: the tensor-core transforms (operands rounded to BF16 / TF32, FP32 sums)
   const TcPlan& t = h->tc;
   const int valid = h->g.nx - 1;
+  const bool sp = h->opt.tc_split != 0;
   KKT_TRY(tc_pack(t, in, 1.0, valid, st));
-  KKT_TRY(tc_gemm(t, 0, 3, t.x1, valid, st, true, t.x1_lo));
-  return tc_gemm(t, 1, 2, out, valid, st, true);
+  KKT_TRY(tc_gemm(t, 0, sp ? 3 : (t.bf16 ? 0 : 1), t.x1, valid, st, sp, t.x1_lo));
+  return tc_gemm(t, 1, 2, out, valid, st, sp);
 }
 
 int kkt_schur_apply(kkt_handle* h, const double* x, double* y, void* stream) {

@@ -76,10 +76,11 @@ struct TcPlan {
   void* x0_lo = nullptr;   // lo part of the packed input
   void* x1 = nullptr;      // first transform output (hi part)
   void* x1_lo = nullptr;   // its lo part
-  void* yin = nullptr;     // sweep output, input of the inverse transform
+  void* yin = nullptr;     // sweep output, input of the inverse transform (hi part)
+  void* yin_lo = nullptr;  // its lo part
   float* rhat = nullptr;   // spectral coefficients [n][l][k], FP32
   int* err = nullptr;      // device flag: a pipeline wait timed out
-  CUtensorMap map_q, map_q_lo, map_x0, map_x0_lo, map_x1, map_x1_lo, map_yin;
+  CUtensorMap map_q, map_q_lo, map_x0, map_x0_lo, map_x1, map_x1_lo, map_yin, map_yin_lo;
   size_t bytes = 0;
 };
 
@@ -182,7 +183,9 @@ const kkt_mlp_config& mlp_config(const kkt_mlp* m);
 // per-mode block-Thomas factors of the coarse operator (depend on mu and the decomposition only)
 int spectral_coarse_factor(const kkt_handle* h, bool padded, double* cf, cudaStream_t st);
 // reduced-precision forms: FP32 spectral input (padded modes), output BF16 (bf16 != 0) or FP32
-int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, int bf16, cudaStream_t st);
+// (yhat_lo non-null: also the lo part, yhat + yhat_lo = the FP32 result)
+int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, void* yhat_lo, int bf16,
+                                 cudaStream_t st);
 
 // tensor-core transforms (kkt_tc_gemm.cu)
 int tc_padded_size(int n);

@@ -66,6 +66,28 @@ __device__ __forceinline__ __nv_bfloat16 store_cast<__nv_bfloat16>(double v) {
   return __double2bfloat16(v);
 }
 
+// hi + lo parts in the output type (for the split inverse transforms): hi = rounded value,
+// lo = rounded remainder; TF32 operands read FP32 words, so hi is rounded to 10 mantissa bits
+template <typename TO>
+__device__ __forceinline__ void store_split(TO* hi, TO* lo, long long i, float v);
+template <>
+__device__ __forceinline__ void store_split<__nv_bfloat16>(__nv_bfloat16* hi, __nv_bfloat16* lo, long long i, float v) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  hi[i] = h;
+  lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+template <>
+__device__ __forceinline__ void store_split<float>(float* hi, float* lo, long long i, float v) {
+  const float h = __uint_as_float((__float_as_uint(v) + 0x1000u) & 0xFFFFE000u);
+  hi[i] = h;
+  lo[i] = v - h;
+}
+template <>
+__device__ __forceinline__ void store_split<double>(double* hi, double* lo, long long i, float v) {
+  hi[i] = v;
+  lo[i] = 0.0;
+}
+
 // Block-Thomas factorisation of the per-mode coarse operator h S_0 = Z_t^T T(mu) Z_t, which
 // depends on mu and the decomposition only: run once per configuration. Diagonal blocks
 // G_s = mu^2 P0 + P1 - mu P2; the coupling between s-1 and s is E = -mu a b^T with
@@ -262,8 +284,8 @@ __device__ __forceinline__ TC coarse_value(const SpecParams& p, int n, int s, co
 
 template <typename TI, typename TC, typename TO>
 __global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* __restrict__ yhat,
-                             SpecParams p, const double* __restrict__ cc, TC* __restrict__ vglobal,
-                             int max_len) {
+                             TO* __restrict__ yhat_lo, SpecParams p, const double* __restrict__ cc,
+                             TC* __restrict__ vglobal, int max_len) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
   TC* vs_smem = reinterpret_cast<TC*>(vs_raw);
   const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -324,7 +346,11 @@ __global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* _
     if (n >= o1 && n <= o2) {
       TC out = y;
       if (p.two_level) out += coarse_value<TC>(p, n, s, c3);
-      yhat[static_cast<long long>(n - 1) * N + q] = store_cast<TO>(static_cast<double>(out));
+      const long long o = static_cast<long long>(n - 1) * N + q;
+      if (yhat_lo)
+        store_split<TO>(yhat, yhat_lo, o, static_cast<float>(out));
+      else
+        yhat[o] = store_cast<TO>(static_cast<double>(out));
     }
   }
 }
@@ -381,7 +407,7 @@ int launch_coarse(const kkt_handle* h, const SpecParams& p, const TI* rhat, doub
 
 template <typename TI, typename TC, typename TO>
 int launch_sweeps(const kkt_handle* h, const SpecParams& p, const TI* rhat, double in_scale, TO* yhat,
-                  cudaStream_t st, bool padded) {
+                  cudaStream_t st, bool padded, TO* yhat_lo = nullptr) {
   if (static_cast<const void*>(rhat) == static_cast<const void*>(yhat))
     return set_error(KKT_ERR_INVALID_ARG, "spectral sweep needs distinct buffers");
   if (p.two_level) KKT_TRY(launch_coarse<TI>(h, p, rhat, in_scale, st));
@@ -416,7 +442,7 @@ int launch_sweeps(const kkt_handle* h, const SpecParams& p, const TI* rhat, doub
   // per mode and subdomain node: residual update (8 flops) + forward and backward steps (4)
   const double visits = static_cast<double>(p.N) * (p.Nt + p.n_sub);
   ProfScope ps(KKT_K_SWEEP, st, 12.0 * visits, visits * sizeof(TI) + static_cast<double>(p.N) * p.Nt * sizeof(TO));
-  kern<<<grid, tb, smem, st>>>(rhat, in_scale, yhat, p, h->coarse_c, vglob, h->td.max_len);
+  kern<<<grid, tb, smem, st>>>(rhat, in_scale, yhat, yhat_lo, p, h->coarse_c, vglob, h->td.max_len);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
@@ -429,11 +455,14 @@ int spectral_schur_precond(const kkt_handle* h, const double* rhat, double* yhat
   return launch_sweeps<double, double, double>(h, p, rhat, in_scale, yhat, st, false);
 }
 
-int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, int bf16, cudaStream_t st) {
+int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, void* yhat_lo, int bf16,
+                                 cudaStream_t st) {
   SpecParams p = make_params(h, true);
   if (bf16)
-    return launch_sweeps<float, float, __nv_bfloat16>(h, p, rhat, 1.0, static_cast<__nv_bfloat16*>(yhat), st, true);
-  return launch_sweeps<float, float, float>(h, p, rhat, 1.0, static_cast<float*>(yhat), st, true);
+    return launch_sweeps<float, float, __nv_bfloat16>(h, p, rhat, 1.0, static_cast<__nv_bfloat16*>(yhat), st, true,
+                                                      static_cast<__nv_bfloat16*>(yhat_lo));
+  return launch_sweeps<float, float, float>(h, p, rhat, 1.0, static_cast<float*>(yhat), st, true,
+                                            static_cast<float*>(yhat_lo));
 }
 
 int spectral_learned_apply(const kkt_handle* h, bool padded, const float* y, cudaStream_t st) {

@@ -459,10 +459,11 @@ int tc_plan_create(TcPlan& t, int n, int slices, int bf16) {
   KKT_CUDA_TRY(cudaMalloc(&t.x1, elems * eb));
   KKT_CUDA_TRY(cudaMalloc(&t.x1_lo, elems * eb));
   KKT_CUDA_TRY(cudaMalloc(&t.yin, elems * eb));
+  KKT_CUDA_TRY(cudaMalloc(&t.yin_lo, elems * eb));
   KKT_CUDA_TRY(cudaMalloc(&t.rhat, elems * sizeof(float)));
   KKT_CUDA_TRY(cudaMalloc(&t.err, sizeof(int)));
   KKT_CUDA_TRY(cudaMemset(t.err, 0, sizeof(int)));
-  t.bytes = 2 * plane * eb + 5 * elems * eb + elems * sizeof(float) + sizeof(int);
+  t.bytes = 2 * plane * eb + 6 * elems * eb + elems * sizeof(float) + sizeof(int);
   const long long rows = static_cast<long long>(slices) * P;
   KKT_TRY(make_map(&t.map_q, t.q, eb, P, P, t.tile_n));
   KKT_TRY(make_map(&t.map_q_lo, t.q_lo, eb, P, P, t.tile_n));
@@ -471,6 +472,7 @@ int tc_plan_create(TcPlan& t, int n, int slices, int bf16) {
   KKT_TRY(make_map(&t.map_x1, t.x1, eb, rows, P, kTileM));
   KKT_TRY(make_map(&t.map_x1_lo, t.x1_lo, eb, rows, P, kTileM));
   KKT_TRY(make_map(&t.map_yin, t.yin, eb, rows, P, kTileM));
+  KKT_TRY(make_map(&t.map_yin_lo, t.yin_lo, eb, rows, P, kTileM));
   return KKT_OK;
 }
 
@@ -482,6 +484,7 @@ void tc_plan_destroy(TcPlan& t) {
   cudaFree(t.x1);
   cudaFree(t.x1_lo);
   cudaFree(t.yin);
+  cudaFree(t.yin_lo);
   cudaFree(t.rhat);
   cudaFree(t.err);
   t = TcPlan();
@@ -492,8 +495,7 @@ void tc_plan_destroy(TcPlan& t) {
 int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, cudaStream_t st, bool split,
             void* out_lo) {
   const CUtensorMap& a = which_in == 0 ? t.map_x0 : (which_in == 1 ? t.map_x1 : t.map_yin);
-  const CUtensorMap& alo = which_in == 0 ? t.map_x0_lo : t.map_x1_lo;
-  if (split && which_in == 2) return set_error(KKT_ERR_INVALID_ARG, "no lo part for the sweep output");
+  const CUtensorMap& alo = which_in == 0 ? t.map_x0_lo : (which_in == 1 ? t.map_x1_lo : t.map_yin_lo);
   TcParams p;
   p.P = t.P;
   p.slices = t.slices;
@@ -506,6 +508,7 @@ int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, c
     return launch_gemm<TIN, TN, OM, SP>(a, t.map_q, alo, t.map_q_lo, p, st);
 #define KKT_TC_TYPE(TIN)                                                                   \
   KKT_TC_CASE(TIN, 256, kOutF32, true) KKT_TC_CASE(TIN, 256, kOutSplit, true)              \
+  KKT_TC_CASE(TIN, 256, kOutBF16, true) KKT_TC_CASE(TIN, 128, kOutBF16, true)               \
   KKT_TC_CASE(TIN, 256, kOutF64, true) KKT_TC_CASE(TIN, 128, kOutF64, true)                 \
   KKT_TC_CASE(TIN, 256, kOutBF16, false) KKT_TC_CASE(TIN, 256, kOutF32, false)             \
   KKT_TC_CASE(TIN, 256, kOutF64, false)                                                     \

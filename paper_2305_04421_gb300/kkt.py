@@ -38,7 +38,8 @@ HISTORY_MAX = 1024
 class KKTOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coarse", ctypes.c_int), ("variant", ctypes.c_int),
                 ("pou", ctypes.c_int), ("restart", ctypes.c_int), ("jhat_sign", ctypes.c_int),
-                ("residual_norm", ctypes.c_int), ("Lx", ctypes.c_double), ("Ly", ctypes.c_double)]
+                ("residual_norm", ctypes.c_int), ("tc_split", ctypes.c_int), ("Lx", ctypes.c_double),
+                ("Ly", ctypes.c_double)]
 
 
 class KKTInfo(ctypes.Structure):
@@ -367,16 +368,16 @@ class Solver:
 
     def __init__(self, nx, ny, Nt, T=1.0, nu=1.0, omega=1e-4, n_sub=1, *, precision="fp64",
                  coarse="exact", variant="multiplicative", pou="left", restart=30, jhat_sign=-1,
-                 residual_norm="l2", Lx=1.0, Ly=1.0):
+                 residual_norm="l2", tc_split=True, Lx=1.0, Ly=1.0):
         self.h = kkt_create(nx, ny, Nt, T, nu, omega, n_sub)
         self.set_options(precision=precision, coarse=coarse, variant=variant, pou=pou, restart=restart,
-                         jhat_sign=jhat_sign, residual_norm=residual_norm, Lx=Lx, Ly=Ly)
+                         jhat_sign=jhat_sign, residual_norm=residual_norm, tc_split=tc_split, Lx=Lx, Ly=Ly)
         self.info = kkt_get_info(self.h)
 
     def set_options(self, *, precision="fp64", coarse="exact", variant="multiplicative", pou="left",
-                    restart=30, jhat_sign=-1, residual_norm="l2", Lx=1.0, Ly=1.0):
+                    restart=30, jhat_sign=-1, residual_norm="l2", tc_split=True, Lx=1.0, Ly=1.0):
         opt = KKTOptions(PREC[precision], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
-                         NORM[residual_norm], Lx, Ly)
+                         NORM[residual_norm], 1 if tc_split else 0, Lx, Ly)
         kkt_set_options(self.h, opt)
         self.info = kkt_get_info(self.h)
 
