@@ -332,6 +332,70 @@ def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
     return out
 
 
+def measure_batched(kkt_mod, dev) -> dict:
+    """The 64 uneven instances of the batched workload (sizes 64^2..256^2, Nt 128..1024, N_D
+    8..64, spread nu and omega): one batched solve (memory waves, one launch per phase over all
+    instances, graph replay) against the same instances solved one after another with
+    kkt_solve. Both to the same 1e-8 weighted tolerance from x_0 = 0; device time of the solve
+    calls only (CUDA events), inputs resident."""
+    import torch
+
+    ws = workloads.batched_instances(64, seed=3)
+    fs, seq_ms, seq_its = [], 0.0, []
+    stream = torch.cuda.current_stream()
+    for w in ws:
+        s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
+        ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
+        f = s.build_rhs(ut)
+        x = torch.zeros_like(f)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = s.solve(f, x, tol=TOL, maxit=MAXIT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        seq_ms += e0.elapsed_time(e1)
+        seq_its.append(r.iterations if r.status == kkt_mod.KKT_OK else -1)
+        fs.append(f)
+        del x, ut
+        s.close()
+        torch.cuda.empty_cache()
+    b = kkt_mod.Batch(ws)
+    runs = []
+    for _ in range(2):       # the first call also autotunes the tiles and sweep blocks
+        xs = [torch.zeros_like(f) for f in fs]
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = b.solve(fs, xs, tol=TOL, maxit=MAXIT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        runs.append((e0.elapsed_time(e1), res))
+        del xs
+    b.close()
+    ms, res = runs[1]
+    its = res.iterations
+    unknowns = sum(3 * w.V for w in ws)
+    out = {"workload": "64 uneven instances: nx=ny in {64,128,256}, Nt in {128..1024}, N_D in {8..64}, "
+                       "nu in [0.1,10], omega in [1e-6,1e-2] (log-uniform), seed 3",
+           "instances": len(ws), "unknowns_total": unknowns,
+           "batched": {"solves_per_s": len(ws) / (ms / 1e3), "time_ms": ms, "first_call_ms": runs[0][0],
+                       "waves": res.waves, "graphs": res.graphs, "graph_launches": res.graph_launches,
+                       "tile_lines": res.tile_lines, "sweep_block": res.sweep_block,
+                       "tune_ms_dst_tl8_16_32": res.tune_ms_dst, "tune_ms_sweep_tb64_128_256": res.tune_ms_sweep,
+                       "iterations_min_median_max": [min(its), int(np.median(its)), max(its)],
+                       "all_converged": all(st == kkt_mod.KKT_OK for st in res.statuses)},
+           "sequential": {"solves_per_s": len(ws) / (seq_ms / 1e3), "time_ms": seq_ms,
+                          "all_converged": all(i >= 0 for i in seq_its)},
+           "iteration_count_mismatches_gt1": sum(1 for a, c in zip(its, seq_its) if abs(a - c) > 1)}
+    out["speedup_batched_vs_sequential"] = seq_ms / ms
+    del fs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -384,7 +448,7 @@ def run_ours(args):
     ok = all(r.status == kkt.KKT_OK and r.rel_residual <= TOL for r in results)
     its = results[-1].iterations
     value = world * args.steps / (ms / 1e3)
-    launches = sum(v["launches"] for v in prof.values())
+    launches = sum(v["launches"] for k, v in prof.items() if k != "graph")   # kernels only
     applies = sum(r.iterations for r in results)
     # end to end through the C ABI with host buffers: H2D of f and x0, D2H of x inside the timed region
     f_host = f.cpu().pin_memory()
@@ -423,6 +487,8 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_forms:
         line["forms"] = measure_forms(kkt, dev, steps=2, warmup=1)
+    if rank == 0 and world == 1 and not args.no_batched:
+        line["batched"] = measure_batched(kkt, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s, sample = oracle_iteration_sample(w, min(its, 30) // 2 + 1)
         line["cpu_baseline"] = {"value": 1.0 / (s * its), "unit": "solves/s", "cores": cpu_threads(),
@@ -444,6 +510,8 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=32,
                     help="iterations the reference arm scales its per-iteration sample by")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 64-instance batched vs one-after-another comparison")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64/BF16/TF32 time-to-solution comparison on the 512 x 512 workload")
     args = ap.parse_args()

@@ -75,6 +75,17 @@ enum kkt_residual_norm {
   KKT_NORM_EUCLIDEAN = 1
 };
 
+/* Orthogonalisation of the Arnoldi step. */
+enum kkt_orth {
+  /* modified Gram-Schmidt, one pass: for k = 0..j, h_kj = <q_k, w>, w -= h_kj q_k. Each step is
+   * one streaming pass over q_k, q_k+1 and w (2 FP64 FMAs per element); GMRES with MGS is
+   * backward stable (Paige, Rozloznik and Strakos, 2006). */
+  KKT_ORTH_MGS = 0,
+  /* classical Gram-Schmidt with one conditional repeat (||w'||^2 < ||w||^2 / 2): all dots of a
+   * pass in one multi-dot, one multi-axpy; 4 FMAs per element and basis vector when it repeats */
+  KKT_ORTH_CGS2 = 1
+};
+
 /* Owner of the time node shared by neighbouring subdomains (boolean partition of unity D_s). */
 enum kkt_pou {
   KKT_POU_LEFT = 0,   /* the subdomain whose last step ends on the node */
@@ -91,6 +102,7 @@ typedef struct kkt_options {
   int residual_norm;  /* enum kkt_residual_norm, default KKT_NORM_L2 */
   int tc_split;     /* BF16 / TF32 only: 1 (default) every tensor-core transform uses hi + lo operands
                        (three products, FP32 accumulation); 0 single operands */
+  int orth;         /* enum kkt_orth, default KKT_ORTH_MGS */
   double Lx, Ly;    /* domain (0,Lx) x (0,Ly), default 1, 1 */
 } kkt_options;
 
@@ -280,6 +292,55 @@ int kkt_attach_mlp(kkt_handle* h, kkt_mlp* m, int mode);
 /* Learned-mode coarse corrections kept and replaced by the exact solve since the last call. */
 int kkt_learned_stats(kkt_handle* h, long long* kept, long long* fallback, int reset);
 
+/* ---- batched form: many independent instances of uneven sizes ------------------------
+ *
+ * Not part of the paper's method: a throughput form that solves many independent KKT systems
+ * (Eq 5) with the same preconditioner and FGMRES as kkt_solve. Instances are packed into waves
+ * that fit in device memory; inside a wave every Arnoldi step runs each phase (sine transforms,
+ * coarse solve, sweeps, matvec, Gram-Schmidt) as ONE launch over all instances of the wave, and
+ * the preconditioner + matvec phase of each step index is captured once as a CUDA graph and
+ * replayed. FP64 only, exact or one-level coarse level; instances keep their own sizes and
+ * parameters. Iterations and residual histories equal those of kkt_solve up to rounding.
+ */
+#define KKT_BATCH_MAX 256
+typedef struct kkt_instance {
+  int nx, ny, Nt, n_sub;
+  double T, nu, omega;
+} kkt_instance;
+
+typedef struct kkt_batch_stats {
+  int waves;               /* memory waves the instances were packed into */
+  int graphs;              /* CUDA graphs captured (one per wave and Arnoldi step index used) */
+  long long graph_launches;
+  int tile_lines;          /* sine-transform tile height the autotuner chose */
+  int sweep_block;         /* sweep block size the autotuner chose */
+  double tune_ms_dst[3];   /* autotuner timings of tile heights 8, 16, 32 (ms per forward pair) */
+  double tune_ms_sweep[3]; /* and of sweep blocks 64, 128, 256 */
+  double time_ms;          /* wall time, host clock */
+  int iterations[KKT_BATCH_MAX];
+  int status[KKT_BATCH_MAX];
+  double rel_residual[KKT_BATCH_MAX];  /* recomputed from x at exit, options' residual norm */
+} kkt_batch_stats;
+
+typedef struct kkt_batch kkt_batch;
+
+/* count (1..KKT_BATCH_MAX) instances with the shared options (NULL = defaults; precision must
+ * be FP64 and coarse EXACT or NONE, else NULL with KKT_ERR_UNSUPPORTED). NULL on failure. */
+kkt_batch* kkt_batch_create(int count, const kkt_instance* inst, const kkt_options* opt);
+void kkt_batch_destroy(kkt_batch* b);
+int kkt_batch_get_info(const kkt_batch* b, int i, kkt_info* info);
+/* Cap the Krylov storage of one wave at `bytes` (0: 85% of the free device memory at solve time,
+ * the default). A smaller cap gives more, smaller waves; an instance larger than the cap fails
+ * the solve with KKT_ERR_OOM. */
+int kkt_batch_set_memory_limit(kkt_batch* b, long long bytes);
+/* Solve K_i x_i = f_i for every instance. f, x: host arrays of count DEVICE pointers, 3 V_i
+ * doubles each; x_i holds the initial guess on entry. Synchronises `stream`. Returns KKT_OK
+ * when every instance converged, KKT_NOT_CONVERGED if some stopped at maxit, else the most
+ * severe per-instance error; per-instance outcomes are in stats. Device memory for the Krylov
+ * bases is taken per wave (about 8 (4 restart + 3) V_i bytes per instance) and released. */
+int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, double tol, int maxit,
+                    kkt_batch_stats* stats, void* stream);
+
 /* ---- instrumentation ------------------------------------------------------------------ */
 
 /* Kernel classes counted and timed by the library (process-wide, all handles). */
@@ -292,7 +353,9 @@ enum kkt_kernel_class {
   KKT_K_UPDATE = 5,    /* Gram-Schmidt update + norm */
   KKT_K_AXPY = 6,      /* solution update and elementwise passes */
   KKT_K_REDUCE = 7,    /* reduction finalisation and norms */
-  KKT_K_COUNT = 8
+  KKT_K_GRAPH = 8,     /* a replayed CUDA graph (batched form): its kernels are counted in their
+                          own classes, its time, flops and bytes here */
+  KKT_K_COUNT = 9
 };
 
 typedef struct kkt_kernel_stats {

@@ -1,0 +1,847 @@
+// Batched form (not in the paper): many independent KKT instances of uneven sizes solved
+// together. Instances are packed into memory waves (the FGMRES(30) basis of all 64 instances of
+// the batched workload does not fit in HBM); inside a wave every instance runs the same FGMRES
+// in lockstep, and each phase of an Arnoldi step is ONE launch over all instances: persistent
+// kernels that walk a table of (instance, tile) work items. The preconditioner + matvec phase of
+// step j reads every per-step pointer from tables prepared once per wave, and the only value
+// that changes between restart cycles (1 / eta of the basis vector) from a device array, so it
+// is captured once per (wave, j) as a CUDA graph and replayed. A small autotuner times the
+// candidate tile heights of the batched sine transform and block sizes of the batched sweeps
+// on the wave's own data and keeps the fastest.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "kkt_internal.cuh"
+
+namespace kkt {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr long long kChunk = kThreads * 8;   // elements per work item of the vector kernels
+
+struct Seg {
+  const double* V;   // first vector (basis V_0 or a single vector)
+  long long stride;  // distance between basis vectors
+  double* w;         // target vector
+  long long n;       // elements
+};
+
+__device__ __forceinline__ int find_seg(const long long* __restrict__ prefix, int nj, long long t) {
+  int lo = 0, hi = nj - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    t = lane < (blockDim.x >> 5) ? sh[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// part[t][k] = sum over item t's elements of V_k w (k < NV), part[t][NV] = sum w^2
+template <int NV>
+__global__ void __launch_bounds__(kThreads) multidot_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+                                                       int nj, long long total, double* __restrict__ part) {
+  __shared__ double sh[32];
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int k = find_seg(prefix, nj, t);
+    const Seg S = segs[k];
+    const long long e0 = (t - prefix[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    double acc[NV + 1];
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) acc[v] = 0.0;
+    for (long long i = e0 + threadIdx.x; i < e1; i += kThreads) {
+      const double wi = S.w[i];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) acc[v] = fma(S.V[v * S.stride + i], wi, acc[v]);
+      acc[NV] = fma(wi, wi, acc[NV]);
+    }
+#pragma unroll
+    for (int v = 0; v <= NV; ++v) {
+      const double s = block_sum(acc[v], sh);
+      if (threadIdx.x == 0) part[t * (NV + 1) + v] = s;
+    }
+  }
+}
+
+// w -= sum_k coef[inst][k] V_k over the item; part[t] = sum w^2 (NV = 0: norm only)
+template <int NV>
+__global__ void __launch_bounds__(kThreads) update_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+                                                     int nj, long long total, const double* __restrict__ coef, int ldc,
+                                                     double* __restrict__ part, int want_norm) {
+  __shared__ double sh[32];
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int k = find_seg(prefix, nj, t);
+    const Seg S = segs[k];
+    double c[NV > 0 ? NV : 1];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) c[v] = coef[k * ldc + v];
+    const long long e0 = (t - prefix[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    double acc = 0.0;
+    for (long long i = e0 + threadIdx.x; i < e1; i += kThreads) {
+      double wi = S.w[i];
+#pragma unroll
+      for (int v = 0; v < NV; ++v)   // uniform per item: zero coefficients skip their vector
+        if (c[v] != 0.0) wi = fma(-c[v], S.V[v * S.stride + i], wi);
+      if (NV > 0) S.w[i] = wi;
+      acc = fma(wi, wi, acc);
+    }
+    if (want_norm) {
+      const double s = block_sum(acc, sh);
+      if (threadIdx.x == 0) part[t] = s;
+    }
+  }
+}
+
+// out = alpha[inst] * x + beta[inst] * y, x = V, y = w of the segment (out = w)
+__global__ void __launch_bounds__(kThreads) axpby_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+                                                    int nj, long long total, const double* __restrict__ ab) {
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int k = find_seg(prefix, nj, t);
+    const Seg S = segs[k];
+    const double a = ab[2 * k], b = ab[2 * k + 1];
+    const long long e0 = (t - prefix[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    for (long long i = e0 + threadIdx.x; i < e1; i += kThreads) S.w[i] = fma(a, S.V[i], b * S.w[i]);
+  }
+}
+
+// out[inst][v] = sum of part[t][v] over the instance's items, one warp per (inst, v)
+__global__ void finalize_b(const double* __restrict__ part, const long long* __restrict__ prefix, int nj, int width,
+                           double* __restrict__ out) {
+  const int inst = blockIdx.x / width, v = blockIdx.x % width;
+  if (inst >= nj) return;
+  double acc = 0.0;
+  for (long long t = prefix[inst] + threadIdx.x; t < prefix[inst + 1]; t += 32) acc += part[t * width + v];
+  acc = warp_sum(acc);
+  if (threadIdx.x == 0) out[inst * width + v] = acc;
+}
+
+template <template <int> class Run, typename... A>
+int dispatch(int count, A... a) {
+  switch (count) {
+#define KKT_B_CASE(k) \
+  case k:             \
+    return Run<k>::go(a...);
+    KKT_B_CASE(0) KKT_B_CASE(1) KKT_B_CASE(2) KKT_B_CASE(3) KKT_B_CASE(4) KKT_B_CASE(5) KKT_B_CASE(6)
+    KKT_B_CASE(7) KKT_B_CASE(8) KKT_B_CASE(9) KKT_B_CASE(10) KKT_B_CASE(11) KKT_B_CASE(12) KKT_B_CASE(13)
+    KKT_B_CASE(14) KKT_B_CASE(15) KKT_B_CASE(16) KKT_B_CASE(17) KKT_B_CASE(18) KKT_B_CASE(19) KKT_B_CASE(20)
+    KKT_B_CASE(21) KKT_B_CASE(22) KKT_B_CASE(23) KKT_B_CASE(24) KKT_B_CASE(25) KKT_B_CASE(26) KKT_B_CASE(27)
+    KKT_B_CASE(28) KKT_B_CASE(29) KKT_B_CASE(30) KKT_B_CASE(31) KKT_B_CASE(32)
+#undef KKT_B_CASE
+    default:
+      return set_error(KKT_ERR_INVALID_ARG, "batched Krylov: vector count out of range");
+  }
+}
+
+int persistent_grid() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return std::max(sms, 1) * 4;
+}
+
+template <int NV>
+struct MultidotB {
+  static int go(const Seg* s, const long long* p, int nj, long long tot, double* part, double flops, cudaStream_t st) {
+    ProfScope ps(KKT_K_MULTIDOT, st, flops * (NV + 1), 8.0 * flops / 2 * (NV + 1));
+    multidot_b<NV><<<static_cast<unsigned>(std::min<long long>(tot, persistent_grid())), kThreads, 0, st>>>(s, p, nj, tot, part);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
+};
+
+template <int NV>
+struct UpdateB {
+  static int go(const Seg* s, const long long* p, int nj, long long tot, const double* coef, int ldc, double* part,
+                int want_norm, double flops, cudaStream_t st) {
+    ProfScope ps(NV > 0 ? KKT_K_UPDATE : KKT_K_REDUCE, st, flops * (NV + 1), 8.0 * flops / 2 * (NV > 0 ? NV + 2 : 1));
+    update_b<NV><<<static_cast<unsigned>(std::min<long long>(tot, persistent_grid())), kThreads, 0, st>>>(
+        s, p, nj, tot, coef, ldc, part, want_norm);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
+};
+
+// device + pinned host tables of one family of segments (e.g. "the new basis vector of every
+// instance against its basis")
+struct SegTable {
+  int nj = 0;
+  Seg* dev = nullptr;
+  long long* prefix = nullptr;
+  long long total = 0;
+  double elems = 0;
+  int set(const std::vector<Seg>& segs) {
+    nj = static_cast<int>(segs.size());
+    std::vector<long long> pre(nj + 1, 0);
+    elems = 0;
+    for (int k = 0; k < nj; ++k) {
+      pre[k + 1] = pre[k] + (segs[k].n + kChunk - 1) / kChunk;
+      elems += static_cast<double>(segs[k].n);
+    }
+    total = pre[nj];
+    if (!dev) {
+      KKT_CUDA_TRY(cudaMalloc(&dev, nj * sizeof(Seg)));
+      KKT_CUDA_TRY(cudaMalloc(&prefix, (nj + 1) * sizeof(long long)));
+    }
+    KKT_CUDA_TRY(cudaMemcpy(dev, segs.data(), nj * sizeof(Seg), cudaMemcpyHostToDevice));
+    KKT_CUDA_TRY(cudaMemcpy(prefix, pre.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+    return KKT_OK;
+  }
+  void free() {
+    cudaFree(dev);
+    cudaFree(prefix);
+    dev = nullptr;
+    prefix = nullptr;
+  }
+};
+
+}  // namespace
+}  // namespace kkt
+
+struct kkt_batch {
+  std::vector<kkt_handle*> inst;
+  kkt_options opt;
+  int tuned_tile_lines = 0;   // 0 = not tuned yet
+  int tuned_sweep_tb = 0;
+  double tune_ms_dst[3] = {0, 0, 0};
+  double tune_ms_sweep[3] = {0, 0, 0};
+  long long mem_limit = 0;    // bytes of Krylov storage per wave; 0: 85% of the free device memory
+};
+
+using namespace kkt;
+
+namespace {
+
+// One instance's FGMRES state inside a wave.
+struct InstState {
+  kkt_handle* h;
+  const double* f;
+  double* x;
+  double du, dz, dw;
+  double fnorm = 0, beta = 0;
+  int its = 0, restarts = 0, status = 1, active = 1, jused = 0, cycle_done = 0;
+  std::vector<double> H, cs, sn, g, eta, y, hist;
+  double rel = 0;
+};
+
+}  // namespace
+
+extern "C" {
+
+kkt_batch* kkt_batch_create(int count, const kkt_instance* desc, const kkt_options* opt) {
+  if (count < 1 || count > KKT_BATCH_MAX || !desc) {
+    set_error(KKT_ERR_INVALID_ARG, "need 1 to KKT_BATCH_MAX instances");
+    return nullptr;
+  }
+  kkt_options o;
+  kkt_default_options(&o);
+  if (opt) o = *opt;
+  if (o.precision != KKT_PREC_FP64 || o.coarse == KKT_COARSE_LEARNED) {
+    set_error(KKT_ERR_UNSUPPORTED, "the batched form runs the FP64 exact or one-level preconditioner");
+    return nullptr;
+  }
+  kkt_batch* b = new kkt_batch();
+  b->opt = o;
+  for (int i = 0; i < count; ++i) {
+    const kkt_instance& d = desc[i];
+    kkt_handle* h = kkt_create(d.nx, d.ny, d.Nt, d.T, d.nu, d.omega, d.n_sub);
+    if (!h || kkt_set_options(h, &o) < 0) {
+      const std::string msg = std::string("instance ") + std::to_string(i) + ": " + kkt_last_error();
+      if (h) kkt_destroy(h);
+      kkt_batch_destroy(b);
+      set_error(KKT_ERR_INVALID_ARG, msg);
+      return nullptr;
+    }
+    b->inst.push_back(h);
+  }
+  return b;
+}
+
+void kkt_batch_destroy(kkt_batch* b) {
+  if (!b) return;
+  for (kkt_handle* h : b->inst) kkt_destroy(h);
+  delete b;
+}
+
+int kkt_batch_set_memory_limit(kkt_batch* b, long long bytes) {
+  if (!b || bytes < 0) return set_error(KKT_ERR_INVALID_ARG, "bad memory limit");
+  b->mem_limit = bytes;
+  return KKT_OK;
+}
+
+int kkt_batch_get_info(const kkt_batch* b, int i, kkt_info* info) {
+  if (!b || i < 0 || i >= static_cast<int>(b->inst.size())) return set_error(KKT_ERR_INVALID_ARG, "bad instance index");
+  return kkt_get_info(b->inst[i], info);
+}
+
+int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, double tol, int maxit,
+                    kkt_batch_stats* stats, void* stream) {
+  if (!b || !f || !x) return set_error(KKT_ERR_INVALID_ARG, "null argument");
+  if (!(tol > 0.0) || maxit < 1) return set_error(KKT_ERR_INVALID_ARG, "bad tol or maxit");
+  const auto t_start = std::chrono::steady_clock::now();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n_inst = static_cast<int>(b->inst.size());
+  const int m = b->opt.restart;
+  const bool l2 = b->opt.residual_norm == KKT_NORM_L2;
+  // memory waves: first-fit by decreasing size against the free device memory
+  size_t free_b = 0, total_b = 0;
+  KKT_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  double budget = 0.85 * static_cast<double>(free_b);
+  if (b->mem_limit > 0) budget = std::min(budget, static_cast<double>(b->mem_limit));
+  std::vector<int> order(n_inst);
+  std::iota(order.begin(), order.end(), 0);
+  auto need = [&](int i) { return 8.0 * ((m + 1) * 3.0 + m) * static_cast<double>(b->inst[i]->g.V); };
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return need(a) > need(c); });
+  std::vector<std::vector<int>> waves;
+  std::vector<double> wave_mem;
+  for (int i : order) {
+    if (need(i) > budget) return set_error(KKT_ERR_OOM, "an instance's Krylov basis does not fit in device memory");
+    bool placed = false;
+    for (size_t w = 0; w < waves.size() && !placed; ++w)
+      if (wave_mem[w] + need(i) <= budget) {
+        waves[w].push_back(i);
+        wave_mem[w] += need(i);
+        placed = true;
+      }
+    if (!placed) {
+      waves.push_back({i});
+      wave_mem.push_back(need(i));
+    }
+  }
+  double* h_tmp = nullptr;   // pinned: reductions and coefficients
+  const int ldc = 64;
+  KKT_CUDA_TRY(cudaMallocHost(&h_tmp, sizeof(double) * (3 * ldc * n_inst + 2 * 33 * n_inst + 4 * n_inst)));
+  double* d_small = nullptr;
+  KKT_CUDA_TRY(cudaMalloc(&d_small, sizeof(double) * (3 * ldc * n_inst + 33 * n_inst + 4 * n_inst)));
+  double* d_coef = d_small;                       // [3][n][ldc]
+  double* d_out = d_coef + 3 * ldc * n_inst;      // [n][33]
+  double* d_scale = d_out + 33 * n_inst;          // [n] 1 / eta
+  double* d_ab = d_scale + n_inst;                // [n][2]
+  double* h_coef = h_tmp;
+  double* h_out = h_coef + 3 * ldc * n_inst;
+  double* h_scale = h_out + 2 * 33 * n_inst;
+  int waves_done = 0, graphs_made = 0;
+  long long graph_launches = 0;
+  int rc_all = KKT_OK;
+  std::vector<InstState> all(n_inst);
+  for (const auto& wave : waves) {
+    const int nw = static_cast<int>(wave.size());
+    // per-instance Krylov arenas
+    std::vector<double*> Vb(nw, nullptr), Zw(nw, nullptr);
+    std::vector<InstState*> S(nw);
+    double* part = nullptr;
+    long long max_items = 0;
+    int rc = KKT_OK;
+    for (int k = 0; k < nw && rc == KKT_OK; ++k) {
+      kkt_handle* h = b->inst[wave[k]];
+      const long long V = h->g.V;
+      if (cudaMalloc(&Vb[k], sizeof(double) * (m + 1) * 3 * V) != cudaSuccess ||
+          cudaMalloc(&Zw[k], sizeof(double) * m * V) != cudaSuccess)
+        rc = set_error(KKT_ERR_OOM, "batched Krylov arena");
+      max_items += (3 * V + kChunk - 1) / kChunk;
+      InstState& I = all[wave[k]];
+      I.h = h;
+      I.f = f[wave[k]];
+      I.x = x[wave[k]];
+      I.du = l2 ? 1.0 / std::sqrt(h->g.h) : 1.0;
+      I.dz = I.du;
+      I.dw = l2 ? std::sqrt(h->g.h) : 1.0;
+      I.H.assign((m + 1) * m, 0.0);
+      I.cs.assign(m, 0.0);
+      I.sn.assign(m, 0.0);
+      I.g.assign(m + 1, 0.0);
+      I.eta.assign(m + 1, 0.0);
+      I.y.assign(m, 0.0);
+      S[k] = &I;
+    }
+    if (rc == KKT_OK && cudaMalloc(&part, sizeof(double) * max_items * 33) != cudaSuccess)
+      rc = set_error(KKT_ERR_OOM, "batched reduction scratch");
+    std::vector<BatchSlot> slots(m);
+    BatchSlot resid_slot;
+    std::vector<cudaGraphExec_t> graphs(m, nullptr);
+    std::vector<ProfCapture> graph_work(m);
+    SegTable t_full, t_new, t_f[3], t_xu, t_xz, t_xw;
+    auto Hs = [&](InstState& I, int i, int j) -> double& { return I.H[static_cast<size_t>(i) * m + j]; };
+    auto fetch = [&](int cnt) -> int {
+      KKT_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+      KKT_CUDA_TRY(cudaStreamSynchronize(st));
+      return KKT_OK;
+    };
+    // per-instance sums of the per-item partials (width columns) into h_out[k * width + v]
+    auto finalize = [&](const SegTable& t, int width) -> int {
+      {
+        ProfScope ps(KKT_K_REDUCE, st);
+        finalize_b<<<t.nj * width, 32, 0, st>>>(part, t.prefix, t.nj, width, d_out);
+        KKT_CUDA_TRY(cudaGetLastError());
+      }
+      return fetch(t.nj * width);
+    };
+    // per-instance squared norms of segment tables into h_out[k]
+    auto norms = [&](SegTable& t) -> int {
+      KKT_TRY(dispatch<UpdateB>(0, t.dev, t.prefix, t.nj, t.total, d_coef, ldc, part, 1, 2.0 * t.elems, st));
+      return finalize(t, 1);
+    };
+    // preconditioner + matvec tables of step j (pointers fixed per j)
+    auto prepare_slot = [&](int j) -> int {
+      BatchSlot& sl = slots[j];
+      sl.sweep_tb = b->tuned_sweep_tb > 0 ? b->tuned_sweep_tb : 128;
+      std::vector<DstJob> fwd(nw), inv(nw);
+      std::vector<SpecJob> sj(nw);
+      std::vector<MatvecJob> mj(nw);
+      for (int k = 0; k < nw; ++k) {
+        InstState& I = *S[k];
+        kkt_handle* h = I.h;
+        const Geometry& g = h->g;
+        const long long V = g.V;
+        double* Vj = Vb[k] + static_cast<size_t>(j) * 3 * V;
+        double* Zj = Zw[k] + static_cast<size_t>(j) * V;
+        fwd[k] = DstJob{h, Vj + 2 * V, h->spec};
+        inv[k] = DstJob{h, h->spec2, Zj};
+        SpecJob& J = sj[k];
+        J.p = make_spec_params(h);
+        J.rhat = h->spec;
+        J.yhat = h->spec2;
+        J.cc = h->coarse_c;
+        J.cy = h->coarse_w;
+        J.scale_base = 1.0 / I.dw;
+        J.max_len = h->td.max_len;
+        J.scale_index = k;
+        MatvecJob& M = mj[k];
+        M.u = Vj;
+        M.z = Vj + V;
+        M.w = Zj;
+        M.y = Vj + 3 * V;
+        M.Mx = g.Mx;
+        M.My = g.My;
+        M.Nt = g.Nt;
+        M.N = g.N;
+        M.V = V;
+        const double c0 = 1.0 + 2.0 * g.cx + 2.0 * g.cy;
+        const double su = 1.0 / (g.h * I.du), sz = 1.0 / (g.omega * g.h * I.dz);
+        M.uu = I.du * g.h * su;
+        M.wc0 = I.du * c0;
+        M.wcx = I.du * g.cx;
+        M.wcy = I.du * g.cy;
+        M.wn = I.du;
+        M.zz = I.dz * g.omega * g.h * sz;
+        M.zw = I.dz * g.dt;
+        M.uc0 = I.dw * su * c0;
+        M.ucx = I.dw * su * g.cx;
+        M.ucy = I.dw * su * g.cy;
+        M.up = I.dw * su;
+        M.wz = I.dw * g.dt * sz;
+        M.scale_index = k;
+      }
+      const int tl = b->tuned_tile_lines;
+      KKT_TRY(dst_batched_prepare(sl, 0, fwd.data(), nw, tl));
+      KKT_TRY(dst_batched_prepare(sl, 2, inv.data(), nw, tl));
+      KKT_TRY(spectral_batched_prepare(sl, sj.data(), nw));
+      KKT_TRY(matvec_batched_prepare(sl, mj.data(), nw));
+      return KKT_OK;
+    };
+    auto phase_launch = [&](const BatchSlot& sl, cudaStream_t s2) -> int {
+      KKT_TRY(dst_batched_launch(sl, 0, s2));
+      KKT_TRY(dst_batched_launch(sl, 1, s2));
+      KKT_TRY(spectral_batched_launch(sl, d_scale, s2));
+      KKT_TRY(dst_batched_launch(sl, 2, s2));
+      KKT_TRY(dst_batched_launch(sl, 3, s2));
+      KKT_TRY(matvec_batched_launch(sl, d_scale, s2));
+      return KKT_OK;
+    };
+    // autotune once per batch on the first wave: sine-transform tile height, sweep block size.
+    // Candidates that a wave's sizes rule out (shared memory) are skipped.
+    if (rc == KKT_OK && b->tuned_tile_lines == 0) {
+      const int cand_tl[3] = {8, 16, 32}, cand_tb[3] = {64, 128, 256};
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      KKT_CUDA_TRY(cudaEventCreate(&e0));
+      KKT_CUDA_TRY(cudaEventCreate(&e1));
+      for (int k = 0; k < nw; ++k) KKT_CUDA_TRY(cudaMemsetAsync(Vb[k], 0, sizeof(double) * 3 * S[k]->h->g.V, st));
+      for (int k = 0; k < nw; ++k) h_scale[k] = 1.0;
+      KKT_CUDA_TRY(cudaMemcpyAsync(d_scale, h_scale, sizeof(double) * nw, cudaMemcpyHostToDevice, st));
+      KKT_CUDA_TRY(cudaStreamSynchronize(st));
+      // mean ms of two runs of body (1e30 if a launch was refused, e.g. too much shared memory)
+      auto time_it = [&](auto&& body) -> double {
+        bool ok = true;
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2 && ok; ++r) ok = body() == KKT_OK;
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (!ok) cudaGetLastError();
+        return ok ? ms / 2.0 : 1e30;
+      };
+      int best_tl = 1, best_tb = 1;
+      for (int a = 0; a < 3; ++a) {
+        b->tuned_tile_lines = cand_tl[a];
+        b->tuned_sweep_tb = 128;
+        b->tune_ms_dst[a] = 1e30;
+        if (prepare_slot(0) == KKT_OK)
+          b->tune_ms_dst[a] = time_it([&] {
+            const int r = dst_batched_launch(slots[0], 0, st);
+            return r != KKT_OK ? r : dst_batched_launch(slots[0], 1, st);
+          });
+        batch_slot_free(slots[0]);
+        if (b->tune_ms_dst[a] < b->tune_ms_dst[best_tl]) best_tl = a;
+      }
+      b->tuned_tile_lines = cand_tl[best_tl];
+      for (int a = 0; a < 3; ++a) {
+        b->tuned_sweep_tb = cand_tb[a];
+        b->tune_ms_sweep[a] = 1e30;
+        if (prepare_slot(0) == KKT_OK && dst_batched_launch(slots[0], 0, st) == KKT_OK &&
+            dst_batched_launch(slots[0], 1, st) == KKT_OK)
+          b->tune_ms_sweep[a] = time_it([&] { return spectral_batched_launch(slots[0], d_scale, st); });
+        batch_slot_free(slots[0]);
+        if (b->tune_ms_sweep[a] < b->tune_ms_sweep[best_tb]) best_tb = a;
+      }
+      b->tuned_sweep_tb = cand_tb[best_tb];
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      const cudaError_t e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) rc = set_error(KKT_ERR_CUDA, std::string("autotuning: ") + cudaGetErrorString(e));
+      else if (b->tune_ms_dst[best_tl] >= 1e30 || b->tune_ms_sweep[best_tb] >= 1e30)
+        rc = set_error(KKT_ERR_UNSUPPORTED, "batched form: no tile or sweep block fits this wave");
+      else
+        set_error(KKT_OK, "");
+    }
+    // static segment tables of the wave: full vectors f and x blocks
+    std::vector<Seg> sf[3], sxu, sxz, sxw;
+    for (int k = 0; k < nw && rc == KKT_OK; ++k) {
+      const long long V = S[k]->h->g.V;
+      for (int bl = 0; bl < 3; ++bl) sf[bl].push_back(Seg{S[k]->f + bl * V, 0, Vb[k] + bl * V, V});
+      sxu.push_back(Seg{Vb[k], 3 * V, S[k]->x, V});
+      sxz.push_back(Seg{Vb[k] + V, 3 * V, S[k]->x + V, V});
+      sxw.push_back(Seg{Zw[k], V, S[k]->x + 2 * V, V});
+    }
+    if (rc == KKT_OK) {
+      for (int bl = 0; bl < 3 && rc == KKT_OK; ++bl) rc = t_f[bl].set(sf[bl]);
+      if (rc == KKT_OK) rc = t_xu.set(sxu);
+      if (rc == KKT_OK) rc = t_xz.set(sxz);
+      if (rc == KKT_OK) rc = t_xw.set(sxw);
+    }
+    // residual: V_0 = D (f - K x): matvec of x (scales 1) then V_0 = d f - V_0, blockwise
+    auto residual = [&]() -> int {
+      std::vector<MatvecJob> mj(nw);
+      for (int k = 0; k < nw; ++k) {
+        InstState& I = *S[k];
+        const Geometry& g = I.h->g;
+        MatvecJob& M = mj[k];
+        M.u = I.x;
+        M.z = I.x + g.V;
+        M.w = I.x + 2 * g.V;
+        M.y = Vb[k];
+        M.Mx = g.Mx;
+        M.My = g.My;
+        M.Nt = g.Nt;
+        M.N = g.N;
+        M.V = g.V;
+        const double c0 = 1.0 + 2.0 * g.cx + 2.0 * g.cy;
+        M.uu = I.du * g.h;
+        M.wc0 = I.du * c0;
+        M.wcx = I.du * g.cx;
+        M.wcy = I.du * g.cy;
+        M.wn = I.du;
+        M.zz = I.dz * g.omega * g.h;
+        M.zw = I.dz * g.dt;
+        M.uc0 = I.dw * c0;
+        M.ucx = I.dw * g.cx;
+        M.ucy = I.dw * g.cy;
+        M.up = I.dw;
+        M.wz = I.dw * g.dt;
+        M.scale_index = k;
+        h_scale[k] = 1.0;
+      }
+      KKT_CUDA_TRY(cudaMemcpyAsync(d_scale, h_scale, sizeof(double) * nw, cudaMemcpyHostToDevice, st));
+      KKT_TRY(matvec_batched_prepare(resid_slot, mj.data(), nw));
+      KKT_TRY(matvec_batched_launch(resid_slot, d_scale, st));
+      for (int bl = 0; bl < 3; ++bl) {
+        for (int k = 0; k < nw; ++k) {
+          const double d = bl == 0 ? S[k]->du : (bl == 1 ? S[k]->dz : S[k]->dw);
+          h_coef[2 * k] = d;
+          h_coef[2 * k + 1] = -1.0;
+        }
+        KKT_CUDA_TRY(cudaMemcpyAsync(d_ab, h_coef, sizeof(double) * 2 * nw, cudaMemcpyHostToDevice, st));
+        ProfScope ps(KKT_K_AXPY, st, 3.0 * t_f[bl].elems, 24.0 * t_f[bl].elems);
+        axpby_b<<<static_cast<unsigned>(std::min<long long>(t_f[bl].total, persistent_grid())), kThreads, 0, st>>>(
+            t_f[bl].dev, t_f[bl].prefix, nw, t_f[bl].total, d_ab);
+        KKT_CUDA_TRY(cudaGetLastError());
+        KKT_CUDA_TRY(cudaStreamSynchronize(st));
+      }
+      std::vector<Seg> s0(nw);
+      for (int k = 0; k < nw; ++k) s0[k] = Seg{Vb[k], 0, Vb[k], 3 * S[k]->h->g.V};
+      KKT_TRY(t_full.set(s0));
+      KKT_TRY(norms(t_full));
+      for (int k = 0; k < nw; ++k) S[k]->beta = std::sqrt(h_out[k]);
+      return KKT_OK;
+    };
+    // right-hand side norms (weighted)
+    if (rc == KKT_OK) {
+      std::vector<double> acc(nw, 0.0);
+      for (int bl = 0; bl < 3 && rc == KKT_OK; ++bl) {
+        std::vector<Seg> sfb(nw);
+        for (int k = 0; k < nw; ++k) sfb[k] = Seg{S[k]->f + bl * S[k]->h->g.V, 0, const_cast<double*>(S[k]->f) + bl * S[k]->h->g.V, S[k]->h->g.V};
+        SegTable tt;
+        rc = tt.set(sfb);
+        if (rc == KKT_OK) rc = norms(tt);
+        for (int k = 0; k < nw && rc == KKT_OK; ++k) {
+          const double d = bl == 0 ? S[k]->du : (bl == 1 ? S[k]->dz : S[k]->dw);
+          acc[k] += d * d * h_out[k];
+        }
+        tt.free();
+      }
+      for (int k = 0; k < nw; ++k) S[k]->fnorm = std::sqrt(acc[k]);
+    }
+    if (rc == KKT_OK) rc = residual();
+    for (int k = 0; k < nw && rc == KKT_OK; ++k) {
+      InstState& I = *S[k];
+      if (!std::isfinite(I.fnorm) || !std::isfinite(I.beta)) {
+        I.status = KKT_ERR_NONFINITE;
+        I.active = 0;
+      } else if (I.fnorm == 0.0 || I.beta / I.fnorm <= tol) {
+        I.rel = I.fnorm == 0.0 ? 0.0 : I.beta / I.fnorm;
+        I.status = KKT_OK;
+        I.active = 0;
+      }
+    }
+    // restart cycles in lockstep
+    while (rc == KKT_OK) {
+      int n_active = 0;
+      for (int k = 0; k < nw; ++k) n_active += S[k]->active;
+      if (n_active == 0) break;
+      for (int k = 0; k < nw; ++k) {
+        InstState& I = *S[k];
+        std::fill(I.H.begin(), I.H.end(), 0.0);
+        std::fill(I.g.begin(), I.g.end(), 0.0);
+        I.g[0] = I.beta;
+        I.eta[0] = I.beta > 0 ? I.beta : 1.0;
+        I.jused = 0;
+        I.cycle_done = !I.active;
+      }
+      for (int j = 0; j < m && rc == KKT_OK; ++j) {
+        int running = 0;
+        for (int k = 0; k < nw; ++k) running += !S[k]->cycle_done;
+        if (running == 0) break;
+        if (!slots[j].dst) {
+          rc = prepare_slot(j);
+          if (rc != KKT_OK) break;
+        }
+        for (int k = 0; k < nw; ++k) h_scale[k] = 1.0 / S[k]->eta[j];
+        KKT_CUDA_TRY(cudaMemcpyAsync(d_scale, h_scale, sizeof(double) * nw, cudaMemcpyHostToDevice, st));
+        if (!graphs[j]) {
+          cudaStream_t cs_ = nullptr;
+          KKT_CUDA_TRY(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
+          cudaGraph_t gr = nullptr;
+          KKT_CUDA_TRY(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeRelaxed));
+          graph_work[j] = ProfCapture();
+          prof_capture(&graph_work[j]);
+          const int prc = phase_launch(slots[j], cs_);
+          prof_capture(nullptr);
+          const cudaError_t ec = cudaStreamEndCapture(cs_, &gr);
+          cudaStreamDestroy(cs_);
+          if (prc < 0 || ec != cudaSuccess) {
+            rc = set_error(KKT_ERR_CUDA, "graph capture of the batched phase failed");
+            break;
+          }
+          KKT_CUDA_TRY(cudaGraphInstantiate(&graphs[j], gr, 0));
+          cudaGraphDestroy(gr);
+          ++graphs_made;
+        }
+        rc = prof_graph_launch(graphs[j], graph_work[j], st);
+        if (rc != KKT_OK) break;
+        ++graph_launches;
+        // Gram-Schmidt of the new vectors against each instance's basis (CGS, one conditional repeat)
+        std::vector<Seg> sn(nw);
+        for (int k = 0; k < nw; ++k) {
+          const long long V = S[k]->h->g.V;
+          sn[k] = Seg{Vb[k], 3 * V, Vb[k] + static_cast<size_t>(j + 1) * 3 * V, 3 * V};
+        }
+        rc = t_new.set(sn);
+        if (rc != KKT_OK) break;
+        std::vector<double> wn2(nw, 0.0), before(nw, 0.0);
+        std::vector<char> need(nw, 1);
+        for (int pass = 0; pass < 2 && rc == KKT_OK; ++pass) {
+          rc = dispatch<MultidotB>(j + 1, t_new.dev, t_new.prefix, nw, t_new.total, part, 2.0 * t_new.elems, st);
+          if (rc != KKT_OK) break;
+          rc = finalize(t_new, j + 2);
+          if (rc != KKT_OK) break;
+          for (int k = 0; k < nw; ++k) {
+            InstState& I = *S[k];
+            const bool on = need[k] && !I.cycle_done;
+            if (on) before[k] = h_out[k * (j + 2) + j + 1];
+            for (int i = 0; i <= j; ++i) {
+              const double hk = on ? h_out[k * (j + 2) + i] / I.eta[i] : 0.0;
+              Hs(I, i, j) += hk;
+              h_coef[k * ldc + i] = hk / I.eta[i];
+            }
+          }
+          KKT_CUDA_TRY(cudaMemcpyAsync(d_coef, h_coef, sizeof(double) * ldc * nw, cudaMemcpyHostToDevice, st));
+          rc = dispatch<UpdateB>(j + 1, t_new.dev, t_new.prefix, nw, t_new.total, d_coef, ldc, part, 1,
+                                 2.0 * t_new.elems, st);
+          if (rc != KKT_OK) break;
+          rc = finalize(t_new, 1);
+          if (rc != KKT_OK) break;
+          bool again = false;
+          for (int k = 0; k < nw; ++k) {
+            // instances that finished their cycle still get normalised (their vectors stay finite)
+            if (pass == 0 && S[k]->cycle_done) wn2[k] = h_out[k];
+            if (!need[k] || S[k]->cycle_done) continue;
+            wn2[k] = h_out[k];
+            need[k] = wn2[k] < 0.5 * before[k];
+            again = again || need[k];
+          }
+          if (!again) break;
+        }
+        if (rc != KKT_OK) break;
+        for (int k = 0; k < nw; ++k) {
+          InstState& I = *S[k];
+          const double hn = std::sqrt(wn2[k]);
+          I.eta[j + 1] = (hn > 0 && std::isfinite(hn)) ? hn : 1.0;
+          if (I.cycle_done) continue;
+          if (!std::isfinite(hn)) {
+            I.status = KKT_ERR_NONFINITE;
+            I.active = 0;
+            I.cycle_done = 1;
+            continue;
+          }
+          Hs(I, j + 1, j) = hn;
+          for (int i = 0; i < j; ++i) {
+            const double t = I.cs[i] * Hs(I, i, j) + I.sn[i] * Hs(I, i + 1, j);
+            Hs(I, i + 1, j) = -I.sn[i] * Hs(I, i, j) + I.cs[i] * Hs(I, i + 1, j);
+            Hs(I, i, j) = t;
+          }
+          const double d = std::hypot(Hs(I, j, j), Hs(I, j + 1, j));
+          I.cs[j] = d > 0 ? Hs(I, j, j) / d : 1.0;
+          I.sn[j] = d > 0 ? Hs(I, j + 1, j) / d : 0.0;
+          Hs(I, j, j) = d;
+          Hs(I, j + 1, j) = 0.0;
+          I.g[j + 1] = -I.sn[j] * I.g[j];
+          I.g[j] = I.cs[j] * I.g[j];
+          I.its++;
+          I.jused = j + 1;
+          const double est = std::fabs(I.g[j + 1]) / I.fnorm;
+          I.hist.push_back(est);
+          if (est <= tol || I.its >= maxit || hn == 0.0) I.cycle_done = 1;
+        }
+      }
+      if (rc != KKT_OK) break;
+      // x += Z y per instance (coefficients zero for instances without steps this cycle)
+      int jmax = 0;
+      for (int k = 0; k < nw; ++k) {
+        InstState& I = *S[k];
+        jmax = std::max(jmax, I.jused);
+        for (int i = I.jused - 1; i >= 0; --i) {
+          double s = I.g[i];
+          for (int c = i + 1; c < I.jused; ++c) s -= Hs(I, i, c) * I.y[c];
+          I.y[i] = Hs(I, i, i) != 0.0 ? s / Hs(I, i, i) : 0.0;
+        }
+        for (int i = 0; i < ldc; ++i) {
+          const bool on = I.active && i < I.jused;
+          h_coef[k * ldc + i] = on ? -I.y[i] / (I.h->g.h * I.du * I.eta[i]) : 0.0;
+          h_coef[(nw + k) * ldc + i] = on ? -I.y[i] / (I.h->g.omega * I.h->g.h * I.dz * I.eta[i]) : 0.0;
+          h_coef[(2 * nw + k) * ldc + i] = on ? -I.y[i] : 0.0;
+        }
+      }
+      if (jmax > 0) {
+        KKT_CUDA_TRY(cudaMemcpyAsync(d_coef, h_coef, sizeof(double) * 3 * ldc * nw, cudaMemcpyHostToDevice, st));
+        // update_b subtracts: x -= (-y) V
+        rc = dispatch<UpdateB>(jmax, t_xu.dev, t_xu.prefix, nw, t_xu.total, d_coef, ldc, part, 0, 2.0 * t_xu.elems, st);
+        if (rc == KKT_OK)
+          rc = dispatch<UpdateB>(jmax, t_xz.dev, t_xz.prefix, nw, t_xz.total, d_coef + nw * ldc, ldc, part, 0,
+                                 2.0 * t_xz.elems, st);
+        if (rc == KKT_OK)
+          rc = dispatch<UpdateB>(jmax, t_xw.dev, t_xw.prefix, nw, t_xw.total, d_coef + 2 * nw * ldc, ldc, part, 0,
+                                 2.0 * t_xw.elems, st);
+      }
+      if (rc != KKT_OK) break;
+      for (int k = 0; k < nw; ++k)
+        if (S[k]->active && S[k]->jused > 0) S[k]->restarts++;
+      rc = residual();
+      if (rc != KKT_OK) break;
+      for (int k = 0; k < nw; ++k) {
+        InstState& I = *S[k];
+        if (!I.active) continue;
+        I.rel = I.beta / I.fnorm;
+        if (!std::isfinite(I.rel)) {
+          I.status = KKT_ERR_NONFINITE;
+          I.active = 0;
+        } else if (I.rel <= tol) {
+          I.status = KKT_OK;
+          I.active = 0;
+        } else if (I.its >= maxit) {
+          I.status = KKT_NOT_CONVERGED;
+          I.active = 0;
+        }
+      }
+    }
+    for (int j = 0; j < m; ++j) {
+      if (graphs[j]) cudaGraphExecDestroy(graphs[j]);
+      batch_slot_free(slots[j]);
+    }
+    batch_slot_free(resid_slot);
+    t_full.free();
+    t_new.free();
+    for (int bl = 0; bl < 3; ++bl) t_f[bl].free();
+    t_xu.free();
+    t_xz.free();
+    t_xw.free();
+    cudaFree(part);
+    for (int k = 0; k < nw; ++k) {
+      cudaFree(Vb[k]);
+      cudaFree(Zw[k]);
+    }
+    if (rc != KKT_OK) {
+      rc_all = rc;
+      break;
+    }
+    ++waves_done;
+  }
+  cudaFreeHost(h_tmp);
+  cudaFree(d_small);
+  if (rc_all < 0) return rc_all;
+  int worst = KKT_OK;
+  for (int i = 0; i < n_inst; ++i) {
+    if (all[i].status < 0) worst = std::min(worst, all[i].status);
+    else if (all[i].status == KKT_NOT_CONVERGED && worst == KKT_OK) worst = KKT_NOT_CONVERGED;
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->waves = waves_done;
+    stats->graphs = graphs_made;
+    stats->graph_launches = graph_launches;
+    stats->tile_lines = b->tuned_tile_lines;
+    stats->sweep_block = b->tuned_sweep_tb;
+    for (int a = 0; a < 3; ++a) {
+      stats->tune_ms_dst[a] = b->tune_ms_dst[a];
+      stats->tune_ms_sweep[a] = b->tune_ms_sweep[a];
+    }
+    stats->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    for (int i = 0; i < n_inst && i < KKT_BATCH_MAX; ++i) {
+      stats->iterations[i] = all[i].its;
+      stats->status[i] = all[i].status;
+      stats->rel_residual[i] = all[i].rel;
+    }
+  }
+  return worst;
+}
+
+}  // extern "C"

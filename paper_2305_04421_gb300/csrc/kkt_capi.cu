@@ -325,6 +325,7 @@ int kkt_default_options(kkt_options* opt) {
   opt->jhat_sign = -1;
   opt->residual_norm = KKT_NORM_L2;
   opt->tc_split = 1;
+  opt->orth = KKT_ORTH_MGS;
   opt->Lx = 1.0;
   opt->Ly = 1.0;
   return KKT_OK;
@@ -425,6 +426,7 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
   if (opt->residual_norm != KKT_NORM_L2 && opt->residual_norm != KKT_NORM_EUCLIDEAN)
     return set_error(KKT_ERR_INVALID_ARG, "residual_norm out of range");
   if (opt->tc_split != 0 && opt->tc_split != 1) return set_error(KKT_ERR_INVALID_ARG, "tc_split must be 0 or 1");
+  if (opt->orth != KKT_ORTH_MGS && opt->orth != KKT_ORTH_CGS2) return set_error(KKT_ERR_INVALID_ARG, "orth out of range");
   if (!finite_pos(opt->Lx) || !finite_pos(opt->Ly)) return set_error(KKT_ERR_INVALID_ARG, "Lx, Ly must be positive");
   // with the shared node given to the later subdomain, the first subdomain owns nodes
   // 1 .. b_1 - 1; its linear coarse function needs two of them
@@ -718,10 +720,25 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
       local.precond_applies++;
       KKT_TRY(launch_matvec(h, Vj, 1.0 / (g.h * du * eta[j]), Vj + V, 1.0 / (g.omega * g.h * dz * eta[j]), Zj, 1.0,
                             W, st, du, dz, dw));
-      // classical Gram-Schmidt with one conditional reorthogonalisation (||w'|| < ||w|| / sqrt 2)
       for (int k = 0; k <= j; ++k) Hs(k, j) = 0.0;
       double wnorm2 = 0.0;
-      for (int pass = 0; pass < 2; ++pass) {
+      if (h->opt.orth == KKT_ORTH_MGS) {
+        // modified Gram-Schmidt: d_k = <V_k, w> on the w already orthogonalised against
+        // V_0..V_k-1, then w -= (d_k / eta_k^2) V_k; the dots stay on the device (red_out[k])
+        // and feed the next step's coefficient, so the host reads the column once
+        KKT_TRY(krylov_mgs_step(h, nullptr, nullptr, 0.0, Vb, W, n3, h->red_out, st));
+        for (int k = 0; k <= j; ++k) {
+          const double* Vn = k < j ? Vb + static_cast<size_t>(k + 1) * n3 : nullptr;
+          KKT_TRY(krylov_mgs_step(h, Vb + static_cast<size_t>(k) * n3, h->red_out + k, 1.0 / (eta[k] * eta[k]), Vn, W,
+                                  n3, h->red_out + k + 1, st));
+        }
+        KKT_TRY(fetch(j + 2));
+        for (int k = 0; k <= j; ++k) Hs(k, j) = hr[k] / eta[k];
+        wnorm2 = hr[j + 1];
+        if (!std::isfinite(wnorm2)) return finish(set_error(KKT_ERR_NONFINITE, "Krylov vector is not finite"), NAN);
+      }
+      // classical Gram-Schmidt with one conditional reorthogonalisation (||w'|| < ||w|| / sqrt 2)
+      for (int pass = 0; pass < 2 && h->opt.orth == KKT_ORTH_CGS2; ++pass) {
         KKT_TRY(krylov_multidot(h, Vb, n3, j + 1, W, n3, st));
         KKT_TRY(fetch(j + 2));
         const double before = hr[j + 1];

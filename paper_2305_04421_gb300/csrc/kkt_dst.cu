@@ -15,7 +15,9 @@
 // loads (rows: one contiguous run; columns: 32 consecutive columns per grid row), each of
 // its 8 warps transforms whole lines, and the tile is stored back the same way.
 // Every output element is written by exactly one thread; in == out is allowed.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "kkt_internal.cuh"
 
@@ -25,21 +27,7 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-struct DstLaunch {
-  const double* in;
-  double* out;
-  int n, logn, M, ldt, tile_lines;
-  int mode;                 // 0: lines are rows (along x), 1: lines are columns (along y)
-  long long total_lines;    // rows mode: number of rows in the block
-  int cols;                 // columns mode: columns per slice (the row length Mx)
-  long long slice;          // columns mode: elements per slice
-  int tiles_per_slice;      // columns mode
-  double scale;             // 1 / sqrt(2 n)
-  const double* pre;
-  const double2* tw;
-  const double2* post;
-  const double* sintab;
-};
+
 
 __device__ __forceinline__ int bit_reverse(int v, int bits) {
   return bits > 0 ? static_cast<int>(__brev(static_cast<unsigned>(v)) >> (32 - bits)) : 0;
@@ -123,8 +111,8 @@ __device__ void dst_line_direct(double* x, double* tmp, const DstLaunch& L, int 
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(kThreads) dst_tile_kernel(DstLaunch L) {
-  extern __shared__ double smem[];
+// One tile of lines: load, transform, store. `bid` is the tile index within the launch.
+__device__ void dst_tile_body(const DstLaunch& L, long long bid, double* smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* tile = smem;
   const int tile_words = (L.tile_lines * L.ldt + 1) & ~1;
@@ -133,14 +121,14 @@ __global__ void __launch_bounds__(kThreads) dst_tile_kernel(DstLaunch L) {
   long long base = 0;
   int nl = 0;
   if (L.mode == 0) {
-    const long long first = static_cast<long long>(blockIdx.x) * L.tile_lines;
+    const long long first = bid * L.tile_lines;
     { const long long rem = L.total_lines - first; nl = static_cast<int>(rem < L.tile_lines ? rem : L.tile_lines); }
     base = first * L.M;
     for (int l = warp; l < nl; l += kWarps)
       for (int e = lane; e < L.M; e += 32) tile[l * L.ldt + e] = L.in[base + static_cast<long long>(l) * L.M + e];
   } else {
-    const long long sl = blockIdx.x / L.tiles_per_slice;
-    const int col0 = (blockIdx.x % L.tiles_per_slice) * L.tile_lines;
+    const long long sl = bid / L.tiles_per_slice;
+    const int col0 = static_cast<int>(bid % L.tiles_per_slice) * L.tile_lines;
     nl = min(L.tile_lines, L.cols - col0);
     base = sl * L.slice + col0;
     for (int e = warp; e < L.M; e += kWarps)
@@ -163,18 +151,39 @@ __global__ void __launch_bounds__(kThreads) dst_tile_kernel(DstLaunch L) {
   }
 }
 
+__global__ void __launch_bounds__(kThreads) dst_tile_kernel(DstLaunch L) {
+  extern __shared__ double smem[];
+  dst_tile_body(L, blockIdx.x, smem);
+}
+
+// Several launches (instances, passes) in one grid: item t belongs to launch k with
+// prefix[k] <= t < prefix[k+1]; blocks loop over the items.
+__global__ void __launch_bounds__(kThreads) dst_tile_batched(const DstLaunch* __restrict__ Ls,
+                                                             const long long* __restrict__ prefix, int nl,
+                                                             long long total) {
+  extern __shared__ double smem[];
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = nl - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    dst_tile_body(Ls[lo], t - prefix[lo], smem);
+    __syncthreads();
+  }
+}
+
 int tile_lines_for(int n) { return n > 512 ? 16 : 32; }
 
-size_t smem_bytes(int n) {
+size_t smem_bytes(int n, int tl) {
   const int M = n - 1;
   const int ldt = M | 1;
-  const int tl = tile_lines_for(n);
   const size_t tile_words = (static_cast<size_t>(tl) * ldt + 1) & ~static_cast<size_t>(1);
   return (tile_words + static_cast<size_t>(kWarps) * n) * sizeof(double);
 }
 
-int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long long total_lines,
-                 int cols, long long slice, long long nslices, cudaStream_t st) {
+DstLaunch make_launch(const DstPlan& p, const double* in, double* out, int mode, long long total_lines, int cols,
+                      long long slice, int tile_lines) {
   DstLaunch L;
   L.in = in;
   L.out = out;
@@ -182,7 +191,7 @@ int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long
   L.logn = p.logn;
   L.M = p.n - 1;
   L.ldt = L.M | 1;
-  L.tile_lines = tile_lines_for(p.n);
+  L.tile_lines = tile_lines > 0 ? tile_lines : tile_lines_for(p.n);
   L.mode = mode;
   L.total_lines = total_lines;
   L.cols = cols;
@@ -193,11 +202,20 @@ int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long
   L.tw = p.d_tw;
   L.post = p.d_post;
   L.sintab = p.d_sin;
-  const size_t sm = smem_bytes(p.n);
+  return L;
+}
+
+long long launch_tiles(const DstLaunch& L, long long nslices) {
+  return L.mode == 0 ? (L.total_lines + L.tile_lines - 1) / L.tile_lines : nslices * L.tiles_per_slice;
+}
+
+int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long long total_lines,
+                 int cols, long long slice, long long nslices, cudaStream_t st) {
+  const DstLaunch L = make_launch(p, in, out, mode, total_lines, cols, slice, 0);
+  const size_t sm = smem_bytes(p.n, L.tile_lines);
   KKT_CUDA_TRY(cudaFuncSetAttribute(dst_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(sm)));
-  long long grid = mode == 0 ? (total_lines + L.tile_lines - 1) / L.tile_lines
-                             : nslices * L.tiles_per_slice;
+  long long grid = launch_tiles(L, nslices);
   if (grid <= 0) return KKT_OK;
   if (grid > 2147483647LL) return set_error(KKT_ERR_UNSUPPORTED, "DST grid too large");
   // one real DST-I of M points by FFT: 2.5 M log2(2n) flops; each point read and written once
@@ -242,6 +260,73 @@ void dst_plan_destroy(DstPlan& p) {
   cudaFree(p.d_post);
   cudaFree(p.d_sin);
   p = DstPlan();
+}
+
+// Batched 2D DST over several instances: one launch for all row passes, one for all column
+// passes; tables filled once per slot (outside any graph capture), launches read them.
+int dst_batched_prepare(BatchSlot& slot, int first_pass, const DstJob* jobs, int njobs, int tile_lines) {
+  slot.njobs = njobs;
+  if (!slot.dst) {
+    KKT_CUDA_TRY(cudaMalloc(&slot.dst, 4 * static_cast<size_t>(njobs) * sizeof(DstLaunch)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.dst_prefix, 4 * static_cast<size_t>(njobs + 1) * sizeof(long long)));
+  }
+  for (int pass = first_pass; pass < first_pass + 2; ++pass) {
+    const bool rows = (pass % 2) == 0;
+    std::vector<DstLaunch> L(njobs);
+    std::vector<long long> prefix(njobs + 1, 0);
+    size_t sm = 0;
+    double flops = 0, bytes = 0;
+    for (int k = 0; k < njobs; ++k) {
+      const kkt_handle* h = jobs[k].h;
+      const Geometry& g = h->g;
+      L[k] = rows ? make_launch(h->dst_x, jobs[k].in, jobs[k].out, 0, static_cast<long long>(g.Nt) * g.My, g.Mx, 0,
+                                tile_lines)
+                  : make_launch(h->dst_y, jobs[k].out, jobs[k].out, 1, 0, g.Mx, g.N, tile_lines);
+      prefix[k + 1] = prefix[k] + launch_tiles(L[k], g.Nt);
+      sm = std::max(sm, smem_bytes(L[k].n, L[k].tile_lines));
+      const double lines = rows ? static_cast<double>(g.Nt) * g.My : static_cast<double>(g.Nt) * g.Mx;
+      flops += lines * 2.5 * L[k].M * std::log2(2.0 * L[k].n);
+      bytes += lines * L[k].M * 16.0;
+    }
+    KKT_CUDA_TRY(cudaMemcpy(slot.dst + static_cast<size_t>(pass) * njobs, L.data(), njobs * sizeof(DstLaunch),
+                            cudaMemcpyHostToDevice));
+    KKT_CUDA_TRY(cudaMemcpy(slot.dst_prefix + static_cast<size_t>(pass) * (njobs + 1), prefix.data(),
+                            (njobs + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+    slot.dst_total[pass] = prefix[njobs];
+    slot.dst_smem[pass] = sm;
+    slot.dst_flops[pass] = flops;
+    slot.dst_bytes[pass] = bytes;
+  }
+  return KKT_OK;
+}
+
+int dst_batched_launch(const BatchSlot& slot, int pass, cudaStream_t st) {
+  const long long total = slot.dst_total[pass];
+  if (total <= 0) return KKT_OK;
+  const size_t sm = slot.dst_smem[pass];
+  KKT_CUDA_TRY(cudaFuncSetAttribute(dst_tile_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(sm)));
+  int dev = 0, sms = 0, per_sm = 0;
+  KKT_CUDA_TRY(cudaGetDevice(&dev));
+  KKT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  KKT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dst_tile_batched, kThreads, sm));
+  const long long grid = std::min<long long>(total, static_cast<long long>(std::max(sms, 1)) * std::max(per_sm, 1));
+  ProfScope ps(KKT_K_DST, st, slot.dst_flops[pass], slot.dst_bytes[pass]);
+  dst_tile_batched<<<static_cast<unsigned>(grid), kThreads, sm, st>>>(
+      slot.dst + static_cast<size_t>(pass) * slot.njobs, slot.dst_prefix + static_cast<size_t>(pass) * (slot.njobs + 1),
+      slot.njobs, total);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+void batch_slot_free(BatchSlot& slot) {
+  cudaFree(slot.dst);
+  cudaFree(slot.dst_prefix);
+  cudaFree(slot.spec);
+  cudaFree(slot.coarse_prefix);
+  cudaFree(slot.sweep_prefix);
+  cudaFree(slot.mv);
+  cudaFree(slot.mv_prefix);
+  slot = BatchSlot();
 }
 
 int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st) {

@@ -92,6 +92,7 @@ struct Geometry {
   double dtnu, cx, cy;   // dt nu, dt nu / dx^2, dt nu / dy^2
 };
 
+
 }  // namespace kkt
 
 struct kkt_handle {
@@ -152,6 +153,15 @@ struct ProfScope {
   }
   ~ProfScope() { prof_end(cls, st, flops, bytes); }
 };
+// While a stream is captured into a CUDA graph, launches are tallied into a ProfCapture (not
+// counted, not timed); every replay through prof_graph_launch then adds the tallied kernel
+// launches to the counters and times the whole graph as one KKT_K_GRAPH launch.
+struct ProfCapture {
+  long long launches[KKT_K_COUNT] = {};
+  double flops = 0.0, bytes = 0.0;
+};
+void prof_capture(ProfCapture* acc);   // nullptr ends the capture on this thread
+int prof_graph_launch(cudaGraphExec_t g, const ProfCapture& acc, cudaStream_t st);
 
 // ---- kernels launched from the C ABI (each defined in its own translation unit) ---------
 int dst_plan_create(DstPlan& p, int n);
@@ -206,9 +216,119 @@ int krylov_update_norm(kkt_handle* h, const double* V, long long stride, int cou
 int krylov_axpy_multi(const double* V, long long stride, int count, const double* coef_dev,
                       double* x, long long n, cudaStream_t st);  // x += sum c_k V_k
 int krylov_norm2(kkt_handle* h, const double* x, long long n, cudaStream_t st);  // red_out[0]
+// One modified Gram-Schmidt step over n elements: if Vk, w -= (dot[0] * s) Vk; then *out =
+// <Vn, w> (Vn non-null) or <w, w> (Vn null), reduced deterministically.
+int krylov_mgs_step(kkt_handle* h, const double* Vk, const double* dot, double s, const double* Vn, double* w,
+                    long long n, double* out, cudaStream_t st);
 int krylov_partial_capacity();
+
+// ---- batched forms: several instances per launch ---------------------------------------
+// One tile launch of the DST line kernel (rows or columns of one instance).
+struct DstLaunch {
+  const double* in;
+  double* out;
+  int n, logn, M, ldt, tile_lines;
+  int mode;                 // 0: lines are rows (along x), 1: lines are columns (along y)
+  long long total_lines;    // rows mode: number of rows in the block
+  int cols;                 // columns mode: columns per slice (the row length Mx)
+  long long slice;          // columns mode: elements per slice
+  int tiles_per_slice;      // columns mode
+  double scale;             // 1 / sqrt(2 n)
+  const double* pre;
+  const double2* tw;
+  const double2* post;
+  const double* sintab;
+};
+
+// Per-instance parameters of the spectral kernels (modes, decomposition, coarse buffers).
+struct SpecParams {
+  int Mx, Nt, n_sub;      // Mx: modes per spectral row (the padded size in the mixed forms)
+  long long N;
+  double a, dtnu, h, inv_h;
+  const double* lx;
+  const double* ly;
+  const int* first;
+  const int* last;
+  const int* ofirst;
+  const int* olast;
+  const int* owner;
+  const double* phi;
+  const double* mom;
+  const double* cf;    // coarse factors [s][3][N]: D_s^{-1} of the block-Thomas elimination
+  int learn_k;         // modes k, l < learn_k also write their R_0 r to learn_c
+  double* learn_c;
+  int two_level;       // apply the coarse correction
+  int multiplicative;  // subtract S-hat x_0 before the local solves
+};
+SpecParams make_spec_params(const kkt_handle* h);
+
+// One instance's share of a batched spectral phase: rhat -> yhat with the in-scale
+// scale_base * scale_dev[scale_index] (the Krylov driver keeps 1 / eta per instance on the device).
+struct SpecJob {
+  SpecParams p;
+  const double* rhat;
+  double* yhat;
+  double* cc;            // coarse coefficients [s][2][N]
+  double* cy;            // eliminated coarse right-hand sides [s][2][N]
+  double scale_base;
+  int max_len;
+  int scale_index;
+};
+
+// One instance's matvec: y = diag(du, dz, dw) K (su u, sz z, w) with su, sz = base * scale_dev[index].
+struct MatvecJob {
+  const double* u;
+  const double* z;
+  const double* w;
+  double* y;
+  int Mx, My, Nt;
+  long long N, V;
+  double uu, wc0, wcx, wcy, wn, zz, zw, uc0, ucx, ucy, up, wz;   // su-, sz-dependent terms at su = sz = 1
+  int scale_index;
+};
 // out = alpha * x + beta * y (elementwise; out may alias x or y)
 int launch_axpby(double alpha, const double* x, double beta, const double* y, double* out, long long n,
                  cudaStream_t st);
+
+// Device tables of one batched phase sequence (the launches of one captured graph).
+struct BatchSlot {
+  int njobs = 0;
+  // DST: [pass 0 fwd rows, 1 fwd cols, 2 inv rows, 3 inv cols] x njobs
+  DstLaunch* dst = nullptr;
+  long long* dst_prefix = nullptr;    // [4][njobs + 1]
+  long long dst_total[4] = {0, 0, 0, 0};
+  size_t dst_smem[4] = {0, 0, 0, 0};
+  double dst_flops[4] = {0, 0, 0, 0}, dst_bytes[4] = {0, 0, 0, 0};
+  SpecJob* spec = nullptr;
+  long long* coarse_prefix = nullptr;   // blocks of 128 modes
+  long long* sweep_prefix = nullptr;    // blocks of (modes / tb) x n_sub
+  long long coarse_total = 0, sweep_total = 0;
+  size_t sweep_smem = 0;
+  int sweep_tb = 128;
+  double coarse_flops = 0, coarse_bytes = 0, sweep_flops = 0, sweep_bytes = 0;
+  MatvecJob* mv = nullptr;
+  long long* mv_prefix = nullptr;
+  long long mv_total = 0;
+  double mv_V = 0;
+};
+
+struct DstJob {
+  const kkt_handle* h;
+  const double* in;
+  double* out;
+};
+
+// Fill the DST tables of `slot` for passes `first_pass`, first_pass + 1 (forward rows/cols or
+// inverse rows/cols) from jobs (synchronous copies); launch one pass from the tables.
+int dst_batched_prepare(BatchSlot& slot, int first_pass, const DstJob* jobs, int njobs, int tile_lines);
+int dst_batched_launch(const BatchSlot& slot, int pass, cudaStream_t st);
+// spectral coarse + sweeps for all jobs of the slot (FP64), scale_dev: per-instance 1/eta
+int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int njobs);
+int spectral_batched_launch(const BatchSlot& slot, const double* scale_dev, cudaStream_t st);
+int matvec_batched_prepare(BatchSlot& slot, const MatvecJob* jobs, int njobs);
+int matvec_batched_launch(const BatchSlot& slot, const double* scale_dev, cudaStream_t st);
+void batch_slot_free(BatchSlot& slot);
+
+
 
 }  // namespace kkt

@@ -134,6 +134,42 @@ __global__ void __launch_bounds__(kRedThreads) axpy_multi_kernel(const double* _
   }
 }
 
+// One modified Gram-Schmidt step (AXPY: w -= c Vk with c = dot[0] * s, read once per thread;
+// DOTV: the partial dot is <Vn, w> over the updated w, else <w, w>).
+template <bool AXPY, bool DOTV>
+__global__ void __launch_bounds__(kRedThreads) mgs_step_kernel(const double* __restrict__ Vk,
+                                                               const double* __restrict__ dot, double s,
+                                                               const double* __restrict__ Vn, double* __restrict__ w,
+                                                               long long n, double* __restrict__ part, bool vec2) {
+  __shared__ double sh[32];
+  const double c = AXPY ? dot[0] * s : 0.0;
+  double acc = 0.0;
+  const long long gs = static_cast<long long>(gridDim.x) * blockDim.x;
+  const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long np = pair_count(n, vec2);
+  for (long long i = tid; i < np; i += gs) {
+    double2 wi = reinterpret_cast<const double2*>(w)[i];
+    if (AXPY) {
+      const double2 v = reinterpret_cast<const double2*>(Vk)[i];
+      wi.x = fma(-c, v.x, wi.x);
+      wi.y = fma(-c, v.y, wi.y);
+      reinterpret_cast<double2*>(w)[i] = wi;
+    }
+    const double2 o = DOTV ? reinterpret_cast<const double2*>(Vn)[i] : wi;
+    acc = fma(o.x, wi.x, fma(o.y, wi.y, acc));
+  }
+  for (long long i = 2 * np + tid; i < n; i += gs) {
+    double wi = w[i];
+    if (AXPY) {
+      wi = fma(-c, Vk[i], wi);
+      w[i] = wi;
+    }
+    acc = fma(DOTV ? Vn[i] : wi, wi, acc);
+  }
+  const double t = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
 __global__ void norm_kernel(const double* __restrict__ x, long long n, double* __restrict__ part) {
   __shared__ double sh[32];
   double acc = 0.0;
@@ -276,6 +312,32 @@ int krylov_norm2(kkt_handle* h, const double* x, long long n, cudaStream_t st) {
   {
     ProfScope ps(KKT_K_REDUCE, st);
     finalize_kernel<<<1, 32, 0, st>>>(h->red, nb, 1, h->red_out);
+  }
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int krylov_mgs_step(kkt_handle* h, const double* Vk, const double* dot, double s, const double* Vn, double* w,
+                    long long n, double* out, cudaStream_t st) {
+  const int nb = grid_blocks();
+  const bool vec2 = can_vec2(w, Vk ? Vk : w, 2) && can_vec2(w, Vn ? Vn : w, 2);
+  if (!Vk && !Vn) return set_error(KKT_ERR_INVALID_ARG, "MGS step needs a vector");
+  {
+    // streaming: Vk and Vn read, w read (and written when Vk): 2 FP64 FMAs per element with Vk
+    const double fl = (Vk ? 2.0 : 0.0) * n + 2.0 * n;
+    const double by = 8.0 * n * ((Vk ? 2.0 : 0.0) + (Vn ? 1.0 : 0.0) + 1.0);
+    ProfScope ps(Vk ? KKT_K_UPDATE : KKT_K_MULTIDOT, st, fl, by);
+    if (Vk && Vn)
+      mgs_step_kernel<true, true><<<nb, kRedThreads, 0, st>>>(Vk, dot, s, Vn, w, n, h->red, vec2);
+    else if (Vk)
+      mgs_step_kernel<true, false><<<nb, kRedThreads, 0, st>>>(Vk, dot, s, Vn, w, n, h->red, vec2);
+    else
+      mgs_step_kernel<false, true><<<nb, kRedThreads, 0, st>>>(Vk, dot, s, Vn, w, n, h->red, vec2);
+    KKT_CUDA_TRY(cudaGetLastError());
+  }
+  {
+    ProfScope ps(KKT_K_REDUCE, st);
+    finalize_kernel<<<1, 32, 0, st>>>(h->red, nb, 1, out);
   }
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;

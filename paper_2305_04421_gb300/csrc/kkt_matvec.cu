@@ -9,6 +9,9 @@
 // global memory, neighbours hit L1/L2. The Krylov driver applies the matvec to scaled
 // inputs (su u, sz z, sw w) and scales the three output blocks (ou, oz, ow); every scale is
 // folded into the stencil coefficients so one point costs 16 FP64 instructions.
+#include <algorithm>
+#include <vector>
+
 #include "kkt_internal.cuh"
 
 namespace kkt {
@@ -97,6 +100,42 @@ __global__ void axpby_kernel(double alpha, const double* __restrict__ x, double 
   for (long long k = t; k < n; k += st) out[k] = fma(alpha, x[k], beta * y[k]);
 }
 
+// Batched matvec: item = a block of 256 points of one instance; coefficients of the su / sz
+// terms scaled by the instance's scale_dev entry (1 / eta of the Krylov vector being applied).
+__global__ void matvec_batched(const MatvecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
+                               long long total, const double* __restrict__ scale_dev) {
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    int lo = 0, hi = nj - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const MatvecJob& J = jobs[lo];
+    const long long idx = (t - prefix[lo]) * blockDim.x + threadIdx.x;
+    if (idx >= J.V) continue;
+    const double e = scale_dev[J.scale_index];
+    const int i = static_cast<int>(idx % J.Mx);
+    const long long r = idx / J.Mx;
+    const int j = static_cast<int>(r % J.My);
+    const int n = static_cast<int>(r / J.My);
+    const bool hw = i > 0, he = i + 1 < J.Mx, hs = j > 0, hn = j + 1 < J.My;
+    const double wc = J.w[idx];
+    const double wwe = (hw ? J.w[idx - 1] : 0.0) + (he ? J.w[idx + 1] : 0.0);
+    const double wsn = (hs ? J.w[idx - J.Mx] : 0.0) + (hn ? J.w[idx + J.Mx] : 0.0);
+    const double wnx = n + 1 < J.Nt ? J.w[idx + J.N] : 0.0;
+    const double uc = J.u[idx];
+    const double uwe = (hw ? J.u[idx - 1] : 0.0) + (he ? J.u[idx + 1] : 0.0);
+    const double usn = (hs ? J.u[idx - J.Mx] : 0.0) + (hn ? J.u[idx + J.Mx] : 0.0);
+    const double upr = n > 0 ? J.u[idx - J.N] : 0.0;
+    const double zc = J.z[idx];
+    double tt = fma(J.wcy, wsn, fma(J.wcx, wwe, J.wn * wnx));
+    J.y[idx] = fma(J.uu * e, uc, fma(J.wc0, wc, -tt));
+    J.y[J.V + idx] = fma(J.zz * e, zc, -J.zw * wc);
+    tt = fma(J.ucy * e, usn, fma(J.ucx * e, uwe, fma(J.up * e, upr, (J.wz * e) * zc)));
+    J.y[2 * J.V + idx] = fma(J.uc0 * e, uc, -tt);
+  }
+}
+
 Stencil make_stencil(const Geometry& g, double shift) {
   Stencil s;
   s.Mx = g.Mx;
@@ -134,6 +173,38 @@ int launch_matvec(const kkt_handle* h, const double* u, double su, const double*
   // 16 FP64 instructions (12 FMA) per point: 28 flops; 3 blocks in, 3 out
   ProfScope ps(KKT_K_MATVEC, st, 28.0 * g.V, 48.0 * g.V);
   matvec_kernel<<<grid, tb, 0, st>>>(u, z, w, y, s, c);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int matvec_batched_prepare(BatchSlot& slot, const MatvecJob* jobs, int nj) {
+  std::vector<long long> pre(nj + 1, 0);
+  double V = 0;
+  for (int k = 0; k < nj; ++k) {
+    pre[k + 1] = pre[k] + (jobs[k].V + 255) / 256;
+    V += static_cast<double>(jobs[k].V);
+  }
+  if (!slot.mv) {
+    KKT_CUDA_TRY(cudaMalloc(&slot.mv, nj * sizeof(MatvecJob)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.mv_prefix, (nj + 1) * sizeof(long long)));
+  }
+  KKT_CUDA_TRY(cudaMemcpy(slot.mv, jobs, nj * sizeof(MatvecJob), cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(slot.mv_prefix, pre.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  slot.mv_total = pre[nj];
+  slot.mv_V = V;
+  slot.njobs = nj;
+  return KKT_OK;
+}
+
+int matvec_batched_launch(const BatchSlot& slot, const double* scale_dev, cudaStream_t st) {
+  if (slot.mv_total <= 0) return KKT_OK;
+  int dev = 0, sms = 0;
+  KKT_CUDA_TRY(cudaGetDevice(&dev));
+  KKT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long grid = std::min<long long>(slot.mv_total, static_cast<long long>(sms) * 8);
+  ProfScope ps(KKT_K_MATVEC, st, 28.0 * slot.mv_V, 48.0 * slot.mv_V);
+  matvec_batched<<<static_cast<unsigned>(grid), 256, 0, st>>>(slot.mv, slot.mv_prefix, slot.njobs, slot.mv_total,
+                                                              scale_dev);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }

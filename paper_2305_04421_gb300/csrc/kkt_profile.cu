@@ -24,6 +24,7 @@ double g_bytes[KKT_K_COUNT] = {};
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_pool;
 thread_local cudaEvent_t t_open = nullptr;
+thread_local ProfCapture* t_cap = nullptr;
 
 cudaEvent_t take_event() {
   if (!g_pool.empty()) {
@@ -55,6 +56,10 @@ void drain_locked() {
 }  // namespace
 
 void prof_begin(int cls, cudaStream_t st) {
+  if (t_cap) {   // being captured into a graph: count the launch for every replay instead
+    t_cap->launches[cls] += 1;
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   g_launches[cls] += 1;
   if (!g_on) return;
@@ -63,6 +68,11 @@ void prof_begin(int cls, cudaStream_t st) {
 }
 
 void prof_end(int cls, cudaStream_t st, double flops, double bytes) {
+  if (t_cap) {
+    t_cap->flops += flops;
+    t_cap->bytes += bytes;
+    return;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on || !t_open) return;
   cudaEvent_t b = take_event();
@@ -70,6 +80,18 @@ void prof_end(int cls, cudaStream_t st, double flops, double bytes) {
   g_pending.push_back({t_open, b, cls, flops, bytes});
   t_open = nullptr;
   if (g_pending.size() > 4096) drain_locked();
+}
+
+void prof_capture(ProfCapture* acc) { t_cap = acc; }
+
+int prof_graph_launch(cudaGraphExec_t g, const ProfCapture& acc, cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (int c = 0; c < KKT_K_COUNT; ++c) g_launches[c] += acc.launches[c];
+  }
+  ProfScope ps(KKT_K_GRAPH, st, acc.flops, acc.bytes);
+  KKT_CUDA_TRY(cudaGraphLaunch(g, st));
+  return KKT_OK;
 }
 
 }  // namespace kkt

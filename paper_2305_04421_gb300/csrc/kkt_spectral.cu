@@ -21,30 +21,15 @@
 // formed in FP64 before rounding.
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "kkt_internal.cuh"
 
 namespace kkt {
 namespace {
 
-struct SpecParams {
-  int Mx, Nt, n_sub;      // Mx: modes per spectral row (the padded size in the mixed forms)
-  long long N;
-  double a, dtnu, h, inv_h;
-  const double* lx;
-  const double* ly;
-  const int* first;
-  const int* last;
-  const int* ofirst;
-  const int* olast;
-  const int* owner;
-  const double* phi;
-  const double* mom;
-  const double* cf;    // coarse factors [s][3][N]: D_s^{-1} of the block-Thomas elimination
-  int learn_k;         // modes k, l < learn_k also write their R_0 r to learn_c
-  double* learn_c;
-  int two_level;       // apply the coarse correction
-  int multiplicative;  // subtract S-hat x_0 before the local solves
-};
+
 
 __device__ __forceinline__ double mode_mu(const SpecParams& p, long long q) {
   const long long l = q / p.Mx;
@@ -125,10 +110,8 @@ __global__ void coarse_factor_kernel(SpecParams p, double* __restrict__ cf) {
 
 // R_0 r and the block-Thomas substitutions with the precomputed factors; c' = h x.
 template <typename TI>
-__global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale, SpecParams p,
-                                    double* __restrict__ cc, double* __restrict__ cy) {
-  const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (q >= p.N) return;
+__device__ void coarse_body(const TI* __restrict__ rhat, double in_scale, const SpecParams& p,
+                            double* __restrict__ cc, double* __restrict__ cy, long long q) {
   const long long N = p.N;
   const double mu = mode_mu(p, q);
   double y0 = 0, y1 = 0, t0 = 0, t1 = 0;   // eliminated rhs of s-1 and D_{s-1}^{-1} a_{s-1}
@@ -185,6 +168,13 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
     cc[(2LL * s) * N + q] = p.h * x0;
     cc[(2LL * s + 1) * N + q] = p.h * x1;
   }
+}
+
+template <typename TI>
+__global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale, SpecParams p,
+                                    double* __restrict__ cc, double* __restrict__ cy) {
+  const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q < p.N) coarse_body<TI>(rhat, in_scale, p, cc, cy, q);
 }
 
 // Learned modes: d = network output (a direction), x = alpha d with the Galerkin
@@ -283,14 +273,9 @@ __device__ __forceinline__ TC coarse_value(const SpecParams& p, int n, int s, co
 }
 
 template <typename TI, typename TC, typename TO>
-__global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* __restrict__ yhat,
-                             TO* __restrict__ yhat_lo, SpecParams p, const double* __restrict__ cc,
-                             TC* __restrict__ vglobal, int max_len) {
-  extern __shared__ __align__(16) unsigned char vs_raw[];
-  TC* vs_smem = reinterpret_cast<TC*>(vs_raw);
-  const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (q >= p.N) return;
+__device__ void sweep_body(const TI* __restrict__ rhat, double in_scale, TO* __restrict__ yhat,
+                           TO* __restrict__ yhat_lo, const SpecParams& p, const double* __restrict__ cc,
+                           TC* __restrict__ vglobal, int max_len, long long q, int s, TC* vs_smem) {
   const long long N = p.N;
   const double mud = mode_mu(p, q);
   const TC mu = static_cast<TC>(mud), mu2 = mu * mu;
@@ -355,6 +340,55 @@ __global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* _
   }
 }
 
+template <typename TI, typename TC, typename TO>
+__global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* __restrict__ yhat,
+                             TO* __restrict__ yhat_lo, SpecParams p, const double* __restrict__ cc,
+                             TC* __restrict__ vglobal, int max_len) {
+  extern __shared__ __align__(16) unsigned char vs_raw[];
+  const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q < p.N)
+    sweep_body<TI, TC, TO>(rhat, in_scale, yhat, yhat_lo, p, cc, vglobal, max_len, q, blockIdx.y,
+                           reinterpret_cast<TC*>(vs_raw));
+}
+
+__device__ __forceinline__ int find_job(const long long* __restrict__ prefix, int nj, long long t) {
+  int lo = 0, hi = nj - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Batched coarse solves: item = a block of 128 modes of one instance (FP64).
+__global__ void coarse_batched(const SpecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
+                               long long total, const double* __restrict__ scale_dev) {
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int k = find_job(prefix, nj, t);
+    const SpecJob& J = jobs[k];
+    const long long q = (t - prefix[k]) * blockDim.x + threadIdx.x;
+    if (q < J.p.N && J.p.two_level)
+      coarse_body<double>(J.rhat, J.scale_base * scale_dev[J.scale_index], J.p, J.cc, J.cy, q);
+  }
+}
+
+// Batched sweeps: item = (block of modes, subdomain) of one instance (FP64).
+__global__ void sweep_batched(const SpecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
+                              long long total, const double* __restrict__ scale_dev) {
+  extern __shared__ __align__(16) unsigned char vs_raw[];
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int k = find_job(prefix, nj, t);
+    const SpecJob& J = jobs[k];
+    const long long local = t - prefix[k];
+    const long long mblocks = (J.p.N + blockDim.x - 1) / blockDim.x;
+    const int s = static_cast<int>(local / mblocks);
+    const long long q = (local % mblocks) * blockDim.x + threadIdx.x;
+    if (q < J.p.N)
+      sweep_body<double, double, double>(J.rhat, J.scale_base * scale_dev[J.scale_index], J.yhat, nullptr, J.p, J.cc,
+                                         nullptr, J.max_len, q, s, reinterpret_cast<double*>(vs_raw));
+  }
+}
+
 __global__ void prolong_kernel(SpecParams p, const double* __restrict__ cc, double* __restrict__ xhat) {
   const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const int n = blockIdx.y + 1;
@@ -364,7 +398,7 @@ __global__ void prolong_kernel(SpecParams p, const double* __restrict__ cc, doub
       cc[(2LL * o) * p.N + q] + cc[(2LL * o + 1) * p.N + q] * __ldg(p.phi + n - 1);
 }
 
-SpecParams make_params(const kkt_handle* h, bool padded) {
+SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixed forms' mode grid)
   SpecParams p;
   const Geometry& g = h->g;
   p.Mx = padded ? h->tc.P : g.Mx;
@@ -472,6 +506,73 @@ int spectral_learned_apply(const kkt_handle* h, bool padded, const float* y, cud
   ProfScope ps(KKT_K_COARSE, st, 40.0 * n * p.n_sub, 40.0 * n * p.n_sub);
   learned_apply_kernel<<<(n + 127) / 128, 128, 0, st>>>(p, y, h->mlp_mode, h->coarse_c, h->learn_count);
   KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+SpecParams make_spec_params(const kkt_handle* h) { return make_params(h, false); }
+
+int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
+  slot.njobs = nj;
+  const int tb = slot.sweep_tb > 0 ? slot.sweep_tb : 128;
+  std::vector<long long> cp(nj + 1, 0), sp(nj + 1, 0);
+  int max_len = 0;
+  double cf = 0, cb = 0, sf = 0, sb = 0;
+  for (int k = 0; k < nj; ++k) {
+    const SpecParams& p = jobs[k].p;
+    cp[k + 1] = cp[k] + (p.two_level ? (p.N + 127) / 128 : 0);
+    sp[k + 1] = sp[k] + ((p.N + tb - 1) / tb) * p.n_sub;
+    max_len = std::max(max_len, jobs[k].max_len);
+    const double V = static_cast<double>(p.N) * p.Nt, visits = static_cast<double>(p.N) * (p.Nt + p.n_sub);
+    if (p.two_level) {
+      cf += 2.0 * V + 26.0 * p.n_sub * p.N;
+      cb += 8.0 * V + 12.0 * 8.0 * p.n_sub * p.N;
+    }
+    sf += 12.0 * visits;
+    sb += 8.0 * visits + 8.0 * V;
+  }
+  if (static_cast<size_t>(max_len) * tb * sizeof(double) > 200 * 1024)
+    return set_error(KKT_ERR_UNSUPPORTED, "batched sweeps: a subdomain is too long for shared memory");
+  if (!slot.spec) {
+    KKT_CUDA_TRY(cudaMalloc(&slot.spec, nj * sizeof(SpecJob)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.coarse_prefix, (nj + 1) * sizeof(long long)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.sweep_prefix, (nj + 1) * sizeof(long long)));
+  }
+  KKT_CUDA_TRY(cudaMemcpy(slot.spec, jobs, nj * sizeof(SpecJob), cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(slot.coarse_prefix, cp.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(slot.sweep_prefix, sp.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  slot.coarse_total = cp[nj];
+  slot.sweep_total = sp[nj];
+  slot.sweep_tb = tb;
+  slot.sweep_smem = static_cast<size_t>(max_len) * tb * sizeof(double);
+  slot.coarse_flops = cf;
+  slot.coarse_bytes = cb;
+  slot.sweep_flops = sf;
+  slot.sweep_bytes = sb;
+  return KKT_OK;
+}
+
+int spectral_batched_launch(const BatchSlot& slot, const double* scale_dev, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  KKT_CUDA_TRY(cudaGetDevice(&dev));
+  KKT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (slot.coarse_total > 0) {
+    const long long grid = std::min<long long>(slot.coarse_total, static_cast<long long>(sms) * 16);
+    ProfScope ps(KKT_K_COARSE, st, slot.coarse_flops, slot.coarse_bytes);
+    coarse_batched<<<static_cast<unsigned>(grid), 128, 0, st>>>(slot.spec, slot.coarse_prefix, slot.njobs,
+                                                                slot.coarse_total, scale_dev);
+    KKT_CUDA_TRY(cudaGetLastError());
+  }
+  if (slot.sweep_total > 0) {
+    KKT_CUDA_TRY(cudaFuncSetAttribute(sweep_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(slot.sweep_smem)));
+    int per_sm = 0;
+    KKT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batched, slot.sweep_tb, slot.sweep_smem));
+    const long long grid = std::min<long long>(slot.sweep_total, static_cast<long long>(sms) * std::max(per_sm, 1));
+    ProfScope ps(KKT_K_SWEEP, st, slot.sweep_flops, slot.sweep_bytes);
+    sweep_batched<<<static_cast<unsigned>(grid), slot.sweep_tb, slot.sweep_smem, st>>>(
+        slot.spec, slot.sweep_prefix, slot.njobs, slot.sweep_total, scale_dev);
+    KKT_CUDA_TRY(cudaGetLastError());
+  }
   return KKT_OK;
 }
 

@@ -32,13 +32,15 @@ COARSE = {"exact": 0, "none": 1, "learned": 2}
 VARIANT = {"multiplicative": 0, "additive": 1}
 POU = {"left": 0, "right": 1}
 NORM = {"l2": 0, "euclidean": 1}
+ORTH = {"mgs": 0, "cgs2": 1}
 HISTORY_MAX = 1024
 
 
 class KKTOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coarse", ctypes.c_int), ("variant", ctypes.c_int),
                 ("pou", ctypes.c_int), ("restart", ctypes.c_int), ("jhat_sign", ctypes.c_int),
-                ("residual_norm", ctypes.c_int), ("tc_split", ctypes.c_int), ("Lx", ctypes.c_double),
+                ("residual_norm", ctypes.c_int), ("tc_split", ctypes.c_int), ("orth", ctypes.c_int),
+                ("Lx", ctypes.c_double),
                 ("Ly", ctypes.c_double)]
 
 
@@ -56,12 +58,32 @@ class KKTStats(ctypes.Structure):
                 ("history_len", ctypes.c_int), ("history", ctypes.c_double * HISTORY_MAX)]
 
 
-KERNEL_CLASSES = ["dst", "coarse", "sweep", "matvec", "multidot", "update", "axpy", "reduce"]
+# "graph" is a replayed CUDA graph of the batched form: its kernels are counted in their own
+# classes, its device time, flops and bytes under "graph"; it is not itself a kernel launch.
+KERNEL_CLASSES = ["dst", "coarse", "sweep", "matvec", "multidot", "update", "axpy", "reduce", "graph"]
+_NK = len(KERNEL_CLASSES)
 
 
 class KKTKernelStats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_longlong * 8), ("ms", ctypes.c_double * 8), ("timed", ctypes.c_longlong * 8),
-                ("flops", ctypes.c_double * 8), ("bytes", ctypes.c_double * 8)]
+    _fields_ = [("launches", ctypes.c_longlong * _NK), ("ms", ctypes.c_double * _NK),
+                ("timed", ctypes.c_longlong * _NK), ("flops", ctypes.c_double * _NK),
+                ("bytes", ctypes.c_double * _NK)]
+
+
+BATCH_MAX = 256
+
+
+class KKTInstance(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("Nt", ctypes.c_int), ("n_sub", ctypes.c_int),
+                ("T", ctypes.c_double), ("nu", ctypes.c_double), ("omega", ctypes.c_double)]
+
+
+class KKTBatchStats(ctypes.Structure):
+    _fields_ = [("waves", ctypes.c_int), ("graphs", ctypes.c_int), ("graph_launches", ctypes.c_longlong),
+                ("tile_lines", ctypes.c_int), ("sweep_block", ctypes.c_int),
+                ("tune_ms_dst", ctypes.c_double * 3), ("tune_ms_sweep", ctypes.c_double * 3),
+                ("time_ms", ctypes.c_double), ("iterations", ctypes.c_int * BATCH_MAX),
+                ("status", ctypes.c_int * BATCH_MAX), ("rel_residual", ctypes.c_double * BATCH_MAX)]
 
 
 class KKTMlpConfig(ctypes.Structure):
@@ -121,6 +143,12 @@ SIGNATURES = [
     ("kkt_mlp_load", _P, [ctypes.c_char_p]),
     ("kkt_attach_mlp", _I, [_P, _P, _I]),
     ("kkt_learned_stats", _I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _I]),
+    ("kkt_batch_create", _P, [_I, ctypes.POINTER(KKTInstance), ctypes.POINTER(KKTOptions)]),
+    ("kkt_batch_destroy", None, [_P]),
+    ("kkt_batch_get_info", _I, [_P, _I, ctypes.POINTER(KKTInfo)]),
+    ("kkt_batch_set_memory_limit", _I, [_P, ctypes.c_longlong]),
+    ("kkt_batch_solve", _I, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), _D, _I,
+                             ctypes.POINTER(KKTBatchStats), _P]),
     ("kkt_profile_enable", _I, [_I]),
     ("kkt_profile_read", _I, [ctypes.POINTER(KKTKernelStats), _I]),
 ]
@@ -240,6 +268,38 @@ def kkt_multidot_noalloc(V, stride, count, w, n, out, stream=None) -> int:
     for callers that cannot allocate device memory. Calls must not overlap on the GPU."""
     return _check(load_library().kkt_multidot_noalloc(_ptr(V), stride, count, _ptr(w), n, _ptr(out),
                                                       _stream(stream)))
+
+
+def kkt_batch_create(instances, opt: KKTOptions | None = None) -> int:
+    """instances: a sequence of KKTInstance (or (nx, ny, Nt, n_sub, T, nu, omega) tuples)."""
+    lib = load_library()
+    arr = (KKTInstance * len(instances))(*[i if isinstance(i, KKTInstance) else KKTInstance(*i) for i in instances])
+    b = lib.kkt_batch_create(len(instances), arr, ctypes.byref(opt) if opt is not None else None)
+    if not b:
+        raise KKTError(KKT_ERR_INVALID_ARG, lib.kkt_last_error().decode())
+    return b
+
+
+def kkt_batch_destroy(b) -> None:
+    load_library().kkt_batch_destroy(b)
+
+
+def kkt_batch_get_info(b, i) -> KKTInfo:
+    info = KKTInfo()
+    _check(load_library().kkt_batch_get_info(b, i, ctypes.byref(info)))
+    return info
+
+
+def kkt_batch_set_memory_limit(b, nbytes: int) -> int:
+    return _check(load_library().kkt_batch_set_memory_limit(b, int(nbytes)))
+
+
+def kkt_batch_solve(b, fs, xs, tol, maxit, stats: KKTBatchStats | None = None, stream=None) -> int:
+    n = len(fs)
+    fp = (ctypes.c_void_p * n)(*[_ptr(t).value for t in fs])
+    xp = (ctypes.c_void_p * n)(*[_ptr(t).value for t in xs])
+    st = stats if stats is not None else KKTBatchStats()
+    return _check(load_library().kkt_batch_solve(b, fp, xp, tol, maxit, ctypes.byref(st), _stream(stream)))
 
 
 def kkt_profile_enable(on: bool) -> int:
@@ -368,16 +428,17 @@ class Solver:
 
     def __init__(self, nx, ny, Nt, T=1.0, nu=1.0, omega=1e-4, n_sub=1, *, precision="fp64",
                  coarse="exact", variant="multiplicative", pou="left", restart=30, jhat_sign=-1,
-                 residual_norm="l2", tc_split=True, Lx=1.0, Ly=1.0):
+                 residual_norm="l2", tc_split=True, orth="mgs", Lx=1.0, Ly=1.0):
         self.h = kkt_create(nx, ny, Nt, T, nu, omega, n_sub)
         self.set_options(precision=precision, coarse=coarse, variant=variant, pou=pou, restart=restart,
-                         jhat_sign=jhat_sign, residual_norm=residual_norm, tc_split=tc_split, Lx=Lx, Ly=Ly)
+                         jhat_sign=jhat_sign, residual_norm=residual_norm, tc_split=tc_split, orth=orth,
+                         Lx=Lx, Ly=Ly)
         self.info = kkt_get_info(self.h)
 
     def set_options(self, *, precision="fp64", coarse="exact", variant="multiplicative", pou="left",
-                    restart=30, jhat_sign=-1, residual_norm="l2", tc_split=True, Lx=1.0, Ly=1.0):
+                    restart=30, jhat_sign=-1, residual_norm="l2", tc_split=True, orth="mgs", Lx=1.0, Ly=1.0):
         opt = KKTOptions(PREC[precision], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
-                         NORM[residual_norm], 1 if tc_split else 0, Lx, Ly)
+                         NORM[residual_norm], 1 if tc_split else 0, ORTH[orth], Lx, Ly)
         kkt_set_options(self.h, opt)
         self.info = kkt_get_info(self.h)
 
@@ -452,3 +513,66 @@ class Solver:
         status = kkt_solve(self.h, f, x, tol, maxit, st, stream)
         return SolveResult(x, status, st.iterations, st.restarts, st.rel_residual, st.rel_residual_euclid, st.time_ms,
                            list(st.history[: st.history_len]))
+
+
+@dataclass
+class BatchResult:
+    xs: list
+    status: int
+    statuses: list
+    iterations: list
+    rel_residual: list
+    waves: int
+    graphs: int
+    graph_launches: int
+    tile_lines: int
+    sweep_block: int
+    tune_ms_dst: list
+    tune_ms_sweep: list
+    time_ms: float
+
+
+class Batch:
+    """Many independent KKT instances solved together (owns a kkt_batch). instances: objects
+    with nx, ny, Nt, n_sub, T, nu, omega attributes (e.g. workloads.Workload) or tuples."""
+
+    def __init__(self, instances, *, coarse="exact", variant="multiplicative", pou="left", restart=30,
+                 jhat_sign=-1, residual_norm="l2", Lx=1.0, Ly=1.0):
+        descs = []
+        for w in instances:
+            if isinstance(w, tuple):
+                descs.append(KKTInstance(*w))
+            else:
+                descs.append(KKTInstance(w.nx, w.ny, w.Nt, w.n_sub, w.T, w.nu, w.omega))
+        opt = KKTOptions(PREC["fp64"], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
+                         NORM[residual_norm], 1, ORTH["cgs2"], Lx, Ly)
+        self.b = kkt_batch_create(descs, opt)
+        self.infos = [kkt_batch_get_info(self.b, i) for i in range(len(descs))]
+
+    def __len__(self):
+        return len(self.infos)
+
+    def set_memory_limit(self, nbytes: int) -> None:
+        """Krylov storage per wave in bytes (0: 85% of free device memory)."""
+        kkt_batch_set_memory_limit(self.b, nbytes)
+
+    def close(self):
+        if getattr(self, "b", None):
+            kkt_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, fs, xs=None, tol=1e-8, maxit=420, stream=None) -> BatchResult:
+        if xs is None:
+            xs = [torch.zeros_like(f) for f in fs]
+        st = KKTBatchStats()
+        status = kkt_batch_solve(self.b, fs, xs, tol, maxit, st, stream)
+        n = len(fs)
+        return BatchResult(xs, status, list(st.status[:n]), list(st.iterations[:n]), list(st.rel_residual[:n]),
+                           st.waves, st.graphs, st.graph_launches, st.tile_lines, st.sweep_block,
+                           list(st.tune_ms_dst), list(st.tune_ms_sweep), st.time_ms)

@@ -1,0 +1,162 @@
+"""Batched form: many uneven KKT instances solved together (waves, lockstep FGMRES, one launch
+per phase over all instances, CUDA-graph replay of the preconditioner + matvec phase).
+
+Each instance must behave exactly as its own kkt_solve up to rounding order: the same
+iteration count (+-1) and a solution that matches the oracle's exact solve (Eq 5 diagonalised
+by the sine transform) at the tight tolerance.
+"""
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import problem, spectral
+from oracle.problem import HeatKKT
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def kkt():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2305_04421_gb300.kkt as k
+    k.load_library()
+    return k
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+# uneven sizes: powers of two and not, non-square grids, short and long subdomains, and a spread
+# of nu and omega (several tiles of every batched kernel, ragged tails in each)
+SMALL = [
+    workloads.Workload("b0", nx=32, ny=32, Nt=64, n_sub=4, nu=1.0, omega=1e-4, target="sine-series", seed=11),
+    workloads.Workload("b1", nx=64, ny=64, Nt=128, n_sub=8, nu=0.3, omega=1e-3, target="sine-series", seed=12),
+    workloads.Workload("b2", nx=48, ny=40, Nt=96, n_sub=6, nu=2.0, omega=1e-5, target="cos-mode-noise", seed=13),
+    workloads.Workload("b3", nx=32, ny=64, Nt=64, n_sub=16, nu=0.1, omega=1e-2, target="sine-series", seed=14),
+    workloads.Workload("b4", nx=16, ny=16, Nt=24, n_sub=3, nu=1.0, omega=1e-3, target="cos-mode-noise", seed=15),
+    workloads.Workload("b5", nx=128, ny=128, Nt=32, n_sub=8, nu=5.0, omega=1e-6, target="sine-series", seed=16),
+]
+
+
+def rhs(w):
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    return p, problem.assemble_rhs(p, workloads.make_target(w), None)
+
+
+@pytest.fixture(scope="module")
+def small_case(kkt):
+    ps, fs = zip(*[rhs(w) for w in SMALL])
+    return list(ps), [dev(f) for f in fs]
+
+
+def single(kkt, w, f, tol, coarse="exact"):
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, coarse=coarse, orth="cgs2")
+    r = s.solve(f, tol=tol, maxit=420)
+    s.close()
+    return r
+
+
+@pytest.mark.parametrize("coarse", ["exact", "none"])
+def test_batch_matches_single_instance_solves(kkt, small_case, coarse):
+    ps, fs = small_case
+    b = kkt.Batch(SMALL, coarse=coarse)
+    res = b.solve(fs, tol=1e-8, maxit=420)
+    assert res.status == kkt.KKT_OK
+    for i, w in enumerate(SMALL):
+        ref = single(kkt, w, fs[i], 1e-8, coarse)
+        assert res.statuses[i] == kkt.KKT_OK
+        assert abs(res.iterations[i] - ref.iterations) <= 1, (w.name, res.iterations[i], ref.iterations)
+        assert res.rel_residual[i] <= 1e-8
+        assert rel(host(res.xs[i]), host(ref.x)) < 1e-5
+    # one graph per step index used, replayed once per lockstep step
+    assert res.waves == 1
+    assert res.graphs == min(max(res.iterations), 30)
+    assert res.graph_launches >= max(res.iterations)
+    assert res.tile_lines in (8, 16, 32) and res.sweep_block in (64, 128, 256)
+
+
+def test_batch_tight_solutions_match_the_oracle(kkt, small_case):
+    ps, fs = small_case
+    b = kkt.Batch(SMALL)
+    res = b.solve(fs, tol=1e-12, maxit=420)
+    assert res.status == kkt.KKT_OK
+    for i in range(len(SMALL)):
+        exact = spectral.kkt_exact_solve(ps[i], host(fs[i]))
+        assert rel(host(res.xs[i]), exact) < TOL, SMALL[i].name
+
+
+def test_batch_waves_give_the_same_results(kkt, small_case):
+    ps, fs = small_case
+    one = kkt.Batch(SMALL).solve(fs, tol=1e-8, maxit=420)
+    b = kkt.Batch(SMALL)
+    # the largest instance's storage: several waves, first-fit by decreasing size
+    biggest = max(4 * (31 * 3 + 30) * 2 * w.V for w in SMALL)
+    b.set_memory_limit(biggest)
+    many = b.solve(fs, tol=1e-8, maxit=420)
+    assert many.waves > 1
+    assert many.status == kkt.KKT_OK
+    for i in range(len(SMALL)):
+        assert many.iterations[i] == one.iterations[i]
+        assert rel(host(many.xs[i]), host(one.xs[i])) < 1e-12
+    b.set_memory_limit(1 << 20)            # smaller than any instance: refused, nothing launched
+    with pytest.raises(kkt.KKTError) as e:
+        b.solve(fs, tol=1e-8, maxit=420)
+    assert e.value.status == kkt.KKT_ERR_OOM
+
+
+def test_batch_initial_guess_zero_rhs_and_maxit(kkt, small_case):
+    ps, fs = small_case
+    b = kkt.Batch(SMALL[:3])
+    # the first instance starts from its exact solution, the second has f = 0
+    exact0 = dev(spectral.kkt_exact_solve(ps[0], host(fs[0])))
+    f1 = torch.zeros_like(fs[1])
+    xs = [exact0.clone(), torch.zeros_like(f1), torch.zeros_like(fs[2])]
+    res = b.solve([fs[0], f1, fs[2]], xs, tol=1e-8, maxit=420)
+    assert res.statuses[0] == kkt.KKT_OK and res.iterations[0] == 0
+    assert res.statuses[1] == kkt.KKT_OK and res.iterations[1] == 0
+    assert float(host(res.xs[1]).__abs__().max()) == 0.0
+    assert res.statuses[2] == kkt.KKT_OK and res.iterations[2] > 0
+    # maxit: every instance stops at exactly 3 steps
+    res = b.solve(fs[:3], tol=1e-14, maxit=3)
+    assert res.status == kkt.KKT_NOT_CONVERGED
+    assert res.iterations == [3, 3, 3]
+
+
+def test_batch_rejects_unsupported_options(kkt):
+    opt = kkt.KKTOptions()
+    kkt.load_library().kkt_default_options(opt)
+    opt.precision = kkt.PREC["bf16"]
+    with pytest.raises(kkt.KKTError):
+        kkt.kkt_batch_create([(32, 32, 64, 4, 1.0, 1.0, 1e-4)], opt)
+    with pytest.raises(kkt.KKTError):
+        kkt.kkt_batch_create([(32, 32, 64, 0, 1.0, 1.0, 1e-4)])   # n_sub 0
+
+
+def test_batch_replays_count_their_kernels(kkt, small_case):
+    ps, fs = small_case
+    b = kkt.Batch(SMALL[:2])
+    kkt.kkt_profile_read(reset=True)
+    res = b.solve(fs[:2], tol=1e-8, maxit=420)
+    prof = kkt.kkt_profile_read(reset=True)
+    steps = res.graph_launches
+    # per replay: 4 transform passes, coarse, sweeps, matvec
+    assert prof["graph"]["launches"] == steps
+    assert prof["dst"]["launches"] >= 4 * steps
+    assert prof["matvec"]["launches"] >= steps
+    assert prof["coarse"]["launches"] >= steps and prof["sweep"]["launches"] >= steps
