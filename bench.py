@@ -224,7 +224,7 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -
     else:
         alu_peak = FP64_PEAK_TFLOPS
         alu_kind, alu_src = "alu", "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)"
-        kname = {"dst": "dst_tile_kernel", "multidot": "multidot_kernel", "update": "update_norm_kernel",
+        kname = {"dst": "dst_tile_kernel", "multidot": "mgs_step_kernel", "update": "mgs_step_kernel",
                  "axpy": "axpy_multi_kernel", "matvec": "matvec_kernel", "sweep": "sweep_kernel",
                  "coarse": "coarse_solve_kernel"}.get(top, top)
     t_alu = e["flops"] / (alu_peak * 1e12)
@@ -332,6 +332,28 @@ def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
     return out
 
 
+def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, steps: int, warmup: int) -> dict:
+    """The headline workload's solve in the other FGMRES configurations: the spectral basis
+    (f and x transformed once, no transforms inside the iteration) and CGS2 orthogonalisation
+    (the MGS default's alternative). Same tolerance, x_0 = 0, device time per solve."""
+    import torch
+
+    ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
+    out = {}
+    for name, opts in (("spectral_basis", {"basis": "spectral"}), ("cgs2", {"orth": "cgs2"}),
+                       ("spectral_basis_cgs2", {"basis": "spectral", "orth": "cgs2"})):
+        s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, **opts)
+        f = s.build_rhs(ut)
+        ms, res, x = time_solves(kkt_mod, s, f, steps, warmup)
+        out[name] = {"solve_ms": ms, "solves_per_s": 1e3 / ms, "iterations": res.iterations,
+                     "rel_residual": res.rel_residual, "converged": res.status == kkt_mod.KKT_OK,
+                     "speedup_vs_headline": physical_ms / ms}
+        del f, x
+        s.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def measure_batched(kkt_mod, dev) -> dict:
     """The 64 uneven instances of the batched workload (sizes 64^2..256^2, Nt 128..1024, N_D
     8..64, spread nu and omega): one batched solve (memory waves, one launch per phase over all
@@ -394,6 +416,116 @@ def measure_batched(kkt_mod, dev) -> dict:
     del fs
     torch.cuda.empty_cache()
     return out
+
+
+def measure_learned(kkt_mod, dev) -> dict:
+    """Learned-vs-plain judge on the 256 x 256, Nt = 2048, N_D = 256 workload (m = 8): the
+    network (in 2 N_D + 2 -> 512 -> 512 -> 2 N_D, ReLU) is trained on the GPU on exact coarse
+    solves of modes k, l < 32 with (nu, omega) drawn log-uniform from [0.1, 10] x [1e-6, 1e-2],
+    then every form solves the same seeded right-hand side to 1e-8 from x_0 = 0: one-level RASQ,
+    the exact two-level method, the learned coarse correction, its ablation (no coarse
+    correction on the learned modes), and TF32 transforms with the exact and the learned coarse
+    level. Cases: the workload's own (nu, omega) = (1, 1e-4) and one held-out pair (seed 5)."""
+    import torch
+
+    w0 = workloads.CFG_LEARNED
+    rng = np.random.Generator(np.random.PCG64(5))
+    nu_h, om_h = float(10 ** rng.uniform(-1, 1)), float(10 ** rng.uniform(-6, -2))
+    cases = [w0, workloads.Workload("held-out", nx=w0.nx, ny=w0.ny, Nt=w0.Nt, n_sub=w0.n_sub, nu=nu_h, omega=om_h,
+                                    target=w0.target, seed=5)]
+    net = kkt_mod.Mlp()
+    t0 = time.perf_counter()
+    st = net.train()
+    out = {"workload": f"nx=ny={w0.nx} Nt={w0.Nt} N_D={w0.n_sub}, sine-series targets",
+           "training": {"seconds": time.perf_counter() - t0, "samples": st.samples, "adam_steps": st.steps,
+                        "final_train_loss": st.final_train_loss, "val_loss": st.val_loss,
+                        "val_cosine": st.val_cosine, "modes_learned": f"k, l < {net.cfg.modes}",
+                        "width": net.cfg.width}}
+    forms = [("one_level", "fp64", "none", None), ("exact", "fp64", "exact", None),
+             ("learned", "fp64", "learned", "learned"), ("learned_ablation", "fp64", "learned", "none"),
+             ("tf32_exact", "tf32", "exact", None), ("tf32_learned", "tf32", "learned", "learned")]
+    stream = torch.cuda.current_stream()
+    for w in cases:
+        ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
+        res_case = {"nu": w.nu, "omega": w.omega}
+        for name, prec, coarse, mode in forms:
+            s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=prec)
+            if mode is not None:
+                s.attach_mlp(net, mode)
+            s.set_options(precision=prec, coarse=coarse)
+            f = s.build_rhs(ut)
+            x = torch.zeros_like(f)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = s.solve(f, x, tol=TOL, maxit=MAXIT)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            entry = {"iterations": r.iterations, "solve_ms": e0.elapsed_time(e1),
+                     "converged": r.status == kkt_mod.KKT_OK, "rel_residual": r.rel_residual}
+            if mode == "learned":
+                kept, fb = s.learned_stats()
+                entry["learned_corrections_kept"] = kept
+                entry["exact_fallbacks"] = fb
+            res_case[name] = entry
+            del f, x
+            s.close()
+            torch.cuda.empty_cache()
+        base = res_case["exact"]["solve_ms"]
+        res_case["time_vs_exact_fp64"] = {k: res_case[k]["solve_ms"] / base for k, *_ in forms}
+        out["case_" + ("workload" if w is w0 else "held_out")] = res_case
+    net.close()
+    return out
+
+
+def run_study(args):
+    """Section 4's experiment on this GPU: one-level RASQ against the two-level preconditioner,
+    iterations of FGMRES(30) to a 1e-6 relative residual (max 420) on the paper's problem:
+    (0,1) x (0,2), 17 x 17 mesh points, T = 1, nu = 1, u_0 = -x y (x-1)(y-2),
+    u~ = sin 2 pi t sin 2 pi x sin 2 pi y (Eq 16). Figure 1: Nt = 100 .. 3200 with 80, 20 and 5
+    steps per subdomain (N_D = Nt / m rounded, at least 1) and omega in {1e-2, 1e-3, 1e-4};
+    Figure 2: omega = 1e-2 .. 1e-6 at Nt = 800 with 40 subdomains; the mesh sweep of the text
+    (9, 17, 33 points). The residual is the unweighted Euclidean ||f - K x|| / ||f|| (its
+    rounding floor is far below 1e-6 at these sizes). One JSON line on stdout."""
+    import torch
+
+    import paper_2305_04421_gb300.kkt as kkt
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+
+    def iterations(nx, Nt, n_sub, omega, coarse):
+        w = workloads.Workload("paper", nx=nx, ny=nx, Nt=Nt, n_sub=n_sub, Lx=1.0, Ly=2.0, omega=omega,
+                               target="paper", u0="paper")
+        s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, coarse=coarse, residual_norm="euclidean",
+                       Lx=1.0, Ly=2.0)
+        f = s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev),
+                        torch.from_numpy(workloads.make_u0(w).ravel()).to(dev))
+        r = s.solve(f, tol=1e-6, maxit=420)
+        s.close()
+        return r.iterations if r.status == kkt.KKT_OK else None   # None: not converged in 420
+
+    t0 = time.perf_counter()
+    fig1 = []
+    for omega in (1e-2, 1e-3, 1e-4):
+        for m in (80, 20, 5):
+            for Nt in (100, 200, 400, 800, 1600, 3200):
+                nd = max(1, round(Nt / m))
+                fig1.append({"omega": omega, "steps_per_subdomain": m, "Nt": Nt, "n_sub": nd,
+                             "one_level": iterations(16, Nt, nd, omega, "none"),
+                             "two_level": iterations(16, Nt, nd, omega, "exact")})
+    fig2 = [{"omega": om, "Nt": 800, "n_sub": 40, "one_level": iterations(16, 800, 40, om, "none"),
+             "two_level": iterations(16, 800, 40, om, "exact")} for om in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6)]
+    mesh = [{"mesh_points": nx + 1, "Nt": 400, "n_sub": 20, "omega": 1e-4,
+             "one_level": iterations(nx, 400, 20, 1e-4, "none"), "two_level": iterations(nx, 400, 20, 1e-4, "exact")}
+            for nx in (8, 16, 32)]
+    two = [r["two_level"] for r in fig1 + fig2 if r["two_level"] is not None]
+    print(json.dumps({"study": "Section 4 replication (Eq 16 problem): one-level vs two-level FGMRES iterations",
+                      "tol": 1e-6, "maxit": 420, "seconds": time.perf_counter() - t0,
+                      "two_level_iterations_min_max": [min(two), max(two)],
+                      "fig1": fig1, "fig2": fig2, "mesh": mesh}))
+    return 0
 
 
 def run_ours(args):
@@ -486,9 +618,12 @@ def run_ours(args):
     del f, x, f_host, x_host
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_forms:
+        line["variants"] = measure_variants(kkt, dev, w, ms / args.steps, steps=2, warmup=1)
         line["forms"] = measure_forms(kkt, dev, steps=2, warmup=1)
     if rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = measure_batched(kkt, dev)
+    if rank == 0 and world == 1 and not args.no_learned:
+        line["learned"] = measure_learned(kkt, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s, sample = oracle_iteration_sample(w, min(its, 30) // 2 + 1)
         line["cpu_baseline"] = {"value": 1.0 / (s * its), "unit": "solves/s", "cores": cpu_threads(),
@@ -510,11 +645,17 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=32,
                     help="iterations the reference arm scales its per-iteration sample by")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--study", choices=["paper"], default=None,
+                    help="run Section 4's one- vs two-level iteration study instead of the benchmark")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-vs-plain coarse comparison on the 256 x 256, Nt = 2048 workload")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-instance batched vs one-after-another comparison")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64/BF16/TF32 time-to-solution comparison on the 512 x 512 workload")
     args = ap.parse_args()
+    if args.study == "paper":
+        return run_study(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

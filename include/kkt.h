@@ -86,6 +86,20 @@ enum kkt_orth {
   KKT_ORTH_CGS2 = 1
 };
 
+/* Basis the FGMRES iteration runs in. */
+enum kkt_basis {
+  /* grid values, as Eq 5 is written: every preconditioner apply does a forward and an inverse
+   * 2D sine transform of the w block, every matvec is the 5-point stencil */
+  KKT_BASIS_PHYSICAL = 0,
+  /* sine-mode coefficients: f and x are transformed once (the orthonormal 2D DST-I of every
+   * block, its own inverse), the iteration then runs without transforms (the preconditioner's
+   * sweeps and coarse solve act per mode, the matvec's stencil becomes a product per mode), and
+   * x is transformed back at exit. The transform is orthonormal and the residual weights are
+   * per block, so inner products, norms and hence the iterates are those of the physical basis
+   * in exact arithmetic. FP64 only. */
+  KKT_BASIS_SPECTRAL = 1
+};
+
 /* Owner of the time node shared by neighbouring subdomains (boolean partition of unity D_s). */
 enum kkt_pou {
   KKT_POU_LEFT = 0,   /* the subdomain whose last step ends on the node */
@@ -103,6 +117,7 @@ typedef struct kkt_options {
   int tc_split;     /* BF16 / TF32 only: 1 (default) every tensor-core transform uses hi + lo operands
                        (three products, FP32 accumulation); 0 single operands */
   int orth;         /* enum kkt_orth, default KKT_ORTH_MGS */
+  int basis;        /* enum kkt_basis, default KKT_BASIS_PHYSICAL */
   double Lx, Ly;    /* domain (0,Lx) x (0,Ly), default 1, 1 */
 } kkt_options;
 
@@ -333,6 +348,10 @@ int kkt_batch_get_info(const kkt_batch* b, int i, kkt_info* info);
  * the default). A smaller cap gives more, smaller waves; an instance larger than the cap fails
  * the solve with KKT_ERR_OOM. */
 int kkt_batch_set_memory_limit(kkt_batch* b, long long bytes);
+/* on != 0 (default): the preconditioner + matvec phase of each Arnoldi step index is captured
+ * once per wave as a CUDA graph and replayed; 0: its kernels are launched directly every step
+ * (same kernels and results; their device time is then profiled per kernel class). */
+int kkt_batch_set_graphs(kkt_batch* b, int on);
 /* Solve K_i x_i = f_i for every instance. f, x: host arrays of count DEVICE pointers, 3 V_i
  * doubles each; x_i holds the initial guess on entry. Synchronises `stream`. Returns KKT_OK
  * when every instance converged, KKT_NOT_CONVERGED if some stopped at maxit, else the most

@@ -125,6 +125,46 @@ __global__ void __launch_bounds__(kThreads) axpby_b(const Seg* __restrict__ segs
   }
 }
 
+// One modified Gram-Schmidt step k for every instance: with AXPY, w -= c V_k where
+// c = dots[inst][k] * sc[inst][k] (zero: the instance is left as it is); then the partial of
+// <V_k+1, w> (DOTV) or <w, w> over the updated w. V_k = V + k stride of the segment.
+template <bool AXPY, bool DOTV>
+__global__ void __launch_bounds__(kThreads) mgs_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+                                                  int nj, long long total, int k, const double* __restrict__ dots,
+                                                  const double* __restrict__ sc, int ld, double* __restrict__ part) {
+  __shared__ double sh[32];
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int q = find_seg(prefix, nj, t);
+    const Seg S = segs[q];
+    const double c = AXPY ? dots[q * ld + k] * sc[q * ld + k] : 0.0;
+    const double* Vk = S.V + (AXPY ? k : 0) * S.stride;
+    const double* Vn = S.V + (k + 1) * S.stride;
+    const long long e0 = (t - prefix[q]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    double acc = 0.0;
+    for (long long i = e0 + threadIdx.x; i < e1; i += kThreads) {
+      double wi = S.w[i];
+      if (AXPY && c != 0.0) {
+        wi = fma(-c, Vk[i], wi);
+        S.w[i] = wi;
+      }
+      acc = fma(DOTV ? Vn[i] : wi, wi, acc);
+    }
+    const double r = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[t] = r;
+  }
+}
+
+// out[inst * ld + col] = sum of part[t] over the instance's items
+__global__ void finalize_col_b(const double* __restrict__ part, const long long* __restrict__ prefix, int nj,
+                               double* __restrict__ out, int ld, int col) {
+  const int inst = blockIdx.x;
+  if (inst >= nj) return;
+  double acc = 0.0;
+  for (long long t = prefix[inst] + threadIdx.x; t < prefix[inst + 1]; t += 32) acc += part[t];
+  acc = warp_sum(acc);
+  if (threadIdx.x == 0) out[inst * ld + col] = acc;
+}
+
 // out[inst][v] = sum of part[t][v] over the instance's items, one warp per (inst, v)
 __global__ void finalize_b(const double* __restrict__ part, const long long* __restrict__ prefix, int nj, int width,
                            double* __restrict__ out) {
@@ -226,6 +266,7 @@ struct kkt_batch {
   double tune_ms_dst[3] = {0, 0, 0};
   double tune_ms_sweep[3] = {0, 0, 0};
   long long mem_limit = 0;    // bytes of Krylov storage per wave; 0: 85% of the free device memory
+  int use_graphs = 1;         // replay the preconditioner + matvec phase as CUDA graphs
 };
 
 using namespace kkt;
@@ -281,6 +322,12 @@ void kkt_batch_destroy(kkt_batch* b) {
   if (!b) return;
   for (kkt_handle* h : b->inst) kkt_destroy(h);
   delete b;
+}
+
+int kkt_batch_set_graphs(kkt_batch* b, int on) {
+  if (!b) return set_error(KKT_ERR_INVALID_ARG, "null batch");
+  b->use_graphs = on != 0;
+  return KKT_OK;
 }
 
 int kkt_batch_set_memory_limit(kkt_batch* b, long long bytes) {
@@ -647,7 +694,10 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         }
         for (int k = 0; k < nw; ++k) h_scale[k] = 1.0 / S[k]->eta[j];
         KKT_CUDA_TRY(cudaMemcpyAsync(d_scale, h_scale, sizeof(double) * nw, cudaMemcpyHostToDevice, st));
-        if (!graphs[j]) {
+        if (!b->use_graphs) {
+          rc = phase_launch(slots[j], st);
+          if (rc != KKT_OK) break;
+        } else if (!graphs[j]) {
           cudaStream_t cs_ = nullptr;
           KKT_CUDA_TRY(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
           cudaGraph_t gr = nullptr;
@@ -666,9 +716,11 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
           cudaGraphDestroy(gr);
           ++graphs_made;
         }
-        rc = prof_graph_launch(graphs[j], graph_work[j], st);
-        if (rc != KKT_OK) break;
-        ++graph_launches;
+        if (b->use_graphs) {
+          rc = prof_graph_launch(graphs[j], graph_work[j], st);
+          if (rc != KKT_OK) break;
+          ++graph_launches;
+        }
         // Gram-Schmidt of the new vectors against each instance's basis (CGS, one conditional repeat)
         std::vector<Seg> sn(nw);
         for (int k = 0; k < nw; ++k) {
@@ -679,7 +731,43 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         if (rc != KKT_OK) break;
         std::vector<double> wn2(nw, 0.0), before(nw, 0.0);
         std::vector<char> need(nw, 1);
-        for (int pass = 0; pass < 2 && rc == KKT_OK; ++pass) {
+        if (b->opt.orth == KKT_ORTH_MGS) {
+          // modified Gram-Schmidt, step k over all instances at once; the dots stay on the
+          // device (d_out[inst][k]) and feed the next step, the host reads the columns once
+          for (int k = 0; k < nw; ++k)
+            for (int i = 0; i <= j; ++i)
+              h_coef[k * 33 + i] = S[k]->cycle_done ? 0.0 : 1.0 / (S[k]->eta[i] * S[k]->eta[i]);
+          KKT_CUDA_TRY(cudaMemcpyAsync(d_coef, h_coef, sizeof(double) * 33 * nw, cudaMemcpyHostToDevice, st));
+          const unsigned grid = static_cast<unsigned>(std::min<long long>(t_new.total, persistent_grid()));
+          for (int k = -1; k <= j && rc == KKT_OK; ++k) {
+            {
+              const double el = t_new.elems;
+              ProfScope ps(k < 0 ? KKT_K_MULTIDOT : KKT_K_UPDATE, st, (k < 0 ? 2.0 : 4.0) * el,
+                           8.0 * el * (k < 0 ? 2.0 : (k < j ? 4.0 : 3.0)));
+              if (k < 0)
+                mgs_b<false, true><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nw, t_new.total, -1, d_out,
+                                                              d_coef, 33, part);
+              else if (k < j)
+                mgs_b<true, true><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nw, t_new.total, k, d_out,
+                                                             d_coef, 33, part);
+              else
+                mgs_b<true, false><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nw, t_new.total, k, d_out,
+                                                              d_coef, 33, part);
+              if (cudaGetLastError() != cudaSuccess) rc = set_error(KKT_ERR_CUDA, "batched MGS launch failed");
+            }
+            ProfScope ps(KKT_K_REDUCE, st);
+            finalize_col_b<<<nw, 32, 0, st>>>(part, t_new.prefix, nw, d_out, 33, k + 1);
+          }
+          if (rc != KKT_OK) break;
+          KKT_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, sizeof(double) * 33 * nw, cudaMemcpyDeviceToHost, st));
+          KKT_CUDA_TRY(cudaStreamSynchronize(st));
+          for (int k = 0; k < nw; ++k) {
+            InstState& I = *S[k];
+            for (int i = 0; i <= j; ++i) Hs(I, i, j) = I.cycle_done ? 0.0 : h_out[k * 33 + i] / I.eta[i];
+            wn2[k] = h_out[k * 33 + j + 1];
+          }
+        }
+        for (int pass = 0; pass < 2 && rc == KKT_OK && b->opt.orth == KKT_ORTH_CGS2; ++pass) {
           rc = dispatch<MultidotB>(j + 1, t_new.dev, t_new.prefix, nw, t_new.total, part, 2.0 * t_new.elems, st);
           if (rc != KKT_OK) break;
           rc = finalize(t_new, j + 2);

@@ -326,6 +326,7 @@ int kkt_default_options(kkt_options* opt) {
   opt->residual_norm = KKT_NORM_L2;
   opt->tc_split = 1;
   opt->orth = KKT_ORTH_MGS;
+  opt->basis = KKT_BASIS_PHYSICAL;
   opt->Lx = 1.0;
   opt->Ly = 1.0;
   return KKT_OK;
@@ -391,6 +392,8 @@ void kkt_destroy(kkt_handle* h) {
   cudaFree(h->learn_x);
   cudaFree(h->learn_count);
   if (h->dd.base) cudaFree(h->dd.base);
+  cudaFree(h->ks_f);
+  cudaFree(h->ks_x);
   cudaFree(h->d_lx);
   cudaFree(h->d_ly);
   cudaFree(h->spec);
@@ -427,6 +430,10 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
     return set_error(KKT_ERR_INVALID_ARG, "residual_norm out of range");
   if (opt->tc_split != 0 && opt->tc_split != 1) return set_error(KKT_ERR_INVALID_ARG, "tc_split must be 0 or 1");
   if (opt->orth != KKT_ORTH_MGS && opt->orth != KKT_ORTH_CGS2) return set_error(KKT_ERR_INVALID_ARG, "orth out of range");
+  if (opt->basis != KKT_BASIS_PHYSICAL && opt->basis != KKT_BASIS_SPECTRAL)
+    return set_error(KKT_ERR_INVALID_ARG, "basis out of range");
+  if (opt->basis == KKT_BASIS_SPECTRAL && opt->precision != KKT_PREC_FP64)
+    return set_error(KKT_ERR_UNSUPPORTED, "the spectral basis runs the FP64 preconditioner (it has no transforms)");
   if (!finite_pos(opt->Lx) || !finite_pos(opt->Ly)) return set_error(KKT_ERR_INVALID_ARG, "Lx, Ly must be positive");
   // with the shared node given to the later subdomain, the first subdomain owns nodes
   // 1 .. b_1 - 1; its linear coarse function needs two of them
@@ -613,6 +620,7 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   const Geometry& g = h->g;
   const long long V = g.V, n3 = 3 * V;
   KKT_TRY(ensure_krylov(h));
+  const bool spectral = h->opt.basis == KKT_BASIS_SPECTRAL;
   const bool dev_f = is_device_ptr(f), dev_x = is_device_ptr(x);
   const double* df = f;
   double* dx = x;
@@ -626,6 +634,29 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
     KKT_CUDA_TRY(cudaMemcpyAsync(h->kx, x, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
     dx = h->kx;
   }
+  // physical-space f and x on the device; in the spectral basis the iteration runs on their
+  // sine-mode coefficients (every block through the orthonormal 2D DST-I, which is its own
+  // inverse), and x is transformed back once at exit
+  const double* pf = df;
+  double* px = dx;
+  if (spectral) {
+    if (!h->ks_f) KKT_TRY(dev_alloc(h, &h->ks_f, n3));
+    if (!h->ks_x) KKT_TRY(dev_alloc(h, &h->ks_x, n3));
+    for (int b = 0; b < 3; ++b) {
+      KKT_TRY(dst2d(h, pf + b * V, h->ks_f + b * V, st));
+      KKT_TRY(dst2d(h, px + b * V, h->ks_x + b * V, st));
+    }
+    df = h->ks_f;
+    dx = h->ks_x;
+  }
+  auto matvec = [&](const double* u, double su, const double* z, double sz, const double* w, double sw, double* y,
+                    double ou, double oz, double ow) -> int {
+    return spectral ? launch_matvec_spectral(h, u, su, z, sz, w, sw, y, st, ou, oz, ow)
+                    : launch_matvec(h, u, su, z, sz, w, sw, y, st, ou, oz, ow);
+  };
+  auto precond_w = [&](const double* rw, double scale, double* yw) -> int {
+    return spectral ? spectral_schur_precond(h, rw, yw, scale, st) : schur_precond_w(h, rw, scale, yw, st);
+  };
   const int m = h->opt.restart;
   double* Vb = h->kV;
   double* Zw = h->kZw;
@@ -638,11 +669,14 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   double fnorm_plain = 0.0;
   std::function<double()> euclid_residual;
   auto finish = [&](int status, double rel) -> int {
+    if (spectral)
+      for (int b = 0; b < 3; ++b)
+        if (dst2d(h, dx + b * V, px + b * V, st) < 0 && status >= 0) status = KKT_ERR_CUDA;
     if (status >= 0 && std::isfinite(rel) && fnorm_plain > 0.0 && euclid_residual)
       local.rel_residual_euclid = euclid_residual();
     if (status >= 0 && h->opt.precision != KKT_PREC_FP64 && tc_check(h->tc, st) < 0) status = KKT_ERR_TIMEOUT;
     if (!dev_x) {
-      cudaMemcpyAsync(x, dx, n3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+      cudaMemcpyAsync(x, px, n3 * sizeof(double), cudaMemcpyDeviceToHost, st);
       cudaStreamSynchronize(st);
     }
     local.status = status;
@@ -683,18 +717,18 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   }
   // V_0 = D (f - K x), beta = ||V_0||
   auto residual = [&](double& beta) -> int {
-    KKT_TRY(launch_matvec(h, dx, 1.0, dx + V, 1.0, dx + 2 * V, 1.0, Vb, st, du, dz, dw));
+    KKT_TRY(matvec(dx, 1.0, dx + V, 1.0, dx + 2 * V, 1.0, Vb, du, dz, dw));
     for (int k = 0; k < 3; ++k) KKT_TRY(launch_axpby(dblk[k], df + k * V, -1.0, Vb + k * V, Vb + k * V, V, st));
     KKT_TRY(krylov_norm2(h, Vb, n3, st));
     KKT_TRY(fetch(1));
     beta = std::sqrt(hr[0]);
     return KKT_OK;
   };
-  // unweighted relative residual of x, into the stats (uses V_1 as scratch)
+  // unweighted relative residual of x (physical space), into the stats (uses V_1 as scratch)
   euclid_residual = [&]() -> double {
     double* R = Vb + n3;
-    if (launch_matvec(h, dx, 1.0, dx + V, 1.0, dx + 2 * V, 1.0, R, st) < 0) return NAN;
-    if (launch_axpby(1.0, df, -1.0, R, R, n3, st) < 0) return NAN;
+    if (launch_matvec(h, px, 1.0, px + V, 1.0, px + 2 * V, 1.0, R, st) < 0) return NAN;
+    if (launch_axpby(1.0, pf, -1.0, R, R, n3, st) < 0) return NAN;
     if (krylov_norm2(h, R, n3, st) < 0 || fetch(1) < 0) return NAN;
     return std::sqrt(hr[0]) / fnorm_plain;
   };
@@ -716,10 +750,10 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
       double* Zj = Zw + static_cast<size_t>(j) * V;
       // z_j = P^{-1} D^{-1} v_j: the u, z blocks are scalings (folded into the matvec), the
       // w block goes through S-hat_2level^{-1}; then W = D K z_j
-      KKT_TRY(schur_precond_w(h, Vj + 2 * V, 1.0 / (dw * eta[j]), Zj, st));
+      KKT_TRY(precond_w(Vj + 2 * V, 1.0 / (dw * eta[j]), Zj));
       local.precond_applies++;
-      KKT_TRY(launch_matvec(h, Vj, 1.0 / (g.h * du * eta[j]), Vj + V, 1.0 / (g.omega * g.h * dz * eta[j]), Zj, 1.0,
-                            W, st, du, dz, dw));
+      KKT_TRY(matvec(Vj, 1.0 / (g.h * du * eta[j]), Vj + V, 1.0 / (g.omega * g.h * dz * eta[j]), Zj, 1.0, W, du, dz,
+                     dw));
       for (int k = 0; k <= j; ++k) Hs(k, j) = 0.0;
       double wnorm2 = 0.0;
       if (h->opt.orth == KKT_ORTH_MGS) {

@@ -33,30 +33,78 @@ __device__ __forceinline__ int bit_reverse(int v, int bits) {
   return bits > 0 ? static_cast<int>(__brev(static_cast<unsigned>(v)) >> (32 - bits)) : 0;
 }
 
+// Complex product v w (4 FP64 instructions).
+__device__ __forceinline__ double2 cmul(double2 v, double2 w) {
+  return make_double2(fma(v.x, w.x, -v.y * w.y), fma(v.x, w.y, v.y * w.x));
+}
+
 // One warp, one line x[0..n-2] (x[j-1] holds the j-th point), in place. buf: n/2 double2.
+// FP64 is the bound on this part (2 DFMA-pipe instructions per clock per SM), so the line is
+// arranged to spend as few FP64 instructions as possible: the orthonormal scale is folded into
+// the pre-processing weights (y_j = w+_j x_j + w-_j x_n-j), stages 1 and 2 of the FFT (twiddles
+// 1 and -i) are one radix-4 pass of additions only, later stages go two at a time as radix-4
+// passes (3 complex products per 4 points instead of 4), and R_0 / 2 is taken out of the
+// prefix sum once per lane instead of per output.
 __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int lane) {
   const int n = L.n, P = n >> 1, logp = L.logn - 1;
+  const double2* pw = reinterpret_cast<const double2*>(L.pre);   // c (sin + 1/2), c (sin - 1/2)
   for (int j = lane; j < n; j += 32) {
     double yj = 0.0;
     if (j > 0) {
       const double a = x[j - 1], b = x[n - j - 1];
-      yj = fma(L.pre[j <= P ? j : n - j], a + b, 0.5 * (a - b));
+      const double2 q = pw[j <= P ? j : n - j];
+      yj = fma(q.x, a, q.y * b);
     }
     reinterpret_cast<double*>(buf + bit_reverse(j >> 1, logp))[j & 1] = yj;
   }
   __syncwarp();
-  for (int s = 1; s <= logp; ++s) {
+  int s = 1;
+  if (logp >= 2) {
+    // stages 1 and 2: pairs (0,1), (2,3) with twiddle 1, then (0,2) with 1 and (1,3) with -i
+    for (int b = lane; b < (P >> 2); b += 32) {
+      double2* p = buf + 4 * b;
+      const double2 a0 = p[0], a1 = p[1], a2 = p[2], a3 = p[3];
+      const double2 b0 = make_double2(a0.x + a1.x, a0.y + a1.y), b1 = make_double2(a0.x - a1.x, a0.y - a1.y);
+      const double2 b2 = make_double2(a2.x + a3.x, a2.y + a3.y), b3 = make_double2(a2.x - a3.x, a2.y - a3.y);
+      p[0] = make_double2(b0.x + b2.x, b0.y + b2.y);
+      p[2] = make_double2(b0.x - b2.x, b0.y - b2.y);
+      p[1] = make_double2(b1.x + b3.y, b1.y - b3.x);   // b1 + (-i) b3
+      p[3] = make_double2(b1.x - b3.y, b1.y + b3.x);
+    }
+    __syncwarp();
+    s = 3;
+  }
+  // stages s, s+1 merged: with W = exp(-2 pi i / 2^(s+1)) and k the position in the group,
+  // p0 = a0, p1 = W^k a2, p2 = W^2k a1, p3 = W^3k a3 (a_r at distance r 2^(s-1)), outputs
+  // (p0 + p2) +- (p1 + p3) and (p0 - p2) -+ i (p1 - p3); tw[m] = exp(-2 pi i m / P)
+  for (; s + 1 <= logp; s += 2) {
+    const int half = 1 << (s - 1), tsh = logp - s - 1;
+    for (int b = lane; b < (P >> 2); b += 32) {
+      const int k = b & (half - 1);
+      const int i0 = ((b >> (s - 1)) << (s + 1)) + k;
+      const double2 p0 = buf[i0];
+      const double2 p2 = cmul(buf[i0 + half], L.tw[(2 * k) << tsh]);
+      const double2 p1 = cmul(buf[i0 + 2 * half], L.tw[k << tsh]);
+      const double2 p3 = cmul(buf[i0 + 3 * half], L.tw[(3 * k) << tsh]);
+      const double2 S = make_double2(p0.x + p2.x, p0.y + p2.y), T = make_double2(p1.x + p3.x, p1.y + p3.y);
+      const double2 U = make_double2(p0.x - p2.x, p0.y - p2.y), D = make_double2(p1.x - p3.x, p1.y - p3.y);
+      buf[i0] = make_double2(S.x + T.x, S.y + T.y);
+      buf[i0 + 2 * half] = make_double2(S.x - T.x, S.y - T.y);
+      buf[i0 + half] = make_double2(U.x + D.y, U.y - D.x);       // U - i D
+      buf[i0 + 3 * half] = make_double2(U.x - D.y, U.y + D.x);   // U + i D
+    }
+    __syncwarp();
+  }
+  if (s == logp) {   // one radix-2 stage left
     const int half = 1 << (s - 1);
     for (int b = lane; b < (P >> 1); b += 32) {
       const int k = b & (half - 1);
       const int i0 = ((b >> (s - 1)) << s) + k;
       const int i1 = i0 + half;
-      const double2 w = L.tw[k << (logp - s)];
-      const double2 u = buf[i0], v = buf[i1];
-      const double tr = fma(v.x, w.x, -v.y * w.y);
-      const double ti = fma(v.x, w.y, v.y * w.x);
-      buf[i0] = make_double2(u.x + tr, u.y + ti);
-      buf[i1] = make_double2(u.x - tr, u.y - ti);
+      const double2 u = buf[i0];
+      const double2 t = cmul(buf[i1], L.tw[k << (logp - s)]);
+      buf[i0] = make_double2(u.x + t.x, u.y + t.y);
+      buf[i1] = make_double2(u.x - t.x, u.y - t.y);
     }
     __syncwarp();
   }
@@ -64,20 +112,19 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
   const int chunk = P >= 32 ? P / 32 : 1;
   const int k0 = lane * chunk;
   const bool active = k0 < P;
-  const double c = L.scale;
   double total = 0.0;
   if (active) {
     for (int t = 0; t < chunk; ++t) {
       const int k = k0 + t;
       const double2 zk = buf[k];
       const double2 zc = buf[(P - k) & (P - 1)];
-      const double er = zk.x + zc.x, ei = zk.y - zc.y;     // Z_k + conj(Z_{P-k})
+      const double er = zk.x + zc.x, nei = zc.y - zk.y;    // Z_k + conj(Z_{P-k}) (imaginary part negated)
       const double orr = zk.y + zc.y, oi = zc.x - zk.x;    // (Z_k - conj(Z_{P-k})) / i
       const double2 w = L.post[k];                         // exp(-2 pi i k / n)
       const double yr = fma(w.x, orr, fma(-w.y, oi, er));
-      const double yi = fma(w.x, oi, fma(w.y, orr, ei));
-      if (k > 0) x[2 * k - 1] = -c * yi;                   // S_2k = I_k = -Im Y_k
-      total += (k == 0) ? 0.5 * yr : yr;                   // R_0 / 2 + R_1 + ... + R_k
+      const double nyi = fma(-w.x, oi, fma(-w.y, orr, nei));
+      if (k > 0) x[2 * k - 1] = nyi;                       // S_2k = I_k = -Im Y_k
+      total += yr;                                         // R_0 + R_1 + ... + R_k
       x[2 * k] = total;
     }
   }
@@ -87,9 +134,11 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
     if (lane >= o) incl += v;
   }
   const double prev = __shfl_up_sync(0xffffffffu, incl, 1);
-  const double excl = lane == 0 ? 0.0 : prev;
+  // S_2k+1 = R_0 / 2 + R_1 + ... + R_k: the exclusive prefix of the lanes before, less R_0 / 2
+  // (R_0 = 2 (Z_0.x + Z_0.y) in the times-2 convention)
+  const double corr = (lane == 0 ? 0.0 : prev) - (buf[0].x + buf[0].y);
   if (active)
-    for (int t = 0; t < chunk; ++t) x[2 * (k0 + t)] = c * (x[2 * (k0 + t)] + excl);
+    for (int t = 0; t < chunk; ++t) x[2 * (k0 + t)] += corr;
   __syncwarp();
 }
 
@@ -197,7 +246,6 @@ DstLaunch make_launch(const DstPlan& p, const double* in, double* out, int mode,
   L.cols = cols;
   L.slice = slice;
   L.tiles_per_slice = (cols + L.tile_lines - 1) / L.tile_lines;
-  L.scale = 1.0 / std::sqrt(2.0 * p.n);
   L.pre = p.d_pre;
   L.tw = p.d_tw;
   L.post = p.d_post;
@@ -235,9 +283,13 @@ int dst_plan_create(DstPlan& p, int n) {
   while ((1 << lg) < n) ++lg;
   p.logn = ((1 << lg) == n && n >= 4) ? lg : -1;
   const double pi = 3.14159265358979323846;
-  std::vector<double> pre(n / 2 + 1), sintab(2 * n);
-  std::vector<double2> tw(std::max(n / 4, 1)), post(n / 2 + 1);
-  for (int j = 0; j <= n / 2; ++j) pre[j] = std::sin(j * pi / n);
+  std::vector<double> pre(2 * (n / 2 + 1)), sintab(2 * n);
+  std::vector<double2> tw(std::max(n / 2, 1)), post(n / 2 + 1);
+  const double c = 1.0 / std::sqrt(2.0 * n);   // orthonormal scale of the FFT path's outputs
+  for (int j = 0; j <= n / 2; ++j) {
+    pre[2 * j] = c * (std::sin(j * pi / n) + 0.5);
+    pre[2 * j + 1] = c * (std::sin(j * pi / n) - 0.5);
+  }
   for (int k = 0; k < static_cast<int>(tw.size()); ++k)
     tw[k] = make_double2(std::cos(2 * pi * k / (n / 2)), -std::sin(2 * pi * k / (n / 2)));
   for (int k = 0; k <= n / 2; ++k) post[k] = make_double2(std::cos(2 * pi * k / n), -std::sin(2 * pi * k / n));

@@ -33,8 +33,9 @@ int set_error(int status, const std::string& msg);
 struct DstPlan {
   int n = 0;          // intervals; the transform has n-1 points
   int logn = 0;       // log2(n) when n is a power of two, else -1 (direct transform)
-  double* d_pre = nullptr;    // sin(j pi / n), j = 0..n/2 (pre-processing weights)
-  double2* d_tw = nullptr;    // exp(-2 pi i k / (n/2)), k = 0..n/4-1 (FFT twiddles)
+  double* d_pre = nullptr;    // pairs c (sin(j pi / n) + 1/2), c (sin(j pi / n) - 1/2), j = 0..n/2,
+                              // c = 1 / sqrt(2n) (pre-processing weights with the scale folded in)
+  double2* d_tw = nullptr;    // exp(-2 pi i k / (n/2)), k = 0..n/2-1 (FFT twiddles)
   double2* d_post = nullptr;  // exp(-2 pi i k / n), k = 0..n/2 (real-FFT unpacking)
   double* d_sin = nullptr;    // direct transform: sqrt(2/n) sin(pi m / n), m = 0..2n-1
 };
@@ -130,6 +131,8 @@ struct kkt_handle {
   double* kZw = nullptr;       // restart w-blocks (V each)
   double* kx = nullptr;        // staging for host x / f (3V each)
   double* kf = nullptr;
+  double* ks_f = nullptr;      // spectral basis: sine-mode coefficients of f and x (3V each)
+  double* ks_x = nullptr;
   double* red = nullptr;       // reduction partials
   double* red_out = nullptr;   // reduction results (device)
   double* h_red = nullptr;     // pinned host copy of reduction results
@@ -171,6 +174,10 @@ int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st);
 
 // y = diag(ou, oz, ow) K (su u, sz z, sw w)
 int launch_matvec(const kkt_handle* h, const double* u, double su, const double* z, double sz,
+                  const double* w, double sw, double* y, cudaStream_t st, double ou = 1.0, double oz = 1.0,
+                  double ow = 1.0);
+// The matvec on sine-mode coefficients of all three blocks (same arguments as launch_matvec).
+int launch_matvec_spectral(const kkt_handle* h, const double* u, double su, const double* z, double sz,
                   const double* w, double sw, double* y, cudaStream_t st, double ou = 1.0, double oz = 1.0,
                   double ow = 1.0);
 int launch_build_rhs(const kkt_handle* h, const double* ut, const double* u0, double* f, cudaStream_t st);
@@ -233,7 +240,6 @@ struct DstLaunch {
   int cols;                 // columns mode: columns per slice (the row length Mx)
   long long slice;          // columns mode: elements per slice
   int tiles_per_slice;      // columns mode
-  double scale;             // 1 / sqrt(2 n)
   const double* pre;
   const double2* tw;
   const double2* post;

@@ -65,6 +65,30 @@ __global__ void matvec_kernel(const double* __restrict__ u, const double* __rest
   y[2 * s.V + idx] = fma(c.uc0, uc, -t);
 }
 
+// The same matvec on sine-mode coefficients (every block transformed by the orthonormal 2D
+// DST-I, layout [n][l][k]): B0 acts on mode (k, l) as the scalar mu0 = 1 + dt nu (lx_k + ly_l),
+// so the stencil becomes a product. wc0 and uc0 hold the coefficients without the stencil's
+// centre weight.
+__global__ void matvec_spectral_kernel(const double* __restrict__ u, const double* __restrict__ z,
+                                       const double* __restrict__ w, double* __restrict__ y, Stencil s,
+                                       MatvecCoef c, const double* __restrict__ lx, const double* __restrict__ ly,
+                                       double dtnu) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n = blockIdx.z;
+  if (i >= s.Mx || j >= s.My) return;
+  const long long idx = static_cast<long long>(n) * s.N + static_cast<long long>(j) * s.Mx + i;
+  const double mu0 = fma(dtnu, __ldg(lx + i) + __ldg(ly + j), 1.0);
+  const double wc = w[idx];
+  const double wnx = n + 1 < s.Nt ? w[idx + s.N] : 0.0;
+  const double uc = u[idx];
+  const double upr = n > 0 ? u[idx - s.N] : 0.0;
+  const double zc = z[idx];
+  y[idx] = fma(c.uu, uc, fma(c.wc0 * mu0, wc, -c.wn * wnx));
+  y[s.V + idx] = fma(c.zz, zc, -c.zw * wc);
+  y[2 * s.V + idx] = fma(c.uc0 * mu0, uc, -fma(c.up, upr, c.wz * zc));
+}
+
 // out_n = scale * (B in_n - in_{n+dir}), dir = +1: Jhat^T, dir = -1: Jhat (zero outside 1..Nt)
 __global__ void jhat_time_kernel(const double* __restrict__ in, double* __restrict__ out, Stencil s,
                                  int dir, double scale) {
@@ -173,6 +197,30 @@ int launch_matvec(const kkt_handle* h, const double* u, double su, const double*
   // 16 FP64 instructions (12 FMA) per point: 28 flops; 3 blocks in, 3 out
   ProfScope ps(KKT_K_MATVEC, st, 28.0 * g.V, 48.0 * g.V);
   matvec_kernel<<<grid, tb, 0, st>>>(u, z, w, y, s, c);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int launch_matvec_spectral(const kkt_handle* h, const double* u, double su, const double* z, double sz,
+                           const double* w, double sw, double* y, cudaStream_t st, double ou, double oz, double ow) {
+  const Geometry& g = h->g;
+  const Stencil s = make_stencil(g, 1.0);
+  MatvecCoef c;
+  c.uu = ou * g.h * su;
+  c.wc0 = ou * sw;
+  c.wcx = c.wcy = 0.0;
+  c.wn = ou * sw;
+  c.zz = oz * g.omega * g.h * sz;
+  c.zw = oz * g.dt * sw;
+  c.uc0 = ow * su;
+  c.ucx = c.ucy = 0.0;
+  c.up = ow * su;
+  c.wz = ow * g.dt * sz;
+  dim3 tb(32, 8);
+  dim3 grid((g.Mx + 31) / 32, (g.My + 7) / 8, g.Nt);
+  // 12 FP64 instructions per point; 3 blocks in, 3 out
+  ProfScope ps(KKT_K_MATVEC, st, 20.0 * g.V, 48.0 * g.V);
+  matvec_spectral_kernel<<<grid, tb, 0, st>>>(u, z, w, y, s, c, h->d_lx, h->d_ly, g.dtnu);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }

@@ -33,6 +33,7 @@ VARIANT = {"multiplicative": 0, "additive": 1}
 POU = {"left": 0, "right": 1}
 NORM = {"l2": 0, "euclidean": 1}
 ORTH = {"mgs": 0, "cgs2": 1}
+BASIS = {"physical": 0, "spectral": 1}
 HISTORY_MAX = 1024
 
 
@@ -40,6 +41,7 @@ class KKTOptions(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("coarse", ctypes.c_int), ("variant", ctypes.c_int),
                 ("pou", ctypes.c_int), ("restart", ctypes.c_int), ("jhat_sign", ctypes.c_int),
                 ("residual_norm", ctypes.c_int), ("tc_split", ctypes.c_int), ("orth", ctypes.c_int),
+                ("basis", ctypes.c_int),
                 ("Lx", ctypes.c_double),
                 ("Ly", ctypes.c_double)]
 
@@ -147,6 +149,7 @@ SIGNATURES = [
     ("kkt_batch_destroy", None, [_P]),
     ("kkt_batch_get_info", _I, [_P, _I, ctypes.POINTER(KKTInfo)]),
     ("kkt_batch_set_memory_limit", _I, [_P, ctypes.c_longlong]),
+    ("kkt_batch_set_graphs", _I, [_P, _I]),
     ("kkt_batch_solve", _I, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), _D, _I,
                              ctypes.POINTER(KKTBatchStats), _P]),
     ("kkt_profile_enable", _I, [_I]),
@@ -428,17 +431,18 @@ class Solver:
 
     def __init__(self, nx, ny, Nt, T=1.0, nu=1.0, omega=1e-4, n_sub=1, *, precision="fp64",
                  coarse="exact", variant="multiplicative", pou="left", restart=30, jhat_sign=-1,
-                 residual_norm="l2", tc_split=True, orth="mgs", Lx=1.0, Ly=1.0):
+                 residual_norm="l2", tc_split=True, orth="mgs", basis="physical", Lx=1.0, Ly=1.0):
         self.h = kkt_create(nx, ny, Nt, T, nu, omega, n_sub)
         self.set_options(precision=precision, coarse=coarse, variant=variant, pou=pou, restart=restart,
                          jhat_sign=jhat_sign, residual_norm=residual_norm, tc_split=tc_split, orth=orth,
-                         Lx=Lx, Ly=Ly)
+                         basis=basis, Lx=Lx, Ly=Ly)
         self.info = kkt_get_info(self.h)
 
     def set_options(self, *, precision="fp64", coarse="exact", variant="multiplicative", pou="left",
-                    restart=30, jhat_sign=-1, residual_norm="l2", tc_split=True, orth="mgs", Lx=1.0, Ly=1.0):
+                    restart=30, jhat_sign=-1, residual_norm="l2", tc_split=True, orth="mgs", basis="physical",
+                    Lx=1.0, Ly=1.0):
         opt = KKTOptions(PREC[precision], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
-                         NORM[residual_norm], 1 if tc_split else 0, ORTH[orth], Lx, Ly)
+                         NORM[residual_norm], 1 if tc_split else 0, ORTH[orth], BASIS[basis], Lx, Ly)
         kkt_set_options(self.h, opt)
         self.info = kkt_get_info(self.h)
 
@@ -537,7 +541,7 @@ class Batch:
     with nx, ny, Nt, n_sub, T, nu, omega attributes (e.g. workloads.Workload) or tuples."""
 
     def __init__(self, instances, *, coarse="exact", variant="multiplicative", pou="left", restart=30,
-                 jhat_sign=-1, residual_norm="l2", Lx=1.0, Ly=1.0):
+                 jhat_sign=-1, residual_norm="l2", orth="mgs", Lx=1.0, Ly=1.0):
         descs = []
         for w in instances:
             if isinstance(w, tuple):
@@ -545,12 +549,16 @@ class Batch:
             else:
                 descs.append(KKTInstance(w.nx, w.ny, w.Nt, w.n_sub, w.T, w.nu, w.omega))
         opt = KKTOptions(PREC["fp64"], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
-                         NORM[residual_norm], 1, ORTH["cgs2"], Lx, Ly)
+                         NORM[residual_norm], 1, ORTH[orth], BASIS["physical"], Lx, Ly)
         self.b = kkt_batch_create(descs, opt)
         self.infos = [kkt_batch_get_info(self.b, i) for i in range(len(descs))]
 
     def __len__(self):
         return len(self.infos)
+
+    def set_graphs(self, on: bool) -> None:
+        """Replay the per-step preconditioner + matvec phase as CUDA graphs (default) or not."""
+        _check(load_library().kkt_batch_set_graphs(self.b, 1 if on else 0))
 
     def set_memory_limit(self, nbytes: int) -> None:
         """Krylov storage per wave in bytes (0: 85% of free device memory)."""

@@ -65,21 +65,21 @@ def small_case(kkt):
     return list(ps), [dev(f) for f in fs]
 
 
-def single(kkt, w, f, tol, coarse="exact"):
-    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, coarse=coarse, orth="cgs2")
+def single(kkt, w, f, tol, coarse="exact", orth="mgs"):
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, coarse=coarse, orth=orth)
     r = s.solve(f, tol=tol, maxit=420)
     s.close()
     return r
 
 
-@pytest.mark.parametrize("coarse", ["exact", "none"])
-def test_batch_matches_single_instance_solves(kkt, small_case, coarse):
+@pytest.mark.parametrize("coarse,orth", [("exact", "mgs"), ("none", "mgs"), ("exact", "cgs2")])
+def test_batch_matches_single_instance_solves(kkt, small_case, coarse, orth):
     ps, fs = small_case
-    b = kkt.Batch(SMALL, coarse=coarse)
+    b = kkt.Batch(SMALL, coarse=coarse, orth=orth)
     res = b.solve(fs, tol=1e-8, maxit=420)
     assert res.status == kkt.KKT_OK
     for i, w in enumerate(SMALL):
-        ref = single(kkt, w, fs[i], 1e-8, coarse)
+        ref = single(kkt, w, fs[i], 1e-8, coarse, orth)
         assert res.statuses[i] == kkt.KKT_OK
         assert abs(res.iterations[i] - ref.iterations) <= 1, (w.name, res.iterations[i], ref.iterations)
         assert res.rel_residual[i] <= 1e-8

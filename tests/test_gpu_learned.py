@@ -111,16 +111,44 @@ def _solve_counts(kkt, w, net):
     return its
 
 
-def test_trained_network_reduces_iterations(kkt):
-    """Train on the GPU for the 32 x 32, Nt = 128, N_D = 16 geometry (modes k, l < 8 learned),
-    then solve with the exact coarse solve, none, the learned correction, and the learned modes
-    left without coarse correction: the network must beat its own ablation."""
+@pytest.fixture(scope="module")
+def trained(kkt):
+    """A network trained on the GPU for the 32 x 32, Nt = 128, N_D = 16 geometry (modes k, l < 8)."""
     w = workloads.Workload("t", nx=32, ny=32, Nt=128, n_sub=16, nu=1.0, omega=1e-4, target="sine-series", seed=7)
     net = kkt.Mlp(nx=32, Nt=128, n_sub=16, modes=8, width=128, seed=4, samples=8192, epochs=40, batch=128,
                   nu_lo=0.5, nu_hi=2.0, omega_lo=3e-5, omega_hi=3e-4, lr=2e-3)
     st = net.train()
+    return w, net, st
+
+
+def test_trained_network_reduces_iterations(kkt, trained):
+    """Solve with the exact coarse solve, none, the learned correction, and the learned modes
+    left without coarse correction: the network must beat its own ablation."""
+    w, net, st = trained
     assert st.val_cosine > 0.8, st.val_cosine
     its = _solve_counts(kkt, w, net)
     assert its["kept"] > 0
     assert its["learned"] < its["without-network"], its
     assert its["exact"] <= its["learned"], its
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16"])
+def test_learned_coarse_with_tensor_core_transforms(kkt, trained, prec):
+    """The learned correction inside the reduced-precision preconditioner (padded mode grid):
+    converges to 1e-8, keeps learned corrections, and matches the FP64 learned solve."""
+    w, net, _ = trained
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    fd = torch.from_numpy(problem.assemble_rhs(p, workloads.make_target(w), None)).cuda()
+    out = {}
+    for form in ("fp64", prec):
+        s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=form)
+        s.attach_mlp(net, "learned")
+        s.set_options(precision=form, coarse="learned")
+        r = s.solve(fd, tol=1e-8, maxit=420)
+        assert r.status == kkt.KKT_OK, form
+        kept, _ = s.learned_stats()
+        assert kept > 0, form
+        out[form] = r
+    bound = out["fp64"].iterations + 2 if prec == "tf32" else int(1.5 * out["fp64"].iterations) + 2
+    assert out[prec].iterations <= bound
+    assert float(torch.linalg.vector_norm(out[prec].x - out["fp64"].x) / torch.linalg.vector_norm(out["fp64"].x)) < 1e-6

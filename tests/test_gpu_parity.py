@@ -196,14 +196,16 @@ def test_solve_small_configuration_matches_oracle_and_exact(kkt, norm):
     assert rel(host(tight.x), exact) < TOL
 
 
+@pytest.mark.parametrize("orth", ["mgs", "cgs2"])
 @pytest.mark.parametrize("k", [1, 5, 12, 30])
-def test_fixed_iteration_residuals_match_oracle(kkt, k):
+def test_fixed_iteration_residuals_match_oracle(kkt, k, orth):
     """After the same k Arnoldi steps (one cycle), GPU and oracle agree on every residual
-    estimate and on the true residual of the iterate."""
+    estimate and on the true residual of the iterate, with either orthogonalisation (the
+    oracle uses MGS; CGS2 differs from it by rounding only)."""
     w = workloads.CFG_SMALL
     p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
     f = problem.assemble_rhs(p, workloads.make_target(w), None)
-    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, orth=orth)
     res = s.solve(dev(f), tol=1e-300, maxit=k)
     assert res.status == kkt.KKT_NOT_CONVERGED and res.iterations == k
     K = problem.assemble_K(p)
@@ -217,6 +219,44 @@ def test_fixed_iteration_residuals_match_oracle(kkt, k):
                                rtol=1e-6, atol=1e-13)
     if k == 1:
         assert rel(x, ref.x) < TOL       # one step: x = y_1 z_1, well conditioned
+
+
+@pytest.mark.parametrize("orth", ["mgs", "cgs2"])
+def test_spectral_basis_solve_matches_oracle(kkt, orth):
+    """FGMRES on sine-mode coefficients (transforms only at entry and exit): the same residual
+    history as the oracle's physical-space FGMRES after 12 steps, the oracle's iteration count
+    to 1e-8, and the exact solution after a 1e-12 solve, from a nonzero initial guess and with
+    host buffers."""
+    w = workloads.CFG_SMALL
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    f = problem.assemble_rhs(p, workloads.make_target(w), workloads.make_u0(w))
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, orth=orth, basis="spectral")
+    K = problem.assemble_K(p)
+    d = problem.l2_residual_weights(p)
+    pre = schwarz.schur_preconditioner(p, w.n_sub)
+    ref = krylov.fgmres(lambda v: K @ v, lambda r: schwarz.block_preconditioner_apply(p, pre, r), f,
+                        fixed_iterations=12, row_scale=d)
+    res = s.solve(dev(f), tol=1e-300, maxit=12)
+    assert res.status == kkt.KKT_NOT_CONVERGED and res.iterations == 12
+    np.testing.assert_allclose(res.history, ref.history, rtol=1e-7, atol=1e-13)
+    x = host(res.x)
+    np.testing.assert_allclose(np.linalg.norm(d * (f - K @ x)) / np.linalg.norm(d * f), ref.rel_residual,
+                               rtol=1e-6, atol=1e-13)
+    full = krylov.fgmres(lambda v: K @ v, lambda r: schwarz.block_preconditioner_apply(p, pre, r), f,
+                         tol=1e-8, restart=30, maxit=420, row_scale=d)
+    res = s.solve(dev(f), tol=1e-8, maxit=420)
+    assert res.status == kkt.KKT_OK and abs(res.iterations - full.iterations) <= 1
+    exact = spectral.kkt_exact_solve(p, f)
+    x0 = torch.from_numpy(0.5 * exact + workloads.random_vector(3 * p.V, 3) * 1e-3)   # host, nonzero
+    tight = s.solve(torch.from_numpy(f), x0, tol=1e-12, maxit=420)
+    assert tight.status == kkt.KKT_OK
+    assert rel(x0.numpy(), exact) < TOL
+
+
+def test_spectral_basis_rejects_reduced_precision(kkt):
+    with pytest.raises(kkt.KKTError) as e:
+        kkt.Solver(32, 32, 64, 1.0, 1.0, 1e-4, 4, precision="tf32", basis="spectral")
+    assert e.value.status == kkt.KKT_ERR_UNSUPPORTED
 
 
 def test_solve_with_host_buffers_and_initial_guess(kkt):
