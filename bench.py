@@ -203,6 +203,14 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------------------------
 
+# DRAM traffic per algorithmic byte for kernels captured with ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum over the launch, divided by the launch's algorithmic bytes), from the
+# small-case capture summarised in profiles/ncu_fp64_kernels_256x256_nt96.md. The fused MGS
+# step streams with no reuse, so its traffic grows in proportion to the elements processed and
+# the ratio scales to full-size launches. Kernels not listed report traffic null.
+TRAFFIC_RATIO = {"mgs_step_kernel": 0.952}
+
+
 def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -> dict:
     """Roofline of the kernel class with the largest device time in the timed region.
 
@@ -238,7 +246,11 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -
         ach = e["bytes"] / sec / 1e9
         out = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                "peak_source": f"{peak_kind} HBM copy"}
-    out.update({"traffic": None, "per_launch_ms": per_launch, "launches": e["timed"],
+    bytes_per_launch = e["bytes"] / max(e["timed"], 1)
+    ratio = TRAFFIC_RATIO.get(kname)
+    out.update({"traffic": bytes_per_launch * ratio if ratio else None,
+                "traffic_source": ("ncu small-case capture, scaled by elements processed" if ratio else None),
+                "per_launch_ms": per_launch, "launches": e["timed"],
                 "algorithmic_flops_per_launch": e["flops"] / max(e["timed"], 1),
                 "algorithmic_bytes_per_launch": e["bytes"] / max(e["timed"], 1),
                 "hbm_gbs_algorithmic": e["bytes"] / sec / 1e9, "share_of_step": e["ms"] / sum(v["ms"] for v in prof.values())})
@@ -528,6 +540,27 @@ def run_study(args):
     return 0
 
 
+def run_profile_case(args):
+    """A small solve for counter captures: 256 x 256, Nt = 96, N_D = 8 (a KKT vector of 150 MB,
+    above the 126 MB L2), FGMRES(10) to 1e-8, two solves. Prints the iteration count."""
+    import torch
+
+    import paper_2305_04421_gb300.kkt as kkt
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    w = workloads.Workload("profile", nx=256, ny=256, Nt=96, n_sub=8, target="sine-series", seed=1)
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, restart=10, basis=args.basis,
+                   precision=args.precision)
+    f = s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev))
+    for _ in range(2):
+        r = s.solve(f, tol=1e-8, maxit=200)
+    print(json.dumps({"profile_case": f"256x256 Nt=96 N_D=8 restart=10 {args.precision} {args.basis}",
+                      "iterations": r.iterations,
+                      "status": r.status}))
+    return 0 if r.status == kkt.KKT_OK else 1
+
+
 def run_ours(args):
     import torch
 
@@ -645,6 +678,12 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=32,
                     help="iterations the reference arm scales its per-iteration sample by")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run only a small solve (256 x 256, Nt = 96) for counter captures")
+    ap.add_argument("--basis", choices=["physical", "spectral"], default="physical",
+                    help="FGMRES basis of --profile-case")
+    ap.add_argument("--precision", choices=["fp64", "bf16", "tf32"], default="fp64",
+                    help="preconditioner arithmetic of --profile-case")
     ap.add_argument("--study", choices=["paper"], default=None,
                     help="run Section 4's one- vs two-level iteration study instead of the benchmark")
     ap.add_argument("--no-learned", action="store_true",
@@ -656,6 +695,8 @@ def main():
     args = ap.parse_args()
     if args.study == "paper":
         return run_study(args)
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -21,7 +21,7 @@ namespace kkt {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr long long kChunk = kThreads * 8;   // elements per work item of the vector kernels
+constexpr long long kChunk = kThreads * 16;   // elements per work item of the vector kernels
 
 struct Seg {
   const double* V;   // first vector (basis V_0 or a single vector)
@@ -30,14 +30,13 @@ struct Seg {
   long long n;       // elements
 };
 
-__device__ __forceinline__ int find_seg(const long long* __restrict__ prefix, int nj, long long t) {
-  int lo = 0, hi = nj - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
+// Each block copies the segment table and its item prefix to shared memory once (at most
+// KKT_BATCH_MAX instances), so finding an item's segment costs no global-memory round trips.
+#define KKT_SEG_TABLE                                                       \
+  __shared__ Seg ss[KKT_BATCH_MAX];                                         \
+  __shared__ long long sp[KKT_BATCH_MAX + 1];                               \
+  for (int i_ = threadIdx.x; i_ < nj; i_ += blockDim.x) ss[i_] = segs[i_]; \
+  batch_prefix_load(sp, prefix, nj);
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -63,10 +62,11 @@ template <int NV>
 __global__ void __launch_bounds__(kThreads) multidot_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                        int nj, long long total, double* __restrict__ part) {
   __shared__ double sh[32];
+  KKT_SEG_TABLE
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int k = find_seg(prefix, nj, t);
-    const Seg S = segs[k];
-    const long long e0 = (t - prefix[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    const int k = batch_find(sp, nj, t);
+    const Seg S = ss[k];
+    const long long e0 = (t - sp[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
     double acc[NV + 1];
 #pragma unroll
     for (int v = 0; v <= NV; ++v) acc[v] = 0.0;
@@ -90,13 +90,14 @@ __global__ void __launch_bounds__(kThreads) update_b(const Seg* __restrict__ seg
                                                      int nj, long long total, const double* __restrict__ coef, int ldc,
                                                      double* __restrict__ part, int want_norm) {
   __shared__ double sh[32];
+  KKT_SEG_TABLE
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int k = find_seg(prefix, nj, t);
-    const Seg S = segs[k];
+    const int k = batch_find(sp, nj, t);
+    const Seg S = ss[k];
     double c[NV > 0 ? NV : 1];
 #pragma unroll
     for (int v = 0; v < NV; ++v) c[v] = coef[k * ldc + v];
-    const long long e0 = (t - prefix[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    const long long e0 = (t - sp[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
     double acc = 0.0;
     for (long long i = e0 + threadIdx.x; i < e1; i += kThreads) {
       double wi = S.w[i];
@@ -116,11 +117,12 @@ __global__ void __launch_bounds__(kThreads) update_b(const Seg* __restrict__ seg
 // out = alpha[inst] * x + beta[inst] * y, x = V, y = w of the segment (out = w)
 __global__ void __launch_bounds__(kThreads) axpby_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                     int nj, long long total, const double* __restrict__ ab) {
+  KKT_SEG_TABLE
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int k = find_seg(prefix, nj, t);
-    const Seg S = segs[k];
+    const int k = batch_find(sp, nj, t);
+    const Seg S = ss[k];
     const double a = ab[2 * k], b = ab[2 * k + 1];
-    const long long e0 = (t - prefix[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    const long long e0 = (t - sp[k]) * kChunk, e1 = min(e0 + kChunk, S.n);
     for (long long i = e0 + threadIdx.x; i < e1; i += kThreads) S.w[i] = fma(a, S.V[i], b * S.w[i]);
   }
 }
@@ -133,21 +135,37 @@ __global__ void __launch_bounds__(kThreads) mgs_b(const Seg* __restrict__ segs, 
                                                   int nj, long long total, int k, const double* __restrict__ dots,
                                                   const double* __restrict__ sc, int ld, double* __restrict__ part) {
   __shared__ double sh[32];
+  KKT_SEG_TABLE
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int q = find_seg(prefix, nj, t);
-    const Seg S = segs[q];
+    const int q = batch_find(sp, nj, t);
+    const Seg S = ss[q];
     const double c = AXPY ? dots[q * ld + k] * sc[q * ld + k] : 0.0;
     const double* Vk = S.V + (AXPY ? k : 0) * S.stride;
     const double* Vn = S.V + (k + 1) * S.stride;
-    const long long e0 = (t - prefix[q]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    const long long e0 = (t - sp[q]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    const bool ax = AXPY && c != 0.0;
     double acc = 0.0;
-    for (long long i = e0 + threadIdx.x; i < e1; i += kThreads) {
-      double wi = S.w[i];
-      if (AXPY && c != 0.0) {
-        wi = fma(-c, Vk[i], wi);
-        S.w[i] = wi;
+    // 4 elements per thread per round, all loads issued before the arithmetic (memory-level
+    // parallelism: each thread keeps up to 12 loads in flight)
+    for (long long base = e0 + threadIdx.x; base < e1; base += 4 * kThreads) {
+      double wv[4], kv[4], nv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const long long i = base + r * kThreads;
+        const bool in = i < e1;
+        wv[r] = in ? S.w[i] : 0.0;
+        kv[r] = (in && ax) ? Vk[i] : 0.0;
+        nv[r] = (in && DOTV) ? Vn[i] : 0.0;
       }
-      acc = fma(DOTV ? Vn[i] : wi, wi, acc);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const long long i = base + r * kThreads;
+        if (ax) {
+          wv[r] = fma(-c, kv[r], wv[r]);
+          if (i < e1) S.w[i] = wv[r];
+        }
+        acc = fma(DOTV ? nv[r] : wv[r], wv[r], acc);
+      }
     }
     const double r = block_sum(acc, sh);
     if (threadIdx.x == 0) part[t] = r;
@@ -239,9 +257,10 @@ struct SegTable {
       elems += static_cast<double>(segs[k].n);
     }
     total = pre[nj];
-    if (!dev) {
-      KKT_CUDA_TRY(cudaMalloc(&dev, nj * sizeof(Seg)));
-      KKT_CUDA_TRY(cudaMalloc(&prefix, (nj + 1) * sizeof(long long)));
+    if (nj < 1 || nj > KKT_BATCH_MAX) return set_error(KKT_ERR_INVALID_ARG, "segment table size out of range");
+    if (!dev) {   // capacity for the largest batch: the table is refilled with other counts
+      KKT_CUDA_TRY(cudaMalloc(&dev, KKT_BATCH_MAX * sizeof(Seg)));
+      KKT_CUDA_TRY(cudaMalloc(&prefix, (KKT_BATCH_MAX + 1) * sizeof(long long)));
     }
     KKT_CUDA_TRY(cudaMemcpy(dev, segs.data(), nj * sizeof(Seg), cudaMemcpyHostToDevice));
     KKT_CUDA_TRY(cudaMemcpy(prefix, pre.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));
@@ -424,7 +443,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
     if (rc == KKT_OK && cudaMalloc(&part, sizeof(double) * max_items * 33) != cudaSuccess)
       rc = set_error(KKT_ERR_OOM, "batched reduction scratch");
     std::vector<BatchSlot> slots(m);
-    BatchSlot resid_slot;
+    BatchSlot resid_slot, sub_slot;
     std::vector<cudaGraphExec_t> graphs(m, nullptr);
     std::vector<ProfCapture> graph_work(m);
     SegTable t_full, t_new, t_f[3], t_xu, t_xz, t_xw;
@@ -449,22 +468,26 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       return finalize(t, 1);
     };
     // preconditioner + matvec tables of step j (pointers fixed per j)
-    auto prepare_slot = [&](int j) -> int {
-      BatchSlot& sl = slots[j];
+    std::vector<int> everyone(nw);
+    std::iota(everyone.begin(), everyone.end(), 0);
+    // preconditioner + matvec tables of step j for the wave instances in `mem`
+    auto prepare_slot = [&](BatchSlot& sl, int j, const std::vector<int>& mem) -> int {
       sl.sweep_tb = b->tuned_sweep_tb > 0 ? b->tuned_sweep_tb : 128;
-      std::vector<DstJob> fwd(nw), inv(nw);
-      std::vector<SpecJob> sj(nw);
-      std::vector<MatvecJob> mj(nw);
-      for (int k = 0; k < nw; ++k) {
+      const int nm = static_cast<int>(mem.size());
+      std::vector<DstJob> fwd(nm), inv(nm);
+      std::vector<SpecJob> sj(nm);
+      std::vector<MatvecJob> mj(nm);
+      for (int q = 0; q < nm; ++q) {
+        const int k = mem[q];
         InstState& I = *S[k];
         kkt_handle* h = I.h;
         const Geometry& g = h->g;
         const long long V = g.V;
         double* Vj = Vb[k] + static_cast<size_t>(j) * 3 * V;
         double* Zj = Zw[k] + static_cast<size_t>(j) * V;
-        fwd[k] = DstJob{h, Vj + 2 * V, h->spec};
-        inv[k] = DstJob{h, h->spec2, Zj};
-        SpecJob& J = sj[k];
+        fwd[q] = DstJob{h, Vj + 2 * V, h->spec};
+        inv[q] = DstJob{h, h->spec2, Zj};
+        SpecJob& J = sj[q];
         J.p = make_spec_params(h);
         J.rhat = h->spec;
         J.yhat = h->spec2;
@@ -473,7 +496,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         J.scale_base = 1.0 / I.dw;
         J.max_len = h->td.max_len;
         J.scale_index = k;
-        MatvecJob& M = mj[k];
+        MatvecJob& M = mj[q];
         M.u = Vj;
         M.z = Vj + V;
         M.w = Zj;
@@ -500,10 +523,10 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         M.scale_index = k;
       }
       const int tl = b->tuned_tile_lines;
-      KKT_TRY(dst_batched_prepare(sl, 0, fwd.data(), nw, tl));
-      KKT_TRY(dst_batched_prepare(sl, 2, inv.data(), nw, tl));
-      KKT_TRY(spectral_batched_prepare(sl, sj.data(), nw));
-      KKT_TRY(matvec_batched_prepare(sl, mj.data(), nw));
+      KKT_TRY(dst_batched_prepare(sl, 0, fwd.data(), nm, tl));
+      KKT_TRY(dst_batched_prepare(sl, 2, inv.data(), nm, tl));
+      KKT_TRY(spectral_batched_prepare(sl, sj.data(), nm));
+      KKT_TRY(matvec_batched_prepare(sl, mj.data(), nm));
       return KKT_OK;
     };
     auto phase_launch = [&](const BatchSlot& sl, cudaStream_t s2) -> int {
@@ -543,7 +566,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         b->tuned_tile_lines = cand_tl[a];
         b->tuned_sweep_tb = 128;
         b->tune_ms_dst[a] = 1e30;
-        if (prepare_slot(0) == KKT_OK)
+        if (prepare_slot(slots[0], 0, everyone) == KKT_OK)
           b->tune_ms_dst[a] = time_it([&] {
             const int r = dst_batched_launch(slots[0], 0, st);
             return r != KKT_OK ? r : dst_batched_launch(slots[0], 1, st);
@@ -555,7 +578,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       for (int a = 0; a < 3; ++a) {
         b->tuned_sweep_tb = cand_tb[a];
         b->tune_ms_sweep[a] = 1e30;
-        if (prepare_slot(0) == KKT_OK && dst_batched_launch(slots[0], 0, st) == KKT_OK &&
+        if (prepare_slot(slots[0], 0, everyone) == KKT_OK && dst_batched_launch(slots[0], 0, st) == KKT_OK &&
             dst_batched_launch(slots[0], 1, st) == KKT_OK)
           b->tune_ms_sweep[a] = time_it([&] { return spectral_batched_launch(slots[0], d_scale, st); });
         batch_slot_free(slots[0]);
@@ -685,59 +708,64 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         I.cycle_done = !I.active;
       }
       for (int j = 0; j < m && rc == KKT_OK; ++j) {
-        int running = 0;
-        for (int k = 0; k < nw; ++k) running += !S[k]->cycle_done;
-        if (running == 0) break;
-        if (!slots[j].dst) {
-          rc = prepare_slot(j);
-          if (rc != KKT_OK) break;
-        }
+        // instances still iterating in this cycle; the others are left out of every launch
+        std::vector<int> mem;
+        for (int k = 0; k < nw; ++k)
+          if (!S[k]->cycle_done) mem.push_back(k);
+        const int nr = static_cast<int>(mem.size());
+        if (nr == 0) break;
         for (int k = 0; k < nw; ++k) h_scale[k] = 1.0 / S[k]->eta[j];
         KKT_CUDA_TRY(cudaMemcpyAsync(d_scale, h_scale, sizeof(double) * nw, cudaMemcpyHostToDevice, st));
-        if (!b->use_graphs) {
-          rc = phase_launch(slots[j], st);
+        if (nr < nw || !b->use_graphs) {
+          // a subset (or graphs off): tables for the running instances, direct launches
+          rc = prepare_slot(sub_slot, j, mem);
+          if (rc == KKT_OK) rc = phase_launch(sub_slot, st);
           if (rc != KKT_OK) break;
-        } else if (!graphs[j]) {
-          cudaStream_t cs_ = nullptr;
-          KKT_CUDA_TRY(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
-          cudaGraph_t gr = nullptr;
-          KKT_CUDA_TRY(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeRelaxed));
-          graph_work[j] = ProfCapture();
-          prof_capture(&graph_work[j]);
-          const int prc = phase_launch(slots[j], cs_);
-          prof_capture(nullptr);
-          const cudaError_t ec = cudaStreamEndCapture(cs_, &gr);
-          cudaStreamDestroy(cs_);
-          if (prc < 0 || ec != cudaSuccess) {
-            rc = set_error(KKT_ERR_CUDA, "graph capture of the batched phase failed");
-            break;
+        } else {
+          if (!slots[j].dst) {
+            rc = prepare_slot(slots[j], j, everyone);
+            if (rc != KKT_OK) break;
           }
-          KKT_CUDA_TRY(cudaGraphInstantiate(&graphs[j], gr, 0));
-          cudaGraphDestroy(gr);
-          ++graphs_made;
-        }
-        if (b->use_graphs) {
+          if (!graphs[j]) {
+            cudaStream_t cs_ = nullptr;
+            KKT_CUDA_TRY(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
+            cudaGraph_t gr = nullptr;
+            KKT_CUDA_TRY(cudaStreamBeginCapture(cs_, cudaStreamCaptureModeRelaxed));
+            graph_work[j] = ProfCapture();
+            prof_capture(&graph_work[j]);
+            const int prc = phase_launch(slots[j], cs_);
+            prof_capture(nullptr);
+            const cudaError_t ec = cudaStreamEndCapture(cs_, &gr);
+            cudaStreamDestroy(cs_);
+            if (prc < 0 || ec != cudaSuccess) {
+              rc = set_error(KKT_ERR_CUDA, "graph capture of the batched phase failed");
+              break;
+            }
+            KKT_CUDA_TRY(cudaGraphInstantiate(&graphs[j], gr, 0));
+            cudaGraphDestroy(gr);
+            ++graphs_made;
+          }
           rc = prof_graph_launch(graphs[j], graph_work[j], st);
           if (rc != KKT_OK) break;
           ++graph_launches;
         }
-        // Gram-Schmidt of the new vectors against each instance's basis (CGS, one conditional repeat)
-        std::vector<Seg> sn(nw);
-        for (int k = 0; k < nw; ++k) {
+        // Gram-Schmidt of the new vectors of the running instances (position q = mem index)
+        std::vector<Seg> sn(nr);
+        for (int q = 0; q < nr; ++q) {
+          const int k = mem[q];
           const long long V = S[k]->h->g.V;
-          sn[k] = Seg{Vb[k], 3 * V, Vb[k] + static_cast<size_t>(j + 1) * 3 * V, 3 * V};
+          sn[q] = Seg{Vb[k], 3 * V, Vb[k] + static_cast<size_t>(j + 1) * 3 * V, 3 * V};
         }
         rc = t_new.set(sn);
         if (rc != KKT_OK) break;
-        std::vector<double> wn2(nw, 0.0), before(nw, 0.0);
-        std::vector<char> need(nw, 1);
+        std::vector<double> wn2(nw, 0.0), before(nr, 0.0);
+        std::vector<char> need(nr, 1);
         if (b->opt.orth == KKT_ORTH_MGS) {
-          // modified Gram-Schmidt, step k over all instances at once; the dots stay on the
-          // device (d_out[inst][k]) and feed the next step, the host reads the columns once
-          for (int k = 0; k < nw; ++k)
-            for (int i = 0; i <= j; ++i)
-              h_coef[k * 33 + i] = S[k]->cycle_done ? 0.0 : 1.0 / (S[k]->eta[i] * S[k]->eta[i]);
-          KKT_CUDA_TRY(cudaMemcpyAsync(d_coef, h_coef, sizeof(double) * 33 * nw, cudaMemcpyHostToDevice, st));
+          // modified Gram-Schmidt, step k over all running instances at once; the dots stay on
+          // the device (d_out[q][k]) and feed the next step, the host reads the columns once
+          for (int q = 0; q < nr; ++q)
+            for (int i = 0; i <= j; ++i) h_coef[q * 33 + i] = 1.0 / (S[mem[q]]->eta[i] * S[mem[q]]->eta[i]);
+          KKT_CUDA_TRY(cudaMemcpyAsync(d_coef, h_coef, sizeof(double) * 33 * nr, cudaMemcpyHostToDevice, st));
           const unsigned grid = static_cast<unsigned>(std::min<long long>(t_new.total, persistent_grid()));
           for (int k = -1; k <= j && rc == KKT_OK; ++k) {
             {
@@ -745,57 +773,54 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
               ProfScope ps(k < 0 ? KKT_K_MULTIDOT : KKT_K_UPDATE, st, (k < 0 ? 2.0 : 4.0) * el,
                            8.0 * el * (k < 0 ? 2.0 : (k < j ? 4.0 : 3.0)));
               if (k < 0)
-                mgs_b<false, true><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nw, t_new.total, -1, d_out,
+                mgs_b<false, true><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nr, t_new.total, -1, d_out,
                                                               d_coef, 33, part);
               else if (k < j)
-                mgs_b<true, true><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nw, t_new.total, k, d_out,
+                mgs_b<true, true><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nr, t_new.total, k, d_out,
                                                              d_coef, 33, part);
               else
-                mgs_b<true, false><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nw, t_new.total, k, d_out,
+                mgs_b<true, false><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nr, t_new.total, k, d_out,
                                                               d_coef, 33, part);
               if (cudaGetLastError() != cudaSuccess) rc = set_error(KKT_ERR_CUDA, "batched MGS launch failed");
             }
             ProfScope ps(KKT_K_REDUCE, st);
-            finalize_col_b<<<nw, 32, 0, st>>>(part, t_new.prefix, nw, d_out, 33, k + 1);
+            finalize_col_b<<<nr, 32, 0, st>>>(part, t_new.prefix, nr, d_out, 33, k + 1);
           }
           if (rc != KKT_OK) break;
-          KKT_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, sizeof(double) * 33 * nw, cudaMemcpyDeviceToHost, st));
+          KKT_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, sizeof(double) * 33 * nr, cudaMemcpyDeviceToHost, st));
           KKT_CUDA_TRY(cudaStreamSynchronize(st));
-          for (int k = 0; k < nw; ++k) {
-            InstState& I = *S[k];
-            for (int i = 0; i <= j; ++i) Hs(I, i, j) = I.cycle_done ? 0.0 : h_out[k * 33 + i] / I.eta[i];
-            wn2[k] = h_out[k * 33 + j + 1];
+          for (int q = 0; q < nr; ++q) {
+            InstState& I = *S[mem[q]];
+            for (int i = 0; i <= j; ++i) Hs(I, i, j) = h_out[q * 33 + i] / I.eta[i];
+            wn2[mem[q]] = h_out[q * 33 + j + 1];
           }
         }
         for (int pass = 0; pass < 2 && rc == KKT_OK && b->opt.orth == KKT_ORTH_CGS2; ++pass) {
-          rc = dispatch<MultidotB>(j + 1, t_new.dev, t_new.prefix, nw, t_new.total, part, 2.0 * t_new.elems, st);
+          rc = dispatch<MultidotB>(j + 1, t_new.dev, t_new.prefix, nr, t_new.total, part, 2.0 * t_new.elems, st);
           if (rc != KKT_OK) break;
           rc = finalize(t_new, j + 2);
           if (rc != KKT_OK) break;
-          for (int k = 0; k < nw; ++k) {
-            InstState& I = *S[k];
-            const bool on = need[k] && !I.cycle_done;
-            if (on) before[k] = h_out[k * (j + 2) + j + 1];
+          for (int q = 0; q < nr; ++q) {
+            InstState& I = *S[mem[q]];
+            if (need[q]) before[q] = h_out[q * (j + 2) + j + 1];
             for (int i = 0; i <= j; ++i) {
-              const double hk = on ? h_out[k * (j + 2) + i] / I.eta[i] : 0.0;
+              const double hk = need[q] ? h_out[q * (j + 2) + i] / I.eta[i] : 0.0;
               Hs(I, i, j) += hk;
-              h_coef[k * ldc + i] = hk / I.eta[i];
+              h_coef[q * ldc + i] = hk / I.eta[i];
             }
           }
-          KKT_CUDA_TRY(cudaMemcpyAsync(d_coef, h_coef, sizeof(double) * ldc * nw, cudaMemcpyHostToDevice, st));
-          rc = dispatch<UpdateB>(j + 1, t_new.dev, t_new.prefix, nw, t_new.total, d_coef, ldc, part, 1,
+          KKT_CUDA_TRY(cudaMemcpyAsync(d_coef, h_coef, sizeof(double) * ldc * nr, cudaMemcpyHostToDevice, st));
+          rc = dispatch<UpdateB>(j + 1, t_new.dev, t_new.prefix, nr, t_new.total, d_coef, ldc, part, 1,
                                  2.0 * t_new.elems, st);
           if (rc != KKT_OK) break;
           rc = finalize(t_new, 1);
           if (rc != KKT_OK) break;
           bool again = false;
-          for (int k = 0; k < nw; ++k) {
-            // instances that finished their cycle still get normalised (their vectors stay finite)
-            if (pass == 0 && S[k]->cycle_done) wn2[k] = h_out[k];
-            if (!need[k] || S[k]->cycle_done) continue;
-            wn2[k] = h_out[k];
-            need[k] = wn2[k] < 0.5 * before[k];
-            again = again || need[k];
+          for (int q = 0; q < nr; ++q) {
+            if (!need[q]) continue;
+            wn2[mem[q]] = h_out[q];
+            need[q] = h_out[q] < 0.5 * before[q];
+            again = again || need[q];
           }
           if (!again) break;
         }
@@ -886,6 +911,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       batch_slot_free(slots[j]);
     }
     batch_slot_free(resid_slot);
+    batch_slot_free(sub_slot);
     t_full.free();
     t_new.free();
     for (int bl = 0; bl < 3; ++bl) t_f[bl].free();

@@ -211,13 +211,11 @@ __global__ void __launch_bounds__(kThreads) dst_tile_batched(const DstLaunch* __
                                                              const long long* __restrict__ prefix, int nl,
                                                              long long total) {
   extern __shared__ double smem[];
+  __shared__ long long sp[KKT_BATCH_MAX + 1];
+  batch_prefix_load(sp, prefix, nl);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    int lo = 0, hi = nl - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    dst_tile_body(Ls[lo], t - prefix[lo], smem);
+    const int k = batch_find(sp, nl, t);
+    dst_tile_body(Ls[k], t - sp[k], smem);
     __syncthreads();
   }
 }
@@ -317,10 +315,12 @@ void dst_plan_destroy(DstPlan& p) {
 // Batched 2D DST over several instances: one launch for all row passes, one for all column
 // passes; tables filled once per slot (outside any graph capture), launches read them.
 int dst_batched_prepare(BatchSlot& slot, int first_pass, const DstJob* jobs, int njobs, int tile_lines) {
+  if (njobs < 1 || njobs > KKT_BATCH_MAX) return set_error(KKT_ERR_INVALID_ARG, "batched jobs out of range");
   slot.njobs = njobs;
   if (!slot.dst) {
-    KKT_CUDA_TRY(cudaMalloc(&slot.dst, 4 * static_cast<size_t>(njobs) * sizeof(DstLaunch)));
-    KKT_CUDA_TRY(cudaMalloc(&slot.dst_prefix, 4 * static_cast<size_t>(njobs + 1) * sizeof(long long)));
+    // capacity for the largest batch, so a slot can be refilled with any job count
+    KKT_CUDA_TRY(cudaMalloc(&slot.dst, 4 * static_cast<size_t>(KKT_BATCH_MAX) * sizeof(DstLaunch)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.dst_prefix, 4 * static_cast<size_t>(KKT_BATCH_MAX + 1) * sizeof(long long)));
   }
   for (int pass = first_pass; pass < first_pass + 2; ++pass) {
     const bool rows = (pass % 2) == 0;
@@ -340,9 +340,9 @@ int dst_batched_prepare(BatchSlot& slot, int first_pass, const DstJob* jobs, int
       flops += lines * 2.5 * L[k].M * std::log2(2.0 * L[k].n);
       bytes += lines * L[k].M * 16.0;
     }
-    KKT_CUDA_TRY(cudaMemcpy(slot.dst + static_cast<size_t>(pass) * njobs, L.data(), njobs * sizeof(DstLaunch),
+    KKT_CUDA_TRY(cudaMemcpy(slot.dst + static_cast<size_t>(pass) * KKT_BATCH_MAX, L.data(), njobs * sizeof(DstLaunch),
                             cudaMemcpyHostToDevice));
-    KKT_CUDA_TRY(cudaMemcpy(slot.dst_prefix + static_cast<size_t>(pass) * (njobs + 1), prefix.data(),
+    KKT_CUDA_TRY(cudaMemcpy(slot.dst_prefix + static_cast<size_t>(pass) * (KKT_BATCH_MAX + 1), prefix.data(),
                             (njobs + 1) * sizeof(long long), cudaMemcpyHostToDevice));
     slot.dst_total[pass] = prefix[njobs];
     slot.dst_smem[pass] = sm;
@@ -364,7 +364,7 @@ int dst_batched_launch(const BatchSlot& slot, int pass, cudaStream_t st) {
   const long long grid = std::min<long long>(total, static_cast<long long>(std::max(sms, 1)) * std::max(per_sm, 1));
   ProfScope ps(KKT_K_DST, st, slot.dst_flops[pass], slot.dst_bytes[pass]);
   dst_tile_batched<<<static_cast<unsigned>(grid), kThreads, sm, st>>>(
-      slot.dst + static_cast<size_t>(pass) * slot.njobs, slot.dst_prefix + static_cast<size_t>(pass) * (slot.njobs + 1),
+      slot.dst + static_cast<size_t>(pass) * KKT_BATCH_MAX, slot.dst_prefix + static_cast<size_t>(pass) * (KKT_BATCH_MAX + 1),
       slot.njobs, total);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;

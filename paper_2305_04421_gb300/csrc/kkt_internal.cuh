@@ -318,6 +318,22 @@ struct BatchSlot {
   double mv_V = 0;
 };
 
+// Item lookup of the batched persistent kernels: item t belongs to job k with
+// prefix[k] <= t < prefix[k+1]. Each block copies the prefix table (at most KKT_BATCH_MAX + 1
+// entries) to shared memory once, so the per-item search costs no global-memory round trips.
+__device__ __forceinline__ void batch_prefix_load(long long* sp, const long long* __restrict__ prefix, int nj) {
+  for (int i = threadIdx.x; i <= nj; i += blockDim.x) sp[i] = prefix[i];
+  __syncthreads();
+}
+__device__ __forceinline__ int batch_find(const long long* sp, int nj, long long t) {
+  int lo = 0, hi = nj - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (sp[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 struct DstJob {
   const kkt_handle* h;
   const double* in;

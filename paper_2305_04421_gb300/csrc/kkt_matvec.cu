@@ -35,6 +35,8 @@ __device__ __forceinline__ double apply_b(const double* __restrict__ v, long lon
 //   y_u = uu u + wc0 w - wcx (w_w + w_e) - wcy (w_s + w_n) - wn w^{n+1}
 //   y_z = zz z - zw w
 //   y_w = uc0 u - ucx (u_w + u_e) - ucy (u_s + u_n) - up u^{n-1} - wz z
+constexpr long long kMvItem = 2048;   // points per work item of the batched matvec
+
 struct MatvecCoef {
   double uu, wc0, wcx, wcy, wn;
   double zz, zw;
@@ -128,35 +130,35 @@ __global__ void axpby_kernel(double alpha, const double* __restrict__ x, double 
 // terms scaled by the instance's scale_dev entry (1 / eta of the Krylov vector being applied).
 __global__ void matvec_batched(const MatvecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
                                long long total, const double* __restrict__ scale_dev) {
+  __shared__ long long sp[KKT_BATCH_MAX + 1];
+  batch_prefix_load(sp, prefix, nj);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    int lo = 0, hi = nj - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const MatvecJob& J = jobs[lo];
-    const long long idx = (t - prefix[lo]) * blockDim.x + threadIdx.x;
-    if (idx >= J.V) continue;
+    const int k = batch_find(sp, nj, t);
+    const MatvecJob& J = jobs[k];
     const double e = scale_dev[J.scale_index];
-    const int i = static_cast<int>(idx % J.Mx);
-    const long long r = idx / J.Mx;
-    const int j = static_cast<int>(r % J.My);
-    const int n = static_cast<int>(r / J.My);
-    const bool hw = i > 0, he = i + 1 < J.Mx, hs = j > 0, hn = j + 1 < J.My;
-    const double wc = J.w[idx];
-    const double wwe = (hw ? J.w[idx - 1] : 0.0) + (he ? J.w[idx + 1] : 0.0);
-    const double wsn = (hs ? J.w[idx - J.Mx] : 0.0) + (hn ? J.w[idx + J.Mx] : 0.0);
-    const double wnx = n + 1 < J.Nt ? J.w[idx + J.N] : 0.0;
-    const double uc = J.u[idx];
-    const double uwe = (hw ? J.u[idx - 1] : 0.0) + (he ? J.u[idx + 1] : 0.0);
-    const double usn = (hs ? J.u[idx - J.Mx] : 0.0) + (hn ? J.u[idx + J.Mx] : 0.0);
-    const double upr = n > 0 ? J.u[idx - J.N] : 0.0;
-    const double zc = J.z[idx];
-    double tt = fma(J.wcy, wsn, fma(J.wcx, wwe, J.wn * wnx));
-    J.y[idx] = fma(J.uu * e, uc, fma(J.wc0, wc, -tt));
-    J.y[J.V + idx] = fma(J.zz * e, zc, -J.zw * wc);
-    tt = fma(J.ucy * e, usn, fma(J.ucx * e, uwe, fma(J.up * e, upr, (J.wz * e) * zc)));
-    J.y[2 * J.V + idx] = fma(J.uc0 * e, uc, -tt);
+    const long long idx0 = (t - sp[k]) * kMvItem;
+    const long long idx1 = idx0 + kMvItem < J.V ? idx0 + kMvItem : J.V;
+    for (long long idx = idx0 + threadIdx.x; idx < idx1; idx += blockDim.x) {
+      const int i = static_cast<int>(idx % J.Mx);
+      const long long r = idx / J.Mx;
+      const int j = static_cast<int>(r % J.My);
+      const int n = static_cast<int>(r / J.My);
+      const bool hw = i > 0, he = i + 1 < J.Mx, hs = j > 0, hn = j + 1 < J.My;
+      const double wc = J.w[idx];
+      const double wwe = (hw ? J.w[idx - 1] : 0.0) + (he ? J.w[idx + 1] : 0.0);
+      const double wsn = (hs ? J.w[idx - J.Mx] : 0.0) + (hn ? J.w[idx + J.Mx] : 0.0);
+      const double wnx = n + 1 < J.Nt ? J.w[idx + J.N] : 0.0;
+      const double uc = J.u[idx];
+      const double uwe = (hw ? J.u[idx - 1] : 0.0) + (he ? J.u[idx + 1] : 0.0);
+      const double usn = (hs ? J.u[idx - J.Mx] : 0.0) + (hn ? J.u[idx + J.Mx] : 0.0);
+      const double upr = n > 0 ? J.u[idx - J.N] : 0.0;
+      const double zc = J.z[idx];
+      double tt = fma(J.wcy, wsn, fma(J.wcx, wwe, J.wn * wnx));
+      J.y[idx] = fma(J.uu * e, uc, fma(J.wc0, wc, -tt));
+      J.y[J.V + idx] = fma(J.zz * e, zc, -J.zw * wc);
+      tt = fma(J.ucy * e, usn, fma(J.ucx * e, uwe, fma(J.up * e, upr, (J.wz * e) * zc)));
+      J.y[2 * J.V + idx] = fma(J.uc0 * e, uc, -tt);
+    }
   }
 }
 
@@ -226,15 +228,16 @@ int launch_matvec_spectral(const kkt_handle* h, const double* u, double su, cons
 }
 
 int matvec_batched_prepare(BatchSlot& slot, const MatvecJob* jobs, int nj) {
+  if (nj < 1 || nj > KKT_BATCH_MAX) return set_error(KKT_ERR_INVALID_ARG, "batched jobs out of range");
   std::vector<long long> pre(nj + 1, 0);
   double V = 0;
   for (int k = 0; k < nj; ++k) {
-    pre[k + 1] = pre[k] + (jobs[k].V + 255) / 256;
+    pre[k + 1] = pre[k] + (jobs[k].V + kMvItem - 1) / kMvItem;
     V += static_cast<double>(jobs[k].V);
   }
   if (!slot.mv) {
-    KKT_CUDA_TRY(cudaMalloc(&slot.mv, nj * sizeof(MatvecJob)));
-    KKT_CUDA_TRY(cudaMalloc(&slot.mv_prefix, (nj + 1) * sizeof(long long)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.mv, KKT_BATCH_MAX * sizeof(MatvecJob)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.mv_prefix, (KKT_BATCH_MAX + 1) * sizeof(long long)));
   }
   KKT_CUDA_TRY(cudaMemcpy(slot.mv, jobs, nj * sizeof(MatvecJob), cudaMemcpyHostToDevice));
   KKT_CUDA_TRY(cudaMemcpy(slot.mv_prefix, pre.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));

@@ -351,22 +351,16 @@ __global__ void sweep_kernel(const TI* __restrict__ rhat, double in_scale, TO* _
                            reinterpret_cast<TC*>(vs_raw));
 }
 
-__device__ __forceinline__ int find_job(const long long* __restrict__ prefix, int nj, long long t) {
-  int lo = 0, hi = nj - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
 
 // Batched coarse solves: item = a block of 128 modes of one instance (FP64).
 __global__ void coarse_batched(const SpecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
                                long long total, const double* __restrict__ scale_dev) {
+  __shared__ long long sp[KKT_BATCH_MAX + 1];
+  batch_prefix_load(sp, prefix, nj);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int k = find_job(prefix, nj, t);
+    const int k = batch_find(sp, nj, t);
     const SpecJob& J = jobs[k];
-    const long long q = (t - prefix[k]) * blockDim.x + threadIdx.x;
+    const long long q = (t - sp[k]) * blockDim.x + threadIdx.x;
     if (q < J.p.N && J.p.two_level)
       coarse_body<double>(J.rhat, J.scale_base * scale_dev[J.scale_index], J.p, J.cc, J.cy, q);
   }
@@ -376,10 +370,12 @@ __global__ void coarse_batched(const SpecJob* __restrict__ jobs, const long long
 __global__ void sweep_batched(const SpecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
                               long long total, const double* __restrict__ scale_dev) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
+  __shared__ long long sp[KKT_BATCH_MAX + 1];
+  batch_prefix_load(sp, prefix, nj);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-    const int k = find_job(prefix, nj, t);
+    const int k = batch_find(sp, nj, t);
     const SpecJob& J = jobs[k];
-    const long long local = t - prefix[k];
+    const long long local = t - sp[k];
     const long long mblocks = (J.p.N + blockDim.x - 1) / blockDim.x;
     const int s = static_cast<int>(local / mblocks);
     const long long q = (local % mblocks) * blockDim.x + threadIdx.x;
@@ -512,6 +508,7 @@ int spectral_learned_apply(const kkt_handle* h, bool padded, const float* y, cud
 SpecParams make_spec_params(const kkt_handle* h) { return make_params(h, false); }
 
 int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
+  if (nj < 1 || nj > KKT_BATCH_MAX) return set_error(KKT_ERR_INVALID_ARG, "batched jobs out of range");
   slot.njobs = nj;
   const int tb = slot.sweep_tb > 0 ? slot.sweep_tb : 128;
   std::vector<long long> cp(nj + 1, 0), sp(nj + 1, 0);
@@ -533,9 +530,9 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
   if (static_cast<size_t>(max_len) * tb * sizeof(double) > 200 * 1024)
     return set_error(KKT_ERR_UNSUPPORTED, "batched sweeps: a subdomain is too long for shared memory");
   if (!slot.spec) {
-    KKT_CUDA_TRY(cudaMalloc(&slot.spec, nj * sizeof(SpecJob)));
-    KKT_CUDA_TRY(cudaMalloc(&slot.coarse_prefix, (nj + 1) * sizeof(long long)));
-    KKT_CUDA_TRY(cudaMalloc(&slot.sweep_prefix, (nj + 1) * sizeof(long long)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.spec, KKT_BATCH_MAX * sizeof(SpecJob)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.coarse_prefix, (KKT_BATCH_MAX + 1) * sizeof(long long)));
+    KKT_CUDA_TRY(cudaMalloc(&slot.sweep_prefix, (KKT_BATCH_MAX + 1) * sizeof(long long)));
   }
   KKT_CUDA_TRY(cudaMemcpy(slot.spec, jobs, nj * sizeof(SpecJob), cudaMemcpyHostToDevice));
   KKT_CUDA_TRY(cudaMemcpy(slot.coarse_prefix, cp.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));
