@@ -347,13 +347,14 @@ def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
 def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, steps: int, warmup: int) -> dict:
     """The headline workload's solve in the other FGMRES configurations: the spectral basis
     (f and x transformed once, no transforms inside the iteration) and CGS2 orthogonalisation
-    (the MGS default's alternative). Same tolerance, x_0 = 0, device time per solve."""
+    and paired MGS (the MGS default's alternatives). Same tolerance, x_0 = 0, device time per
+    solve."""
     import torch
 
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
     out = {}
     for name, opts in (("spectral_basis", {"basis": "spectral"}), ("cgs2", {"orth": "cgs2"}),
-                       ("spectral_basis_cgs2", {"basis": "spectral", "orth": "cgs2"})):
+                       ("mgs2", {"orth": "mgs2"}), ("spectral_basis_mgs2", {"basis": "spectral", "orth": "mgs2"})):
         s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, **opts)
         f = s.build_rhs(ut)
         ms, res, x = time_solves(kkt_mod, s, f, steps, warmup)
@@ -369,62 +370,65 @@ def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, st
 def measure_batched(kkt_mod, dev) -> dict:
     """The 64 uneven instances of the batched workload (sizes 64^2..256^2, Nt 128..1024, N_D
     8..64, spread nu and omega): one batched solve (memory waves, one launch per phase over all
-    instances, graph replay) against the same instances solved one after another with
-    kkt_solve. Both to the same 1e-8 weighted tolerance from x_0 = 0; device time of the solve
-    calls only (CUDA events), inputs resident."""
+    running instances, graph replay) against the same instances solved one after another with
+    kkt_solve, in the physical basis and in the spectral basis. All to the same 1e-8 weighted
+    tolerance from x_0 = 0; device time of the solve calls only (CUDA events), inputs
+    resident; the batched value is the second call (the first also autotunes)."""
     import torch
 
     ws = workloads.batched_instances(64, seed=3)
-    fs, seq_ms, seq_its = [], 0.0, []
     stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    fs = []
     for w in ws:
         s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
-        ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
-        f = s.build_rhs(ut)
-        x = torch.zeros_like(f)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        r = s.solve(f, x, tol=TOL, maxit=MAXIT)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        seq_ms += e0.elapsed_time(e1)
-        seq_its.append(r.iterations if r.status == kkt_mod.KKT_OK else -1)
-        fs.append(f)
-        del x, ut
+        fs.append(s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev)))
         s.close()
-        torch.cuda.empty_cache()
-    b = kkt_mod.Batch(ws)
-    runs = []
-    for _ in range(2):       # the first call also autotunes the tiles and sweep blocks
-        xs = [torch.zeros_like(f) for f in fs]
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res = b.solve(fs, xs, tol=TOL, maxit=MAXIT)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        runs.append((e0.elapsed_time(e1), res))
-        del xs
-    b.close()
-    ms, res = runs[1]
-    its = res.iterations
-    unknowns = sum(3 * w.V for w in ws)
     out = {"workload": "64 uneven instances: nx=ny in {64,128,256}, Nt in {128..1024}, N_D in {8..64}, "
                        "nu in [0.1,10], omega in [1e-6,1e-2] (log-uniform), seed 3",
-           "instances": len(ws), "unknowns_total": unknowns,
-           "batched": {"solves_per_s": len(ws) / (ms / 1e3), "time_ms": ms, "first_call_ms": runs[0][0],
-                       "waves": res.waves, "graphs": res.graphs, "graph_launches": res.graph_launches,
-                       "tile_lines": res.tile_lines, "sweep_block": res.sweep_block,
-                       "tune_ms_dst_tl8_16_32": res.tune_ms_dst, "tune_ms_sweep_tb64_128_256": res.tune_ms_sweep,
-                       "iterations_min_median_max": [min(its), int(np.median(its)), max(its)],
-                       "all_converged": all(st == kkt_mod.KKT_OK for st in res.statuses)},
-           "sequential": {"solves_per_s": len(ws) / (seq_ms / 1e3), "time_ms": seq_ms,
-                          "all_converged": all(i >= 0 for i in seq_its)},
-           "iteration_count_mismatches_gt1": sum(1 for a, c in zip(its, seq_its) if abs(a - c) > 1)}
-    out["speedup_batched_vs_sequential"] = seq_ms / ms
+           "instances": len(ws), "unknowns_total": sum(3 * w.V for w in ws)}
+    for basis in ("physical", "spectral"):
+        seq_ms, seq_its = 0.0, []
+        for w, f in zip(ws, fs):
+            s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, basis=basis)
+            x = torch.zeros_like(f)
+            ms, r = timed(lambda: s.solve(f, x, tol=TOL, maxit=MAXIT))
+            seq_ms += ms
+            seq_its.append(r.iterations if r.status == kkt_mod.KKT_OK else -1)
+            del x
+            s.close()
+            torch.cuda.empty_cache()
+        b = kkt_mod.Batch(ws, basis=basis)
+        runs = []
+        for _ in range(2):
+            xs = [torch.zeros_like(f) for f in fs]
+            runs.append(timed(lambda: b.solve(fs, xs, tol=TOL, maxit=MAXIT)))
+            del xs
+        b.close()
+        torch.cuda.empty_cache()
+        ms, res = runs[1]
+        its = res.iterations
+        out[basis] = {
+            "batched": {"solves_per_s": len(ws) / (ms / 1e3), "time_ms": ms, "first_call_ms": runs[0][0],
+                        "waves": res.waves, "graphs": res.graphs, "graph_launches": res.graph_launches,
+                        "tile_lines": res.tile_lines, "sweep_block": res.sweep_block,
+                        "tune_ms_dst_tl8_16_32": res.tune_ms_dst, "tune_ms_sweep_tb64_128_256": res.tune_ms_sweep,
+                        "iterations_min_median_max": [min(its), int(np.median(its)), max(its)],
+                        "all_converged": all(st == kkt_mod.KKT_OK for st in res.statuses)},
+            "sequential": {"solves_per_s": len(ws) / (seq_ms / 1e3), "time_ms": seq_ms,
+                           "all_converged": all(i >= 0 for i in seq_its)},
+            "iteration_count_mismatches_gt1": sum(1 for a, c in zip(its, seq_its) if abs(a - c) > 1),
+            "speedup_batched_vs_sequential": seq_ms / ms}
     del fs
     torch.cuda.empty_cache()
     return out

@@ -83,7 +83,11 @@ enum kkt_orth {
   KKT_ORTH_MGS = 0,
   /* classical Gram-Schmidt with one conditional repeat (||w'||^2 < ||w||^2 / 2): all dots of a
    * pass in one multi-dot, one multi-axpy; 4 FMAs per element and basis vector when it repeats */
-  KKT_ORTH_CGS2 = 1
+  KKT_ORTH_CGS2 = 1,
+  /* MGS over pairs of basis vectors: both dots of a pair are taken on the same w, the pair is
+   * subtracted in one pass that also takes the next pair's dots. 3 vector passes per basis
+   * vector instead of 4, the same FMA count; equals MGS up to the pair's orthogonality error */
+  KKT_ORTH_MGS2 = 2
 };
 
 /* Basis the FGMRES iteration runs in. */

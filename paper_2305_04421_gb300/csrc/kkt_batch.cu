@@ -376,7 +376,11 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   if (b->mem_limit > 0) budget = std::min(budget, static_cast<double>(b->mem_limit));
   std::vector<int> order(n_inst);
   std::iota(order.begin(), order.end(), 0);
-  auto need = [&](int i) { return 8.0 * ((m + 1) * 3.0 + m) * static_cast<double>(b->inst[i]->g.V); };
+  // spectral basis: f and x run on sine-mode coefficients (x transformed in place, f into a copy)
+  const bool spectral = b->opt.basis == KKT_BASIS_SPECTRAL;
+  auto need = [&](int i) {
+    return 8.0 * ((m + 1) * 3.0 + m + (spectral ? 3.0 : 0.0)) * static_cast<double>(b->inst[i]->g.V);
+  };
   std::sort(order.begin(), order.end(), [&](int a, int c) { return need(a) > need(c); });
   std::vector<std::vector<int>> waves;
   std::vector<double> wave_mem;
@@ -413,7 +417,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   for (const auto& wave : waves) {
     const int nw = static_cast<int>(wave.size());
     // per-instance Krylov arenas
-    std::vector<double*> Vb(nw, nullptr), Zw(nw, nullptr);
+    std::vector<double*> Vb(nw, nullptr), Zw(nw, nullptr), Fs(nw, nullptr);
     std::vector<InstState*> S(nw);
     double* part = nullptr;
     long long max_items = 0;
@@ -422,7 +426,8 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       kkt_handle* h = b->inst[wave[k]];
       const long long V = h->g.V;
       if (cudaMalloc(&Vb[k], sizeof(double) * (m + 1) * 3 * V) != cudaSuccess ||
-          cudaMalloc(&Zw[k], sizeof(double) * m * V) != cudaSuccess)
+          cudaMalloc(&Zw[k], sizeof(double) * m * V) != cudaSuccess ||
+          (spectral && cudaMalloc(&Fs[k], sizeof(double) * 3 * V) != cudaSuccess))
         rc = set_error(KKT_ERR_OOM, "batched Krylov arena");
       max_items += (3 * V + kChunk - 1) / kChunk;
       InstState& I = all[wave[k]];
@@ -439,6 +444,16 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       I.eta.assign(m + 1, 0.0);
       I.y.assign(m, 0.0);
       S[k] = &I;
+    }
+    // into the sine-mode basis: f -> Fs (copy), x in place (each block by the orthonormal 2D
+    // DST-I, its own inverse); f then means Fs for the rest of the wave
+    for (int k = 0; k < nw && rc == KKT_OK && spectral; ++k) {
+      const long long V = S[k]->h->g.V;
+      for (int bl = 0; bl < 3 && rc == KKT_OK; ++bl) {
+        rc = dst2d(S[k]->h, S[k]->f + bl * V, Fs[k] + bl * V, st);
+        if (rc == KKT_OK) rc = dst2d(S[k]->h, S[k]->x + bl * V, S[k]->x + bl * V, st);
+      }
+      S[k]->f = Fs[k];
     }
     if (rc == KKT_OK && cudaMalloc(&part, sizeof(double) * max_items * 33) != cudaSuccess)
       rc = set_error(KKT_ERR_OOM, "batched reduction scratch");
@@ -468,6 +483,40 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       return finalize(t, 1);
     };
     // preconditioner + matvec tables of step j (pointers fixed per j)
+    // matvec job y = diag(du, dz, dw) K (su u, sz z, w), su, sz scaled by scale_dev[k] at run time
+    auto fill_matvec = [&](MatvecJob& M, int k, const double* u, const double* z, const double* w, double* y,
+                           double su, double sz) {
+      InstState& I = *S[k];
+      const Geometry& g = I.h->g;
+      M.u = u;
+      M.z = z;
+      M.w = w;
+      M.y = y;
+      M.Mx = g.Mx;
+      M.My = g.My;
+      M.Nt = g.Nt;
+      M.N = g.N;
+      M.V = g.V;
+      const double c0 = spectral ? 1.0 : 1.0 + 2.0 * g.cx + 2.0 * g.cy;
+      const double cx = spectral ? 0.0 : g.cx, cy = spectral ? 0.0 : g.cy;
+      M.uu = I.du * g.h * su;
+      M.wc0 = I.du * c0;
+      M.wcx = I.du * cx;
+      M.wcy = I.du * cy;
+      M.wn = I.du;
+      M.zz = I.dz * g.omega * g.h * sz;
+      M.zw = I.dz * g.dt;
+      M.uc0 = I.dw * su * c0;
+      M.ucx = I.dw * su * cx;
+      M.ucy = I.dw * su * cy;
+      M.up = I.dw * su;
+      M.wz = I.dw * g.dt * sz;
+      M.scale_index = k;
+      M.spectral = spectral ? 1 : 0;
+      M.lx = I.h->d_lx;
+      M.ly = I.h->d_ly;
+      M.dtnu = g.dtnu;
+    };
     std::vector<int> everyone(nw);
     std::iota(everyone.begin(), everyone.end(), 0);
     // preconditioner + matvec tables of step j for the wave instances in `mem`
@@ -489,47 +538,29 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         inv[q] = DstJob{h, h->spec2, Zj};
         SpecJob& J = sj[q];
         J.p = make_spec_params(h);
-        J.rhat = h->spec;
-        J.yhat = h->spec2;
+        J.rhat = spectral ? Vj + 2 * V : h->spec;   // the spectral basis needs no transforms
+        J.yhat = spectral ? Zj : h->spec2;
         J.cc = h->coarse_c;
         J.cy = h->coarse_w;
         J.scale_base = 1.0 / I.dw;
         J.max_len = h->td.max_len;
         J.scale_index = k;
-        MatvecJob& M = mj[q];
-        M.u = Vj;
-        M.z = Vj + V;
-        M.w = Zj;
-        M.y = Vj + 3 * V;
-        M.Mx = g.Mx;
-        M.My = g.My;
-        M.Nt = g.Nt;
-        M.N = g.N;
-        M.V = V;
-        const double c0 = 1.0 + 2.0 * g.cx + 2.0 * g.cy;
-        const double su = 1.0 / (g.h * I.du), sz = 1.0 / (g.omega * g.h * I.dz);
-        M.uu = I.du * g.h * su;
-        M.wc0 = I.du * c0;
-        M.wcx = I.du * g.cx;
-        M.wcy = I.du * g.cy;
-        M.wn = I.du;
-        M.zz = I.dz * g.omega * g.h * sz;
-        M.zw = I.dz * g.dt;
-        M.uc0 = I.dw * su * c0;
-        M.ucx = I.dw * su * g.cx;
-        M.ucy = I.dw * su * g.cy;
-        M.up = I.dw * su;
-        M.wz = I.dw * g.dt * sz;
-        M.scale_index = k;
+        fill_matvec(mj[q], k, Vj, Vj + V, Zj, Vj + 3 * V, 1.0 / (g.h * I.du), 1.0 / (g.omega * g.h * I.dz));
       }
       const int tl = b->tuned_tile_lines;
-      KKT_TRY(dst_batched_prepare(sl, 0, fwd.data(), nm, tl));
-      KKT_TRY(dst_batched_prepare(sl, 2, inv.data(), nm, tl));
+      if (!spectral) {
+        KKT_TRY(dst_batched_prepare(sl, 0, fwd.data(), nm, tl));
+        KKT_TRY(dst_batched_prepare(sl, 2, inv.data(), nm, tl));
+      }
       KKT_TRY(spectral_batched_prepare(sl, sj.data(), nm));
       KKT_TRY(matvec_batched_prepare(sl, mj.data(), nm));
       return KKT_OK;
     };
     auto phase_launch = [&](const BatchSlot& sl, cudaStream_t s2) -> int {
+      if (spectral) {
+        KKT_TRY(spectral_batched_launch(sl, d_scale, s2));
+        return matvec_batched_launch(sl, d_scale, s2);
+      }
       KKT_TRY(dst_batched_launch(sl, 0, s2));
       KKT_TRY(dst_batched_launch(sl, 1, s2));
       KKT_TRY(spectral_batched_launch(sl, d_scale, s2));
@@ -542,6 +573,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
     // Candidates that a wave's sizes rule out (shared memory) are skipped.
     if (rc == KKT_OK && b->tuned_tile_lines == 0) {
       const int cand_tl[3] = {8, 16, 32}, cand_tb[3] = {64, 128, 256};
+      for (int a = 0; a < 3; ++a) b->tune_ms_dst[a] = 0.0;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       KKT_CUDA_TRY(cudaEventCreate(&e0));
       KKT_CUDA_TRY(cudaEventCreate(&e1));
@@ -562,7 +594,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         return ok ? ms / 2.0 : 1e30;
       };
       int best_tl = 1, best_tb = 1;
-      for (int a = 0; a < 3; ++a) {
+      for (int a = 0; a < 3 && !spectral; ++a) {   // the spectral basis has no transforms in the loop
         b->tuned_tile_lines = cand_tl[a];
         b->tuned_sweep_tb = 128;
         b->tune_ms_dst[a] = 1e30;
@@ -613,32 +645,8 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
     auto residual = [&]() -> int {
       std::vector<MatvecJob> mj(nw);
       for (int k = 0; k < nw; ++k) {
-        InstState& I = *S[k];
-        const Geometry& g = I.h->g;
-        MatvecJob& M = mj[k];
-        M.u = I.x;
-        M.z = I.x + g.V;
-        M.w = I.x + 2 * g.V;
-        M.y = Vb[k];
-        M.Mx = g.Mx;
-        M.My = g.My;
-        M.Nt = g.Nt;
-        M.N = g.N;
-        M.V = g.V;
-        const double c0 = 1.0 + 2.0 * g.cx + 2.0 * g.cy;
-        M.uu = I.du * g.h;
-        M.wc0 = I.du * c0;
-        M.wcx = I.du * g.cx;
-        M.wcy = I.du * g.cy;
-        M.wn = I.du;
-        M.zz = I.dz * g.omega * g.h;
-        M.zw = I.dz * g.dt;
-        M.uc0 = I.dw * c0;
-        M.ucx = I.dw * g.cx;
-        M.ucy = I.dw * g.cy;
-        M.up = I.dw;
-        M.wz = I.dw * g.dt;
-        M.scale_index = k;
+        const long long V = S[k]->h->g.V;
+        fill_matvec(mj[k], k, S[k]->x, S[k]->x + V, S[k]->x + 2 * V, Vb[k], 1.0, 1.0);
         h_scale[k] = 1.0;
       }
       KKT_CUDA_TRY(cudaMemcpyAsync(d_scale, h_scale, sizeof(double) * nw, cudaMemcpyHostToDevice, st));
@@ -722,7 +730,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
           if (rc == KKT_OK) rc = phase_launch(sub_slot, st);
           if (rc != KKT_OK) break;
         } else {
-          if (!slots[j].dst) {
+          if (slots[j].njobs == 0) {
             rc = prepare_slot(slots[j], j, everyone);
             if (rc != KKT_OK) break;
           }
@@ -760,7 +768,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         if (rc != KKT_OK) break;
         std::vector<double> wn2(nw, 0.0), before(nr, 0.0);
         std::vector<char> need(nr, 1);
-        if (b->opt.orth == KKT_ORTH_MGS) {
+        if (b->opt.orth != KKT_ORTH_CGS2) {   // MGS (the paired variant runs as MGS here)
           // modified Gram-Schmidt, step k over all running instances at once; the dots stay on
           // the device (d_out[q][k]) and feed the next step, the host reads the columns once
           for (int q = 0; q < nr; ++q)
@@ -919,9 +927,16 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
     t_xz.free();
     t_xw.free();
     cudaFree(part);
+    // back to grid values: x in place
+    for (int k = 0; k < nw && spectral; ++k) {
+      const long long V = S[k]->h->g.V;
+      for (int bl = 0; bl < 3; ++bl)
+        if (dst2d(S[k]->h, S[k]->x + bl * V, S[k]->x + bl * V, st) < 0 && rc == KKT_OK) rc = KKT_ERR_CUDA;
+    }
     for (int k = 0; k < nw; ++k) {
       cudaFree(Vb[k]);
       cudaFree(Zw[k]);
+      cudaFree(Fs[k]);
     }
     if (rc != KKT_OK) {
       rc_all = rc;

@@ -429,7 +429,8 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
   if (opt->residual_norm != KKT_NORM_L2 && opt->residual_norm != KKT_NORM_EUCLIDEAN)
     return set_error(KKT_ERR_INVALID_ARG, "residual_norm out of range");
   if (opt->tc_split != 0 && opt->tc_split != 1) return set_error(KKT_ERR_INVALID_ARG, "tc_split must be 0 or 1");
-  if (opt->orth != KKT_ORTH_MGS && opt->orth != KKT_ORTH_CGS2) return set_error(KKT_ERR_INVALID_ARG, "orth out of range");
+  if (opt->orth != KKT_ORTH_MGS && opt->orth != KKT_ORTH_CGS2 && opt->orth != KKT_ORTH_MGS2)
+    return set_error(KKT_ERR_INVALID_ARG, "orth out of range");
   if (opt->basis != KKT_BASIS_PHYSICAL && opt->basis != KKT_BASIS_SPECTRAL)
     return set_error(KKT_ERR_INVALID_ARG, "basis out of range");
   if (opt->basis == KKT_BASIS_SPECTRAL && opt->precision != KKT_PREC_FP64)
@@ -756,6 +757,29 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
                      dw));
       for (int k = 0; k <= j; ++k) Hs(k, j) = 0.0;
       double wnorm2 = 0.0;
+      if (h->opt.orth == KKT_ORTH_MGS2) {
+        // MGS over pairs of basis vectors: both dots of a pair are taken on the same w (the
+        // vectors of a pair are orthogonal to working accuracy), the pair is subtracted in one
+        // pass that also takes the next pair's dots: 3 vector passes per basis vector
+        auto vec = [&](int i) -> const double* { return Vb + static_cast<size_t>(i) * n3; };
+        const int nd0 = std::min(2, j + 1);
+        KKT_TRY(krylov_mgs2_step(h, 0, nullptr, nullptr, nullptr, 0.0, 0.0, nd0, vec(0), nd0 > 1 ? vec(1) : nullptr, W,
+                                 n3, h->red_out, st));
+        for (int k = 0; k <= j;) {
+          const int na = std::min(2, j + 1 - k);
+          const int nd = std::min(2, j + 1 - (k + na));
+          const double s0 = 1.0 / (eta[k] * eta[k]);
+          const double s1 = na > 1 ? 1.0 / (eta[k + 1] * eta[k + 1]) : 0.0;
+          KKT_TRY(krylov_mgs2_step(h, na, vec(k), na > 1 ? vec(k + 1) : nullptr, h->red_out + k, s0, s1, nd,
+                                   nd > 0 ? vec(k + na) : nullptr, nd > 1 ? vec(k + na + 1) : nullptr, W, n3,
+                                   h->red_out + k + na, st));
+          k += na;
+        }
+        KKT_TRY(fetch(j + 2));
+        for (int k = 0; k <= j; ++k) Hs(k, j) = hr[k] / eta[k];
+        wnorm2 = hr[j + 1];
+        if (!std::isfinite(wnorm2)) return finish(set_error(KKT_ERR_NONFINITE, "Krylov vector is not finite"), NAN);
+      }
       if (h->opt.orth == KKT_ORTH_MGS) {
         // modified Gram-Schmidt: d_k = <V_k, w> on the w already orthogonalised against
         // V_0..V_k-1, then w -= (d_k / eta_k^2) V_k; the dots stay on the device (red_out[k])

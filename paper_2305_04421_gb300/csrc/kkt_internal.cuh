@@ -227,6 +227,11 @@ int krylov_norm2(kkt_handle* h, const double* x, long long n, cudaStream_t st); 
 // <Vn, w> (Vn non-null) or <w, w> (Vn null), reduced deterministically.
 int krylov_mgs_step(kkt_handle* h, const double* Vk, const double* dot, double s, const double* Vn, double* w,
                     long long n, double* out, cudaStream_t st);
+// Paired MGS step: w -= sum_{i < na} (dot[i] s_i) A_i, then out[0..nd) = <B_i, w> (nd > 0) or
+// out[0] = <w, w> (nd = 0); na, nd in 0..2.
+int krylov_mgs2_step(kkt_handle* h, int na, const double* A0, const double* A1, const double* dot, double s0,
+                     double s1, int nd, const double* B0, const double* B1, double* w, long long n, double* out,
+                     cudaStream_t st);
 int krylov_partial_capacity();
 
 // ---- batched forms: several instances per launch ---------------------------------------
@@ -291,6 +296,12 @@ struct MatvecJob {
   long long N, V;
   double uu, wc0, wcx, wcy, wn, zz, zw, uc0, ucx, ucy, up, wz;   // su-, sz-dependent terms at su = sz = 1
   int scale_index;
+  // spectral basis: the stencil acts per sine mode as mu0 = 1 + dtnu (lx_k + ly_l); wc0, uc0 then
+  // exclude the centre weight and wcx, wcy, ucx, ucy are unused
+  int spectral;
+  const double* lx;
+  const double* ly;
+  double dtnu;
 };
 // out = alpha * x + beta * y (elementwise; out may alias x or y)
 int launch_axpby(double alpha, const double* x, double beta, const double* y, double* out, long long n,

@@ -138,6 +138,24 @@ __global__ void matvec_batched(const MatvecJob* __restrict__ jobs, const long lo
     const double e = scale_dev[J.scale_index];
     const long long idx0 = (t - sp[k]) * kMvItem;
     const long long idx1 = idx0 + kMvItem < J.V ? idx0 + kMvItem : J.V;
+    if (J.spectral) {
+      for (long long idx = idx0 + threadIdx.x; idx < idx1; idx += blockDim.x) {
+        const int i = static_cast<int>(idx % J.Mx);
+        const long long r = idx / J.Mx;
+        const int j = static_cast<int>(r % J.My);
+        const int n = static_cast<int>(r / J.My);
+        const double mu0 = fma(J.dtnu, __ldg(J.lx + i) + __ldg(J.ly + j), 1.0);
+        const double wc = J.w[idx];
+        const double wnx = n + 1 < J.Nt ? J.w[idx + J.N] : 0.0;
+        const double uc = J.u[idx];
+        const double upr = n > 0 ? J.u[idx - J.N] : 0.0;
+        const double zc = J.z[idx];
+        J.y[idx] = fma(J.uu * e, uc, fma(J.wc0 * mu0, wc, -J.wn * wnx));
+        J.y[J.V + idx] = fma(J.zz * e, zc, -J.zw * wc);
+        J.y[2 * J.V + idx] = fma(J.uc0 * e * mu0, uc, -fma(J.up * e, upr, (J.wz * e) * zc));
+      }
+      continue;
+    }
     for (long long idx = idx0 + threadIdx.x; idx < idx1; idx += blockDim.x) {
       const int i = static_cast<int>(idx % J.Mx);
       const long long r = idx / J.Mx;

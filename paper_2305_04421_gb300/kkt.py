@@ -32,7 +32,7 @@ COARSE = {"exact": 0, "none": 1, "learned": 2}
 VARIANT = {"multiplicative": 0, "additive": 1}
 POU = {"left": 0, "right": 1}
 NORM = {"l2": 0, "euclidean": 1}
-ORTH = {"mgs": 0, "cgs2": 1}
+ORTH = {"mgs": 0, "cgs2": 1, "mgs2": 2}
 BASIS = {"physical": 0, "spectral": 1}
 HISTORY_MAX = 1024
 
@@ -541,7 +541,7 @@ class Batch:
     with nx, ny, Nt, n_sub, T, nu, omega attributes (e.g. workloads.Workload) or tuples."""
 
     def __init__(self, instances, *, coarse="exact", variant="multiplicative", pou="left", restart=30,
-                 jhat_sign=-1, residual_norm="l2", orth="mgs", Lx=1.0, Ly=1.0):
+                 jhat_sign=-1, residual_norm="l2", orth="mgs", basis="physical", Lx=1.0, Ly=1.0):
         descs = []
         for w in instances:
             if isinstance(w, tuple):
@@ -549,7 +549,7 @@ class Batch:
             else:
                 descs.append(KKTInstance(w.nx, w.ny, w.Nt, w.n_sub, w.T, w.nu, w.omega))
         opt = KKTOptions(PREC["fp64"], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
-                         NORM[residual_norm], 1, ORTH[orth], BASIS["physical"], Lx, Ly)
+                         NORM[residual_norm], 1, ORTH[orth], BASIS[basis], Lx, Ly)
         self.b = kkt_batch_create(descs, opt)
         self.infos = [kkt_batch_get_info(self.b, i) for i in range(len(descs))]
 

@@ -65,21 +65,22 @@ def small_case(kkt):
     return list(ps), [dev(f) for f in fs]
 
 
-def single(kkt, w, f, tol, coarse="exact", orth="mgs"):
-    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, coarse=coarse, orth=orth)
+def single(kkt, w, f, tol, coarse="exact", orth="mgs", basis="physical"):
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, coarse=coarse, orth=orth, basis=basis)
     r = s.solve(f, tol=tol, maxit=420)
     s.close()
     return r
 
 
-@pytest.mark.parametrize("coarse,orth", [("exact", "mgs"), ("none", "mgs"), ("exact", "cgs2")])
-def test_batch_matches_single_instance_solves(kkt, small_case, coarse, orth):
+@pytest.mark.parametrize("coarse,orth,basis", [("exact", "mgs", "physical"), ("none", "mgs", "physical"),
+                                               ("exact", "cgs2", "physical"), ("exact", "mgs", "spectral")])
+def test_batch_matches_single_instance_solves(kkt, small_case, coarse, orth, basis):
     ps, fs = small_case
-    b = kkt.Batch(SMALL, coarse=coarse, orth=orth)
+    b = kkt.Batch(SMALL, coarse=coarse, orth=orth, basis=basis)
     res = b.solve(fs, tol=1e-8, maxit=420)
     assert res.status == kkt.KKT_OK
     for i, w in enumerate(SMALL):
-        ref = single(kkt, w, fs[i], 1e-8, coarse, orth)
+        ref = single(kkt, w, fs[i], 1e-8, coarse, orth, basis)
         assert res.statuses[i] == kkt.KKT_OK
         assert abs(res.iterations[i] - ref.iterations) <= 1, (w.name, res.iterations[i], ref.iterations)
         assert res.rel_residual[i] <= 1e-8
@@ -92,9 +93,10 @@ def test_batch_matches_single_instance_solves(kkt, small_case, coarse, orth):
     assert res.tile_lines in (8, 16, 32) and res.sweep_block in (64, 128, 256)
 
 
-def test_batch_tight_solutions_match_the_oracle(kkt, small_case):
+@pytest.mark.parametrize("basis", ["physical", "spectral"])
+def test_batch_tight_solutions_match_the_oracle(kkt, small_case, basis):
     ps, fs = small_case
-    b = kkt.Batch(SMALL)
+    b = kkt.Batch(SMALL, basis=basis)
     res = b.solve(fs, tol=1e-12, maxit=420)
     assert res.status == kkt.KKT_OK
     for i in range(len(SMALL)):
