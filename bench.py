@@ -345,16 +345,17 @@ def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
 
 
 def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, steps: int, warmup: int) -> dict:
-    """The headline workload's solve in the other FGMRES configurations: the spectral basis
-    (f and x transformed once, no transforms inside the iteration) and CGS2 orthogonalisation
-    and paired MGS (the MGS default's alternatives). Same tolerance, x_0 = 0, device time per
-    solve."""
+    """The headline workload's solve in the other configurations: the spectral basis (f and x
+    transformed once, no transforms inside the iteration), CGS2 orthogonalisation and paired
+    MGS (the MGS default's alternatives), and RAS local solves (Eq 9, an ablation). Same
+    tolerance, x_0 = 0, device time per solve."""
     import torch
 
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
     out = {}
     for name, opts in (("spectral_basis", {"basis": "spectral"}), ("cgs2", {"orth": "cgs2"}),
-                       ("mgs2", {"orth": "mgs2"}), ("spectral_basis_mgs2", {"basis": "spectral", "orth": "mgs2"})):
+                       ("mgs2", {"orth": "mgs2"}), ("spectral_basis_mgs2", {"basis": "spectral", "orth": "mgs2"}),
+                       ("ras_local_solves", {"local": "ras"})):
         s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, **opts)
         f = s.build_rhs(ut)
         ms, res, x = time_solves(kkt_mod, s, f, steps, warmup)
@@ -502,8 +503,10 @@ def run_study(args):
     u~ = sin 2 pi t sin 2 pi x sin 2 pi y (Eq 16). Figure 1: Nt = 100 .. 3200 with 80, 20 and 5
     steps per subdomain (N_D = Nt / m rounded, at least 1) and omega in {1e-2, 1e-3, 1e-4};
     Figure 2: omega = 1e-2 .. 1e-6 at Nt = 800 with 40 subdomains; the mesh sweep of the text
-    (9, 17, 33 points). The residual is the unweighted Euclidean ||f - K x|| / ||f|| (its
-    rounding floor is far below 1e-6 at these sizes). One JSON line on stdout."""
+    (9, 17, 33 points). At omega = 1e-4 Figure 1's cases are also solved with RAS local solves
+    (Eq 9, the explicit local Schur complements) in place of RASQ, one- and two-level. The
+    residual is the unweighted Euclidean ||f - K x|| / ||f|| (its rounding floor is far below
+    1e-6 at these sizes). One JSON line on stdout."""
     import torch
 
     import paper_2305_04421_gb300.kkt as kkt
@@ -511,11 +514,11 @@ def run_study(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
 
-    def iterations(nx, Nt, n_sub, omega, coarse):
+    def iterations(nx, Nt, n_sub, omega, coarse, local="rasq"):
         w = workloads.Workload("paper", nx=nx, ny=nx, Nt=Nt, n_sub=n_sub, Lx=1.0, Ly=2.0, omega=omega,
                                target="paper", u0="paper")
         s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, coarse=coarse, residual_norm="euclidean",
-                       Lx=1.0, Ly=2.0)
+                       local=local, Lx=1.0, Ly=2.0)
         f = s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev),
                         torch.from_numpy(workloads.make_u0(w).ravel()).to(dev))
         r = s.solve(f, tol=1e-6, maxit=420)
@@ -528,9 +531,13 @@ def run_study(args):
         for m in (80, 20, 5):
             for Nt in (100, 200, 400, 800, 1600, 3200):
                 nd = max(1, round(Nt / m))
-                fig1.append({"omega": omega, "steps_per_subdomain": m, "Nt": Nt, "n_sub": nd,
-                             "one_level": iterations(16, Nt, nd, omega, "none"),
-                             "two_level": iterations(16, Nt, nd, omega, "exact")})
+                row = {"omega": omega, "steps_per_subdomain": m, "Nt": Nt, "n_sub": nd,
+                       "one_level": iterations(16, Nt, nd, omega, "none"),
+                       "two_level": iterations(16, Nt, nd, omega, "exact")}
+                if omega == 1e-4:   # the RAS ablation (Eq 9 local solves) on one omega
+                    row["ras_one_level"] = iterations(16, Nt, nd, omega, "none", "ras")
+                    row["ras_two_level"] = iterations(16, Nt, nd, omega, "exact", "ras")
+                fig1.append(row)
     fig2 = [{"omega": om, "Nt": 800, "n_sub": 40, "one_level": iterations(16, 800, 40, om, "none"),
              "two_level": iterations(16, 800, 40, om, "exact")} for om in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6)]
     mesh = [{"mesh_points": nx + 1, "Nt": 400, "n_sub": 20, "omega": 1e-4,

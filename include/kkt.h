@@ -90,6 +90,17 @@ enum kkt_orth {
   KKT_ORTH_MGS2 = 2
 };
 
+/* Local solves of the one-level part. */
+enum kkt_local {
+  /* RASQ (Eq 13): per subdomain (R_s Jhat R_s^T)^-T h (R_s Jhat R_s^T)^-1, the local problems
+   * with zero initial and terminal conditions, as two sweeps */
+  KKT_LOCAL_RASQ = 0,
+  /* RAS (Eq 9): per subdomain the explicit local Schur complement (R_s S-hat R_s^T)^-1, a
+   * tridiagonal solve in time per sine mode; an ablation that differs from RASQ only in the
+   * first node's block (the zero initial condition) */
+  KKT_LOCAL_RAS = 1
+};
+
 /* Basis the FGMRES iteration runs in. */
 enum kkt_basis {
   /* grid values, as Eq 5 is written: every preconditioner apply does a forward and an inverse
@@ -122,6 +133,7 @@ typedef struct kkt_options {
                        (three products, FP32 accumulation); 0 single operands */
   int orth;         /* enum kkt_orth, default KKT_ORTH_MGS */
   int basis;        /* enum kkt_basis, default KKT_BASIS_PHYSICAL */
+  int local;        /* enum kkt_local, default KKT_LOCAL_RASQ */
   double Lx, Ly;    /* domain (0,Lx) x (0,Ly), default 1, 1 */
 } kkt_options;
 

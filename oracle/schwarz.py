@@ -33,6 +33,8 @@ default named first):
 * Two-level composition (Eq 15 prints a product of rank at most 2 N_D N): multiplicative,
   coarse first: x_0 = R_0^T S_0^{-1} R_0 r, y = x_0 + S_RASQ^{-1} (r - S-hat x_0).
   ``variant='additive'`` gives x_0 + S_RASQ^{-1} r and ``variant='one-level'`` the RASQ alone.
+  ``variant='ras'`` is RAS of Eq 9 alone and ``variant='ras-multiplicative'`` the same
+  coarse-first composition with Eq 9's local solves in place of RASQ (an ablation).
 """
 
 from __future__ import annotations
@@ -314,6 +316,9 @@ class SchurPreconditioner:
         if self.variant == "ras":
             return self.ras(r)
         x0 = self.coarse(r)
+        if self.variant == "ras-multiplicative":
+            # Eq 15's coarse-first composition with Eq 9's local solves in place of RASQ
+            return x0 + self.ras(r - self.schur_apply(x0))
         if self.variant == "multiplicative":
             return x0 + self.rasq(r - self.schur_apply(x0))
         if self.variant == "additive":

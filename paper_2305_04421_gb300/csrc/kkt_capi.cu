@@ -212,8 +212,11 @@ int configure(kkt_handle* h) {
   KKT_CUDA_TRY(cudaDeviceSynchronize());
   // sweep storage: shared memory when a subdomain's nodes fit (32 threads x max_len doubles
   // within 200 KB), else a global scratch sized for every mode
-  if (static_cast<size_t>(h->td.max_len) * 32 * sizeof(double) > 200 * 1024) {
-    KKT_TRY(dev_alloc(h, &h->vscratch, static_cast<size_t>(g.n_sub) * h->td.max_len * modes));
+  const size_t words = h->opt.local == KKT_LOCAL_RAS ? 2 : 1;
+  if (words * h->td.max_len * 32 * sizeof(double) > 200 * 1024) {
+    if (h->vscratch) cudaFree(h->vscratch);
+    h->vscratch = nullptr;
+    KKT_TRY(dev_alloc(h, &h->vscratch, words * g.n_sub * h->td.max_len * modes));
   } else if (h->vscratch) {
     cudaFree(h->vscratch);
     h->vscratch = nullptr;
@@ -327,6 +330,7 @@ int kkt_default_options(kkt_options* opt) {
   opt->tc_split = 1;
   opt->orth = KKT_ORTH_MGS;
   opt->basis = KKT_BASIS_PHYSICAL;
+  opt->local = KKT_LOCAL_RASQ;
   opt->Lx = 1.0;
   opt->Ly = 1.0;
   return KKT_OK;
@@ -431,6 +435,7 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
   if (opt->tc_split != 0 && opt->tc_split != 1) return set_error(KKT_ERR_INVALID_ARG, "tc_split must be 0 or 1");
   if (opt->orth != KKT_ORTH_MGS && opt->orth != KKT_ORTH_CGS2 && opt->orth != KKT_ORTH_MGS2)
     return set_error(KKT_ERR_INVALID_ARG, "orth out of range");
+  if (opt->local != KKT_LOCAL_RASQ && opt->local != KKT_LOCAL_RAS) return set_error(KKT_ERR_INVALID_ARG, "local out of range");
   if (opt->basis != KKT_BASIS_PHYSICAL && opt->basis != KKT_BASIS_SPECTRAL)
     return set_error(KKT_ERR_INVALID_ARG, "basis out of range");
   if (opt->basis == KKT_BASIS_SPECTRAL && opt->precision != KKT_PREC_FP64)

@@ -270,6 +270,7 @@ struct SpecParams {
   double* learn_c;
   int two_level;       // apply the coarse correction
   int multiplicative;  // subtract S-hat x_0 before the local solves
+  int ras;             // local solves with R_s S-hat R_s^T (Eq 9) instead of RASQ's (Eq 13)
 };
 SpecParams make_spec_params(const kkt_handle* h);
 

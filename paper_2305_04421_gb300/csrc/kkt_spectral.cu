@@ -285,8 +285,8 @@ __device__ void sweep_body(const TI* __restrict__ rhat, double in_scale, TO* __r
   const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
   TC* vs;
   long long vstride;
-  if (vglobal) {
-    vs = vglobal + static_cast<long long>(s) * max_len * N + q;
+  if (vglobal) {   // (RAS stores two values per node: the scratch holds 2 max_len per mode)
+    vs = vglobal + static_cast<long long>(s) * (p.ras ? 2 : 1) * max_len * N + q;
     vstride = N;
   } else {
     vs = vs_smem + threadIdx.x;
@@ -302,8 +302,55 @@ __device__ void sweep_body(const TI* __restrict__ rhat, double in_scale, TO* __r
       }
     }
   }
-  // forward sweep over the subdomain's nodes
   TC xm = 0, xc = 0, xp = 0;   // x_0 at n-1, n, n+1
+  if (p.ras) {
+    // RAS (Eq 9): the local Schur complement R_s S-hat R_s^T = T_s / h, T_s tridiagonal in time
+    // over the subdomain's nodes (diagonal mu^2 at the global first node, mu^2 + 1 elsewhere,
+    // off-diagonals -mu); T_s y = h r by the Thomas algorithm: forward elimination
+    // m_n = b_n - mu^2 / m_n-1, d'_n = (h r_n + mu d'_n-1) / m_n (stored with 1 / m_n), then
+    // y_n = d'_n + (mu / m_n) y_n+1. It differs from RASQ's (R_s Jhat R_s^T) (R_s Jhat R_s^T)^T
+    // only in the first node's diagonal.
+    TC* ws = vs + static_cast<long long>(max_len) * vstride;
+    if (p.two_level) {
+      xm = coarse_value<TC>(p, first - 1, s, c3);
+      xc = coarse_value<TC>(p, first, s, c3);
+    }
+    TC dp = 0, im = 0;
+    for (int n = first; n <= last; ++n) {
+      TC r = static_cast<TC>(__ldg(rhat + static_cast<long long>(n - 1) * N + q)) * scale;
+      if (p.two_level) {
+        xp = coarse_value<TC>(p, n + 1, s, c3);
+        if (p.multiplicative) {
+          const TC tx = (n >= 2 ? mu2 + TC(1) : mu2) * xc - mu * (xm + xp);
+          r = fma(-tx, inv_h, r);
+        }
+        xm = xc;
+        xc = xp;
+      }
+      const TC bd = n >= 2 ? mu2 + TC(1) : mu2;
+      const TC mth = n == first ? bd : fma(-mu2, im, bd);
+      im = TC(1) / mth;
+      dp = fma(hc, r, mu * dp) * im;
+      vs[static_cast<long long>(n - first) * vstride] = dp;
+      ws[static_cast<long long>(n - first) * vstride] = im;
+    }
+    TC y = 0;
+    for (int n = last; n >= first; --n) {
+      const long long i = static_cast<long long>(n - first) * vstride;
+      y = fma(mu * ws[i], y, vs[i]);
+      if (n >= o1 && n <= o2) {
+        TC out = y;
+        if (p.two_level) out += coarse_value<TC>(p, n, s, c3);
+        const long long o = static_cast<long long>(n - 1) * N + q;
+        if (yhat_lo)
+          store_split<TO>(yhat, yhat_lo, o, static_cast<float>(out));
+        else
+          yhat[o] = store_cast<TO>(static_cast<double>(out));
+      }
+    }
+    return;
+  }
+  // forward sweep over the subdomain's nodes
   if (p.two_level) {
     xm = coarse_value<TC>(p, first - 1, s, c3);
     xc = coarse_value<TC>(p, first, s, c3);
@@ -419,6 +466,7 @@ SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixe
   p.learn_k = (h->opt.coarse == KKT_COARSE_LEARNED && h->mlp) ? h->learn_k : 0;
   p.learn_c = h->learn_c;
   p.multiplicative = h->opt.variant == KKT_MULTIPLICATIVE;
+  p.ras = h->opt.local == KKT_LOCAL_RAS;
   return p;
 }
 
@@ -450,16 +498,17 @@ int launch_sweeps(const kkt_handle* h, const SpecParams& p, const TI* rhat, doub
   }
   // sweep storage: shared memory when a subdomain's nodes fit, else the global scratch
   const size_t limit = 200 * 1024;
+  const size_t words = p.ras ? 2 : 1;   // values stored per node and mode
   int tb = 0;
   for (int cand : {128, 64, 32})
-    if (static_cast<size_t>(h->td.max_len) * cand * sizeof(TC) <= limit) {
+    if (words * h->td.max_len * cand * sizeof(TC) <= limit) {
       tb = cand;
       break;
     }
   size_t smem = 0;
   TC* vglob = nullptr;
   if (tb) {
-    smem = static_cast<size_t>(h->td.max_len) * tb * sizeof(TC);
+    smem = words * h->td.max_len * tb * sizeof(TC);
   } else {
     tb = 128;
     vglob = reinterpret_cast<TC*>(h->vscratch);
@@ -527,7 +576,9 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
     sf += 12.0 * visits;
     sb += 8.0 * visits + 8.0 * V;
   }
-  if (static_cast<size_t>(max_len) * tb * sizeof(double) > 200 * 1024)
+  int words = 1;
+  for (int k = 0; k < nj; ++k) words = std::max(words, jobs[k].p.ras ? 2 : 1);
+  if (static_cast<size_t>(words) * max_len * tb * sizeof(double) > 200 * 1024)
     return set_error(KKT_ERR_UNSUPPORTED, "batched sweeps: a subdomain is too long for shared memory");
   if (!slot.spec) {
     KKT_CUDA_TRY(cudaMalloc(&slot.spec, KKT_BATCH_MAX * sizeof(SpecJob)));
@@ -540,7 +591,7 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
   slot.coarse_total = cp[nj];
   slot.sweep_total = sp[nj];
   slot.sweep_tb = tb;
-  slot.sweep_smem = static_cast<size_t>(max_len) * tb * sizeof(double);
+  slot.sweep_smem = static_cast<size_t>(words) * max_len * tb * sizeof(double);
   slot.coarse_flops = cf;
   slot.coarse_bytes = cb;
   slot.sweep_flops = sf;

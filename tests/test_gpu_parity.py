@@ -133,6 +133,32 @@ def test_schur_preconditioner_matches_oracle(kkt, c, variant, coarse, pou):
     assert rel(host(s.schur_precond_apply(dev(r))), pre.apply(r)) < TOL
 
 
+@pytest.mark.parametrize("c", CASES)
+@pytest.mark.parametrize("coarse", ["none", "exact"])
+@pytest.mark.parametrize("pou", ["left", "right"])
+def test_ras_local_solves_match_oracle(kkt, c, coarse, pou):
+    """RAS (Eq 9): the tridiagonal local Schur solves per mode, alone and inside the
+    coarse-first composition, against the oracle's sparse local Schur matrices."""
+    p, nd = _problem(c)
+    s = _solver(kkt, c, coarse=coarse, pou=pou, local="ras")
+    pre = schwarz.schur_preconditioner(p, nd, variant="ras" if coarse == "none" else "ras-multiplicative", pou=pou)
+    r = workloads.random_vector(p.V, 18)
+    assert rel(host(s.schur_precond_apply(dev(r))), pre.apply(r)) < TOL
+
+
+def test_ras_local_solves_in_fp64_solves_and_tensor_core_forms(kkt):
+    """A 1e-8 solve with RAS locals reaches the exact solution, and the TF32 form runs them too."""
+    w = workloads.CFG_SMALL
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    f = problem.assemble_rhs(p, workloads.make_target(w), None)
+    exact = spectral.kkt_exact_solve(p, f)
+    for prec in ("fp64", "tf32"):
+        s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, local="ras", precision=prec)
+        res = s.solve(dev(f), tol=1e-12 if prec == "fp64" else 1e-8, maxit=420)
+        assert res.status == kkt.KKT_OK
+        assert rel(host(res.x), exact) < (TOL if prec == "fp64" else 1e-6)
+
+
 @pytest.mark.parametrize("c", CASES[:3])
 def test_block_preconditioner_matches_oracle(kkt, c):
     p, nd = _problem(c)

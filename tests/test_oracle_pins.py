@@ -230,10 +230,10 @@ def test_per_mode_exact_solve_matches_dense_lu():
 # ---------------------------------------------------------------------------------------
 
 def test_single_subdomain_gives_exact_schur_inverse():
-    """N_D = 1: RASQ and the two-level preconditioner both equal S-hat^{-1} exactly."""
+    """N_D = 1: RASQ, RAS (Eq 9) and their two-level compositions all equal S-hat^{-1} exactly."""
     p = _tiny(nx=5, ny=6, Nt=9, omega=1e-3)
     x = workloads.random_vector(p.V, 4)
-    for variant in ("one-level", "multiplicative"):
+    for variant in ("one-level", "multiplicative", "ras", "ras-multiplicative"):
         pre = schwarz.schur_preconditioner(p, 1, variant=variant)
         r = pre.S_hat @ x
         np.testing.assert_allclose(pre.apply(r), x, rtol=1e-11, atol=1e-11 * np.abs(x).max())
