@@ -21,7 +21,7 @@ namespace kkt {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr long long kChunk = kThreads * 16;   // elements per work item of the vector kernels
+constexpr long long kChunk = kThreads * 64;   // elements per work item of the vector kernels
 
 struct Seg {
   const double* V;   // first vector (basis V_0 or a single vector)
@@ -571,9 +571,13 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
     };
     // autotune once per batch on the first wave: sine-transform tile height, sweep block size.
     // Candidates that a wave's sizes rule out (shared memory) are skipped.
-    if (rc == KKT_OK && b->tuned_tile_lines == 0) {
+    // the sweep block is re-tuned on every wave (its shared memory depends on the wave's
+    // longest subdomain); the transform tile height once per batch
+    const bool tune_tiles = b->tuned_tile_lines == 0;
+    if (rc == KKT_OK) {
       const int cand_tl[3] = {8, 16, 32}, cand_tb[3] = {64, 128, 256};
-      for (int a = 0; a < 3; ++a) b->tune_ms_dst[a] = 0.0;
+      if (tune_tiles)
+        for (int a = 0; a < 3; ++a) b->tune_ms_dst[a] = 0.0;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       KKT_CUDA_TRY(cudaEventCreate(&e0));
       KKT_CUDA_TRY(cudaEventCreate(&e1));
@@ -594,7 +598,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         return ok ? ms / 2.0 : 1e30;
       };
       int best_tl = 1, best_tb = 1;
-      for (int a = 0; a < 3 && !spectral; ++a) {   // the spectral basis has no transforms in the loop
+      for (int a = 0; a < 3 && !spectral && tune_tiles; ++a) {   // (no transforms in the spectral basis)
         b->tuned_tile_lines = cand_tl[a];
         b->tuned_sweep_tb = 128;
         b->tune_ms_dst[a] = 1e30;
@@ -606,12 +610,13 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         batch_slot_free(slots[0]);
         if (b->tune_ms_dst[a] < b->tune_ms_dst[best_tl]) best_tl = a;
       }
-      b->tuned_tile_lines = cand_tl[best_tl];
+      if (tune_tiles) b->tuned_tile_lines = cand_tl[best_tl];
       for (int a = 0; a < 3; ++a) {
         b->tuned_sweep_tb = cand_tb[a];
         b->tune_ms_sweep[a] = 1e30;
-        if (prepare_slot(slots[0], 0, everyone) == KKT_OK && dst_batched_launch(slots[0], 0, st) == KKT_OK &&
-            dst_batched_launch(slots[0], 1, st) == KKT_OK)
+        // (the first candidate also runs the forward transform once, so the sweeps read data)
+        if (prepare_slot(slots[0], 0, everyone) == KKT_OK &&
+            (a > 0 || (dst_batched_launch(slots[0], 0, st) == KKT_OK && dst_batched_launch(slots[0], 1, st) == KKT_OK)))
           b->tune_ms_sweep[a] = time_it([&] { return spectral_batched_launch(slots[0], d_scale, st); });
         batch_slot_free(slots[0]);
         if (b->tune_ms_sweep[a] < b->tune_ms_sweep[best_tb]) best_tb = a;
@@ -621,7 +626,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       cudaEventDestroy(e1);
       const cudaError_t e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) rc = set_error(KKT_ERR_CUDA, std::string("autotuning: ") + cudaGetErrorString(e));
-      else if (b->tune_ms_dst[best_tl] >= 1e30 || b->tune_ms_sweep[best_tb] >= 1e30)
+      else if ((tune_tiles && b->tune_ms_dst[best_tl] >= 1e30) || b->tune_ms_sweep[best_tb] >= 1e30)
         rc = set_error(KKT_ERR_UNSUPPORTED, "batched form: no tile or sweep block fits this wave");
       else
         set_error(KKT_OK, "");

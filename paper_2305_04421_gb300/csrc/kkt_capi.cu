@@ -88,7 +88,7 @@ int upload_decomp(kkt_handle* h) {
   const size_t ints = 4 * S + Nt;
   const size_t ints_bytes = ((ints * sizeof(int) + 255) / 256) * 256;
   const size_t dbl = Nt + 9 * S;
-  const size_t total = ints_bytes + dbl * sizeof(double);
+  const size_t total = ints_bytes + dbl * sizeof(double) + Nt * sizeof(float);
   void* base = nullptr;
   KKT_CUDA_TRY(cudaMalloc(&base, total));
   std::vector<char> host(total, 0);
@@ -106,6 +106,8 @@ int upload_decomp(kkt_handle* h) {
       dp[Nt + 9 * s + 3 + t] = td.P1[3 * s + t];
       dp[Nt + 9 * s + 6 + t] = td.P2[3 * s + t];
     }
+  float* fp = reinterpret_cast<float*>(dp + dbl);
+  for (int n = 0; n < Nt; ++n) fp[n] = static_cast<float>(td.phi[n]);
   KKT_CUDA_TRY(cudaMemcpy(base, host.data(), total, cudaMemcpyHostToDevice));
   int* dip = static_cast<int*>(base);
   dd.base = base;
@@ -119,6 +121,7 @@ int upload_decomp(kkt_handle* h) {
   dd.owner = dip + 4 * S;
   dd.phi = reinterpret_cast<double*>(static_cast<char*>(base) + ints_bytes);
   dd.moments = dd.phi + Nt;
+  dd.phi_f = reinterpret_cast<float*>(dd.phi + dbl);
   return KKT_OK;
 }
 
@@ -271,10 +274,10 @@ int schur_precond_w(kkt_handle* h, const double* rw, double scale, double* yw, c
   const bool sp = h->opt.tc_split != 0;
   const int mid = sp ? 3 : (t.bf16 ? 0 : 1);
   const int valid = h->g.nx - 1;
-  KKT_TRY(tc_pack(t, rw, scale, valid, st));                       // hi (+ lo) parts
+  KKT_TRY(tc_pack(t, rw, 1.0, valid, st));                         // hi (+ lo) parts, unscaled
   KKT_TRY(tc_gemm(t, 0, mid, t.x1, valid, st, sp, t.x1_lo));        // along x: [n][j][i] -> [n][k][j]
   KKT_TRY(tc_gemm(t, 1, 1, t.rhat, valid, st, sp));                 // along y: -> [n][l][k], FP32
-  KKT_TRY(spectral_schur_precond_mixed(h, t.rhat, t.yin, sp ? t.yin_lo : nullptr, t.bf16, st));
+  KKT_TRY(spectral_schur_precond_mixed(h, t.rhat, scale, t.yin, sp ? t.yin_lo : nullptr, t.bf16, st));
   KKT_TRY(tc_gemm(t, 2, mid, t.x0, valid, st, sp, t.x0_lo));        // back along x: [n][l][k] -> [n][i][l]
   KKT_TRY(tc_gemm(t, 0, 2, yw, valid, st, sp));                     // back along y: -> [n][j][i], FP64
   return KKT_OK;

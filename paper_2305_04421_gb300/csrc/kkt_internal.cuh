@@ -64,6 +64,7 @@ struct DeviceDecomp {
   int* owner = nullptr;
   double* phi = nullptr;
   double* moments = nullptr;   // [s][9]: P0 (3), P1 (3), P2 (3)
+  float* phi_f = nullptr;      // phi in FP32 (the reduced-precision sweeps and restriction)
   void* base = nullptr;
 };
 
@@ -201,8 +202,8 @@ const kkt_mlp_config& mlp_config(const kkt_mlp* m);
 int spectral_coarse_factor(const kkt_handle* h, bool padded, double* cf, cudaStream_t st);
 // reduced-precision forms: FP32 spectral input (padded modes), output BF16 (bf16 != 0) or FP32
 // (yhat_lo non-null: also the lo part, yhat + yhat_lo = the FP32 result)
-int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, void* yhat_lo, int bf16,
-                                 cudaStream_t st);
+int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, double in_scale, void* yhat, void* yhat_lo,
+                                 int bf16, cudaStream_t st);
 
 // tensor-core transforms (kkt_tc_gemm.cu)
 int tc_padded_size(int n);
@@ -264,6 +265,7 @@ struct SpecParams {
   const int* olast;
   const int* owner;
   const double* phi;
+  const float* phi_f;
   const double* mom;
   const double* cf;    // coarse factors [s][3][N]: D_s^{-1} of the block-Thomas elimination
   int learn_k;         // modes k, l < learn_k also write their R_0 r to learn_c

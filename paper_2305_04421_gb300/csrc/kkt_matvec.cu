@@ -128,6 +128,24 @@ __global__ void axpby_kernel(double alpha, const double* __restrict__ x, double 
 
 // Batched matvec: item = a block of 256 points of one instance; coefficients of the su / sz
 // terms scaled by the instance's scale_dev entry (1 / eta of the Krylov vector being applied).
+// (i, j, n) of a flat block index; 32-bit divisions while the block has fewer than 2^32
+// points (64-bit integer division is built from FP64 arithmetic, the scarce pipe here)
+__device__ __forceinline__ void split_index(long long idx, const MatvecJob& J, int& i, int& j, int& n) {
+  if (J.V < (1LL << 32)) {
+    const unsigned int u = static_cast<unsigned int>(idx), mx = J.Mx, my = J.My;
+    const unsigned int r = u / mx;
+    i = static_cast<int>(u - r * mx);
+    const unsigned int nn = r / my;
+    j = static_cast<int>(r - nn * my);
+    n = static_cast<int>(nn);
+  } else {
+    const long long r = idx / J.Mx;
+    i = static_cast<int>(idx - r * J.Mx);
+    j = static_cast<int>(r % J.My);
+    n = static_cast<int>(r / J.My);
+  }
+}
+
 __global__ void matvec_batched(const MatvecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
                                long long total, const double* __restrict__ scale_dev) {
   __shared__ long long sp[KKT_BATCH_MAX + 1];
@@ -140,10 +158,8 @@ __global__ void matvec_batched(const MatvecJob* __restrict__ jobs, const long lo
     const long long idx1 = idx0 + kMvItem < J.V ? idx0 + kMvItem : J.V;
     if (J.spectral) {
       for (long long idx = idx0 + threadIdx.x; idx < idx1; idx += blockDim.x) {
-        const int i = static_cast<int>(idx % J.Mx);
-        const long long r = idx / J.Mx;
-        const int j = static_cast<int>(r % J.My);
-        const int n = static_cast<int>(r / J.My);
+        int i, j, n;
+        split_index(idx, J, i, j, n);
         const double mu0 = fma(J.dtnu, __ldg(J.lx + i) + __ldg(J.ly + j), 1.0);
         const double wc = J.w[idx];
         const double wnx = n + 1 < J.Nt ? J.w[idx + J.N] : 0.0;
@@ -157,10 +173,8 @@ __global__ void matvec_batched(const MatvecJob* __restrict__ jobs, const long lo
       continue;
     }
     for (long long idx = idx0 + threadIdx.x; idx < idx1; idx += blockDim.x) {
-      const int i = static_cast<int>(idx % J.Mx);
-      const long long r = idx / J.Mx;
-      const int j = static_cast<int>(r % J.My);
-      const int n = static_cast<int>(r / J.My);
+      int i, j, n;
+      split_index(idx, J, i, j, n);
       const bool hw = i > 0, he = i + 1 < J.Mx, hs = j > 0, hn = j + 1 < J.My;
       const double wc = J.w[idx];
       const double wwe = (hw ? J.w[idx - 1] : 0.0) + (he ? J.w[idx + 1] : 0.0);

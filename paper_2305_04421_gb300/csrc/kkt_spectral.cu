@@ -31,9 +31,10 @@ namespace {
 
 
 
+// (q < 2^31: at most 1023^2 modes; a 32-bit division stays off the FP64 pipe)
 __device__ __forceinline__ double mode_mu(const SpecParams& p, long long q) {
-  const long long l = q / p.Mx;
-  const int k = static_cast<int>(q - l * p.Mx);
+  const int l = static_cast<int>(q) / p.Mx;
+  const int k = static_cast<int>(q) - l * p.Mx;
   return p.a + p.dtnu * (p.lx[k] + p.ly[l]);
 }
 
@@ -117,17 +118,35 @@ __device__ void coarse_body(const TI* __restrict__ rhat, double in_scale, const 
   double y0 = 0, y1 = 0, t0 = 0, t1 = 0;   // eliminated rhs of s-1 and D_{s-1}^{-1} a_{s-1}
   int learned = -1;                          // index among the learned modes, if any
   if (p.learn_k > 0) {
-    const long long l = q / p.Mx, k = q - l * p.Mx;
+    const int l = static_cast<int>(q) / p.Mx, k = static_cast<int>(q) - l * p.Mx;
     if (k < p.learn_k && l < p.learn_k) learned = static_cast<int>(l * p.learn_k + k);
   }
   for (int s = 0; s < p.n_sub; ++s) {
     double c0 = 0.0, c1 = 0.0;
     const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
+    if constexpr (sizeof(TI) == 4) {
+      // FP32 input (the reduced-precision forms): compensated FP32 sums over the owned nodes,
+      // scaled and widened once per subdomain (the solve below stays FP64)
+      float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
 #pragma unroll 4
-    for (int n = o1; n <= o2; ++n) {
-      const double r = load_d(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
-      c0 += r;
-      c1 = fma(r, __ldg(p.phi + n - 1), c1);
+      for (int n = o1; n <= o2; ++n) {
+        const float r = __ldg(rhat + static_cast<long long>(n - 1) * N + q);
+        const float y0 = r - e0, t0 = s0 + y0;
+        e0 = (t0 - s0) - y0;
+        s0 = t0;
+        const float y1 = fmaf(r, __ldg(p.phi_f + n - 1), -e1), t1 = s1 + y1;
+        e1 = (t1 - s1) - y1;
+        s1 = t1;
+      }
+      c0 = static_cast<double>(s0) * in_scale;
+      c1 = static_cast<double>(s1) * in_scale;
+    } else {
+#pragma unroll 4
+      for (int n = o1; n <= o2; ++n) {
+        const double r = load_d(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
+        c0 += r;
+        c1 = fma(r, __ldg(p.phi + n - 1), c1);
+      }
     }
     if (learned >= 0) {
       p.learn_c[(learned * p.n_sub + s) * 2LL] = c0;
@@ -269,6 +288,9 @@ __device__ __forceinline__ TC coarse_value(const SpecParams& p, int n, int s, co
   if (n < 1 || n > p.Nt) return TC(0);
   const int o = __ldg(p.owner + n - 1) - s + 1;        // 0, 1, 2 for s-1, s, s+1
   if (o < 0 || o > 2) return TC(0);                     // cannot happen when every m_s >= 2
+  // FP32 sweeps read phi in FP32: an FP64 load and conversion per node would run on the
+  // FP64 pipe, which the reduced-precision forms keep for the coarse solve
+  if constexpr (sizeof(TC) == 4) return c3[2 * o] + c3[2 * o + 1] * __ldg(p.phi_f + n - 1);
   return c3[2 * o] + c3[2 * o + 1] * static_cast<TC>(__ldg(p.phi + n - 1));
 }
 
@@ -279,7 +301,7 @@ __device__ void sweep_body(const TI* __restrict__ rhat, double in_scale, TO* __r
   const long long N = p.N;
   const double mud = mode_mu(p, q);
   const TC mu = static_cast<TC>(mud), mu2 = mu * mu;
-  const TC inv_mu = static_cast<TC>(1.0 / mud);
+  const TC inv_mu = TC(1) / mu;   // (FP32 reciprocal in the reduced-precision sweeps)
   const TC hc = static_cast<TC>(p.h), inv_h = static_cast<TC>(p.inv_h), scale = static_cast<TC>(in_scale);
   const int first = __ldg(p.first + s), last = __ldg(p.last + s);
   const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
@@ -461,6 +483,7 @@ SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixe
   p.olast = h->dd.olast;
   p.owner = h->dd.owner;
   p.phi = h->dd.phi;
+  p.phi_f = h->dd.phi_f;
   p.mom = h->dd.moments;
   p.two_level = h->opt.coarse != KKT_COARSE_NONE;
   p.learn_k = (h->opt.coarse == KKT_COARSE_LEARNED && h->mlp) ? h->learn_k : 0;
@@ -534,13 +557,13 @@ int spectral_schur_precond(const kkt_handle* h, const double* rhat, double* yhat
   return launch_sweeps<double, double, double>(h, p, rhat, in_scale, yhat, st, false);
 }
 
-int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, void* yhat, void* yhat_lo, int bf16,
-                                 cudaStream_t st) {
+int spectral_schur_precond_mixed(const kkt_handle* h, const float* rhat, double in_scale, void* yhat, void* yhat_lo,
+                                 int bf16, cudaStream_t st) {
   SpecParams p = make_params(h, true);
   if (bf16)
-    return launch_sweeps<float, float, __nv_bfloat16>(h, p, rhat, 1.0, static_cast<__nv_bfloat16*>(yhat), st, true,
-                                                      static_cast<__nv_bfloat16*>(yhat_lo));
-  return launch_sweeps<float, float, float>(h, p, rhat, 1.0, static_cast<float*>(yhat), st, true,
+    return launch_sweeps<float, float, __nv_bfloat16>(h, p, rhat, in_scale, static_cast<__nv_bfloat16*>(yhat), st,
+                                                      true, static_cast<__nv_bfloat16*>(yhat_lo));
+  return launch_sweeps<float, float, float>(h, p, rhat, in_scale, static_cast<float*>(yhat), st, true,
                                             static_cast<float*>(yhat_lo));
 }
 

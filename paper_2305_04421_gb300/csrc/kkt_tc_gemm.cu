@@ -141,6 +141,36 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
+// FP64 -> FP32 conversion in integer arithmetic. On this part the FP64 pipe (2 instructions
+// per clock per SM) also executes F2F conversions, so the pack builds the bit patterns with
+// integer operations instead. Values below FP32's normal range are
+// flushed to zero, values above it become infinities, NaNs stay NaNs.
+__device__ __forceinline__ float f64_to_f32_rne(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
+  const int e = static_cast<int>((b >> 52) & 0x7ff);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x00400000u : 0u));
+  int e32 = e - 1023 + 127;
+  if (e32 <= 0) return __uint_as_float(sign);
+  m += 0x0FFFFFFFull + ((m >> 29) & 1ull);   // round the 52-bit fraction to 23 bits, ties to even
+  if (m >> 52) {
+    m = 0;
+    ++e32;
+  }
+  if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | (static_cast<unsigned int>(e32) << 23) | static_cast<unsigned int>(m >> 29));
+}
+
+// v rounded to `bits` significant bits (ties to even), in the FP64 bit pattern
+template <int BITS>
+__device__ __forceinline__ double round_bits(double v) {
+  constexpr int drop = 53 - BITS;
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+  const unsigned long long r = (b + ((1ull << (drop - 1)) - 1) + ((b >> drop) & 1ull)) & ~((1ull << drop) - 1);
+  return __longlong_as_double(static_cast<long long>(r));
+}
+
 // hi + lo split of a value in the operand type
 template <typename TIn>
 struct Split;
@@ -150,9 +180,13 @@ struct Split<__nv_bfloat16> {
     hi = __float2bfloat16_rn(v);
     lo = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
+  // hi = v to 8 significant bits (exact in BF16), lo = v - hi (one exact FP64 subtraction)
+  // rounded to BF16; the conversions in integer arithmetic
   static __device__ __forceinline__ void make_d(double v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    hi = __double2bfloat16(v);
-    lo = __double2bfloat16(v - static_cast<double>(__bfloat162float(hi)));
+    const double h = round_bits<8>(v);
+    hi = __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(f64_to_f32_rne(h)) >> 16));
+    const double l = round_bits<8>(v - h);   // one rounding of the exact remainder
+    lo = __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(f64_to_f32_rne(l)) >> 16));
   }
 };
 template <>
@@ -161,9 +195,11 @@ struct Split<float> {
     hi = tf32_round(v);
     lo = v - hi;
   }
+  // hi = v to 11 significant bits (exact in TF32), lo = v - hi in FP32
   static __device__ __forceinline__ void make_d(double v, float& hi, float& lo) {
-    hi = tf32_round(static_cast<float>(v));
-    lo = static_cast<float>(v - static_cast<double>(hi));
+    const double h = round_bits<11>(v);
+    hi = f64_to_f32_rne(h);
+    lo = f64_to_f32_rne(v - h);
   }
 };
 
@@ -318,17 +354,21 @@ __global__ void __launch_bounds__(128, 1)
 
 // out + out_lo (P x P per slice, zero padded) = scale * in[s][j][i] (valid x valid), split into
 // hi and lo parts of the operand type
+// Grid (P / 256 rounded up, P, slices): no 64-bit index divisions (the compiler builds those
+// from FP64 arithmetic, the scarce pipe here).
 template <typename TIn>
 __global__ void pack_kernel(const double* __restrict__ in, double scale, TIn* __restrict__ out,
-                            TIn* __restrict__ out_lo, int P, int valid, long long total) {
-  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const int i = static_cast<int>(t % P);
-  const long long sj = t / P;
-  const int j = static_cast<int>(sj % P);
-  const long long s = sj / P;
+                            TIn* __restrict__ out_lo, int P, int valid) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  const long long s = blockIdx.z;
+  if (i >= P) return;
+  const long long t = (s * P + j) * P + i;
   double v = 0.0;
-  if (i < valid && j < valid) v = scale * in[(s * valid + j) * valid + i];
+  if (i < valid && j < valid) {
+    v = in[(s * valid + j) * valid + i];
+    if (scale != 1.0) v *= scale;   // callers fold their scale downstream where they can
+  }
   TIn hi, lo;
   Split<TIn>::make_d(v, hi, lo);
   out[t] = hi;
@@ -528,14 +568,15 @@ int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, c
 int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStream_t st) {
   const long long total = static_cast<long long>(t.slices) * t.P * t.P;
   const int tb = 256;
-  const long long nb = (total + tb - 1) / tb;
+  if (t.slices > 65535) return set_error(KKT_ERR_UNSUPPORTED, "too many time slices for the pack grid");
+  const dim3 grid((t.P + tb - 1) / tb, t.P, t.slices);
   ProfScope ps(KKT_K_AXPY, st, 0.0, 8.0 * t.slices * static_cast<double>(valid) * valid + 2.0 * (t.bf16 ? 2.0 : 4.0) * total);
   if (t.bf16)
-    pack_kernel<__nv_bfloat16><<<static_cast<unsigned>(nb), tb, 0, st>>>(
-        in, scale, static_cast<__nv_bfloat16*>(t.x0), static_cast<__nv_bfloat16*>(t.x0_lo), t.P, valid, total);
+    pack_kernel<__nv_bfloat16><<<grid, tb, 0, st>>>(in, scale, static_cast<__nv_bfloat16*>(t.x0),
+                                                     static_cast<__nv_bfloat16*>(t.x0_lo), t.P, valid);
   else
-    pack_kernel<float><<<static_cast<unsigned>(nb), tb, 0, st>>>(in, scale, static_cast<float*>(t.x0),
-                                                                 static_cast<float*>(t.x0_lo), t.P, valid, total);
+    pack_kernel<float><<<grid, tb, 0, st>>>(in, scale, static_cast<float*>(t.x0), static_cast<float*>(t.x0_lo), t.P,
+                                            valid);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
