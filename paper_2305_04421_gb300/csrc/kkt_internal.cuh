@@ -324,6 +324,10 @@ struct BatchSlot {
   long long* sweep_prefix = nullptr;    // blocks of (modes / tb) x n_sub
   long long coarse_total = 0, sweep_total = 0;
   size_t sweep_smem = 0;
+  // jobs are ordered by subdomain length: items [0, sweep_split) belong to short subdomains and
+  // run in their own launch with sweep_smem_short, so long ones do not set everyone's occupancy
+  long long sweep_split = 0;
+  size_t sweep_smem_short = 0;
   int sweep_tb = 128;
   double coarse_flops = 0, coarse_bytes = 0, sweep_flops = 0, sweep_bytes = 0;
   MatvecJob* mv = nullptr;

@@ -437,11 +437,11 @@ __global__ void coarse_batched(const SpecJob* __restrict__ jobs, const long long
 
 // Batched sweeps: item = (block of modes, subdomain) of one instance (FP64).
 __global__ void sweep_batched(const SpecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
-                              long long total, const double* __restrict__ scale_dev) {
+                              long long t_begin, long long t_end, const double* __restrict__ scale_dev) {
   extern __shared__ __align__(16) unsigned char vs_raw[];
   __shared__ long long sp[KKT_BATCH_MAX + 1];
   batch_prefix_load(sp, prefix, nj);
-  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+  for (long long t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
     const int k = batch_find(sp, nj, t);
     const SpecJob& J = jobs[k];
     const long long local = t - sp[k];
@@ -583,11 +583,20 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
   if (nj < 1 || nj > KKT_BATCH_MAX) return set_error(KKT_ERR_INVALID_ARG, "batched jobs out of range");
   slot.njobs = nj;
   const int tb = slot.sweep_tb > 0 ? slot.sweep_tb : 128;
+  // order by subdomain length; subdomains of at most kShort nodes form the first group
+  constexpr int kShort = 40;
+  std::vector<SpecJob> js(jobs, jobs + nj);
+  std::stable_sort(js.begin(), js.end(), [](const SpecJob& a, const SpecJob& b) { return a.max_len < b.max_len; });
+  jobs = js.data();
   std::vector<long long> cp(nj + 1, 0), sp(nj + 1, 0);
-  int max_len = 0;
+  int max_len = 0, short_len = 0, n_short = 0;
   double cf = 0, cb = 0, sf = 0, sb = 0;
   for (int k = 0; k < nj; ++k) {
     const SpecParams& p = jobs[k].p;
+    if (jobs[k].max_len <= kShort) {
+      short_len = std::max(short_len, jobs[k].max_len);
+      n_short = k + 1;
+    }
     cp[k + 1] = cp[k] + (p.two_level ? (p.N + 127) / 128 : 0);
     sp[k + 1] = sp[k] + ((p.N + tb - 1) / tb) * p.n_sub;
     max_len = std::max(max_len, jobs[k].max_len);
@@ -615,6 +624,8 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
   slot.sweep_total = sp[nj];
   slot.sweep_tb = tb;
   slot.sweep_smem = static_cast<size_t>(words) * max_len * tb * sizeof(double);
+  slot.sweep_split = (n_short > 0 && n_short < nj) ? sp[n_short] : 0;
+  slot.sweep_smem_short = static_cast<size_t>(words) * short_len * tb * sizeof(double);
   slot.coarse_flops = cf;
   slot.coarse_bytes = cb;
   slot.sweep_flops = sf;
@@ -636,13 +647,22 @@ int spectral_batched_launch(const BatchSlot& slot, const double* scale_dev, cuda
   if (slot.sweep_total > 0) {
     KKT_CUDA_TRY(cudaFuncSetAttribute(sweep_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(slot.sweep_smem)));
-    int per_sm = 0;
-    KKT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batched, slot.sweep_tb, slot.sweep_smem));
-    const long long grid = std::min<long long>(slot.sweep_total, static_cast<long long>(sms) * std::max(per_sm, 1));
+    auto launch = [&](long long t0, long long t1, size_t smem) -> int {
+      int per_sm = 0;
+      KKT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_batched, slot.sweep_tb, smem));
+      const long long grid = std::min<long long>(t1 - t0, static_cast<long long>(sms) * std::max(per_sm, 1));
+      sweep_batched<<<static_cast<unsigned>(grid), slot.sweep_tb, smem, st>>>(slot.spec, slot.sweep_prefix,
+                                                                            slot.njobs, t0, t1, scale_dev);
+      KKT_CUDA_TRY(cudaGetLastError());
+      return KKT_OK;
+    };
     ProfScope ps(KKT_K_SWEEP, st, slot.sweep_flops, slot.sweep_bytes);
-    sweep_batched<<<static_cast<unsigned>(grid), slot.sweep_tb, slot.sweep_smem, st>>>(
-        slot.spec, slot.sweep_prefix, slot.njobs, slot.sweep_total, scale_dev);
-    KKT_CUDA_TRY(cudaGetLastError());
+    if (slot.sweep_split > 0) {   // short subdomains, then long ones
+      KKT_TRY(launch(0, slot.sweep_split, slot.sweep_smem_short));
+      KKT_TRY(launch(slot.sweep_split, slot.sweep_total, slot.sweep_smem));
+    } else {
+      KKT_TRY(launch(0, slot.sweep_total, slot.sweep_smem));
+    }
   }
   return KKT_OK;
 }
