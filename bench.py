@@ -60,6 +60,7 @@ def describe(w: workloads.Workload) -> dict:
             "nx": w.nx, "ny": w.ny, "Nt": w.Nt, "n_sub": w.n_sub, "nu": w.nu, "omega": w.omega,
             "unknowns": 3 * w.V, "tol": TOL, "restart": 30, "coarse": "exact two-level, multiplicative",
             "residual_norm": "discrete L2 pair (u, z rows weighted h^-1/2, state rows h^1/2)",
+            "orthogonalisation": "modified Gram-Schmidt over pairs of basis vectors",
             "l2": "inputs larger than L2 (KKT vector 1.6 GB, Krylov basis ~66 GB)"}
 
 
@@ -206,10 +207,10 @@ def run_reference(args):
 
 # DRAM traffic per algorithmic byte for kernels captured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over the launch, divided by the launch's algorithmic bytes), from the
-# small-case capture summarised in profiles/ncu_fp64_kernels_256x256_nt96.md. The fused MGS
-# step streams with no reuse, so its traffic grows in proportion to the elements processed and
-# the ratio scales to full-size launches. Kernels not listed report traffic null.
-TRAFFIC_RATIO = {"mgs_step_kernel": 0.952}
+# small-case captures summarised in profiles/ncu_fp64_kernels_256x256_nt96.md. The MGS steps
+# stream with no reuse, so their traffic grows in proportion to the elements processed and the
+# ratio scales to full-size launches. Kernels not listed report traffic null.
+TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgs2_step_kernel": 0.982}
 
 
 def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -> dict:
@@ -233,7 +234,7 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -
     else:
         alu_peak = FP64_PEAK_TFLOPS
         alu_kind, alu_src = "alu", "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)"
-        kname = {"dst": "dst_tile_kernel", "multidot": "mgs_step_kernel", "update": "mgs_step_kernel",
+        kname = {"dst": "dst_tile_kernel", "multidot": "mgs2_step_kernel", "update": "mgs2_step_kernel",
                  "axpy": "axpy_multi_kernel", "matvec": "matvec_kernel", "sweep": "sweep_kernel",
                  "coarse": "coarse_solve_kernel"}.get(top, top)
     t_alu = e["flops"] / (alu_peak * 1e12)
@@ -347,15 +348,14 @@ def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
 
 def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, steps: int, warmup: int) -> dict:
     """The headline workload's solve in the other configurations: the spectral basis (f and x
-    transformed once, no transforms inside the iteration), CGS2 orthogonalisation and paired
-    MGS (the MGS default's alternatives), and RAS local solves (Eq 9, an ablation). Same
-    tolerance, x_0 = 0, device time per solve."""
+    transformed once, no transforms inside the iteration), one-pass MGS and CGS2 (the paired-MGS
+    default's alternatives), and RAS local solves (Eq 9, an ablation). Same tolerance,
+    x_0 = 0, device time per solve."""
     import torch
 
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
     out = {}
-    for name, opts in (("spectral_basis", {"basis": "spectral"}), ("cgs2", {"orth": "cgs2"}),
-                       ("mgs2", {"orth": "mgs2"}), ("spectral_basis_mgs2", {"basis": "spectral", "orth": "mgs2"}),
+    for name, opts in (("spectral_basis", {"basis": "spectral"}), ("mgs", {"orth": "mgs"}), ("cgs2", {"orth": "cgs2"}),
                        ("ras_local_solves", {"local": "ras"})):
         s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, **opts)
         f = s.build_rhs(ut)
@@ -659,6 +659,8 @@ def run_ours(args):
     f_host = f.cpu().pin_memory()
     x_host = torch.zeros(f.numel(), dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
+    x_host.zero_()
+    solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT)   # warm-up: stages the host-buffer path once
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()

@@ -79,14 +79,15 @@ enum kkt_residual_norm {
 enum kkt_orth {
   /* modified Gram-Schmidt, one pass: for k = 0..j, h_kj = <q_k, w>, w -= h_kj q_k. Each step is
    * one streaming pass over q_k, q_k+1 and w (2 FP64 FMAs per element); GMRES with MGS is
-   * backward stable (Paige, Rozloznik and Strakos, 2006). */
+   * backward stable (Paige, Rozloznik and Strakos, 2006). The oracle's orthogonalisation. */
   KKT_ORTH_MGS = 0,
   /* classical Gram-Schmidt with one conditional repeat (||w'||^2 < ||w||^2 / 2): all dots of a
    * pass in one multi-dot, one multi-axpy; 4 FMAs per element and basis vector when it repeats */
   KKT_ORTH_CGS2 = 1,
   /* MGS over pairs of basis vectors: both dots of a pair are taken on the same w, the pair is
    * subtracted in one pass that also takes the next pair's dots. 3 vector passes per basis
-   * vector instead of 4, the same FMA count; equals MGS up to the pair's orthogonality error */
+   * vector instead of 4, the same FMA count; equals MGS up to the pair's orthogonality error.
+   * The default. */
   KKT_ORTH_MGS2 = 2
 };
 
@@ -131,7 +132,7 @@ typedef struct kkt_options {
   int residual_norm;  /* enum kkt_residual_norm, default KKT_NORM_L2 */
   int tc_split;     /* BF16 / TF32 only: 1 (default) every tensor-core transform uses hi + lo operands
                        (three products, FP32 accumulation); 0 single operands */
-  int orth;         /* enum kkt_orth, default KKT_ORTH_MGS */
+  int orth;         /* enum kkt_orth, default KKT_ORTH_MGS2 */
   int basis;        /* enum kkt_basis, default KKT_BASIS_PHYSICAL */
   int local;        /* enum kkt_local, default KKT_LOCAL_RASQ */
   double Lx, Ly;    /* domain (0,Lx) x (0,Ly), default 1, 1 */

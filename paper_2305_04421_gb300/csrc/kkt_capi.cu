@@ -331,7 +331,7 @@ int kkt_default_options(kkt_options* opt) {
   opt->jhat_sign = -1;
   opt->residual_norm = KKT_NORM_L2;
   opt->tc_split = 1;
-  opt->orth = KKT_ORTH_MGS;
+  opt->orth = KKT_ORTH_MGS2;
   opt->basis = KKT_BASIS_PHYSICAL;
   opt->local = KKT_LOCAL_RASQ;
   opt->Lx = 1.0;

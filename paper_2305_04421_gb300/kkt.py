@@ -432,7 +432,7 @@ class Solver:
 
     def __init__(self, nx, ny, Nt, T=1.0, nu=1.0, omega=1e-4, n_sub=1, *, precision="fp64",
                  coarse="exact", variant="multiplicative", pou="left", restart=30, jhat_sign=-1,
-                 residual_norm="l2", tc_split=True, orth="mgs", basis="physical", local="rasq", Lx=1.0,
+                 residual_norm="l2", tc_split=True, orth="mgs2", basis="physical", local="rasq", Lx=1.0,
                  Ly=1.0):
         self.h = kkt_create(nx, ny, Nt, T, nu, omega, n_sub)
         self.set_options(precision=precision, coarse=coarse, variant=variant, pou=pou, restart=restart,
@@ -441,7 +441,7 @@ class Solver:
         self.info = kkt_get_info(self.h)
 
     def set_options(self, *, precision="fp64", coarse="exact", variant="multiplicative", pou="left",
-                    restart=30, jhat_sign=-1, residual_norm="l2", tc_split=True, orth="mgs", basis="physical",
+                    restart=30, jhat_sign=-1, residual_norm="l2", tc_split=True, orth="mgs2", basis="physical",
                     local="rasq", Lx=1.0, Ly=1.0):
         opt = KKTOptions(PREC[precision], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
                          NORM[residual_norm], 1 if tc_split else 0, ORTH[orth], BASIS[basis], LOCAL[local],
@@ -544,7 +544,7 @@ class Batch:
     with nx, ny, Nt, n_sub, T, nu, omega attributes (e.g. workloads.Workload) or tuples."""
 
     def __init__(self, instances, *, coarse="exact", variant="multiplicative", pou="left", restart=30,
-                 jhat_sign=-1, residual_norm="l2", orth="mgs", basis="physical", Lx=1.0, Ly=1.0):
+                 jhat_sign=-1, residual_norm="l2", orth="mgs2", basis="physical", Lx=1.0, Ly=1.0):
         descs = []
         for w in instances:
             if isinstance(w, tuple):
