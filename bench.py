@@ -206,11 +206,12 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 
 # DRAM traffic per algorithmic byte for kernels captured with ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum over the launch, divided by the launch's algorithmic bytes), from the
-# small-case captures summarised in profiles/ncu_fp64_kernels_256x256_nt96.md. The MGS steps
-# stream with no reuse, so their traffic grows in proportion to the elements processed and the
-# ratio scales to full-size launches. Kernels not listed report traffic null.
-TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgs2_step_kernel": 0.982}
+# dram__bytes_write.sum over the launch, divided by the launch's algorithmic bytes). The paired
+# MGS step and the sine transform come from a single-pass capture of the benchmark workload
+# itself (profiles/ncu_traffic_256x256_nt1024.md); one-pass MGS from the small-case capture
+# (profiles/ncu_fp64_kernels_256x256_nt96.md), whose traffic grows in proportion to the
+# elements processed. Kernels not listed report traffic null.
+TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgs2_step_kernel": 0.998, "dst_tile_kernel": 0.947}
 
 
 def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -> dict:
@@ -251,7 +252,8 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -
     bytes_per_launch = e["bytes"] / max(e["timed"], 1)
     ratio = TRAFFIC_RATIO.get(kname)
     out.update({"traffic": bytes_per_launch * ratio if ratio else None,
-                "traffic_source": ("ncu small-case capture, scaled by elements processed" if ratio else None),
+                "traffic_source": ("ncu dram bytes / algorithmic bytes of the same kernel, times this launch's "
+                                   "algorithmic bytes" if ratio else None),
                 "per_launch_ms": per_launch, "launches": e["timed"],
                 "algorithmic_flops_per_launch": e["flops"] / max(e["timed"], 1),
                 "algorithmic_bytes_per_launch": e["bytes"] / max(e["timed"], 1),

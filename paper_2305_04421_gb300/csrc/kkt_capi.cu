@@ -376,6 +376,7 @@ kkt_handle* kkt_create(int nx, int ny, int Nt, double T, double nu, double omega
   if (st >= 0) st = dst_plan_create(h->dst_y, ny);
   if (st >= 0) st = dev_alloc(h, &h->spec, g.V);
   if (st >= 0) st = dev_alloc(h, &h->spec2, g.V);
+  if (st >= 0) st = dst_autotune(h);
   if (st >= 0) st = dev_alloc(h, &h->red, static_cast<size_t>(krylov_partial_capacity()));
   if (st >= 0) st = dev_alloc(h, &h->red_out, 128);
   if (st < 0) {

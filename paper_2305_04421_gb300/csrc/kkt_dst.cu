@@ -257,7 +257,7 @@ long long launch_tiles(const DstLaunch& L, long long nslices) {
 
 int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long long total_lines,
                  int cols, long long slice, long long nslices, cudaStream_t st) {
-  const DstLaunch L = make_launch(p, in, out, mode, total_lines, cols, slice, 0);
+  const DstLaunch L = make_launch(p, in, out, mode, total_lines, cols, slice, p.tile_lines);
   const size_t sm = smem_bytes(p.n, L.tile_lines);
   KKT_CUDA_TRY(cudaFuncSetAttribute(dst_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(sm)));
@@ -379,6 +379,51 @@ void batch_slot_free(BatchSlot& slot) {
   cudaFree(slot.mv);
   cudaFree(slot.mv_prefix);
   slot = BatchSlot();
+}
+
+int dst_autotune(kkt_handle* h) {
+  const Geometry& g = h->g;
+  KKT_CUDA_TRY(cudaMemset(h->spec, 0, static_cast<size_t>(g.V) * sizeof(double)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  KKT_CUDA_TRY(cudaEventCreate(&e0));
+  KKT_CUDA_TRY(cudaEventCreate(&e1));
+  auto time_pass = [&](DstPlan& p, int tl, bool rows) -> double {
+    p.tile_lines = tl;
+    auto run = [&]() {
+      return rows ? launch_lines(h->dst_x, h->spec, h->spec2, 0, static_cast<long long>(g.Nt) * g.My, g.Mx, 0, 0, nullptr)
+                  : launch_lines(h->dst_y, h->spec2, h->spec2, 1, 0, g.Mx, g.N, g.Nt, nullptr);
+    };
+    if (run() != KKT_OK) {   // refused (shared memory): not a candidate
+      cudaGetLastError();
+      return 1e30;
+    }
+    cudaEventRecord(e0, nullptr);
+    for (int r = 0; r < 2; ++r) run();
+    cudaEventRecord(e1, nullptr);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  for (int pass = 0; pass < 2; ++pass) {
+    DstPlan& p = pass == 0 ? h->dst_x : h->dst_y;
+    int best = 0;
+    double best_ms = 1e30;
+    for (int tl : {8, 16, 32}) {
+      const double ms = time_pass(p, tl, pass == 0);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = tl;
+      }
+    }
+    p.tile_lines = best;   // 0 (the default) if no candidate ran
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  const cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return set_error(KKT_ERR_CUDA, std::string("transform autotuning: ") + cudaGetErrorString(e));
+  set_error(KKT_OK, "");
+  return KKT_OK;
 }
 
 int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st) {

@@ -38,6 +38,7 @@ struct DstPlan {
   double2* d_tw = nullptr;    // exp(-2 pi i k / (n/2)), k = 0..n/2-1 (FFT twiddles)
   double2* d_post = nullptr;  // exp(-2 pi i k / n), k = 0..n/2 (real-FFT unpacking)
   double* d_sin = nullptr;    // direct transform: sqrt(2/n) sin(pi m / n), m = 0..2n-1
+  int tile_lines = 0;         // lines per CTA tile (0: the size-based default; set by dst_autotune)
 };
 
 // Time decomposition of Section 3 and the data of the Nicolaides coarse space (Eq 14).
@@ -169,6 +170,9 @@ int prof_graph_launch(cudaGraphExec_t g, const ProfCapture& acc, cudaStream_t st
 
 // ---- kernels launched from the C ABI (each defined in its own translation unit) ---------
 int dst_plan_create(DstPlan& p, int n);
+// Times the candidate tile heights (8, 16, 32 lines) of the row and column passes on the
+// handle's spectral buffers and keeps the fastest in dst_x / dst_y (at create).
+int dst_autotune(kkt_handle* h);
 void dst_plan_destroy(DstPlan& p);
 // orthonormal 2D DST-I of every slice: rows (along x) then columns (along y)
 int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st);
