@@ -676,6 +676,18 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_s = float(t.item())
     nbytes = f.numel() * 8
+    # the host link's own bandwidth on this machine (context for e2e): one pinned H2D and D2H copy
+    link = {}
+    d_tmp = torch.empty_like(f)
+    for name, dst, src in (("h2d_gbs", d_tmp, f_host), ("d2h_gbs", x_host, f)):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        dst.copy_(src, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        link[name] = nbytes / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+    del d_tmp
     peaks, peak_kind = measured_peaks()
     apply_stats = time_applies(kkt, solver, w.V, 10, dev)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -685,6 +697,7 @@ def run_ours(args):
             "rel_residual_euclid": results[-1].rel_residual_euclid,
             "precond_applies_per_s": apply_stats["applies_per_s"], "precond_apply": apply_stats,
             "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
+                    "host_link_gbs": link,
                     "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches,
             "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},

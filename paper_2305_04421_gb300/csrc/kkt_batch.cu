@@ -172,6 +172,75 @@ __global__ void __launch_bounds__(kThreads) mgs_b(const Seg* __restrict__ segs, 
   }
 }
 
+// Paired MGS step over all instances: w -= c0 V_k + c1 V_k+1 (NA of them, c_i = dots[inst][k+i]
+// * sc[inst][k+i]), then partial dots <V_k+NA, w>, <V_k+NA+1, w> (ND of them) or <w, w> when
+// ND = 0, max(ND, 1) columns per item.
+template <int NA, int ND>
+__global__ void __launch_bounds__(kThreads) mgs2_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+                                                   int nj, long long total, int k, const double* __restrict__ dots,
+                                                   const double* __restrict__ sc, int ld, double* __restrict__ part) {
+  __shared__ double sh[32];
+  KKT_SEG_TABLE
+  constexpr int W = ND > 1 ? 2 : 1;
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int q = batch_find(sp, nj, t);
+    const Seg S = ss[q];
+    const double c0 = NA > 0 ? dots[q * ld + k] * sc[q * ld + k] : 0.0;
+    const double c1 = NA > 1 ? dots[q * ld + k + 1] * sc[q * ld + k + 1] : 0.0;
+    const double* A0 = S.V + k * S.stride;
+    const double* A1 = A0 + S.stride;
+    const double* B0 = S.V + (k + NA) * S.stride;
+    const double* B1 = B0 + S.stride;
+    const long long e0 = (t - sp[q]) * kChunk, e1 = min(e0 + kChunk, S.n);
+    double acc0 = 0.0, acc1 = 0.0;
+    for (long long base = e0 + threadIdx.x; base < e1; base += 4 * kThreads) {
+      double wv[4], a0[4], a1[4], b0[4], b1[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const long long i = base + r * kThreads;
+        const bool in = i < e1;
+        wv[r] = in ? S.w[i] : 0.0;
+        a0[r] = (in && NA > 0) ? A0[i] : 0.0;
+        a1[r] = (in && NA > 1) ? A1[i] : 0.0;
+        b0[r] = (in && ND > 0) ? B0[i] : 0.0;
+        b1[r] = (in && ND > 1) ? B1[i] : 0.0;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const long long i = base + r * kThreads;
+        if (NA > 0) {
+          wv[r] = fma(-c0, a0[r], wv[r]);
+          if (NA > 1) wv[r] = fma(-c1, a1[r], wv[r]);
+          if (i < e1) S.w[i] = wv[r];
+        }
+        if (ND == 0) {
+          acc0 = fma(wv[r], wv[r], acc0);
+        } else {
+          acc0 = fma(b0[r], wv[r], acc0);
+          if (ND > 1) acc1 = fma(b1[r], wv[r], acc1);
+        }
+      }
+    }
+    const double r0 = block_sum(acc0, sh);
+    if (threadIdx.x == 0) part[t * W] = r0;
+    if (ND > 1) {
+      const double r1 = block_sum(acc1, sh);
+      if (threadIdx.x == 0) part[t * W + 1] = r1;
+    }
+  }
+}
+
+// out[inst * ld + col0 + c] = sum over the instance's items of part[t * width + c]
+__global__ void finalize_cols_b(const double* __restrict__ part, const long long* __restrict__ prefix, int nj,
+                                int width, double* __restrict__ out, int ld, int col0) {
+  const int inst = blockIdx.x / width, c = blockIdx.x % width;
+  if (inst >= nj) return;
+  double acc = 0.0;
+  for (long long t = prefix[inst] + threadIdx.x; t < prefix[inst + 1]; t += 32) acc += part[t * width + c];
+  acc = warp_sum(acc);
+  if (threadIdx.x == 0) out[inst * ld + col0 + c] = acc;
+}
+
 // out[inst * ld + col] = sum of part[t] over the instance's items
 __global__ void finalize_col_b(const double* __restrict__ part, const long long* __restrict__ prefix, int nj,
                                double* __restrict__ out, int ld, int col) {
@@ -773,7 +842,49 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         if (rc != KKT_OK) break;
         std::vector<double> wn2(nw, 0.0), before(nr, 0.0);
         std::vector<char> need(nr, 1);
-        if (b->opt.orth != KKT_ORTH_CGS2) {   // MGS (the paired variant runs as MGS here)
+        if (b->opt.orth == KKT_ORTH_MGS2) {
+          // paired MGS over all running instances: one pass subtracts a pair of basis vectors
+          // and takes the next pair's dots (as kkt_solve does)
+          for (int q = 0; q < nr; ++q)
+            for (int i = 0; i <= j; ++i) h_coef[q * 33 + i] = 1.0 / (S[mem[q]]->eta[i] * S[mem[q]]->eta[i]);
+          KKT_CUDA_TRY(cudaMemcpyAsync(d_coef, h_coef, sizeof(double) * 33 * nr, cudaMemcpyHostToDevice, st));
+          const unsigned grid = static_cast<unsigned>(std::min<long long>(t_new.total, persistent_grid()));
+          auto step = [&](int na, int nd, int k) -> int {
+            const double el = t_new.elems;
+            {
+              ProfScope ps(na > 0 ? KKT_K_UPDATE : KKT_K_MULTIDOT, st, 2.0 * el * (na + (nd > 0 ? nd : 1)),
+                           8.0 * el * (na + nd + 1 + (na > 0 ? 1 : 0)));
+#define KKT_MGS2B(NA_, ND_)                                                                                     \
+  if (na == NA_ && nd == ND_)                                                                                   \
+    mgs2_b<NA_, ND_><<<grid, kThreads, 0, st>>>(t_new.dev, t_new.prefix, nr, t_new.total, k, d_out, d_coef, 33, part);
+              KKT_MGS2B(0, 1) KKT_MGS2B(0, 2) KKT_MGS2B(1, 0) KKT_MGS2B(1, 1) KKT_MGS2B(1, 2) KKT_MGS2B(2, 0)
+              KKT_MGS2B(2, 1) KKT_MGS2B(2, 2)
+#undef KKT_MGS2B
+              KKT_CUDA_TRY(cudaGetLastError());
+            }
+            const int width = nd > 1 ? 2 : 1;
+            ProfScope ps(KKT_K_REDUCE, st);
+            finalize_cols_b<<<nr * width, 32, 0, st>>>(part, t_new.prefix, nr, width, d_out, 33, nd > 0 ? k + na : j + 1);
+            KKT_CUDA_TRY(cudaGetLastError());
+            return KKT_OK;
+          };
+          rc = step(0, std::min(2, j + 1), 0);
+          for (int k = 0; k <= j && rc == KKT_OK;) {
+            const int na = std::min(2, j + 1 - k);
+            const int nd = std::min(2, j + 1 - (k + na));
+            rc = step(na, nd, k);
+            k += na;
+          }
+          if (rc != KKT_OK) break;
+          KKT_CUDA_TRY(cudaMemcpyAsync(h_out, d_out, sizeof(double) * 33 * nr, cudaMemcpyDeviceToHost, st));
+          KKT_CUDA_TRY(cudaStreamSynchronize(st));
+          for (int q = 0; q < nr; ++q) {
+            InstState& I = *S[mem[q]];
+            for (int i = 0; i <= j; ++i) Hs(I, i, j) = h_out[q * 33 + i] / I.eta[i];
+            wn2[mem[q]] = h_out[q * 33 + j + 1];
+          }
+        }
+        if (b->opt.orth == KKT_ORTH_MGS) {
           // modified Gram-Schmidt, step k over all running instances at once; the dots stay on
           // the device (d_out[q][k]) and feed the next step, the host reads the columns once
           for (int q = 0; q < nr; ++q)

@@ -73,7 +73,8 @@ def single(kkt, w, f, tol, coarse="exact", orth="mgs", basis="physical"):
 
 
 @pytest.mark.parametrize("coarse,orth,basis", [("exact", "mgs", "physical"), ("none", "mgs", "physical"),
-                                               ("exact", "cgs2", "physical"), ("exact", "mgs", "spectral")])
+                                               ("exact", "cgs2", "physical"), ("exact", "mgs", "spectral"),
+                                               ("exact", "mgs2", "physical"), ("none", "mgs2", "spectral")])
 def test_batch_matches_single_instance_solves(kkt, small_case, coarse, orth, basis):
     ps, fs = small_case
     b = kkt.Batch(SMALL, coarse=coarse, orth=orth, basis=basis)
