@@ -116,6 +116,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, device, world: int) -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's); x itself at N = 1."""
+    if world <= 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, solves_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's solves over the slowest rank's time (replicas)."""
+    return world * solves_per_rank / seconds
+
+
 # ---------------------------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------------------------
@@ -647,14 +663,10 @@ def run_ours(args):
     kkt.kkt_profile_enable(False)
     prof = kkt.kkt_profile_read(reset=True)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev, world)
     ok = all(r.status == kkt.KKT_OK and r.rel_residual <= TOL for r in results)
     its = results[-1].iterations
-    value = world * args.steps / (ms / 1e3)
+    value = job_value(world, args.steps, ms / 1e3)
     launches = sum(v["launches"] for k, v in prof.items() if k != "graph")   # kernels only
     applies = sum(r.iterations for r in results)
     # end to end through the C ABI with host buffers: H2D of f and x0, D2H of x inside the timed region
@@ -670,11 +682,7 @@ def run_ours(args):
         x_host.zero_()
         solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dev, world)
     nbytes = f.numel() * 8
     # the host link's own bandwidth on this machine (context for e2e): one pinned H2D and D2H copy
     link = {}
@@ -696,7 +704,7 @@ def run_ours(args):
             "iterations": its, "converged": ok, "rel_residual": results[-1].rel_residual,
             "rel_residual_euclid": results[-1].rel_residual_euclid,
             "precond_applies_per_s": apply_stats["applies_per_s"], "precond_apply": apply_stats,
-            "e2e": {"value": world * e2e_steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
+            "e2e": {"value": job_value(world, e2e_steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
                     "host_link_gbs": link,
                     "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches,
