@@ -33,6 +33,12 @@ __device__ __forceinline__ int bit_reverse(int v, int bits) {
   return bits > 0 ? static_cast<int>(__brev(static_cast<unsigned>(v)) >> (32 - bits)) : 0;
 }
 
+// Padded position of complex element i in a warp's FFT buffer: one spare 16-byte slot after
+// every 8 elements, so the butterflies' power-of-two strides spread over the banks.
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+// doubles per warp: n/2 + n/16 double2 and slack, kept even so every warp's buffer is 16-byte aligned
+constexpr int fft_buf_words(int n) { return (n + n / 8 + 2 + 1) & ~1; }
+
 // Complex product v w (4 FP64 instructions).
 __device__ __forceinline__ double2 cmul(double2 v, double2 w) {
   return make_double2(fma(v.x, w.x, -v.y * w.y), fma(v.x, w.y, v.y * w.x));
@@ -55,21 +61,21 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
       const double2 q = pw[j <= P ? j : n - j];
       yj = fma(q.x, a, q.y * b);
     }
-    reinterpret_cast<double*>(buf + bit_reverse(j >> 1, logp))[j & 1] = yj;
+    reinterpret_cast<double*>(buf + pidx(bit_reverse(j >> 1, logp)))[j & 1] = yj;
   }
   __syncwarp();
   int s = 1;
   if (logp >= 2) {
     // stages 1 and 2: pairs (0,1), (2,3) with twiddle 1, then (0,2) with 1 and (1,3) with -i
     for (int b = lane; b < (P >> 2); b += 32) {
-      double2* p = buf + 4 * b;
-      const double2 a0 = p[0], a1 = p[1], a2 = p[2], a3 = p[3];
+      const int i0 = 4 * b;
+      const double2 a0 = buf[pidx(i0)], a1 = buf[pidx(i0 + 1)], a2 = buf[pidx(i0 + 2)], a3 = buf[pidx(i0 + 3)];
       const double2 b0 = make_double2(a0.x + a1.x, a0.y + a1.y), b1 = make_double2(a0.x - a1.x, a0.y - a1.y);
       const double2 b2 = make_double2(a2.x + a3.x, a2.y + a3.y), b3 = make_double2(a2.x - a3.x, a2.y - a3.y);
-      p[0] = make_double2(b0.x + b2.x, b0.y + b2.y);
-      p[2] = make_double2(b0.x - b2.x, b0.y - b2.y);
-      p[1] = make_double2(b1.x + b3.y, b1.y - b3.x);   // b1 + (-i) b3
-      p[3] = make_double2(b1.x - b3.y, b1.y + b3.x);
+      buf[pidx(i0)] = make_double2(b0.x + b2.x, b0.y + b2.y);
+      buf[pidx(i0 + 2)] = make_double2(b0.x - b2.x, b0.y - b2.y);
+      buf[pidx(i0 + 1)] = make_double2(b1.x + b3.y, b1.y - b3.x);   // b1 + (-i) b3
+      buf[pidx(i0 + 3)] = make_double2(b1.x - b3.y, b1.y + b3.x);
     }
     __syncwarp();
     s = 3;
@@ -82,16 +88,16 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
     for (int b = lane; b < (P >> 2); b += 32) {
       const int k = b & (half - 1);
       const int i0 = ((b >> (s - 1)) << (s + 1)) + k;
-      const double2 p0 = buf[i0];
-      const double2 p2 = cmul(buf[i0 + half], L.tw[(2 * k) << tsh]);
-      const double2 p1 = cmul(buf[i0 + 2 * half], L.tw[k << tsh]);
-      const double2 p3 = cmul(buf[i0 + 3 * half], L.tw[(3 * k) << tsh]);
+      const double2 p0 = buf[pidx(i0)];
+      const double2 p2 = cmul(buf[pidx(i0 + half)], L.tw[(2 * k) << tsh]);
+      const double2 p1 = cmul(buf[pidx(i0 + 2 * half)], L.tw[k << tsh]);
+      const double2 p3 = cmul(buf[pidx(i0 + 3 * half)], L.tw[(3 * k) << tsh]);
       const double2 S = make_double2(p0.x + p2.x, p0.y + p2.y), T = make_double2(p1.x + p3.x, p1.y + p3.y);
       const double2 U = make_double2(p0.x - p2.x, p0.y - p2.y), D = make_double2(p1.x - p3.x, p1.y - p3.y);
-      buf[i0] = make_double2(S.x + T.x, S.y + T.y);
-      buf[i0 + 2 * half] = make_double2(S.x - T.x, S.y - T.y);
-      buf[i0 + half] = make_double2(U.x + D.y, U.y - D.x);       // U - i D
-      buf[i0 + 3 * half] = make_double2(U.x - D.y, U.y + D.x);   // U + i D
+      buf[pidx(i0)] = make_double2(S.x + T.x, S.y + T.y);
+      buf[pidx(i0 + 2 * half)] = make_double2(S.x - T.x, S.y - T.y);
+      buf[pidx(i0 + half)] = make_double2(U.x + D.y, U.y - D.x);       // U - i D
+      buf[pidx(i0 + 3 * half)] = make_double2(U.x - D.y, U.y + D.x);   // U + i D
     }
     __syncwarp();
   }
@@ -101,10 +107,10 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
       const int k = b & (half - 1);
       const int i0 = ((b >> (s - 1)) << s) + k;
       const int i1 = i0 + half;
-      const double2 u = buf[i0];
-      const double2 t = cmul(buf[i1], L.tw[k << (logp - s)]);
-      buf[i0] = make_double2(u.x + t.x, u.y + t.y);
-      buf[i1] = make_double2(u.x - t.x, u.y - t.y);
+      const double2 u = buf[pidx(i0)];
+      const double2 t = cmul(buf[pidx(i1)], L.tw[k << (logp - s)]);
+      buf[pidx(i0)] = make_double2(u.x + t.x, u.y + t.y);
+      buf[pidx(i1)] = make_double2(u.x - t.x, u.y - t.y);
     }
     __syncwarp();
   }
@@ -116,8 +122,8 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
   if (active) {
     for (int t = 0; t < chunk; ++t) {
       const int k = k0 + t;
-      const double2 zk = buf[k];
-      const double2 zc = buf[(P - k) & (P - 1)];
+      const double2 zk = buf[pidx(k)];
+      const double2 zc = buf[pidx((P - k) & (P - 1))];
       const double er = zk.x + zc.x, nei = zc.y - zk.y;    // Z_k + conj(Z_{P-k}) (imaginary part negated)
       const double orr = zk.y + zc.y, oi = zc.x - zk.x;    // (Z_k - conj(Z_{P-k})) / i
       const double2 w = L.post[k];                         // exp(-2 pi i k / n)
@@ -136,7 +142,7 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
   const double prev = __shfl_up_sync(0xffffffffu, incl, 1);
   // S_2k+1 = R_0 / 2 + R_1 + ... + R_k: the exclusive prefix of the lanes before, less R_0 / 2
   // (R_0 = 2 (Z_0.x + Z_0.y) in the times-2 convention)
-  const double corr = (lane == 0 ? 0.0 : prev) - (buf[0].x + buf[0].y);
+  const double corr = (lane == 0 ? 0.0 : prev) - (buf[0].x + buf[0].y);   // (pidx(0) = 0)
   if (active)
     for (int t = 0; t < chunk; ++t) x[2 * (k0 + t)] += corr;
   __syncwarp();
@@ -165,7 +171,7 @@ __device__ void dst_tile_body(const DstLaunch& L, long long bid, double* smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* tile = smem;
   const int tile_words = (L.tile_lines * L.ldt + 1) & ~1;
-  double2* fbuf = reinterpret_cast<double2*>(smem + tile_words) + warp * (L.n >> 1);
+  double2* fbuf = reinterpret_cast<double2*>(smem + tile_words + warp * fft_buf_words(L.n));
 
   long long base = 0;
   int nl = 0;
@@ -226,7 +232,7 @@ size_t smem_bytes(int n, int tl) {
   const int M = n - 1;
   const int ldt = M | 1;
   const size_t tile_words = (static_cast<size_t>(tl) * ldt + 1) & ~static_cast<size_t>(1);
-  return (tile_words + static_cast<size_t>(kWarps) * n) * sizeof(double);
+  return (tile_words + static_cast<size_t>(kWarps) * fft_buf_words(n)) * sizeof(double);
 }
 
 DstLaunch make_launch(const DstPlan& p, const double* in, double* out, int mode, long long total_lines, int cols,

@@ -45,7 +45,26 @@ def test_status_strings_and_defaults(lib):
     opt = kkt.KKTOptions()
     assert lib.kkt_default_options(ctypes.byref(opt)) == 0
     assert (opt.precision, opt.coarse, opt.variant, opt.pou, opt.restart, opt.jhat_sign) == (0, 0, 0, 0, 30, -1)
+    assert (opt.residual_norm, opt.tc_split, opt.orth, opt.basis, opt.local) == (
+        kkt.NORM["l2"], 1, kkt.ORTH["mgs2"], kkt.BASIS["physical"], kkt.LOCAL["rasq"])
     assert (opt.Lx, opt.Ly) == (1.0, 1.0)
+
+
+def test_options_struct_matches_the_header():
+    """The binding's option and stats structures have the header's field order and size."""
+    import ctypes
+    import re
+    from paper_2305_04421_gb300 import kkt
+    text = open(os.path.join(ROOT, "include", "kkt.h")).read()
+    body = re.search(r"typedef struct kkt_options \{(.*?)\} kkt_options;", text, re.S).group(1)
+    fields = []
+    for line in body.splitlines():
+        m = re.match(r"\s*(int|double)\s+([\w, ]+);", line)
+        if m:
+            fields += [f.strip() for f in m.group(2).split(",")]
+    assert [f[0] for f in kkt.KKTOptions._fields_] == fields
+    assert ctypes.sizeof(kkt.KKTKernelStats) == 5 * 8 * len(kkt.KERNEL_CLASSES)
+    assert "KKT_K_COUNT = %d" % len(kkt.KERNEL_CLASSES) in text
 
 
 def test_invalid_sizes_rejected_before_any_device_call(lib):
