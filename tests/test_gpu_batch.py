@@ -164,3 +164,31 @@ def test_batch_replays_count_their_kernels(kkt, small_case):
     assert prof["dst"]["launches"] >= 4 * steps
     assert prof["matvec"]["launches"] >= steps
     assert prof["coarse"]["launches"] >= steps and prof["sweep"]["launches"] >= steps
+
+
+def test_batch_restart_cycles_and_ras_locals(kkt, small_case):
+    """FGMRES(5) in the batched form (several lockstep restart cycles, instances finishing in
+    different cycles) with RAS local solves: each instance matches its own kkt_solve."""
+    ps, fs = small_case
+    b = kkt.Batch(SMALL, restart=5)
+    opt = kkt.KKTOptions()
+    kkt.load_library().kkt_default_options(opt)
+    res = b.solve(fs, tol=1e-8, maxit=420)
+    assert res.status == kkt.KKT_OK
+    for i, w in enumerate(SMALL):
+        s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, restart=5)
+        ref = s.solve(fs[i], tol=1e-8, maxit=420)
+        s.close()
+        assert abs(res.iterations[i] - ref.iterations) <= 1, (w.name, res.iterations[i], ref.iterations)
+        assert rel(host(res.xs[i]), host(ref.x)) < 1e-5
+    exact = [spectral.kkt_exact_solve(ps[i], host(fs[i])) for i in range(len(SMALL))]
+    for local_opt in ("ras",):
+        descs = [(w.nx, w.ny, w.Nt, w.n_sub, w.T, w.nu, w.omega) for w in SMALL]
+        opt.local = kkt.LOCAL[local_opt]
+        bh = kkt.kkt_batch_create(descs, opt)
+        xs = [torch.zeros_like(f) for f in fs]
+        st = kkt.KKTBatchStats()
+        assert kkt.kkt_batch_solve(bh, fs, xs, 1e-12, 420, st) == kkt.KKT_OK
+        kkt.kkt_batch_destroy(bh)
+        for i in range(len(SMALL)):
+            assert rel(host(xs[i]), exact[i]) < TOL, SMALL[i].name

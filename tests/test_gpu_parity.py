@@ -279,6 +279,26 @@ def test_spectral_basis_solve_matches_oracle(kkt, orth):
     assert rel(x0.numpy(), exact) < TOL
 
 
+@pytest.mark.parametrize("orth", ["mgs", "cgs2", "mgs2"])
+def test_restarted_fgmres_matches_oracle(kkt, orth):
+    """FGMRES(5): several restart cycles; the oracle's FGMRES(5) takes the same iteration count
+    within 1, and a 1e-12 solve reaches the exact solution."""
+    w = workloads.CFG_SMALL
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    f = problem.assemble_rhs(p, workloads.make_target(w), None)
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, restart=5, orth=orth)
+    K = problem.assemble_K(p)
+    pre = schwarz.schur_preconditioner(p, w.n_sub)
+    ref = krylov.fgmres(lambda v: K @ v, lambda r: schwarz.block_preconditioner_apply(p, pre, r), f,
+                        tol=1e-8, restart=5, maxit=420, row_scale=problem.l2_residual_weights(p))
+    res = s.solve(dev(f), tol=1e-8, maxit=420)
+    assert res.status == kkt.KKT_OK and res.restarts >= 3
+    assert abs(res.iterations - ref.iterations) <= 1, (res.iterations, ref.iterations)
+    tight = s.solve(dev(f), tol=1e-12, maxit=600)
+    assert tight.status == kkt.KKT_OK
+    assert rel(host(tight.x), spectral.kkt_exact_solve(p, f)) < TOL
+
+
 def test_spectral_basis_rejects_reduced_precision(kkt):
     with pytest.raises(kkt.KKTError) as e:
         kkt.Solver(32, 32, 64, 1.0, 1.0, 1e-4, 4, precision="tf32", basis="spectral")
