@@ -17,16 +17,20 @@
 // need this extra accuracy; the inverse transforms do not (their error is relative to their
 // own output) and use single operands.
 //
-// Per CTA: one 128 x TILE_N output tile. Warp 0 lane 0 streams A and B chunks of 128 bytes of
-// K through a 2-stage ring with TMA (128B swizzle) and mbarriers, warp 1 lane 0 issues
-// tcgen05.mma (M = 128, N = TILE_N, K = 16 for BF16 / 8 for TF32, FP32 accumulation in TMEM),
-// and after the last commit all four warps read the accumulator with tcgen05.ld (each warp
-// its 32-lane quarter) and store. Every mbarrier wait is bounded (about 2 s of clock); on a
-// timeout the kernel records an error flag, skips its remaining work, still waits (bounded)
-// for its own copies and MMAs, frees its TMEM and returns.
+// The transforms run the persistent, warp-specialised kernel: one CTA per SM walks its tiles
+// (128 x TILE_N outputs each); warp 0 lane 0 streams A and B chunks of 128 bytes of K through
+// a shared-memory ring with TMA (128B swizzle) and mbarriers, warp 1 lane 0 issues tcgen05.mma
+// (M = 128, N = TILE_N, K = 16 for BF16 / 8 for TF32, FP32 accumulation) into one of two TMEM
+// accumulators, and warps 2-5 read the other accumulator back with tcgen05.ld (each warp its
+// 32-lane quarter) and store, so the epilogue of one tile overlaps the loads and MMAs of the
+// next. The one-tile-per-CTA kernel below it is the same pipeline without that overlap.
+// Every mbarrier wait is bounded (about 2 s of clock); on a timeout the kernel records an
+// error flag, skips its remaining work, still waits (bounded) for its own copies and MMAs,
+// frees its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -40,6 +44,8 @@ constexpr int kTileM = 128;
 constexpr int kStages = 2;
 constexpr int kChunkBytes = 128;                      // K bytes per TMA box row (one swizzle span)
 constexpr long long kWaitCycles = 4000000000LL;       // ~2 s at 2 GHz
+// the transforms run the persistent, warp-specialised kernel (false: one tile per CTA)
+constexpr bool kPersistentGemm = true;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -352,6 +358,208 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TILE_N));
 }
 
+// Epilogue store of one accumulator value (row r, column c of slice s) in the output mode.
+template <typename TIn, int OUT>
+__device__ __forceinline__ void store_out(const TcParams& p, int s, int r, int c, float val) {
+  if (OUT == kOutBF16) {
+    reinterpret_cast<__nv_bfloat16*>(p.out)[(static_cast<long long>(s) * p.P + c) * p.P + r] = __float2bfloat16_rn(val);
+  } else if (OUT == kOutSplit) {
+    TIn hi, lo;
+    Split<TIn>::make(val, hi, lo);
+    const long long o = (static_cast<long long>(s) * p.P + c) * p.P + r;
+    reinterpret_cast<TIn*>(p.out)[o] = hi;
+    reinterpret_cast<TIn*>(p.out_lo)[o] = lo;
+  } else if (OUT == kOutF32) {
+    reinterpret_cast<float*>(p.out)[(static_cast<long long>(s) * p.P + c) * p.P + r] = val;
+  } else {
+    if (c < p.valid && r < p.valid)
+      reinterpret_cast<double*>(p.out)[(static_cast<long long>(s) * p.valid + c) * p.valid + r] = static_cast<double>(val);
+  }
+}
+
+// Persistent, warp-specialised form of the same transform: one CTA per SM walks tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ...; warp 0 lane 0 streams A and Q chunks through the
+// shared-memory ring (TMA), warp 1 lane 0 issues the MMAs into one of two TMEM accumulators
+// (2 x TILE_N columns), and warps 2-5 read the other accumulator back and store it, so a tile's
+// epilogue overlaps the next tile's loads and MMAs. Barriers: full/empty per ring stage,
+// tmem_full/tmem_empty per accumulator (the four epilogue warps arrive on tmem_empty), done at
+// teardown. Every wait is bounded; a timeout sets the error flag and every role stops at its
+// next check; teardown waits (bounded) for the CTA's own copies and MMAs and frees TMEM.
+constexpr int kPersistThreads = 192;
+
+template <typename TIn, int TILE_N, int OUT, bool SPLIT>
+__global__ void __launch_bounds__(kPersistThreads, 1)
+    tc_dst_gemm_persistent(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                           const __grid_constant__ CUtensorMap tmAlo, const __grid_constant__ CUtensorMap tmBlo,
+                           TcParams p, int stages) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int A_BYTES = kTileM * kChunkBytes;
+  constexpr int B_BYTES = TILE_N * kChunkBytes;
+  constexpr int PART = A_BYTES + B_BYTES;
+  constexpr int STAGE = SPLIT ? 2 * PART : PART;
+  constexpr int KCHUNK = kChunkBytes / static_cast<int>(sizeof(TIn));
+  constexpr int UMMA_K = MmaKind<TIn>::kUmmaK;
+  constexpr int K_STEPS = KCHUNK / UMMA_K;
+  constexpr uint32_t IDESC = instr_desc<TIn, TILE_N>();
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + stages * STAGE);
+  uint64_t* empty = full + stages;
+  uint64_t* tfull = empty + stages;        // [2]
+  uint64_t* tempty = tfull + 2;            // [2]
+  uint64_t* done = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntile_c = p.P / TILE_N, ntile_r = p.P / kTileM;
+  const int per_slice = ntile_c * ntile_r;
+  const long long ntiles = static_cast<long long>(p.slices) * per_slice;
+  const int nchunks = p.P / KCHUNK;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < stages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(tfull + i, 1);
+      mbar_init(tempty + i, 4);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(2 * TILE_N));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  long long issued = 0;   // chunks whose copies were issued (producer)
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;
+      for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+        const int s = static_cast<int>(tile / per_slice);
+        const int rem = static_cast<int>(tile - static_cast<long long>(s) * per_slice);
+        const int rt = rem / ntile_c, ct = rem - rt * ntile_c;
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int st = static_cast<int>(g % stages);
+          if (g >= stages && !mbar_wait(empty + st, static_cast<uint32_t>(((g / stages) & 1) ^ 1))) {
+            *abort_flag = 1;
+            break;
+          }
+          if (*abort_flag) break;
+          uint8_t* sa = smem + st * STAGE;
+          mbar_expect_tx(full + st, STAGE);
+          tma_load_2d(sa, &tmA, c * KCHUNK, s * p.P + rt * kTileM, full + st);
+          tma_load_2d(sa + A_BYTES, &tmB, c * KCHUNK, ct * TILE_N, full + st);
+          if (SPLIT) {
+            tma_load_2d(sa + PART, &tmAlo, c * KCHUNK, s * p.P + rt * kTileM, full + st);
+            tma_load_2d(sa + PART + A_BYTES, &tmBlo, c * KCHUNK, ct * TILE_N, full + st);
+          }
+          ++issued;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long g = 0;
+      int local = 0;
+      for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++local) {
+        const int acc = local & 1;
+        if (local >= 2 && !mbar_wait(tempty + acc, static_cast<uint32_t>(((local >> 1) & 1) ^ 1))) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tacc = tmem + static_cast<uint32_t>(acc * TILE_N);
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int st = static_cast<int>(g % stages);
+          if (!mbar_wait(full + st, static_cast<uint32_t>((g / stages) & 1))) {
+            *abort_flag = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint8_t* sa = smem + st * STAGE;
+          const uint64_t da = smem_desc(sa), db = smem_desc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < K_STEPS; ++kk)
+            MmaKind<TIn>::mma(tacc, da + 2ull * kk, db + 2ull * kk, IDESC, (c | kk) != 0);
+          if (SPLIT) {
+            const uint64_t dal = smem_desc(sa + PART), dbl = smem_desc(sa + PART + A_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < K_STEPS; ++kk) {
+              MmaKind<TIn>::mma(tacc, da + 2ull * kk, dbl + 2ull * kk, IDESC, 1u);
+              MmaKind<TIn>::mma(tacc, dal + 2ull * kk, db + 2ull * kk, IDESC, 1u);
+            }
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       ::"r"(smem_u32(empty + st)) : "memory");
+        }
+        if (*abort_flag) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(tfull + acc)) : "memory");
+      }
+      // completes after every MMA this thread issued
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(done)) : "memory");
+    }
+  } else {
+    // epilogue warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. + 31 (rows of the tile)
+    const int quad = warp & 3;
+    int local = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++local) {
+      if (*abort_flag) break;
+      const int acc = local & 1;
+      if (!mbar_wait(tfull + acc, static_cast<uint32_t>((local >> 1) & 1))) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int s = static_cast<int>(tile / per_slice);
+      const int rem = static_cast<int>(tile - static_cast<long long>(s) * per_slice);
+      const int rt = rem / ntile_c, ct = rem - rt * ntile_c;
+      const int r = rt * kTileM + quad * 32 + lane;
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(quad * 32) << 16) + static_cast<uint32_t>(acc * TILE_N);
+#pragma unroll 1
+      for (int c0 = 0; c0 < TILE_N; c0 += 16) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tbase + c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < 16; ++t) store_out<TIn, OUT>(p, s, r, ct * TILE_N + c0 + t, __uint_as_float(v[t]));
+      }
+      // this warp's reads of the accumulator are complete: release it to the MMA warp
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tempty + acc)) : "memory");
+    }
+  }
+  __syncwarp();
+  // teardown: every MMA issued (the done commit), then, after a timeout, the producer's copies
+  if (!mbar_wait(done, 0)) *abort_flag = 1;
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) atomicExch(p.err, 1);
+    if (warp == 0 && lane == 0) {
+      for (long long c = issued > stages ? issued - stages : 0; c < issued; ++c)
+        mbar_wait(full + static_cast<int>(c % stages), static_cast<uint32_t>((c / stages) & 1));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TILE_N));
+}
+
 // out + out_lo (P x P per slice, zero padded) = scale * in[s][j][i] (valid x valid), split into
 // hi and lo parts of the operand type
 // Grid (P / 256 rounded up, P, slices): no 64-bit index divisions (the compiler builds those
@@ -412,9 +620,7 @@ template <typename TIn, int TILE_N, int OUT, bool SPLIT>
 int launch_gemm(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& alo, const CUtensorMap& blo,
                 const TcParams& p, cudaStream_t st) {
   constexpr int PART = (kTileM + TILE_N) * kChunkBytes;
-  const size_t smem = 1024 + kStages * (SPLIT ? 2 * PART : PART) + 256;
-  auto kern = tc_dst_gemm_kernel<TIn, TILE_N, OUT, SPLIT>;
-  KKT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  constexpr int STAGE = SPLIT ? 2 * PART : PART;
   const long long tiles = static_cast<long long>(p.slices) * (p.P / kTileM) * (p.P / TILE_N);
   // dense GEMM with Q per slice: 2 P^3 flops (x3 for split operands); operands in, result out
   const double planes = static_cast<double>(p.slices) * p.P * p.P;
@@ -422,7 +628,23 @@ int launch_gemm(const CUtensorMap& a, const CUtensorMap& b, const CUtensorMap& a
                        : (OUT == kOutSplit ? 2.0 * sizeof(TIn) * planes
                                            : (OUT == kOutF32 ? 4.0 * planes : 8.0 * static_cast<double>(p.slices) * p.valid * p.valid));
   ProfScope ps(KKT_K_DST, st, (SPLIT ? 6.0 : 2.0) * planes * p.P, planes * sizeof(TIn) * (SPLIT ? 2 : 1) + out_b);
-  kern<<<static_cast<unsigned>(tiles), 128, smem, st>>>(a, b, alo, blo, p);
+  if (kPersistentGemm) {
+    // as many ring stages as fit beside the barriers (2 with split 256-wide tiles, up to 4)
+    const int stages = std::max(2, std::min(4, static_cast<int>((220 * 1024 - 1024 - 256) / STAGE)));
+    const size_t smem = 1024 + static_cast<size_t>(stages) * STAGE + 256;
+    auto kern = tc_dst_gemm_persistent<TIn, TILE_N, OUT, SPLIT>;
+    KKT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int dev = 0, sms = 0;
+    KKT_CUDA_TRY(cudaGetDevice(&dev));
+    KKT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long grid = std::min<long long>(tiles, sms);
+    kern<<<static_cast<unsigned>(grid), kPersistThreads, smem, st>>>(a, b, alo, blo, p, stages);
+  } else {
+    const size_t smem = 1024 + kStages * STAGE + 256;
+    auto kern = tc_dst_gemm_kernel<TIn, TILE_N, OUT, SPLIT>;
+    KKT_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    kern<<<static_cast<unsigned>(tiles), 128, smem, st>>>(a, b, alo, blo, p);
+  }
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
