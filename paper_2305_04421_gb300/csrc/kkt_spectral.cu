@@ -196,90 +196,91 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
   if (q < p.N) coarse_body<TI>(rhat, in_scale, p, cc, cy, q);
 }
 
-// Learned modes: d = network output (a direction), x = alpha d with the Galerkin
-// alpha = d^T c / d^T G d in the mode's coarse operator G = h S_0 (block tridiagonal, 2x2
-// blocks), kept when ||c - G x|| <= ||c|| / 2, else the exact c' already in cc stays. mode 1
-// zeroes the coarse correction of the learned modes instead.
+// Learned coarse correction of one mode: the network's direction d, scaled by the Galerkin
+// condition alpha = d^T c / d^T G d on the mode's coarse operator G = h S_0(mu), is kept when
+// its coarse residual satisfies ||c - alpha G d||^2 <= ||c||^2 / 4, else the exact solve's
+// result stays. One warp per learned mode: lanes stride over the subdomains (coalesced reads
+// of d and c) and the four sums are reduced with shuffles.
+__device__ __forceinline__ double warp_sum_d(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// (G d)_s for the block-tridiagonal G (2 x 2 blocks mu^2 P0 + P1 - mu P2, couplings -mu a b^T)
+__device__ __forceinline__ void coarse_op_row(const SpecParams& p, double mu, double mu2, const float* __restrict__ d,
+                                              int s, double& e0, double& e1) {
+  const double* M = p.mom + 9 * s;
+  const double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
+  const double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
+  const double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
+  const double d0 = d[2 * s], d1 = d[2 * s + 1];
+  e0 = g00 * d0 + g01 * d1;
+  e1 = g01 * d0 + g11 * d1;
+  if (s + 1 < p.n_sub) {   // E_s d_{s+1}, E_s = -mu a_s b_{s+1}^T
+    const double a1 = __ldg(p.phi + __ldg(p.olast + s) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
+    const double bd = d[2 * s + 2] + b1 * d[2 * s + 3];
+    e0 -= mu * bd;
+    e1 -= mu * a1 * bd;
+  }
+  if (s > 0) {             // E_{s-1}^T d_{s-1} = -mu b_s (a_{s-1}^T d_{s-1})
+    const double a1 = __ldg(p.phi + __ldg(p.olast + s - 1) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s) - 1);
+    const double ad = d[2 * s - 2] + a1 * d[2 * s - 1];
+    e0 -= mu * ad;
+    e1 -= mu * b1 * ad;
+  }
+}
+
 __global__ void learned_apply_kernel(SpecParams p, const float* __restrict__ y, int mode, double* __restrict__ cc,
                                      long long* __restrict__ counts) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
   const int K = p.learn_k;
-  if (i >= K * K) return;
-  const int k = i % K, l = i / K;
+  if (w >= K * K) return;   // uniform per warp
+  const int k = w % K, l = w / K;
   const long long q = static_cast<long long>(l) * p.Mx + k, N = p.N;
   if (mode == 1) {
-    for (int s = 0; s < p.n_sub; ++s) {
+    for (int s = lane; s < p.n_sub; s += 32) {
       cc[(2LL * s) * N + q] = 0.0;
       cc[(2LL * s + 1) * N + q] = 0.0;
     }
     return;
   }
   const double mu = mode_mu(p, q), mu2 = mu * mu;
-  const float* d = y + static_cast<long long>(i) * 2 * p.n_sub;
-  const double* c = p.learn_c + static_cast<long long>(i) * 2 * p.n_sub;
-  // G d, d^T G d, d^T c, ||c||^2 in one pass over the subdomains
+  const float* d = y + static_cast<long long>(w) * 2 * p.n_sub;
+  const double* c = p.learn_c + static_cast<long long>(w) * 2 * p.n_sub;
   double dGd = 0, dc = 0, cc2 = 0;
-  for (int s = 0; s < p.n_sub; ++s) {
-    const double* M = p.mom + 9 * s;
-    const double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
-    const double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
-    const double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
-    const double d0 = d[2 * s], d1 = d[2 * s + 1];
-    double e0 = g00 * d0 + g01 * d1, e1 = g01 * d0 + g11 * d1;
-    if (s + 1 < p.n_sub) {   // E_s d_{s+1}, E_s = -mu a_s b_{s+1}^T
-      const double a1 = __ldg(p.phi + __ldg(p.olast + s) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
-      const double bd = d[2 * s + 2] + b1 * d[2 * s + 3];
-      e0 -= mu * bd;
-      e1 -= mu * a1 * bd;
-    }
-    if (s > 0) {             // E_{s-1}^T d_{s-1} = -mu b_s (a_{s-1}^T d_{s-1})
-      const double a1 = __ldg(p.phi + __ldg(p.olast + s - 1) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s) - 1);
-      const double ad = d[2 * s - 2] + a1 * d[2 * s - 1];
-      e0 -= mu * ad;
-      e1 -= mu * b1 * ad;
-    }
-    dGd += d0 * e0 + d1 * e1;
-    dc += d0 * c[2 * s] + d1 * c[2 * s + 1];
+  for (int s = lane; s < p.n_sub; s += 32) {
+    double e0, e1;
+    coarse_op_row(p, mu, mu2, d, s, e0, e1);
+    dGd += d[2 * s] * e0 + d[2 * s + 1] * e1;
+    dc += d[2 * s] * c[2 * s] + d[2 * s + 1] * c[2 * s + 1];
     cc2 += c[2 * s] * c[2 * s] + c[2 * s + 1] * c[2 * s + 1];
   }
+  dGd = warp_sum_d(dGd);
+  dc = warp_sum_d(dc);
+  cc2 = warp_sum_d(cc2);
   if (!(dGd > 0.0)) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
+    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
     return;
   }
   const double alpha = dc / dGd;
-  // residual ||c - alpha G d||^2 = ||c||^2 - 2 alpha d^T G c... computed directly
   double res2 = 0;
-  for (int s = 0; s < p.n_sub; ++s) {
-    const double* M = p.mom + 9 * s;
-    const double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
-    const double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
-    const double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
-    const double d0 = d[2 * s], d1 = d[2 * s + 1];
-    double e0 = g00 * d0 + g01 * d1, e1 = g01 * d0 + g11 * d1;
-    if (s + 1 < p.n_sub) {
-      const double a1 = __ldg(p.phi + __ldg(p.olast + s) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
-      const double bd = d[2 * s + 2] + b1 * d[2 * s + 3];
-      e0 -= mu * bd;
-      e1 -= mu * a1 * bd;
-    }
-    if (s > 0) {
-      const double a1 = __ldg(p.phi + __ldg(p.olast + s - 1) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s) - 1);
-      const double ad = d[2 * s - 2] + a1 * d[2 * s - 1];
-      e0 -= mu * ad;
-      e1 -= mu * b1 * ad;
-    }
+  for (int s = lane; s < p.n_sub; s += 32) {
+    double e0, e1;
+    coarse_op_row(p, mu, mu2, d, s, e0, e1);
     const double r0 = c[2 * s] - alpha * e0, r1 = c[2 * s + 1] - alpha * e1;
     res2 += r0 * r0 + r1 * r1;
   }
+  res2 = warp_sum_d(res2);
   if (res2 > 0.25 * cc2) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
+    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
     return;
   }
-  for (int s = 0; s < p.n_sub; ++s) {
+  for (int s = lane; s < p.n_sub; s += 32) {
     cc[(2LL * s) * N + q] = p.h * alpha * d[2 * s];
     cc[(2LL * s + 1) * N + q] = p.h * alpha * d[2 * s + 1];
   }
-  atomicAdd(reinterpret_cast<unsigned long long*>(counts), 1ull);
+  if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(counts), 1ull);
 }
 
 // x_0 at node n (1-based), given the coarse pairs of the three subdomains around s.
@@ -572,7 +573,8 @@ int spectral_learned_apply(const kkt_handle* h, bool padded, const float* y, cud
   const int n = p.learn_k * p.learn_k;
   if (n == 0) return KKT_OK;
   ProfScope ps(KKT_K_COARSE, st, 40.0 * n * p.n_sub, 40.0 * n * p.n_sub);
-  learned_apply_kernel<<<(n + 127) / 128, 128, 0, st>>>(p, y, h->mlp_mode, h->coarse_c, h->learn_count);
+  learned_apply_kernel<<<static_cast<unsigned>((32LL * n + 127) / 128), 128, 0, st>>>(p, y, h->mlp_mode, h->coarse_c,
+                                                                                       h->learn_count);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
