@@ -390,8 +390,10 @@ def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, st
 def measure_batched(kkt_mod, dev) -> dict:
     """The 64 uneven instances of the batched workload (sizes 64^2..256^2, Nt 128..1024, N_D
     8..64, spread nu and omega): one batched solve (memory waves, one launch per phase over all
-    running instances, graph replay) against the same instances solved one after another with
-    kkt_solve, in the physical basis and in the spectral basis. All to the same 1e-8 weighted
+    running instances, graph replay; instances of at least 2^23 unknowns per block, which fill
+    the GPU alone, take the single-solve path) against the same instances solved one after
+    another with kkt_solve, in the physical basis and in the spectral basis; also every
+    instance forced through the batched kernels. All to the same 1e-8 weighted
     tolerance from x_0 = 0; device time of the solve calls only (CUDA events), inputs
     resident; the batched value is the second call (the first also autotunes)."""
     import torch
@@ -434,12 +436,19 @@ def measure_batched(kkt_mod, dev) -> dict:
             xs = [torch.zeros_like(f) for f in fs]
             runs.append(timed(lambda: b.solve(fs, xs, tol=TOL, maxit=MAXIT)))
             del xs
+        # every instance through the batched kernels (no single-solve dispatch), for comparison
+        b.set_single_threshold(0)
+        xs = [torch.zeros_like(f) for f in fs]
+        all_ms, all_res = timed(lambda: b.solve(fs, xs, tol=TOL, maxit=MAXIT))
+        del xs
         b.close()
         torch.cuda.empty_cache()
         ms, res = runs[1]
         its = res.iterations
         out[basis] = {
             "batched": {"solves_per_s": len(ws) / (ms / 1e3), "time_ms": ms, "first_call_ms": runs[0][0],
+                        "solo_instances": res.solo,
+                        "all_batched_solves_per_s": len(ws) / (all_ms / 1e3), "all_batched_waves": all_res.waves,
                         "waves": res.waves, "graphs": res.graphs, "graph_launches": res.graph_launches,
                         "tile_lines": res.tile_lines, "sweep_block": res.sweep_block,
                         "tune_ms_dst_tl8_16_32": res.tune_ms_dst, "tune_ms_sweep_tb64_128_256": res.tune_ms_sweep,

@@ -341,7 +341,8 @@ typedef struct kkt_instance {
 } kkt_instance;
 
 typedef struct kkt_batch_stats {
-  int waves;               /* memory waves the instances were packed into */
+  int solo;                /* instances at or above the single-solve threshold, solved one by one */
+  int waves;               /* memory waves the other instances were packed into */
   int graphs;              /* CUDA graphs captured (one per wave and Arnoldi step index used) */
   long long graph_launches;
   int tile_lines;          /* sine-transform tile height the autotuner chose */
@@ -369,6 +370,10 @@ int kkt_batch_set_memory_limit(kkt_batch* b, long long bytes);
  * once per wave as a CUDA graph and replayed; 0: its kernels are launched directly every step
  * (same kernels and results; their device time is then profiled per kernel class). */
 int kkt_batch_set_graphs(kkt_batch* b, int on);
+/* Instances with at least `points` unknowns per block (V) fill the GPU on their own: they are
+ * solved one after another with kkt_solve's path (their Krylov storage released after each),
+ * before the batched waves of the others. Default 2^23; 0 batches every instance. */
+int kkt_batch_set_single_threshold(kkt_batch* b, long long points);
 /* Solve K_i x_i = f_i for every instance. f, x: host arrays of count DEVICE pointers, 3 V_i
  * doubles each; x_i holds the initial guess on entry. Synchronises `stream`. Returns KKT_OK
  * when every instance converged, KKT_NOT_CONVERGED if some stopped at maxit, else the most

@@ -355,6 +355,7 @@ struct kkt_batch {
   double tune_ms_sweep[3] = {0, 0, 0};
   long long mem_limit = 0;    // bytes of Krylov storage per wave; 0: 85% of the free device memory
   int use_graphs = 1;         // replay the preconditioner + matvec phase as CUDA graphs
+  long long single_threshold = 1LL << 23;   // V at or above which an instance is solved alone
 };
 
 using namespace kkt;
@@ -418,6 +419,12 @@ int kkt_batch_set_graphs(kkt_batch* b, int on) {
   return KKT_OK;
 }
 
+int kkt_batch_set_single_threshold(kkt_batch* b, long long points) {
+  if (!b || points < 0) return set_error(KKT_ERR_INVALID_ARG, "bad single-solve threshold");
+  b->single_threshold = points;
+  return KKT_OK;
+}
+
 int kkt_batch_set_memory_limit(kkt_batch* b, long long bytes) {
   if (!b || bytes < 0) return set_error(KKT_ERR_INVALID_ARG, "bad memory limit");
   b->mem_limit = bytes;
@@ -443,8 +450,22 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   KKT_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   double budget = 0.85 * static_cast<double>(free_b);
   if (b->mem_limit > 0) budget = std::min(budget, static_cast<double>(b->mem_limit));
-  std::vector<int> order(n_inst);
-  std::iota(order.begin(), order.end(), 0);
+  // instances that fill the GPU alone: kkt_solve's path, one after another, before the waves
+  std::vector<int> order, solo;
+  for (int i = 0; i < n_inst; ++i)
+    if (b->single_threshold > 0 && b->inst[i]->g.V >= b->single_threshold) solo.push_back(i);
+    else order.push_back(i);
+  std::vector<int> solo_its(n_inst, 0), solo_status(n_inst, KKT_OK);
+  std::vector<double> solo_rel(n_inst, 0.0);
+  for (int i : solo) {
+    kkt_stats ks;
+    const int r = kkt_solve(b->inst[i], f[i], x[i], tol, maxit, &ks, stream);
+    release_krylov(b->inst[i]);
+    if (r < 0 && r != KKT_ERR_NONFINITE) return r;
+    solo_its[i] = ks.iterations;
+    solo_status[i] = r;
+    solo_rel[i] = ks.rel_residual;
+  }
   // spectral basis: f and x run on sine-mode coefficients (x transformed in place, f into a copy)
   const bool spectral = b->opt.basis == KKT_BASIS_SPECTRAL;
   auto need = [&](int i) {
@@ -1063,6 +1084,11 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   cudaFreeHost(h_tmp);
   cudaFree(d_small);
   if (rc_all < 0) return rc_all;
+  for (int i : solo) {
+    all[i].its = solo_its[i];
+    all[i].status = solo_status[i];
+    all[i].rel = solo_rel[i];
+  }
   int worst = KKT_OK;
   for (int i = 0; i < n_inst; ++i) {
     if (all[i].status < 0) worst = std::min(worst, all[i].status);
@@ -1070,6 +1096,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   }
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
+    stats->solo = static_cast<int>(solo.size());
     stats->waves = waves_done;
     stats->graphs = graphs_made;
     stats->graph_launches = graph_launches;

@@ -283,6 +283,18 @@ int schur_precond_w(kkt_handle* h, const double* rw, double scale, double* yw, c
   return KKT_OK;
 }
 
+}  // namespace
+
+void release_krylov(kkt_handle* h) {
+  for (double** b : {&h->kV, &h->kZw, &h->kx, &h->kf, &h->ks_f, &h->ks_x}) {
+    cudaFree(*b);
+    *b = nullptr;
+  }
+  h->kry_restart = 0;
+}
+
+namespace {
+
 int ensure_krylov(kkt_handle* h) {
   const int m = h->opt.restart;
   if (h->kry_restart == m && h->kV) return KKT_OK;

@@ -170,6 +170,8 @@ int prof_graph_launch(cudaGraphExec_t g, const ProfCapture& acc, cudaStream_t st
 
 // ---- kernels launched from the C ABI (each defined in its own translation unit) ---------
 int dst_plan_create(DstPlan& p, int n);
+// Frees a handle's Krylov storage and host-buffer staging (reallocated by the next kkt_solve).
+void release_krylov(kkt_handle* h);
 // Times the candidate tile heights (8, 16, 32 lines) of the row and column passes on the
 // handle's spectral buffers and keeps the fastest in dst_x / dst_y (at create).
 int dst_autotune(kkt_handle* h);

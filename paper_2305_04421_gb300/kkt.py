@@ -82,7 +82,8 @@ class KKTInstance(ctypes.Structure):
 
 
 class KKTBatchStats(ctypes.Structure):
-    _fields_ = [("waves", ctypes.c_int), ("graphs", ctypes.c_int), ("graph_launches", ctypes.c_longlong),
+    _fields_ = [("solo", ctypes.c_int), ("waves", ctypes.c_int), ("graphs", ctypes.c_int),
+                ("graph_launches", ctypes.c_longlong),
                 ("tile_lines", ctypes.c_int), ("sweep_block", ctypes.c_int),
                 ("tune_ms_dst", ctypes.c_double * 3), ("tune_ms_sweep", ctypes.c_double * 3),
                 ("time_ms", ctypes.c_double), ("iterations", ctypes.c_int * BATCH_MAX),
@@ -151,6 +152,7 @@ SIGNATURES = [
     ("kkt_batch_get_info", _I, [_P, _I, ctypes.POINTER(KKTInfo)]),
     ("kkt_batch_set_memory_limit", _I, [_P, ctypes.c_longlong]),
     ("kkt_batch_set_graphs", _I, [_P, _I]),
+    ("kkt_batch_set_single_threshold", _I, [_P, ctypes.c_longlong]),
     ("kkt_batch_solve", _I, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), _D, _I,
                              ctypes.POINTER(KKTBatchStats), _P]),
     ("kkt_profile_enable", _I, [_I]),
@@ -526,6 +528,7 @@ class Solver:
 class BatchResult:
     xs: list
     status: int
+    solo: int
     statuses: list
     iterations: list
     rel_residual: list
@@ -559,6 +562,10 @@ class Batch:
     def __len__(self):
         return len(self.infos)
 
+    def set_single_threshold(self, points: int) -> None:
+        """Instances with at least `points` unknowns per block are solved one by one (0: none)."""
+        _check(load_library().kkt_batch_set_single_threshold(self.b, int(points)))
+
     def set_graphs(self, on: bool) -> None:
         """Replay the per-step preconditioner + matvec phase as CUDA graphs (default) or not."""
         _check(load_library().kkt_batch_set_graphs(self.b, 1 if on else 0))
@@ -584,6 +591,6 @@ class Batch:
         st = KKTBatchStats()
         status = kkt_batch_solve(self.b, fs, xs, tol, maxit, st, stream)
         n = len(fs)
-        return BatchResult(xs, status, list(st.status[:n]), list(st.iterations[:n]), list(st.rel_residual[:n]),
+        return BatchResult(xs, status, st.solo, list(st.status[:n]), list(st.iterations[:n]), list(st.rel_residual[:n]),
                            st.waves, st.graphs, st.graph_launches, st.tile_lines, st.sweep_block,
                            list(st.tune_ms_dst), list(st.tune_ms_sweep), st.time_ms)

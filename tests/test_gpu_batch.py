@@ -78,6 +78,7 @@ def single(kkt, w, f, tol, coarse="exact", orth="mgs", basis="physical"):
 def test_batch_matches_single_instance_solves(kkt, small_case, coarse, orth, basis):
     ps, fs = small_case
     b = kkt.Batch(SMALL, coarse=coarse, orth=orth, basis=basis)
+    b.set_single_threshold(0)          # every instance through the batched kernels
     res = b.solve(fs, tol=1e-8, maxit=420)
     assert res.status == kkt.KKT_OK
     for i, w in enumerate(SMALL):
@@ -192,3 +193,21 @@ def test_batch_restart_cycles_and_ras_locals(kkt, small_case):
         kkt.kkt_batch_destroy(bh)
         for i in range(len(SMALL)):
             assert rel(host(xs[i]), exact[i]) < TOL, SMALL[i].name
+
+
+def test_batch_large_instances_take_the_single_solve_path(kkt, small_case):
+    """With a threshold below the largest instance, those instances are solved one by one
+    (kkt_solve's path) and the rest in waves; every instance still matches its own solve."""
+    ps, fs = small_case
+    b = kkt.Batch(SMALL)
+    biggest = max(w.V for w in SMALL)
+    b.set_single_threshold(biggest)
+    res = b.solve(fs, tol=1e-12, maxit=420)
+    assert res.status == kkt.KKT_OK
+    assert res.solo == sum(1 for w in SMALL if w.V >= biggest) and res.waves == 1
+    for i in range(len(SMALL)):
+        exact = spectral.kkt_exact_solve(ps[i], host(fs[i]))
+        assert rel(host(res.xs[i]), exact) < TOL, SMALL[i].name
+    b.set_single_threshold(1)          # every instance alone: no waves
+    res = b.solve(fs, tol=1e-8, maxit=420)
+    assert res.status == kkt.KKT_OK and res.solo == len(SMALL) and res.waves == 0
