@@ -390,7 +390,7 @@ def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, st
 def measure_batched(kkt_mod, dev) -> dict:
     """The 64 uneven instances of the batched workload (sizes 64^2..256^2, Nt 128..1024, N_D
     8..64, spread nu and omega): one batched solve (memory waves, one launch per phase over all
-    running instances, graph replay; instances of at least 2^23 unknowns per block, which fill
+    running instances, graph replay; instances of at least 2^20 unknowns per block, which fill
     the GPU alone, take the single-solve path) against the same instances solved one after
     another with kkt_solve, in the physical basis and in the spectral basis; also every
     instance forced through the batched kernels. All to the same 1e-8 weighted

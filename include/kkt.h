@@ -372,7 +372,8 @@ int kkt_batch_set_memory_limit(kkt_batch* b, long long bytes);
 int kkt_batch_set_graphs(kkt_batch* b, int on);
 /* Instances with at least `points` unknowns per block (V) fill the GPU on their own: they are
  * solved one after another with kkt_solve's path (their Krylov storage released after each),
- * before the batched waves of the others. Default 2^23; 0 batches every instance. */
+ * before the batched waves of the others. Default 2^20 (measured: batching gains 2.6x below
+ * about 5e5 unknowns per block and loses above about 1e6); 0 batches every instance. */
 int kkt_batch_set_single_threshold(kkt_batch* b, long long points);
 /* Solve K_i x_i = f_i for every instance. f, x: host arrays of count DEVICE pointers, 3 V_i
  * doubles each; x_i holds the initial guess on entry. Synchronises `stream`. Returns KKT_OK

@@ -355,7 +355,7 @@ struct kkt_batch {
   double tune_ms_sweep[3] = {0, 0, 0};
   long long mem_limit = 0;    // bytes of Krylov storage per wave; 0: 85% of the free device memory
   int use_graphs = 1;         // replay the preconditioner + matvec phase as CUDA graphs
-  long long single_threshold = 1LL << 23;   // V at or above which an instance is solved alone
+  long long single_threshold = 1LL << 20;   // V at or above which an instance is solved alone
 };
 
 using namespace kkt;
