@@ -450,6 +450,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   KKT_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
   double budget = 0.85 * static_cast<double>(free_b);
   if (b->mem_limit > 0) budget = std::min(budget, static_cast<double>(b->mem_limit));
+  const bool spectral = b->opt.basis == KKT_BASIS_SPECTRAL;
   // instances that fill the GPU alone: kkt_solve's path, one after another, before the waves
   std::vector<int> order, solo;
   for (int i = 0; i < n_inst; ++i)
@@ -457,17 +458,43 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
     else order.push_back(i);
   std::vector<int> solo_its(n_inst, 0), solo_status(n_inst, KKT_OK);
   std::vector<double> solo_rel(n_inst, 0.0);
-  for (int i : solo) {
-    kkt_stats ks;
-    const int r = kkt_solve(b->inst[i], f[i], x[i], tol, maxit, &ks, stream);
-    release_krylov(b->inst[i]);
-    if (r < 0 && r != KKT_ERR_NONFINITE) return r;
-    solo_its[i] = ks.iterations;
-    solo_status[i] = r;
-    solo_rel[i] = ks.rel_residual;
+  if (!solo.empty()) {
+    // one Krylov arena (and spectral copies) sized for the largest of them, lent to each
+    // handle in turn: a single allocation instead of one per instance
+    long long vmax = 0;
+    for (int i : solo) vmax = std::max(vmax, b->inst[i]->g.V);
+    double *sv = nullptr, *sz = nullptr, *sf = nullptr, *sx = nullptr;
+    int rc = KKT_OK;
+    if (cudaMalloc(&sv, sizeof(double) * (m + 1) * 3 * vmax) != cudaSuccess ||
+        cudaMalloc(&sz, sizeof(double) * m * vmax) != cudaSuccess ||
+        (spectral && (cudaMalloc(&sf, sizeof(double) * 3 * vmax) != cudaSuccess ||
+                      cudaMalloc(&sx, sizeof(double) * 3 * vmax) != cudaSuccess)))
+      rc = set_error(KKT_ERR_OOM, "single-solve Krylov arena");
+    for (size_t q = 0; q < solo.size() && rc == KKT_OK; ++q) {
+      const int i = solo[q];
+      kkt_handle* h = b->inst[i];
+      release_krylov(h);
+      h->kV = sv;
+      h->kZw = sz;
+      h->ks_f = sf;
+      h->ks_x = sx;
+      h->kry_restart = m;
+      kkt_stats ks;
+      const int r = kkt_solve(h, f[i], x[i], tol, maxit, &ks, stream);
+      h->kV = h->kZw = h->ks_f = h->ks_x = nullptr;   // borrowed: not freed with the handle
+      h->kry_restart = 0;
+      if (r < 0 && r != KKT_ERR_NONFINITE) rc = r;
+      solo_its[i] = ks.iterations;
+      solo_status[i] = r;
+      solo_rel[i] = ks.rel_residual;
+    }
+    cudaFree(sv);
+    cudaFree(sz);
+    cudaFree(sf);
+    cudaFree(sx);
+    if (rc < 0) return rc;
   }
   // spectral basis: f and x run on sine-mode coefficients (x transformed in place, f into a copy)
-  const bool spectral = b->opt.basis == KKT_BASIS_SPECTRAL;
   auto need = [&](int i) {
     return 8.0 * ((m + 1) * 3.0 + m + (spectral ? 3.0 : 0.0)) * static_cast<double>(b->inst[i]->g.V);
   };
