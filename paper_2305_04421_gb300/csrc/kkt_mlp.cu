@@ -3,7 +3,8 @@
 // (log dt nu lambda, log dt / sqrt(omega)) to the direction of its coarse correction
 // S_0^{-1} R_0 r. The magnitude along that direction comes from an exact one-dimensional
 // Galerkin step with the mode's coarse operator, so the correction never increases the coarse
-// energy error; a residual guard falls back to the exact coarse solve, which stays the judge.
+// energy error; a residual guard falls back to the exact coarse solve, which stays the reference
+// the learned correction is measured against.
 // FGMRES admits the resulting preconditioner because it tolerates a variable one.
 //
 // Training runs on the GPU with the kernels of this file: the coarse right-hand sides come
