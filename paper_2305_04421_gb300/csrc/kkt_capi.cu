@@ -297,14 +297,15 @@ namespace {
 
 int ensure_krylov(kkt_handle* h) {
   const int m = h->opt.restart;
-  if (h->kry_restart == m && h->kV) return KKT_OK;
-  const size_t n3 = 3 * static_cast<size_t>(h->g.V);
-  KKT_TRY(dev_alloc(h, &h->kV, (m + 1) * n3));
-  KKT_TRY(dev_alloc(h, &h->kZw, static_cast<size_t>(m) * h->g.V));
+  // the small reduction and coefficient buffers, also when the basis storage is lent
   if (!h->red) KKT_TRY(dev_alloc(h, &h->red, static_cast<size_t>(krylov_partial_capacity())));
   if (!h->red_out) KKT_TRY(dev_alloc(h, &h->red_out, 128));
   if (!h->dcoef) KKT_TRY(dev_alloc(h, &h->dcoef, 4 * 128));
   if (!h->h_red) KKT_CUDA_TRY(cudaMallocHost(&h->h_red, 6 * 128 * sizeof(double)));
+  if (h->kry_restart == m && h->kV) return KKT_OK;
+  const size_t n3 = 3 * static_cast<size_t>(h->g.V);
+  KKT_TRY(dev_alloc(h, &h->kV, (m + 1) * n3));
+  KKT_TRY(dev_alloc(h, &h->kZw, static_cast<size_t>(m) * h->g.V));
   h->kry_restart = m;
   return KKT_OK;
 }
