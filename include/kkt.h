@@ -116,6 +116,26 @@ enum kkt_basis {
   KKT_BASIS_SPECTRAL = 1
 };
 
+/* Solver of the coarse problem S_0 c' = R_0 r (the operator after Eq 14). Per sine mode S_0 is
+ * block tridiagonal in time: N_D blocks of 2 x 2, symmetric positive definite. Both solvers
+ * are exact; they differ in how the work is spread over the GPU. */
+enum kkt_coarse_solve {
+  /* cyclic reduction when the modes alone leave the GPU idle (fewer than 16384 spatial modes)
+   * and one mode's system fits in shared memory, block Thomas otherwise */
+  KKT_COARSE_SOLVE_AUTO = 0,
+  /* block Thomas elimination, one thread per mode: R_0 r summed node by node, then N_D
+   * dependent elimination steps and N_D back-substitution steps. The fewest FLOPs. */
+  KKT_COARSE_SOLVE_THOMAS = 1,
+  /* a multilevel hierarchy in time (the paper's conclusion names more levels as future work
+   * without fixing them; this is its exact reading): block cyclic reduction. Level l+1 is the
+   * exact Schur complement of level l onto every second of its blocks, again block
+   * tridiagonal, down to one block after ceil(log2 N_D) levels, then back up. The subdomain
+   * sums of R_0 r and each level's eliminations run in parallel over subdomains, so the
+   * dependent chain is O(log N_D) instead of O(Nt). About three times Thomas's FLOPs.
+   * Not used with the learned coarse correction (which falls back to Thomas). */
+  KKT_COARSE_SOLVE_CYCLIC = 2
+};
+
 /* Owner of the time node shared by neighbouring subdomains (boolean partition of unity D_s). */
 enum kkt_pou {
   KKT_POU_LEFT = 0,   /* the subdomain whose last step ends on the node */
@@ -136,6 +156,7 @@ typedef struct kkt_options {
   int basis;        /* enum kkt_basis, default KKT_BASIS_PHYSICAL */
   int local;        /* enum kkt_local, default KKT_LOCAL_RASQ */
   double Lx, Ly;    /* domain (0,Lx) x (0,Ly), default 1, 1 */
+  int coarse_solve; /* enum kkt_coarse_solve, default KKT_COARSE_SOLVE_AUTO */
 } kkt_options;
 
 typedef struct kkt_info {

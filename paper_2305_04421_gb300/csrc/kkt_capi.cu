@@ -349,6 +349,7 @@ int kkt_default_options(kkt_options* opt) {
   opt->local = KKT_LOCAL_RASQ;
   opt->Lx = 1.0;
   opt->Ly = 1.0;
+  opt->coarse_solve = KKT_COARSE_SOLVE_AUTO;
   return KKT_OK;
 }
 
@@ -458,6 +459,8 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
   if (opt->basis == KKT_BASIS_SPECTRAL && opt->precision != KKT_PREC_FP64)
     return set_error(KKT_ERR_UNSUPPORTED, "the spectral basis runs the FP64 preconditioner (it has no transforms)");
   if (!finite_pos(opt->Lx) || !finite_pos(opt->Ly)) return set_error(KKT_ERR_INVALID_ARG, "Lx, Ly must be positive");
+  if (opt->coarse_solve < KKT_COARSE_SOLVE_AUTO || opt->coarse_solve > KKT_COARSE_SOLVE_CYCLIC)
+    return set_error(KKT_ERR_INVALID_ARG, "coarse_solve out of range");
   // with the shared node given to the later subdomain, the first subdomain owns nodes
   // 1 .. b_1 - 1; its linear coarse function needs two of them
   if (opt->pou == KKT_POU_RIGHT && h->g.Nt / h->g.n_sub < 3)

@@ -109,6 +109,40 @@ __global__ void coarse_factor_kernel(SpecParams p, double* __restrict__ cf) {
   }
 }
 
+// R_0 r of subdomain s for mode q: the sums of r over the subdomain's owned nodes against
+// (1, phi_n), times in_scale. FP32 input (the reduced-precision forms) is summed in compensated
+// FP32 and widened once per subdomain; FP64 input in FP64.
+template <typename TI>
+__device__ __forceinline__ void restrict_sub(const TI* __restrict__ rhat, double in_scale, const SpecParams& p,
+                                             long long q, int s, double& c0, double& c1) {
+  const long long N = p.N;
+  const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
+  if constexpr (sizeof(TI) == 4) {
+    float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
+#pragma unroll 4
+    for (int n = o1; n <= o2; ++n) {
+      const float r = __ldg(rhat + static_cast<long long>(n - 1) * N + q);
+      const float y0 = r - e0, t0 = s0 + y0;
+      e0 = (t0 - s0) - y0;
+      s0 = t0;
+      const float y1 = fmaf(r, __ldg(p.phi_f + n - 1), -e1), t1 = s1 + y1;
+      e1 = (t1 - s1) - y1;
+      s1 = t1;
+    }
+    c0 = static_cast<double>(s0) * in_scale;
+    c1 = static_cast<double>(s1) * in_scale;
+  } else {
+    c0 = 0.0;
+    c1 = 0.0;
+#pragma unroll 4
+    for (int n = o1; n <= o2; ++n) {
+      const double r = load_d(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
+      c0 += r;
+      c1 = fma(r, __ldg(p.phi + n - 1), c1);
+    }
+  }
+}
+
 // R_0 r and the block-Thomas substitutions with the precomputed factors; c' = h x.
 template <typename TI>
 __device__ void coarse_body(const TI* __restrict__ rhat, double in_scale, const SpecParams& p,
@@ -122,32 +156,9 @@ __device__ void coarse_body(const TI* __restrict__ rhat, double in_scale, const 
     if (k < p.learn_k && l < p.learn_k) learned = static_cast<int>(l * p.learn_k + k);
   }
   for (int s = 0; s < p.n_sub; ++s) {
-    double c0 = 0.0, c1 = 0.0;
+    double c0, c1;
+    restrict_sub<TI>(rhat, in_scale, p, q, s, c0, c1);
     const int o1 = __ldg(p.ofirst + s), o2 = __ldg(p.olast + s);
-    if constexpr (sizeof(TI) == 4) {
-      // FP32 input (the reduced-precision forms): compensated FP32 sums over the owned nodes,
-      // scaled and widened once per subdomain (the solve below stays FP64)
-      float s0 = 0.f, e0 = 0.f, s1 = 0.f, e1 = 0.f;
-#pragma unroll 4
-      for (int n = o1; n <= o2; ++n) {
-        const float r = __ldg(rhat + static_cast<long long>(n - 1) * N + q);
-        const float y0 = r - e0, t0 = s0 + y0;
-        e0 = (t0 - s0) - y0;
-        s0 = t0;
-        const float y1 = fmaf(r, __ldg(p.phi_f + n - 1), -e1), t1 = s1 + y1;
-        e1 = (t1 - s1) - y1;
-        s1 = t1;
-      }
-      c0 = static_cast<double>(s0) * in_scale;
-      c1 = static_cast<double>(s1) * in_scale;
-    } else {
-#pragma unroll 4
-      for (int n = o1; n <= o2; ++n) {
-        const double r = load_d(rhat + static_cast<long long>(n - 1) * N + q) * in_scale;
-        c0 += r;
-        c1 = fma(r, __ldg(p.phi + n - 1), c1);
-      }
-    }
     if (learned >= 0) {
       p.learn_c[(learned * p.n_sub + s) * 2LL] = c0;
       p.learn_c[(learned * p.n_sub + s) * 2LL + 1] = c1;
@@ -194,6 +205,169 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
                                     double* __restrict__ cc, double* __restrict__ cy) {
   const long long q = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q < p.N) coarse_body<TI>(rhat, in_scale, p, cc, cy, q);
+}
+
+// Multilevel solve of the same per-mode coarse system (Z_t^T T(mu) Z_t) x = R_0 r by block
+// cyclic reduction. Block s (subdomain s) has the symmetric diagonal block
+// D_s = mu^2 P0 + P1 - mu P2 and the coupling U_s = -mu a_s b_{s+1}^T to block s+1
+// (a_s = (1, phi_last(s)), b_{s+1} = (1, phi_first(s+1))); row s reads
+//   U_{s-1}^T x_{s-1} + D_s x_s + U_s x_{s+1} = c_s.
+// Level l works on the blocks whose index is a multiple of 2^l. Each even-positioned block j
+// takes in its odd-positioned neighbours o1 < j < o2 (the Schur complement onto the even
+// blocks, again symmetric block tridiagonal):
+//   D_j <- D_j - U_o1^T D_o1^-1 U_o1 - U_j D_o2^-1 U_j^T
+//   c_j <- c_j - U_o1^T D_o1^-1 c_o1 - U_j D_o2^-1 c_o2
+//   U_j <- -U_j D_o2^-1 U_o2             (its coupling to the next even block)
+// and the old U_j is kept as o2's left coupling. After ceil(log2 N_D) levels block 0 is
+// alone; the way back solves, level by level, x_o = D_o^-1 (c_o - L_o^T x_left - U_o x_right)
+// with the values the block had when it was eliminated. c' = h x as in block Thomas.
+//
+// A CTA holds `mpc` modes in shared memory, 13 doubles per block and mode: D (3), U (4),
+// L (4), c (2, overwritten by x). Thread t serves mode t % mpc (consecutive threads read
+// consecutive modes) and, with the other blockDim.x / mpc threads of that mode, strides over
+// its subdomains and eliminations. Threads past the last mode only join the barriers.
+constexpr int kCrThreads = 256;
+constexpr int kCrFields = 13;
+// AUTO picks cyclic reduction below this many spatial modes (per mode, Thomas is one thread)
+constexpr long long kCyclicBelowModes = 16384;
+
+__device__ __forceinline__ void sym_inv(double d00, double d01, double d11, double& i00, double& i01, double& i11) {
+  const double id = 1.0 / (d00 * d11 - d01 * d01);
+  i00 = d11 * id;
+  i01 = -d01 * id;
+  i11 = d00 * id;
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(kCrThreads) coarse_cr_kernel(const TI* __restrict__ rhat, double in_scale,
+                                                                SpecParams p, int mpc, double* __restrict__ cc) {
+  extern __shared__ __align__(16) double cr_sm[];
+  const int n = p.n_sub;
+  const int m = threadIdx.x % mpc, w = threadIdx.x / mpc, W = blockDim.x / mpc;
+  const long long q = static_cast<long long>(blockIdx.x) * mpc + m;
+  const bool active = q < p.N;
+  // field f of mode m: cr_sm[(f * mpc + m) * n + s]
+  double* const F = cr_sm + static_cast<long long>(m) * n;
+  const long long fs = static_cast<long long>(mpc) * n;   // stride between fields
+  double *D00 = F, *D01 = F + fs, *D11 = F + 2 * fs;
+  double *U00 = F + 3 * fs, *U01 = F + 4 * fs, *U10 = F + 5 * fs, *U11 = F + 6 * fs;
+  double *L00 = F + 7 * fs, *L01 = F + 8 * fs, *L10 = F + 9 * fs, *L11 = F + 10 * fs;
+  double *C0 = F + 11 * fs, *C1 = F + 12 * fs;
+
+  const double mu = active ? mode_mu(p, q) : 1.0, mu2 = mu * mu;
+  for (int s = w; s < n; s += W) {
+    if (!active) continue;
+    double c0, c1;
+    restrict_sub<TI>(rhat, in_scale, p, q, s, c0, c1);
+    C0[s] = c0;
+    C1[s] = c1;
+    const double* M = p.mom + 9 * s;
+    D00[s] = fma(mu2, M[0], M[3]) - mu * M[6];
+    D01[s] = fma(mu2, M[1], M[4]) - mu * M[7];
+    D11[s] = fma(mu2, M[2], M[5]) - mu * M[8];
+    double a1 = 0.0, b1 = 0.0, g = 0.0;
+    if (s + 1 < n) {
+      a1 = __ldg(p.phi + __ldg(p.olast + s) - 1);
+      b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
+      g = -mu;
+    }
+    U00[s] = g;
+    U01[s] = g * b1;
+    U10[s] = g * a1;
+    U11[s] = g * a1 * b1;
+  }
+  __syncthreads();
+
+  int top = 1;   // first stride at which one block is left
+  for (int st = 1; st < n; st *= 2) {
+    const int cnt = (n + st - 1) / st;   // blocks of this level
+    for (int e = w; 2 * e < cnt; e += W) {
+      if (!active) continue;
+      const int k = 2 * e, j = k * st;
+      double d00 = D00[j], d01 = D01[j], d11 = D11[j], c0 = C0[j], c1 = C1[j];
+      if (k >= 1) {   // left neighbour o1: D_j -= U^T D_o1^-1 U, c_j -= U^T D_o1^-1 c_o1 (U = U_o1)
+        const int o = j - st;
+        double i00, i01, i11;
+        sym_inv(D00[o], D01[o], D11[o], i00, i01, i11);
+        const double u00 = U00[o], u01 = U01[o], u10 = U10[o], u11 = U11[o];
+        const double x00 = i00 * u00 + i01 * u10, x01 = i00 * u01 + i01 * u11;   // X = D^-1 U
+        const double x10 = i01 * u00 + i11 * u10, x11 = i01 * u01 + i11 * u11;
+        d00 -= u00 * x00 + u10 * x10;
+        d01 -= u00 * x01 + u10 * x11;
+        d11 -= u01 * x01 + u11 * x11;
+        const double y0 = i00 * C0[o] + i01 * C1[o], y1 = i01 * C0[o] + i11 * C1[o];
+        c0 -= u00 * y0 + u10 * y1;
+        c1 -= u01 * y0 + u11 * y1;
+      }
+      if (k + 1 < cnt) {   // right neighbour o2: Y = U_j D_o2^-1
+        const int o = j + st;
+        double i00, i01, i11;
+        sym_inv(D00[o], D01[o], D11[o], i00, i01, i11);
+        const double u00 = U00[j], u01 = U01[j], u10 = U10[j], u11 = U11[j];
+        L00[o] = u00;
+        L01[o] = u01;
+        L10[o] = u10;
+        L11[o] = u11;
+        const double y00 = u00 * i00 + u01 * i01, y01 = u00 * i01 + u01 * i11;
+        const double y10 = u10 * i00 + u11 * i01, y11 = u10 * i01 + u11 * i11;
+        d00 -= y00 * u00 + y01 * u01;   // D_j -= Y U_j^T
+        d01 -= y00 * u10 + y01 * u11;
+        d11 -= y10 * u10 + y11 * u11;
+        c0 -= y00 * C0[o] + y01 * C1[o];
+        c1 -= y10 * C0[o] + y11 * C1[o];
+        const double v00 = U00[o], v01 = U01[o], v10 = U10[o], v11 = U11[o];   // U_j <- -Y U_o2
+        U00[j] = -(y00 * v00 + y01 * v10);
+        U01[j] = -(y00 * v01 + y01 * v11);
+        U10[j] = -(y10 * v00 + y11 * v10);
+        U11[j] = -(y10 * v01 + y11 * v11);
+      }
+      D00[j] = d00;
+      D01[j] = d01;
+      D11[j] = d11;
+      C0[j] = c0;
+      C1[j] = c1;
+    }
+    __syncthreads();
+    top = 2 * st;
+  }
+
+  if (active && w == 0) {   // the last block: x_0 = D_0^-1 c_0
+    double i00, i01, i11;
+    sym_inv(D00[0], D01[0], D11[0], i00, i01, i11);
+    const double c0 = C0[0], c1 = C1[0];
+    C0[0] = i00 * c0 + i01 * c1;
+    C1[0] = i01 * c0 + i11 * c1;
+  }
+  __syncthreads();
+
+  for (int st = top / 2; st >= 1; st /= 2) {
+    const int cnt = (n + st - 1) / st;
+    for (int e = w; 2 * e + 1 < cnt; e += W) {
+      if (!active) continue;
+      const int k = 2 * e + 1, o = k * st, left = o - st;
+      const double xl0 = C0[left], xl1 = C1[left];
+      double r0 = C0[o] - (L00[o] * xl0 + L10[o] * xl1);   // c_o - L^T x_left
+      double r1 = C1[o] - (L01[o] * xl0 + L11[o] * xl1);
+      if (k + 1 < cnt) {
+        const int right = o + st;
+        const double xr0 = C0[right], xr1 = C1[right];
+        r0 -= U00[o] * xr0 + U01[o] * xr1;
+        r1 -= U10[o] * xr0 + U11[o] * xr1;
+      }
+      double i00, i01, i11;
+      sym_inv(D00[o], D01[o], D11[o], i00, i01, i11);
+      C0[o] = i00 * r0 + i01 * r1;
+      C1[o] = i01 * r0 + i11 * r1;
+    }
+    __syncthreads();
+  }
+
+  const long long N = p.N;
+  for (int s = w; s < n; s += W) {
+    if (!active) continue;
+    cc[(2LL * s) * N + q] = p.h * C0[s];
+    cc[(2LL * s + 1) * N + q] = p.h * C1[s];
+  }
 }
 
 // Learned coarse correction of one mode: the network's direction d, scaled by the Galerkin
@@ -494,13 +668,42 @@ SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixe
   return p;
 }
 
+// Modes per CTA of the cyclic-reduction solve: the largest power of two up to 32 whose blocks
+// fit in 96 KB of shared memory (two CTAs per SM); 0 when one mode does not fit in 200 KB.
+int cr_modes_per_cta(int n_sub) {
+  const size_t per_mode = static_cast<size_t>(kCrFields) * n_sub * sizeof(double);
+  if (per_mode > 200 * 1024) return 0;
+  int mpc = 32;
+  while (mpc > 1 && mpc * per_mode > 96 * 1024) mpc /= 2;
+  return mpc;
+}
+
+bool use_cyclic(const kkt_handle* h, const SpecParams& p) {
+  if (p.learn_k > 0 || cr_modes_per_cta(p.n_sub) == 0) return false;
+  if (h->opt.coarse_solve == KKT_COARSE_SOLVE_CYCLIC) return true;
+  return h->opt.coarse_solve == KKT_COARSE_SOLVE_AUTO && p.N < kCyclicBelowModes;
+}
+
 template <typename TI>
 int launch_coarse(const kkt_handle* h, const SpecParams& p, const TI* rhat, double in_scale, cudaStream_t st) {
+  const double V = static_cast<double>(p.N) * p.Nt;
+  if (use_cyclic(h, p)) {
+    const int mpc = cr_modes_per_cta(p.n_sub);
+    const size_t smem = static_cast<size_t>(kCrFields) * p.n_sub * mpc * sizeof(double);
+    KKT_CUDA_TRY(cudaFuncSetAttribute(coarse_cr_kernel<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+    // restriction: 2 flops per node; reduction and substitution: ~90 flops per block (two 2 x 2
+    // inverses and the block products of both neighbours, then one back-substitution)
+    ProfScope ps(KKT_K_COARSE, st, 2.0 * V + 90.0 * p.n_sub * p.N, V * sizeof(TI) + 16.0 * p.n_sub * p.N);
+    const long long nb = (p.N + mpc - 1) / mpc;
+    coarse_cr_kernel<TI><<<static_cast<unsigned>(nb), kCrThreads, smem, st>>>(rhat, in_scale, p, mpc, h->coarse_c);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
   const int tb = 128;
   const long long nb = (p.N + tb - 1) / tb;
   // restriction: 2 flops per node; substitutions: ~26 flops per subdomain; reads the coefficients
   // once, the factors twice, writes and reads the eliminated right-hand sides
-  const double V = static_cast<double>(p.N) * p.Nt;
   ProfScope ps(KKT_K_COARSE, st, 2.0 * V + 26.0 * p.n_sub * p.N, V * sizeof(TI) + 12.0 * 8.0 * p.n_sub * p.N);
   coarse_solve_kernel<TI><<<static_cast<unsigned>(nb), tb, 0, st>>>(rhat, in_scale, p, h->coarse_c, h->coarse_w);
   KKT_CUDA_TRY(cudaGetLastError());

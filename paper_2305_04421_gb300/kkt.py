@@ -35,6 +35,7 @@ NORM = {"l2": 0, "euclidean": 1}
 ORTH = {"mgs": 0, "cgs2": 1, "mgs2": 2}
 BASIS = {"physical": 0, "spectral": 1}
 LOCAL = {"rasq": 0, "ras": 1}
+COARSE_SOLVE = {"auto": 0, "thomas": 1, "cyclic": 2}
 HISTORY_MAX = 1024
 
 
@@ -44,7 +45,7 @@ class KKTOptions(ctypes.Structure):
                 ("residual_norm", ctypes.c_int), ("tc_split", ctypes.c_int), ("orth", ctypes.c_int),
                 ("basis", ctypes.c_int), ("local", ctypes.c_int),
                 ("Lx", ctypes.c_double),
-                ("Ly", ctypes.c_double)]
+                ("Ly", ctypes.c_double), ("coarse_solve", ctypes.c_int)]
 
 
 class KKTInfo(ctypes.Structure):
@@ -435,19 +436,19 @@ class Solver:
     def __init__(self, nx, ny, Nt, T=1.0, nu=1.0, omega=1e-4, n_sub=1, *, precision="fp64",
                  coarse="exact", variant="multiplicative", pou="left", restart=30, jhat_sign=-1,
                  residual_norm="l2", tc_split=True, orth="mgs2", basis="physical", local="rasq", Lx=1.0,
-                 Ly=1.0):
+                 Ly=1.0, coarse_solve="auto"):
         self.h = kkt_create(nx, ny, Nt, T, nu, omega, n_sub)
         self.set_options(precision=precision, coarse=coarse, variant=variant, pou=pou, restart=restart,
                          jhat_sign=jhat_sign, residual_norm=residual_norm, tc_split=tc_split, orth=orth,
-                         basis=basis, local=local, Lx=Lx, Ly=Ly)
+                         basis=basis, local=local, Lx=Lx, Ly=Ly, coarse_solve=coarse_solve)
         self.info = kkt_get_info(self.h)
 
     def set_options(self, *, precision="fp64", coarse="exact", variant="multiplicative", pou="left",
                     restart=30, jhat_sign=-1, residual_norm="l2", tc_split=True, orth="mgs2", basis="physical",
-                    local="rasq", Lx=1.0, Ly=1.0):
+                    local="rasq", Lx=1.0, Ly=1.0, coarse_solve="auto"):
         opt = KKTOptions(PREC[precision], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
                          NORM[residual_norm], 1 if tc_split else 0, ORTH[orth], BASIS[basis], LOCAL[local],
-                         Lx, Ly)
+                         Lx, Ly, COARSE_SOLVE[coarse_solve])
         kkt_set_options(self.h, opt)
         self.info = kkt_get_info(self.h)
 
@@ -555,7 +556,8 @@ class Batch:
             else:
                 descs.append(KKTInstance(w.nx, w.ny, w.Nt, w.n_sub, w.T, w.nu, w.omega))
         opt = KKTOptions(PREC["fp64"], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
-                         NORM[residual_norm], 1, ORTH[orth], BASIS[basis], LOCAL["rasq"], Lx, Ly)
+                         NORM[residual_norm], 1, ORTH[orth], BASIS[basis], LOCAL["rasq"], Lx, Ly,
+                         COARSE_SOLVE["auto"])
         self.b = kkt_batch_create(descs, opt)
         self.infos = [kkt_batch_get_info(self.b, i) for i in range(len(descs))]
 

@@ -47,7 +47,7 @@ def test_status_strings_and_defaults(lib):
     assert (opt.precision, opt.coarse, opt.variant, opt.pou, opt.restart, opt.jhat_sign) == (0, 0, 0, 0, 30, -1)
     assert (opt.residual_norm, opt.tc_split, opt.orth, opt.basis, opt.local) == (
         kkt.NORM["l2"], 1, kkt.ORTH["mgs2"], kkt.BASIS["physical"], kkt.LOCAL["rasq"])
-    assert (opt.Lx, opt.Ly) == (1.0, 1.0)
+    assert (opt.Lx, opt.Ly, opt.coarse_solve) == (1.0, 1.0, kkt.COARSE_SOLVE["auto"])
 
 
 def test_options_struct_matches_the_header():
