@@ -601,11 +601,36 @@ def run_study(args):
     mesh = [{"mesh_points": nx + 1, "Nt": 400, "n_sub": 20, "omega": 1e-4,
              "one_level": iterations(nx, 400, 20, 1e-4, "none"), "two_level": iterations(nx, 400, 20, 1e-4, "exact")}
             for nx in (8, 16, 32)]
+    # the coarse solver on the paper's mesh (225 modes): block Thomas against the multilevel
+    # (cyclic-reduction) hierarchy, both exact; wall time per solve after one warm-up solve
+    def timed(Nt, n_sub, solver):
+        w = workloads.Workload("paper", nx=16, ny=16, Nt=Nt, n_sub=n_sub, Lx=1.0, Ly=2.0, omega=1e-4,
+                               target="paper", u0="paper")
+        s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, residual_norm="euclidean", Lx=1.0, Ly=2.0,
+                       coarse_solve=solver)
+        f = s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev),
+                        torch.from_numpy(workloads.make_u0(w).ravel()).to(dev))
+        s.solve(f, tol=1e-6, maxit=420)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = s.solve(f, tol=1e-6, maxit=420)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t) * 1e3
+        s.close()
+        return r.iterations, ms
+
+    coarse_solvers = []
+    for Nt in (400, 800, 1600, 3200):
+        nd = Nt // 5
+        it_t, ms_t = timed(Nt, nd, "thomas")
+        it_c, ms_c = timed(Nt, nd, "cyclic")
+        coarse_solvers.append({"Nt": Nt, "n_sub": nd, "iterations": [it_t, it_c], "thomas_ms": ms_t,
+                               "cyclic_ms": ms_c, "speedup": ms_t / ms_c})
     two = [r["two_level"] for r in fig1 + fig2 if r["two_level"] is not None]
     print(json.dumps({"study": "Section 4 replication (Eq 16 problem): one-level vs two-level FGMRES iterations",
                       "tol": 1e-6, "maxit": 420, "seconds": time.perf_counter() - t0,
                       "two_level_iterations_min_max": [min(two), max(two)],
-                      "fig1": fig1, "fig2": fig2, "mesh": mesh}))
+                      "fig1": fig1, "fig2": fig2, "mesh": mesh, "coarse_solvers": coarse_solvers}))
     return 0
 
 
@@ -680,18 +705,17 @@ def run_ours(args):
     value = job_value(world, args.steps, ms / 1e3)
     launches = sum(v["launches"] for k, v in prof.items() if k != "graph")   # kernels only
     applies = sum(r.iterations for r in results)
-    # end to end through the C ABI with host buffers: H2D of f and x0, D2H of x inside the timed region
+    # end to end through the C ABI with host buffers: the solve from x_0 = 0 (kkt_solve_zero_guess)
+    # uploads f and downloads x inside the timed region
     f_host = f.cpu().pin_memory()
     x_host = torch.zeros(f.numel(), dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
-    x_host.zero_()
-    solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT)   # warm-up: stages the host-buffer path once
+    solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT, zero_guess=True)   # warm-up: stages the host path once
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        x_host.zero_()
-        solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT)
+        solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT, zero_guess=True)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dev, world)
     nbytes = f.numel() * 8
@@ -715,7 +739,7 @@ def run_ours(args):
             "iterations": its, "converged": ok, "rel_residual": results[-1].rel_residual,
             "rel_residual_euclid": results[-1].rel_residual_euclid,
             "precond_applies_per_s": apply_stats["applies_per_s"], "precond_apply": apply_stats,
-            "e2e": {"value": job_value(world, e2e_steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": 2 * nbytes,
+            "e2e": {"value": job_value(world, e2e_steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                     "host_link_gbs": link,
                     "d2h_bytes_per_step": nbytes},
             "gpu_launches": launches,

@@ -238,6 +238,11 @@ int kkt_precond_apply(kkt_handle* h, const double* r, double* y, void* stream);
 int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit,
               kkt_stats* stats, void* stream);
 
+/* kkt_solve from the initial guess x_0 = 0: x is output only (its contents on entry are not
+ * read, and a host x is not uploaded). Otherwise identical, including the iterates. */
+int kkt_solve_zero_guess(kkt_handle* h, const double* f, double* x, double tol, int maxit,
+                         kkt_stats* stats, void* stream);
+
 /* ---- single steps of the path (device pointers, asynchronous) ------------------------- */
 
 /* out = Q in for every time slice: the orthonormal 2D DST-I along x then y (Q^2 = I), which

@@ -636,7 +636,20 @@ int kkt_multidot(kkt_handle* h, const double* V, long long stride, int count, co
   return krylov_multidot(h, V, stride, count, w, n, as_stream(stream), out);
 }
 
+static int solve_impl(kkt_handle* h, const double* f, double* x, double tol, int maxit, kkt_stats* stats,
+                      void* stream, bool zero_guess);
+
 int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, kkt_stats* stats, void* stream) {
+  return solve_impl(h, f, x, tol, maxit, stats, stream, false);
+}
+
+int kkt_solve_zero_guess(kkt_handle* h, const double* f, double* x, double tol, int maxit, kkt_stats* stats,
+                         void* stream) {
+  return solve_impl(h, f, x, tol, maxit, stats, stream, true);
+}
+
+static int solve_impl(kkt_handle* h, const double* f, double* x, double tol, int maxit, kkt_stats* stats,
+                      void* stream, bool zero_guess) {
   KKT_TRY(check_handle(h));
   if (!f || !x) return set_error(KKT_ERR_INVALID_ARG, "null pointer");
   if (!(tol > 0.0) || !std::isfinite(tol)) return set_error(KKT_ERR_INVALID_ARG, "tol must be positive");
@@ -657,8 +670,13 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   }
   if (!dev_x) {
     if (!h->kx) KKT_TRY(dev_alloc(h, &h->kx, n3));
-    KKT_CUDA_TRY(cudaMemcpyAsync(h->kx, x, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (zero_guess)   // x is output only: nothing to upload
+      KKT_CUDA_TRY(cudaMemsetAsync(h->kx, 0, n3 * sizeof(double), st));
+    else
+      KKT_CUDA_TRY(cudaMemcpyAsync(h->kx, x, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
     dx = h->kx;
+  } else if (zero_guess) {
+    KKT_CUDA_TRY(cudaMemsetAsync(x, 0, n3 * sizeof(double), st));
   }
   // physical-space f and x on the device; in the spectral basis the iteration runs on their
   // sine-mode coefficients (every block through the orthonormal 2D DST-I, which is its own

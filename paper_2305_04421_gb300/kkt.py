@@ -127,6 +127,7 @@ SIGNATURES = [
     ("kkt_matvec", _I, [_P, _P, _P, _P]),
     ("kkt_precond_apply", _I, [_P, _P, _P, _P]),
     ("kkt_solve", _I, [_P, _P, _P, _D, _I, ctypes.POINTER(KKTStats), _P]),
+    ("kkt_solve_zero_guess", _I, [_P, _P, _P, _D, _I, ctypes.POINTER(KKTStats), _P]),
     ("kkt_dst2d", _I, [_P, _P, _P, _P]),
     ("kkt_schur_apply", _I, [_P, _P, _P, _P]),
     ("kkt_schur_precond_apply", _I, [_P, _P, _P, _P]),
@@ -247,6 +248,12 @@ def kkt_precond_apply(h, r, y, stream=None) -> int:
 def kkt_solve(h, f, x, tol, maxit, stats: KKTStats | None = None, stream=None) -> int:
     st = stats if stats is not None else KKTStats()
     return _check(load_library().kkt_solve(h, _ptr(f), _ptr(x), tol, maxit, ctypes.byref(st), _stream(stream)))
+
+
+def kkt_solve_zero_guess(h, f, x, tol, maxit, stats: KKTStats | None = None, stream=None) -> int:
+    st = stats if stats is not None else KKTStats()
+    return _check(load_library().kkt_solve_zero_guess(h, _ptr(f), _ptr(x), tol, maxit, ctypes.byref(st),
+                                                      _stream(stream)))
 
 
 def kkt_dst2d(h, x, y, stream=None) -> int:
@@ -516,11 +523,14 @@ class Solver:
         _check(load_library().kkt_learned_stats(self.h, ctypes.byref(kept), ctypes.byref(fb), 1 if reset else 0))
         return kept.value, fb.value
 
-    def solve(self, f, x=None, tol=1e-8, maxit=420, stream=None) -> SolveResult:
+    def solve(self, f, x=None, tol=1e-8, maxit=420, stream=None, zero_guess=False) -> SolveResult:
+        """x: the initial guess, overwritten by the solution (zeros when None). zero_guess=True
+        starts from 0 whatever x holds and never reads it (a host x is not uploaded)."""
         if x is None:
-            x = torch.zeros_like(f)
+            x = torch.empty_like(f)
+            zero_guess = True
         st = KKTStats()
-        status = kkt_solve(self.h, f, x, tol, maxit, st, stream)
+        status = (kkt_solve_zero_guess if zero_guess else kkt_solve)(self.h, f, x, tol, maxit, st, stream)
         return SolveResult(x, status, st.iterations, st.restarts, st.rel_residual, st.rel_residual_euclid, st.time_ms,
                            list(st.history[: st.history_len]))
 

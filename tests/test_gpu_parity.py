@@ -320,6 +320,21 @@ def test_solve_with_host_buffers_and_initial_guess(kkt):
     assert res2.status == kkt.KKT_OK and res2.iterations == 0
 
 
+def test_zero_guess_solve_ignores_the_contents_of_x(kkt):
+    """kkt_solve_zero_guess starts from 0 whatever x holds (NaN here), for host and device x,
+    and takes the same steps as kkt_solve from a zeroed x."""
+    w = workloads.Workload("t", nx=16, ny=16, Nt=24, n_sub=3, omega=1e-3, seed=5)
+    p = HeatKKT(nx=16, ny=16, Nt=24, omega=1e-3)
+    f = problem.assemble_rhs(p, workloads.make_target(w), None)
+    s = kkt.Solver(16, 16, 24, 1.0, 1.0, 1e-3, 3)
+    ref = s.solve(dev(f), dev(np.zeros(3 * p.V)), tol=1e-10, maxit=300)
+    for x in (torch.full((3 * p.V,), float("nan"), dtype=torch.float64),
+              torch.full((3 * p.V,), float("nan"), dtype=torch.float64, device="cuda")):
+        res = s.solve(dev(f) if x.is_cuda else torch.from_numpy(f), x, tol=1e-10, maxit=300, zero_guess=True)
+        assert res.status == kkt.KKT_OK and res.iterations == ref.iterations
+        assert np.array_equal(host(x) if x.is_cuda else x.numpy(), host(ref.x))
+
+
 def test_full_size_preconditioner_on_sampled_modes(kkt):
     """256 x 256, Nt = 1024, N_D = 64 (the benchmark size): an input living on a few sine modes
     is mapped mode by mode; each mode's time series must equal the scalar oracle's."""
