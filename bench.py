@@ -635,23 +635,33 @@ def run_study(args):
 
 
 def run_profile_case(args):
-    """A small solve for counter captures: 256 x 256, Nt = 96, N_D = 8 (a KKT vector of 150 MB,
-    above the 126 MB L2), FGMRES(10) to 1e-8, two solves. Prints the iteration count."""
+    """A small solve for counter captures, two solves; prints the iteration count. 'grid':
+    256 x 256, Nt = 96, N_D = 8 (a KKT vector of 150 MB, above the 126 MB L2), FGMRES(10) to
+    1e-8. 'paper': Section 4's mesh with Nt = 3200 and 640 subdomains, FGMRES(30) to 1e-6."""
     import torch
 
     import paper_2305_04421_gb300.kkt as kkt
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    w = workloads.Workload("profile", nx=256, ny=256, Nt=96, n_sub=8, target="sine-series", seed=1)
-    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, restart=10, basis=args.basis,
-                   precision=args.precision)
-    f = s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev))
+    if args.profile_case == "paper":
+        # the Eq 16 problem on the 17 x 17 mesh, 5 steps per subdomain: 225 modes, so the coarse
+        # solve runs the multilevel (cyclic-reduction) kernel
+        w = workloads.Workload("profile-paper", nx=16, ny=16, Nt=3200, n_sub=640, Lx=1.0, Ly=2.0, omega=1e-4,
+                               target="paper", u0="paper")
+        s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, residual_norm="euclidean", Lx=1.0, Ly=2.0)
+        f = s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev),
+                        torch.from_numpy(workloads.make_u0(w).ravel()).to(dev))
+        tol, name = 1e-6, "Eq 16 problem 16x16 intervals Nt=3200 N_D=640 restart=30 fp64"
+    else:
+        w = workloads.Workload("profile", nx=256, ny=256, Nt=96, n_sub=8, target="sine-series", seed=1)
+        s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, restart=10, basis=args.basis,
+                       precision=args.precision)
+        f = s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev))
+        tol, name = 1e-8, f"256x256 Nt=96 N_D=8 restart=10 {args.precision} {args.basis}"
     for _ in range(2):
-        r = s.solve(f, tol=1e-8, maxit=200)
-    print(json.dumps({"profile_case": f"256x256 Nt=96 N_D=8 restart=10 {args.precision} {args.basis}",
-                      "iterations": r.iterations,
-                      "status": r.status}))
+        r = s.solve(f, tol=tol, maxit=200)
+    print(json.dumps({"profile_case": name, "iterations": r.iterations, "status": r.status}))
     return 0 if r.status == kkt.KKT_OK else 1
 
 
@@ -778,8 +788,9 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=25,
                     help="iterations the reference arm scales its per-iteration sample by")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", action="store_true",
-                    help="run only a small solve (256 x 256, Nt = 96) for counter captures")
+    ap.add_argument("--profile-case", nargs="?", const="grid", choices=["grid", "paper"], default=None,
+                    help="run only a small solve for counter captures: 'grid' (default) 256 x 256, Nt = 96; "
+                         "'paper' the Section 4 mesh (17 x 17 points) with Nt = 3200, 640 subdomains")
     ap.add_argument("--basis", choices=["physical", "spectral"], default="physical",
                     help="FGMRES basis of --profile-case")
     ap.add_argument("--precision", choices=["fp64", "bf16", "tf32"], default="fp64",

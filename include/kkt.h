@@ -120,7 +120,7 @@ enum kkt_basis {
  * block tridiagonal in time: N_D blocks of 2 x 2, symmetric positive definite. Both solvers
  * are exact; they differ in how the work is spread over the GPU. */
 enum kkt_coarse_solve {
-  /* cyclic reduction when the modes alone leave the GPU idle (fewer than 16384 spatial modes)
+  /* cyclic reduction when the modes alone leave the GPU idle (fewer than 12288 spatial modes)
    * and one mode's system fits in shared memory, block Thomas otherwise */
   KKT_COARSE_SOLVE_AUTO = 0,
   /* block Thomas elimination, one thread per mode: R_0 r summed node by node, then N_D
