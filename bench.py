@@ -369,14 +369,15 @@ def measure_forms(kkt_mod, dev, steps: int, warmup: int) -> dict:
 def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, steps: int, warmup: int) -> dict:
     """The headline workload's solve in the other configurations: the spectral basis (f and x
     transformed once, no transforms inside the iteration), one-pass MGS and CGS2 (the paired-MGS
-    default's alternatives), and RAS local solves (Eq 9, an ablation). Same tolerance,
-    x_0 = 0, device time per solve."""
+    default's alternatives), RAS local solves (Eq 9, an ablation), and the multilevel
+    (cyclic-reduction) coarse solve in place of block Thomas. Same tolerance, x_0 = 0, device
+    time per solve."""
     import torch
 
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
     out = {}
     for name, opts in (("spectral_basis", {"basis": "spectral"}), ("mgs", {"orth": "mgs"}), ("cgs2", {"orth": "cgs2"}),
-                       ("ras_local_solves", {"local": "ras"})):
+                       ("ras_local_solves", {"local": "ras"}), ("coarse_cyclic", {"coarse_solve": "cyclic"})):
         s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, **opts)
         f = s.build_rhs(ut)
         ms, res, x = time_solves(kkt_mod, s, f, steps, warmup)

@@ -218,19 +218,20 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
 //   D_j <- D_j - U_o1^T D_o1^-1 U_o1 - U_j D_o2^-1 U_j^T
 //   c_j <- c_j - U_o1^T D_o1^-1 c_o1 - U_j D_o2^-1 c_o2
 //   U_j <- -U_j D_o2^-1 U_o2             (its coupling to the next even block)
-// and the old U_j is kept as o2's left coupling. After ceil(log2 N_D) levels block 0 is
-// alone; the way back solves, level by level, x_o = D_o^-1 (c_o - L_o^T x_left - U_o x_right)
-// with the values the block had when it was eliminated. c' = h x as in block Thomas.
+// and the old U_j is kept as o2's left coupling. Each odd block's D is inverted once, in
+// place, before its neighbours use it. After ceil(log2 N_D) levels block 0 is alone; the way
+// back solves, level by level, x_o = D_o^-1 (c_o - L_o^T x_left - U_o x_right) with the values
+// the block had when it was eliminated. c' = h x as in block Thomas.
 //
-// A CTA holds `mpc` modes in shared memory, 13 doubles per block and mode: D (3), U (4),
-// L (4), c (2, overwritten by x). Thread t serves mode t % mpc (consecutive threads read
+// A CTA holds `mpc` modes in shared memory, 13 doubles per block and mode: D (3, D^-1 once
+// the block is eliminated), U (4), L (4), c (2, overwritten by x). Thread t serves mode t % mpc (consecutive threads read
 // consecutive modes) and, with the other blockDim.x / mpc threads of that mode, strides over
 // its subdomains and eliminations. Threads past the last mode only join the barriers.
 constexpr int kCrThreads = 256;
 constexpr int kCrFields = 13;
 // AUTO picks cyclic reduction below this many spatial modes (per mode, Thomas is one thread).
-// Measured crossover on GB300: cyclic ahead by 2 % at 9025 modes (N_D = 64), Thomas ahead by 9 %
-// at 16129 modes with N_D = 410 and by 7 % at 65025 modes.
+// Measured crossover on GB300: cyclic ahead by 3 % at 9025 modes (N_D = 64), Thomas ahead by 5 %
+// at 16129 modes with N_D = 410 and by 6 % at 65025 modes.
 constexpr long long kCyclicBelowModes = 12288;
 
 __device__ __forceinline__ void sym_inv(double d00, double d01, double d11, double& i00, double& i01, double& i11) {
@@ -283,14 +284,25 @@ __global__ void __launch_bounds__(kCrThreads) coarse_cr_kernel(const TI* __restr
   int top = 1;   // first stride at which one block is left
   for (int st = 1; st < n; st *= 2) {
     const int cnt = (n + st - 1) / st;   // blocks of this level
+    // the blocks eliminated at this level replace D by D^-1 (used by both neighbours and on
+    // the way back)
+    for (int e = w; 2 * e + 1 < cnt; e += W) {
+      if (!active) continue;
+      const int o = (2 * e + 1) * st;
+      double i00, i01, i11;
+      sym_inv(D00[o], D01[o], D11[o], i00, i01, i11);
+      D00[o] = i00;
+      D01[o] = i01;
+      D11[o] = i11;
+    }
+    __syncthreads();
     for (int e = w; 2 * e < cnt; e += W) {
       if (!active) continue;
       const int k = 2 * e, j = k * st;
       double d00 = D00[j], d01 = D01[j], d11 = D11[j], c0 = C0[j], c1 = C1[j];
       if (k >= 1) {   // left neighbour o1: D_j -= U^T D_o1^-1 U, c_j -= U^T D_o1^-1 c_o1 (U = U_o1)
         const int o = j - st;
-        double i00, i01, i11;
-        sym_inv(D00[o], D01[o], D11[o], i00, i01, i11);
+        const double i00 = D00[o], i01 = D01[o], i11 = D11[o];
         const double u00 = U00[o], u01 = U01[o], u10 = U10[o], u11 = U11[o];
         const double x00 = i00 * u00 + i01 * u10, x01 = i00 * u01 + i01 * u11;   // X = D^-1 U
         const double x10 = i01 * u00 + i11 * u10, x11 = i01 * u01 + i11 * u11;
@@ -303,8 +315,7 @@ __global__ void __launch_bounds__(kCrThreads) coarse_cr_kernel(const TI* __restr
       }
       if (k + 1 < cnt) {   // right neighbour o2: Y = U_j D_o2^-1
         const int o = j + st;
-        double i00, i01, i11;
-        sym_inv(D00[o], D01[o], D11[o], i00, i01, i11);
+        const double i00 = D00[o], i01 = D01[o], i11 = D11[o];
         const double u00 = U00[j], u01 = U01[j], u10 = U10[j], u11 = U11[j];
         L00[o] = u00;
         L01[o] = u01;
@@ -356,8 +367,7 @@ __global__ void __launch_bounds__(kCrThreads) coarse_cr_kernel(const TI* __restr
         r0 -= U00[o] * xr0 + U01[o] * xr1;
         r1 -= U10[o] * xr0 + U11[o] * xr1;
       }
-      double i00, i01, i11;
-      sym_inv(D00[o], D01[o], D11[o], i00, i01, i11);
+      const double i00 = D00[o], i01 = D01[o], i11 = D11[o];   // D_o^-1, stored at its level
       C0[o] = i00 * r0 + i01 * r1;
       C1[o] = i01 * r0 + i11 * r1;
     }
@@ -694,9 +704,9 @@ int launch_coarse(const kkt_handle* h, const SpecParams& p, const TI* rhat, doub
     const size_t smem = static_cast<size_t>(kCrFields) * p.n_sub * mpc * sizeof(double);
     KKT_CUDA_TRY(cudaFuncSetAttribute(coarse_cr_kernel<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem)));
-    // restriction: 2 flops per node; reduction and substitution: ~90 flops per block (two 2 x 2
-    // inverses and the block products of both neighbours, then one back-substitution)
-    ProfScope ps(KKT_K_COARSE, st, 2.0 * V + 90.0 * p.n_sub * p.N, V * sizeof(TI) + 16.0 * p.n_sub * p.N);
+    // restriction: 2 flops per node; reduction and substitution: ~80 flops per block (one 2 x 2
+    // inverse, the block products with both neighbours, one back-substitution)
+    ProfScope ps(KKT_K_COARSE, st, 2.0 * V + 80.0 * p.n_sub * p.N, V * sizeof(TI) + 16.0 * p.n_sub * p.N);
     const long long nb = (p.N + mpc - 1) / mpc;
     coarse_cr_kernel<TI><<<static_cast<unsigned>(nb), kCrThreads, smem, st>>>(rhat, in_scale, p, mpc, h->coarse_c);
     KKT_CUDA_TRY(cudaGetLastError());
