@@ -604,7 +604,7 @@ def run_study(args):
             for nx in (8, 16, 32)]
     # the coarse solver on the paper's mesh (225 modes): block Thomas against the multilevel
     # (cyclic-reduction) hierarchy, both exact; wall time per solve after one warm-up solve
-    def timed(Nt, n_sub, solver):
+    def timed(Nt, n_sub, solver, breakdown=False):
         w = workloads.Workload("paper", nx=16, ny=16, Nt=Nt, n_sub=n_sub, Lx=1.0, Ly=2.0, omega=1e-4,
                                target="paper", u0="paper")
         s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, residual_norm="euclidean", Lx=1.0, Ly=2.0,
@@ -617,16 +617,30 @@ def run_study(args):
         r = s.solve(f, tol=1e-6, maxit=420)
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t) * 1e3
+        kern = None
+        if breakdown:   # device time per kernel class over one more solve (events around each launch)
+            kkt.kkt_profile_read(reset=True)
+            kkt.kkt_profile_enable(True)
+            s.solve(f, tol=1e-6, maxit=420)
+            torch.cuda.synchronize()
+            kkt.kkt_profile_enable(False)
+            kern = {k: {"ms": round(v["ms"], 3), "launches": v["launches"]}
+                    for k, v in kkt.kkt_profile_read(reset=True).items() if v["launches"]}
         s.close()
-        return r.iterations, ms
+        return r.iterations, ms, kern
 
+    # wall time per solve on the paper's mesh, m = 5 (N_D = Nt / 5): the time-parallel weak scaling
+    # on one GPU, with the sequential (Thomas) and the multilevel (cyclic) coarse solve
     coarse_solvers = []
-    for Nt in (400, 800, 1600, 3200):
+    for Nt in (100, 200, 400, 800, 1600, 3200):
         nd = Nt // 5
-        it_t, ms_t = timed(Nt, nd, "thomas")
-        it_c, ms_c = timed(Nt, nd, "cyclic")
-        coarse_solvers.append({"Nt": Nt, "n_sub": nd, "iterations": [it_t, it_c], "thomas_ms": ms_t,
-                               "cyclic_ms": ms_c, "speedup": ms_t / ms_c})
+        it_t, ms_t, _ = timed(Nt, nd, "thomas")
+        it_c, ms_c, kern = timed(Nt, nd, "cyclic", breakdown=Nt == 3200)
+        row = {"Nt": Nt, "n_sub": nd, "iterations": [it_t, it_c], "thomas_ms": ms_t, "cyclic_ms": ms_c,
+               "cyclic_ms_per_iteration": ms_c / max(it_c, 1), "speedup": ms_t / ms_c}
+        if kern:
+            row["cyclic_kernel_ms"] = kern
+        coarse_solvers.append(row)
     two = [r["two_level"] for r in fig1 + fig2 if r["two_level"] is not None]
     print(json.dumps({"study": "Section 4 replication (Eq 16 problem): one-level vs two-level FGMRES iterations",
                       "tol": 1e-6, "maxit": 420, "seconds": time.perf_counter() - t0,
@@ -722,13 +736,22 @@ def run_ours(args):
     x_host = torch.zeros(f.numel(), dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 3))
     solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT, zero_guess=True)   # warm-up: stages the host path once
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT, zero_guess=True)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0, dev, world)
+
+    def e2e_seconds():
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            solver.solve(f_host, x_host, tol=TOL, maxit=MAXIT, zero_guess=True)
+        torch.cuda.synchronize()
+        return max_over_ranks(time.perf_counter() - t0, dev, world)
+
+    # the pinned buffers move by the library's copy kernel (default staging); for context the
+    # same steps with the copy engine (cudaMemcpyAsync)
+    e2e_s = e2e_seconds()
+    solver.set_staging("copy_engine")
+    e2e_ce_s = e2e_seconds()
+    solver.set_staging("auto")
     nbytes = f.numel() * 8
     # the host link's own bandwidth on this machine (context for e2e): one pinned H2D and D2H copy
     link = {}
@@ -751,8 +774,8 @@ def run_ours(args):
             "rel_residual_euclid": results[-1].rel_residual_euclid,
             "precond_applies_per_s": apply_stats["applies_per_s"], "precond_apply": apply_stats,
             "e2e": {"value": job_value(world, e2e_steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
-                    "host_link_gbs": link,
-                    "d2h_bytes_per_step": nbytes},
+                    "d2h_bytes_per_step": nbytes, "staging": "copy kernel through the pinned buffers' device mapping",
+                    "value_copy_engine": job_value(world, e2e_steps, e2e_ce_s), "host_link_gbs": link},
             "gpu_launches": launches,
             "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "kernel_launches": {k: v["launches"] for k, v in prof.items()},

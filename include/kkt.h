@@ -238,6 +238,17 @@ int kkt_precond_apply(kkt_handle* h, const double* r, double* y, void* stream);
 int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit,
               kkt_stats* stats, void* stream);
 
+/* How kkt_solve moves host vectors (f in, x in and out) to and from the device. */
+enum kkt_staging {
+  /* pinned (page-locked) host buffers are read and written by a copy kernel through their
+   * device mapping: on a coherent CPU-GPU link the SMs reach a higher rate than the copy
+   * engine; pageable buffers go through cudaMemcpyAsync. The default. */
+  KKT_STAGING_AUTO = 0,
+  /* every host buffer through cudaMemcpyAsync (the copy engine) */
+  KKT_STAGING_COPY_ENGINE = 1
+};
+int kkt_set_staging(kkt_handle* h, int mode);
+
 /* kkt_solve from the initial guess x_0 = 0: x is output only (its contents on entry are not
  * read, and a host x is not uploaded). Otherwise identical, including the iterates. */
 int kkt_solve_zero_guess(kkt_handle* h, const double* f, double* x, double tol, int maxit,

@@ -240,6 +240,61 @@ bool is_device_ptr(const void* p) {
 
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 
+// Device-side address of a pinned (mapped) host buffer; nullptr for any other memory.
+const void* mapped_host(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+// dst[0..n) = src[0..n) with the SMs, one side being mapped host memory: 16-byte accesses when
+// both are 16-byte aligned, four independent loads per thread in flight to cover the link's
+// latency; every element is copied by exactly one thread.
+__global__ void link_copy_kernel(const double* __restrict__ src, double* __restrict__ dst, long long n) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const long long stride = static_cast<long long>(gridDim.x) * blockDim.x;
+  const bool vec = ((reinterpret_cast<unsigned long long>(src) | reinterpret_cast<unsigned long long>(dst)) & 15) == 0;
+  if (vec) {
+    const double2* s2 = reinterpret_cast<const double2*>(src);
+    double2* d2 = reinterpret_cast<double2*>(dst);
+    const long long n2 = n / 2;
+    long long i = t;
+    for (; i + 3 * stride < n2; i += 4 * stride) {
+      const double2 a = s2[i], b = s2[i + stride], c = s2[i + 2 * stride], d = s2[i + 3 * stride];
+      d2[i] = a;
+      d2[i + stride] = b;
+      d2[i + 2 * stride] = c;
+      d2[i + 3 * stride] = d;
+    }
+    for (; i < n2; i += stride) d2[i] = s2[i];
+    if (t == 0 && (n & 1)) dst[n - 1] = src[n - 1];
+  } else {
+    for (long long i = t; i < n; i += stride) dst[i] = src[i];
+  }
+}
+
+// Host <-> device copy of n doubles for kkt_solve's staging (one side is device memory).
+int stage_copy(const kkt_handle* h, double* dst, const double* src, long long n, cudaMemcpyKind kind,
+               cudaStream_t st) {
+  const void* mapped = nullptr;
+  if (h->staging == KKT_STAGING_AUTO)
+    mapped = mapped_host(kind == cudaMemcpyHostToDevice ? static_cast<const void*>(src) : static_cast<const void*>(dst));
+  if (!mapped) {
+    KKT_CUDA_TRY(cudaMemcpyAsync(dst, src, n * sizeof(double), kind, st));
+    return KKT_OK;
+  }
+  const double* s = kind == cudaMemcpyHostToDevice ? static_cast<const double*>(mapped) : src;
+  double* d = kind == cudaMemcpyHostToDevice ? dst : static_cast<double*>(const_cast<void*>(mapped));
+  int sms = 0;
+  KKT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+  link_copy_kernel<<<static_cast<unsigned>(sms * 8), 256, 0, st>>>(s, d, n);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
 int check_handle(const kkt_handle* h) {
   if (!h) return set_error(KKT_ERR_INVALID_ARG, "null handle");
   return KKT_OK;
@@ -643,6 +698,14 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   return solve_impl(h, f, x, tol, maxit, stats, stream, false);
 }
 
+int kkt_set_staging(kkt_handle* h, int mode) {
+  KKT_TRY(check_handle(h));
+  if (mode != KKT_STAGING_AUTO && mode != KKT_STAGING_COPY_ENGINE)
+    return set_error(KKT_ERR_INVALID_ARG, "staging mode out of range");
+  h->staging = mode;
+  return KKT_OK;
+}
+
 int kkt_solve_zero_guess(kkt_handle* h, const double* f, double* x, double tol, int maxit, kkt_stats* stats,
                          void* stream) {
   return solve_impl(h, f, x, tol, maxit, stats, stream, true);
@@ -665,7 +728,7 @@ static int solve_impl(kkt_handle* h, const double* f, double* x, double tol, int
   double* dx = x;
   if (!dev_f) {
     if (!h->kf) KKT_TRY(dev_alloc(h, &h->kf, n3));
-    KKT_CUDA_TRY(cudaMemcpyAsync(h->kf, f, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    KKT_TRY(stage_copy(h, h->kf, f, n3, cudaMemcpyHostToDevice, st));
     df = h->kf;
   }
   if (!dev_x) {
@@ -673,7 +736,7 @@ static int solve_impl(kkt_handle* h, const double* f, double* x, double tol, int
     if (zero_guess)   // x is output only: nothing to upload
       KKT_CUDA_TRY(cudaMemsetAsync(h->kx, 0, n3 * sizeof(double), st));
     else
-      KKT_CUDA_TRY(cudaMemcpyAsync(h->kx, x, n3 * sizeof(double), cudaMemcpyHostToDevice, st));
+      KKT_TRY(stage_copy(h, h->kx, x, n3, cudaMemcpyHostToDevice, st));
     dx = h->kx;
   } else if (zero_guess) {
     KKT_CUDA_TRY(cudaMemsetAsync(x, 0, n3 * sizeof(double), st));
@@ -720,7 +783,7 @@ static int solve_impl(kkt_handle* h, const double* f, double* x, double tol, int
       local.rel_residual_euclid = euclid_residual();
     if (status >= 0 && h->opt.precision != KKT_PREC_FP64 && tc_check(h->tc, st) < 0) status = KKT_ERR_TIMEOUT;
     if (!dev_x) {
-      cudaMemcpyAsync(x, px, n3 * sizeof(double), cudaMemcpyDeviceToHost, st);
+      if (stage_copy(h, x, px, n3, cudaMemcpyDeviceToHost, st) < 0 && status >= 0) status = KKT_ERR_CUDA;
       cudaStreamSynchronize(st);
     }
     local.status = status;

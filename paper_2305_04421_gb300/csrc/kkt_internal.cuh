@@ -102,6 +102,7 @@ struct kkt_handle {
   kkt::Geometry g;
   kkt_options opt;
   int device = 0;
+  int staging = KKT_STAGING_AUTO;   // how kkt_solve moves host vectors (enum kkt_staging)
   kkt::DstPlan dst_x, dst_y;
   kkt::TimeDecomp td;
   kkt::DeviceDecomp dd;

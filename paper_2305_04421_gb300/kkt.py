@@ -36,6 +36,7 @@ ORTH = {"mgs": 0, "cgs2": 1, "mgs2": 2}
 BASIS = {"physical": 0, "spectral": 1}
 LOCAL = {"rasq": 0, "ras": 1}
 COARSE_SOLVE = {"auto": 0, "thomas": 1, "cyclic": 2}
+STAGING = {"auto": 0, "copy_engine": 1}
 HISTORY_MAX = 1024
 
 
@@ -128,6 +129,7 @@ SIGNATURES = [
     ("kkt_precond_apply", _I, [_P, _P, _P, _P]),
     ("kkt_solve", _I, [_P, _P, _P, _D, _I, ctypes.POINTER(KKTStats), _P]),
     ("kkt_solve_zero_guess", _I, [_P, _P, _P, _D, _I, ctypes.POINTER(KKTStats), _P]),
+    ("kkt_set_staging", _I, [_P, _I]),
     ("kkt_dst2d", _I, [_P, _P, _P, _P]),
     ("kkt_schur_apply", _I, [_P, _P, _P, _P]),
     ("kkt_schur_precond_apply", _I, [_P, _P, _P, _P]),
@@ -254,6 +256,10 @@ def kkt_solve_zero_guess(h, f, x, tol, maxit, stats: KKTStats | None = None, str
     st = stats if stats is not None else KKTStats()
     return _check(load_library().kkt_solve_zero_guess(h, _ptr(f), _ptr(x), tol, maxit, ctypes.byref(st),
                                                       _stream(stream)))
+
+
+def kkt_set_staging(h, mode: int) -> int:
+    return _check(load_library().kkt_set_staging(h, mode))
 
 
 def kkt_dst2d(h, x, y, stream=None) -> int:
@@ -458,6 +464,11 @@ class Solver:
                          Lx, Ly, COARSE_SOLVE[coarse_solve])
         kkt_set_options(self.h, opt)
         self.info = kkt_get_info(self.h)
+
+    def set_staging(self, mode="auto"):
+        """How solve() moves host vectors: 'auto' (pinned buffers by a copy kernel, pageable by
+        cudaMemcpyAsync) or 'copy_engine' (always cudaMemcpyAsync)."""
+        kkt_set_staging(self.h, STAGING[mode])
 
     def close(self):
         if getattr(self, "h", None):

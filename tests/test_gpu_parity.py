@@ -320,6 +320,36 @@ def test_solve_with_host_buffers_and_initial_guess(kkt):
     assert res2.status == kkt.KKT_OK and res2.iterations == 0
 
 
+def test_host_staging_modes_give_identical_solves(kkt):
+    """Host vectors reach the device by the copy kernel (pinned buffers, 16-byte aligned or
+    not) or by cudaMemcpyAsync (pageable buffers, or the copy-engine mode): the solve and the
+    returned x are bit-identical to a device-memory solve. 3V is odd here (15 x 15 x 3 points),
+    so the vector copy has a scalar tail."""
+    w = workloads.Workload("t", nx=16, ny=16, Nt=3, n_sub=1, omega=1e-3, seed=6)
+    p = HeatKKT(nx=16, ny=16, Nt=3, omega=1e-3)
+    f = problem.assemble_rhs(p, workloads.make_target(w), None)
+    n = 3 * p.V
+    assert n % 2 == 1
+    x0 = workloads.random_vector(n, 9) * 1e-3
+    s = kkt.Solver(16, 16, 3, 1.0, 1.0, 1e-3, 1)
+    ref = s.solve(dev(f), dev(x0), tol=1e-10, maxit=100)
+    big_f = torch.zeros(n + 1, dtype=torch.float64).pin_memory()
+    big_x = torch.zeros(n + 1, dtype=torch.float64).pin_memory()
+    layouts = {"pinned": (torch.from_numpy(f).pin_memory(), lambda: torch.from_numpy(x0.copy()).pin_memory()),
+               "pinned+8B": (big_f[1:].copy_(torch.from_numpy(f)), lambda: big_x[1:].copy_(torch.from_numpy(x0))),
+               "pageable": (torch.from_numpy(f.copy()), lambda: torch.from_numpy(x0.copy()))}
+    for mode in ("auto", "copy_engine"):
+        s.set_staging(mode)
+        for name, (fh, make_x) in layouts.items():
+            xh = make_x()
+            res = s.solve(fh, xh, tol=1e-10, maxit=100)
+            assert res.status == kkt.KKT_OK and res.iterations == ref.iterations, (mode, name)
+            assert np.array_equal(xh.numpy(), host(ref.x)), (mode, name)
+    with pytest.raises(kkt.KKTError):
+        kkt.kkt_set_staging(s.h, 2)
+    s.close()
+
+
 def test_zero_guess_solve_ignores_the_contents_of_x(kkt):
     """kkt_solve_zero_guess starts from 0 whatever x holds (NaN here), for host and device x,
     and takes the same steps as kkt_solve from a zeroed x."""
