@@ -249,6 +249,20 @@ enum kkt_staging {
 };
 int kkt_set_staging(kkt_handle* h, int mode);
 
+/* How the FP64 sine transforms are computed (kkt_dst2d and every FP64 preconditioner apply). */
+enum kkt_dst_method {
+  /* chosen per direction at kkt_create by timing the candidates (the default) */
+  KKT_DST_AUTO = 0,
+  /* tiles of lines in shared memory, one warp per line: the half-length FFT when the number
+   * of intervals is a power of two (>= 4), else the direct sum over the line */
+  KKT_DST_TILES = 1,
+  /* one thread per line, the direct sum: lines of at most 31 points (n <= 32) */
+  KKT_DST_LANE = 2
+};
+/* Re-selects the method (KKT_DST_AUTO re-runs the timing). KKT_ERR_UNSUPPORTED for
+ * KKT_DST_LANE when a direction has more than 31 points. */
+int kkt_set_dst_method(kkt_handle* h, int method);
+
 /* kkt_solve from the initial guess x_0 = 0: x is output only (its contents on entry are not
  * read, and a host x is not uploaded). Otherwise identical, including the iterates. */
 int kkt_solve_zero_guess(kkt_handle* h, const double* f, double* x, double tol, int maxit,

@@ -698,6 +698,12 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
   return solve_impl(h, f, x, tol, maxit, stats, stream, false);
 }
 
+int kkt_set_dst_method(kkt_handle* h, int method) {
+  KKT_TRY(check_handle(h));
+  if (method < KKT_DST_AUTO || method > KKT_DST_LANE) return set_error(KKT_ERR_INVALID_ARG, "dst method out of range");
+  return dst_set_method(h, method);
+}
+
 int kkt_set_staging(kkt_handle* h, int mode) {
   KKT_TRY(check_handle(h));
   if (mode != KKT_STAGING_AUTO && mode != KKT_STAGING_COPY_ENGINE)

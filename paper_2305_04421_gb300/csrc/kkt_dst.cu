@@ -206,6 +206,48 @@ __device__ void dst_tile_body(const DstLaunch& L, long long bid, double* smem) {
   }
 }
 
+// Short lines (at most kLaneMaxM points, n <= 32): one thread transforms one whole line by
+// the direct sum S_k = sum_j x_j sin(pi j k / n) (M FMAs per output, the same order as
+// dst_line_direct), its inputs held in registers. A warp's 32 lines keep every lane busy, where
+// the warp-per-line FFT of an 8- or 16-point half-length transform leaves most lanes idle. The
+// sine table index is the same on every lane (a broadcast load). Lines are read and written in
+// place of the tile staging: rows mode line t starts at t M (stride 1), columns mode line
+// (slice, c) at slice * slice_size + c (stride cols). A thread writes only its own line, after
+// reading all of it, so in == out is allowed.
+constexpr int kLaneMaxM = 31;
+
+__global__ void __launch_bounds__(kThreads) dst_lane_kernel(DstLaunch L, long long lines) {
+  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= lines) return;
+  long long base;
+  long long stride;
+  if (L.mode == 0) {
+    base = t * L.M;
+    stride = 1;
+  } else {
+    const long long sl = t / L.cols;
+    base = sl * L.slice + (t - sl * L.cols);
+    stride = L.cols;
+  }
+  const int M = L.M, n2 = 2 * L.n;
+  double x[kLaneMaxM];
+#pragma unroll
+  for (int j = 0; j < kLaneMaxM; ++j) x[j] = j < M ? L.in[base + j * stride] : 0.0;
+  for (int k = 1; k <= M; ++k) {
+    double acc = 0.0;
+    int idx = 0;   // (j k) mod 2n for j = 1, 2, ...
+#pragma unroll
+    for (int j = 0; j < kLaneMaxM; ++j) {
+      if (j < M) {
+        idx += k;
+        if (idx >= n2) idx -= n2;
+        acc = fma(x[j], __ldg(L.sintab + idx), acc);
+      }
+    }
+    L.out[base + (k - 1) * stride] = acc;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) dst_tile_kernel(DstLaunch L) {
   extern __shared__ double smem[];
   dst_tile_body(L, blockIdx.x, smem);
@@ -264,6 +306,18 @@ long long launch_tiles(const DstLaunch& L, long long nslices) {
 int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long long total_lines,
                  int cols, long long slice, long long nslices, cudaStream_t st) {
   const DstLaunch L = make_launch(p, in, out, mode, total_lines, cols, slice, p.tile_lines);
+  if (p.lane_direct && L.M <= kLaneMaxM) {
+    const long long lines = mode == 0 ? total_lines : nslices * cols;
+    if (lines <= 0) return KKT_OK;
+    const long long grid = (lines + kThreads - 1) / kThreads;
+    if (grid > 2147483647LL) return set_error(KKT_ERR_UNSUPPORTED, "DST grid too large");
+    // the same algorithmic count as the FFT path (the work the transform needs), not the
+    // direct sum's M FMAs per output
+    ProfScope ps(KKT_K_DST, st, lines * 2.5 * L.M * std::log2(2.0 * p.n), lines * L.M * 16.0);
+    dst_lane_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(L, lines);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
   const size_t sm = smem_bytes(p.n, L.tile_lines);
   KKT_CUDA_TRY(cudaFuncSetAttribute(dst_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(sm)));
@@ -415,6 +469,7 @@ int dst_autotune(kkt_handle* h) {
     DstPlan& p = pass == 0 ? h->dst_x : h->dst_y;
     int best = 0;
     double best_ms = 1e30;
+    p.lane_direct = false;
     for (int tl : {8, 16, 32}) {
       const double ms = time_pass(p, tl, pass == 0);
       if (ms < best_ms) {
@@ -423,12 +478,27 @@ int dst_autotune(kkt_handle* h) {
       }
     }
     p.tile_lines = best;   // 0 (the default) if no candidate ran
+    if (p.n - 1 <= kLaneMaxM) {   // short lines: the thread-per-line transform is a candidate too
+      p.lane_direct = true;
+      const double ms = time_pass(p, best, pass == 0);
+      p.lane_direct = ms < best_ms;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   const cudaError_t e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return set_error(KKT_ERR_CUDA, std::string("transform autotuning: ") + cudaGetErrorString(e));
   set_error(KKT_OK, "");
+  return KKT_OK;
+}
+
+int dst_set_method(kkt_handle* h, int method) {
+  for (DstPlan* p : {&h->dst_x, &h->dst_y}) {
+    if (method == KKT_DST_LANE && p->n - 1 > kLaneMaxM)
+      return set_error(KKT_ERR_UNSUPPORTED, "the thread-per-line transform needs lines of at most 31 points");
+  }
+  if (method == KKT_DST_AUTO) return dst_autotune(h);
+  for (DstPlan* p : {&h->dst_x, &h->dst_y}) p->lane_direct = method == KKT_DST_LANE;
   return KKT_OK;
 }
 

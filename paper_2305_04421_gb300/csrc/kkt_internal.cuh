@@ -39,6 +39,8 @@ struct DstPlan {
   double2* d_post = nullptr;  // exp(-2 pi i k / n), k = 0..n/2 (real-FFT unpacking)
   double* d_sin = nullptr;    // direct transform: sqrt(2/n) sin(pi m / n), m = 0..2n-1
   int tile_lines = 0;         // lines per CTA tile (0: the size-based default; set by dst_autotune)
+  bool lane_direct = false;   // one thread per line, direct sum (lines of at most 31 points;
+                              // chosen by dst_autotune or kkt_set_dst_method)
 };
 
 // Time decomposition of Section 3 and the data of the Nicolaides coarse space (Eq 14).
@@ -176,6 +178,7 @@ void release_krylov(kkt_handle* h);
 // Times the candidate tile heights (8, 16, 32 lines) of the row and column passes on the
 // handle's spectral buffers and keeps the fastest in dst_x / dst_y (at create).
 int dst_autotune(kkt_handle* h);
+int dst_set_method(kkt_handle* h, int method);
 void dst_plan_destroy(DstPlan& p);
 // orthonormal 2D DST-I of every slice: rows (along x) then columns (along y)
 int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st);

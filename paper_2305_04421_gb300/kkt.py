@@ -37,6 +37,7 @@ BASIS = {"physical": 0, "spectral": 1}
 LOCAL = {"rasq": 0, "ras": 1}
 COARSE_SOLVE = {"auto": 0, "thomas": 1, "cyclic": 2}
 STAGING = {"auto": 0, "copy_engine": 1}
+DST_METHOD = {"auto": 0, "tiles": 1, "lane": 2}
 HISTORY_MAX = 1024
 
 
@@ -130,6 +131,7 @@ SIGNATURES = [
     ("kkt_solve", _I, [_P, _P, _P, _D, _I, ctypes.POINTER(KKTStats), _P]),
     ("kkt_solve_zero_guess", _I, [_P, _P, _P, _D, _I, ctypes.POINTER(KKTStats), _P]),
     ("kkt_set_staging", _I, [_P, _I]),
+    ("kkt_set_dst_method", _I, [_P, _I]),
     ("kkt_dst2d", _I, [_P, _P, _P, _P]),
     ("kkt_schur_apply", _I, [_P, _P, _P, _P]),
     ("kkt_schur_precond_apply", _I, [_P, _P, _P, _P]),
@@ -464,6 +466,11 @@ class Solver:
                          Lx, Ly, COARSE_SOLVE[coarse_solve])
         kkt_set_options(self.h, opt)
         self.info = kkt_get_info(self.h)
+
+    def set_dst_method(self, method="auto"):
+        """FP64 sine transforms: 'auto' (timed at create), 'tiles' (warp per line) or 'lane'
+        (thread per line; lines of at most 31 points)."""
+        _check(load_library().kkt_set_dst_method(self.h, DST_METHOD[method]))
 
     def set_staging(self, mode="auto"):
         """How solve() moves host vectors: 'auto' (pinned buffers by a copy kernel, pageable by

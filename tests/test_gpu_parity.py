@@ -92,6 +92,34 @@ def test_dst2d_matches_scipy_dst(kkt, c):
     assert rel(host(t), x) < 1e-13
 
 
+@pytest.mark.parametrize("c", [c for c in CASES if max(c[0], c[1]) <= 32] + [(16, 16, 200, 40, 1e-4, 1.0, 1.0, 2.0)])
+@pytest.mark.parametrize("method", ["tiles", "lane"])
+def test_dst_methods_match_scipy_dst(kkt, c, method):
+    """Both FP64 transform methods on grids with at most 31 points per direction (power-of-two
+    and other interval counts, rows and columns, in place), and a preconditioner apply with each
+    against the oracle."""
+    p, nd = _problem(c)
+    s = _solver(kkt, c)
+    s.set_dst_method(method)
+    x = workloads.random_vector(p.V, 13)
+    assert rel(host(s.dst2d(dev(x))), spectral.dst2(x, p).ravel()) < 1e-13
+    t = dev(x)
+    s.dst2d(t, out=t)
+    s.dst2d(t, out=t)
+    assert rel(host(t), x) < 1e-13
+    pre = schwarz.schur_preconditioner(p, nd)
+    assert rel(host(s.schur_precond_apply(dev(x))), pre.apply(x)) < TOL
+
+
+def test_lane_dst_refused_for_long_lines(kkt):
+    s = kkt.Solver(64, 16, 8, 1.0, 1.0, 1e-3, 2)
+    with pytest.raises(kkt.KKTError):
+        s.set_dst_method("lane")
+    s.set_dst_method("tiles")
+    s.set_dst_method("auto")
+    s.close()
+
+
 @pytest.mark.parametrize("c", CASES)
 def test_matvec_matches_sparse_kkt(kkt, c):
     p, _ = _problem(c)
