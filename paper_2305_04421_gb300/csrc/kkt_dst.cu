@@ -233,18 +233,25 @@ __global__ void __launch_bounds__(kThreads) dst_lane_kernel(DstLaunch L, long lo
   double x[kLaneMaxM];
 #pragma unroll
   for (int j = 0; j < kLaneMaxM; ++j) x[j] = j < M ? L.in[base + j * stride] : 0.0;
-  for (int k = 1; k <= M; ++k) {
-    double acc = 0.0;
-    int idx = 0;   // (j k) mod 2n for j = 1, 2, ...
+  // four outputs at a time: four independent FMA chains (outputs past M are computed with
+  // k <= M + 3 < 2n and not stored)
+  for (int k = 1; k <= M; k += 4) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int idx[4] = {0, 0, 0, 0};   // (j (k + u)) mod 2n for j = 1, 2, ...
 #pragma unroll
     for (int j = 0; j < kLaneMaxM; ++j) {
       if (j < M) {
-        idx += k;
-        if (idx >= n2) idx -= n2;
-        acc = fma(x[j], __ldg(L.sintab + idx), acc);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          idx[u] += k + u;
+          if (idx[u] >= n2) idx[u] -= n2;
+          acc[u] = fma(x[j], __ldg(L.sintab + idx[u]), acc[u]);
+        }
       }
     }
-    L.out[base + (k - 1) * stride] = acc;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k + u <= M) L.out[base + (k + u - 1) * stride] = acc[u];
   }
 }
 
