@@ -443,6 +443,8 @@ void batch_slot_free(BatchSlot& slot) {
   cudaFree(slot.spec);
   cudaFree(slot.coarse_prefix);
   cudaFree(slot.sweep_prefix);
+  cudaFree(slot.spec_cr);
+  cudaFree(slot.cr_prefix);
   cudaFree(slot.mv);
   cudaFree(slot.mv_prefix);
   slot = BatchSlot();

@@ -283,6 +283,7 @@ struct SpecParams {
   int two_level;       // apply the coarse correction
   int multiplicative;  // subtract S-hat x_0 before the local solves
   int ras;             // local solves with R_s S-hat R_s^T (Eq 9) instead of RASQ's (Eq 13)
+  int cyclic;          // coarse solve by cyclic reduction (else block Thomas)
 };
 SpecParams make_spec_params(const kkt_handle* h);
 
@@ -340,6 +341,12 @@ struct BatchSlot {
   size_t sweep_smem_short = 0;
   int sweep_tb = 128;
   double coarse_flops = 0, coarse_bytes = 0, sweep_flops = 0, sweep_bytes = 0;
+  // instances whose coarse solve is the cyclic reduction: their own job and item tables
+  SpecJob* spec_cr = nullptr;
+  long long* cr_prefix = nullptr;
+  int cr_njobs = 0;
+  long long cr_total = 0;
+  size_t cr_smem = 0;
   MatvecJob* mv = nullptr;
   long long* mv_prefix = nullptr;
   long long mv_total = 0;

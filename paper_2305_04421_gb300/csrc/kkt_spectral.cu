@@ -241,13 +241,24 @@ __device__ __forceinline__ void sym_inv(double d00, double d01, double d11, doub
   i11 = d00 * id;
 }
 
+// Modes per CTA of the cyclic-reduction solve: the largest power of two up to 32 whose blocks
+// fit in 96 KB of shared memory (two CTAs per SM); 0 when one mode does not fit in 200 KB.
+__host__ __device__ inline int cr_modes_per_cta(int n_sub) {
+  const size_t per_mode = static_cast<size_t>(kCrFields) * n_sub * sizeof(double);
+  if (per_mode > 200 * 1024) return 0;
+  int mpc = 32;
+  while (mpc > 1 && mpc * per_mode > 96 * 1024) mpc /= 2;
+  return mpc;
+}
+
+// One CTA's group of modes (group * mpc ..): the whole solve, ending with c' in cc. Every thread
+// of the block must call it (it synchronises the block).
 template <typename TI>
-__global__ void __launch_bounds__(kCrThreads) coarse_cr_kernel(const TI* __restrict__ rhat, double in_scale,
-                                                                SpecParams p, int mpc, double* __restrict__ cc) {
-  extern __shared__ __align__(16) double cr_sm[];
+__device__ void coarse_cr_body(const TI* __restrict__ rhat, double in_scale, const SpecParams& p, int mpc,
+                               long long group, double* __restrict__ cc, double* __restrict__ cr_sm) {
   const int n = p.n_sub;
   const int m = threadIdx.x % mpc, w = threadIdx.x / mpc, W = blockDim.x / mpc;
-  const long long q = static_cast<long long>(blockIdx.x) * mpc + m;
+  const long long q = group * mpc + m;
   const bool active = q < p.N;
   // field f of mode m: cr_sm[(f * mpc + m) * n + s]
   double* const F = cr_sm + static_cast<long long>(m) * n;
@@ -380,6 +391,13 @@ __global__ void __launch_bounds__(kCrThreads) coarse_cr_kernel(const TI* __restr
     cc[(2LL * s) * N + q] = p.h * C0[s];
     cc[(2LL * s + 1) * N + q] = p.h * C1[s];
   }
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(kCrThreads) coarse_cr_kernel(const TI* __restrict__ rhat, double in_scale,
+                                                                SpecParams p, int mpc, double* __restrict__ cc) {
+  extern __shared__ __align__(16) double cr_sm[];
+  coarse_cr_body<TI>(rhat, in_scale, p, mpc, blockIdx.x, cc, cr_sm);
 }
 
 // Learned coarse correction of one mode: the network's direction d, scaled by the Galerkin
@@ -622,6 +640,23 @@ __global__ void coarse_batched(const SpecJob* __restrict__ jobs, const long long
   }
 }
 
+// Batched cyclic-reduction coarse solves: item = a group of cr_modes_per_cta(N_D) modes of one
+// instance (FP64); the dynamic shared memory fits the largest group of the launch.
+__global__ void __launch_bounds__(kCrThreads) coarse_cr_batched(const SpecJob* __restrict__ jobs,
+                                                                 const long long* __restrict__ prefix, int nj,
+                                                                 long long total, const double* __restrict__ scale_dev) {
+  extern __shared__ __align__(16) double cr_sm[];
+  __shared__ long long sp[KKT_BATCH_MAX + 1];
+  batch_prefix_load(sp, prefix, nj);
+  for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+    const int k = batch_find(sp, nj, t);
+    const SpecJob& J = jobs[k];
+    coarse_cr_body<double>(J.rhat, J.scale_base * scale_dev[J.scale_index], J.p, cr_modes_per_cta(J.p.n_sub),
+                           t - sp[k], J.cc, cr_sm);
+    __syncthreads();   // the next item reuses the shared memory
+  }
+}
+
 // Batched sweeps: item = (block of modes, subdomain) of one instance (FP64).
 __global__ void sweep_batched(const SpecJob* __restrict__ jobs, const long long* __restrict__ prefix, int nj,
                               long long t_begin, long long t_end, const double* __restrict__ scale_dev) {
@@ -648,6 +683,12 @@ __global__ void prolong_kernel(SpecParams p, const double* __restrict__ cc, doub
   const int o = __ldg(p.owner + n - 1);
   xhat[static_cast<long long>(n - 1) * p.N + q] =
       cc[(2LL * o) * p.N + q] + cc[(2LL * o + 1) * p.N + q] * __ldg(p.phi + n - 1);
+}
+
+bool use_cyclic(const kkt_handle* h, const SpecParams& p) {
+  if (p.learn_k > 0 || cr_modes_per_cta(p.n_sub) == 0) return false;
+  if (h->opt.coarse_solve == KKT_COARSE_SOLVE_CYCLIC) return true;
+  return h->opt.coarse_solve == KKT_COARSE_SOLVE_AUTO && p.N < kCyclicBelowModes;
 }
 
 SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixed forms' mode grid)
@@ -677,29 +718,14 @@ SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixe
   p.learn_c = h->learn_c;
   p.multiplicative = h->opt.variant == KKT_MULTIPLICATIVE;
   p.ras = h->opt.local == KKT_LOCAL_RAS;
+  p.cyclic = p.two_level && use_cyclic(h, p);
   return p;
-}
-
-// Modes per CTA of the cyclic-reduction solve: the largest power of two up to 32 whose blocks
-// fit in 96 KB of shared memory (two CTAs per SM); 0 when one mode does not fit in 200 KB.
-int cr_modes_per_cta(int n_sub) {
-  const size_t per_mode = static_cast<size_t>(kCrFields) * n_sub * sizeof(double);
-  if (per_mode > 200 * 1024) return 0;
-  int mpc = 32;
-  while (mpc > 1 && mpc * per_mode > 96 * 1024) mpc /= 2;
-  return mpc;
-}
-
-bool use_cyclic(const kkt_handle* h, const SpecParams& p) {
-  if (p.learn_k > 0 || cr_modes_per_cta(p.n_sub) == 0) return false;
-  if (h->opt.coarse_solve == KKT_COARSE_SOLVE_CYCLIC) return true;
-  return h->opt.coarse_solve == KKT_COARSE_SOLVE_AUTO && p.N < kCyclicBelowModes;
 }
 
 template <typename TI>
 int launch_coarse(const kkt_handle* h, const SpecParams& p, const TI* rhat, double in_scale, cudaStream_t st) {
   const double V = static_cast<double>(p.N) * p.Nt;
-  if (use_cyclic(h, p)) {
+  if (p.cyclic) {
     const int mpc = cr_modes_per_cta(p.n_sub);
     const size_t smem = static_cast<size_t>(kCrFields) * p.n_sub * mpc * sizeof(double);
     KKT_CUDA_TRY(cudaFuncSetAttribute(coarse_cr_kernel<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -814,13 +840,13 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
       short_len = std::max(short_len, jobs[k].max_len);
       n_short = k + 1;
     }
-    cp[k + 1] = cp[k] + (p.two_level ? (p.N + 127) / 128 : 0);
+    cp[k + 1] = cp[k] + (p.two_level && !p.cyclic ? (p.N + 127) / 128 : 0);
     sp[k + 1] = sp[k] + ((p.N + tb - 1) / tb) * p.n_sub;
     max_len = std::max(max_len, jobs[k].max_len);
     const double V = static_cast<double>(p.N) * p.Nt, visits = static_cast<double>(p.N) * (p.Nt + p.n_sub);
     if (p.two_level) {
-      cf += 2.0 * V + 26.0 * p.n_sub * p.N;
-      cb += 8.0 * V + 12.0 * 8.0 * p.n_sub * p.N;
+      cf += 2.0 * V + (p.cyclic ? 80.0 : 26.0) * p.n_sub * p.N;
+      cb += 8.0 * V + (p.cyclic ? 16.0 : 12.0 * 8.0) * p.n_sub * p.N;
     }
     sf += 12.0 * visits;
     sb += 8.0 * visits + 8.0 * V;
@@ -835,6 +861,29 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
     KKT_CUDA_TRY(cudaMalloc(&slot.sweep_prefix, (KKT_BATCH_MAX + 1) * sizeof(long long)));
   }
   KKT_CUDA_TRY(cudaMemcpy(slot.spec, jobs, nj * sizeof(SpecJob), cudaMemcpyHostToDevice));
+  // the instances whose coarse solve is the cyclic reduction, with their own item table
+  std::vector<SpecJob> cr;
+  std::vector<long long> crp(1, 0);
+  size_t cr_smem = 0;
+  for (int k = 0; k < nj; ++k) {
+    const SpecParams& p = jobs[k].p;
+    if (!p.two_level || !p.cyclic) continue;
+    const int mpc = cr_modes_per_cta(p.n_sub);
+    cr.push_back(jobs[k]);
+    crp.push_back(crp.back() + (p.N + mpc - 1) / mpc);
+    cr_smem = std::max(cr_smem, static_cast<size_t>(kCrFields) * p.n_sub * mpc * sizeof(double));
+  }
+  slot.cr_njobs = static_cast<int>(cr.size());
+  slot.cr_total = crp.back();
+  slot.cr_smem = cr_smem;
+  if (!cr.empty()) {
+    if (!slot.spec_cr) {
+      KKT_CUDA_TRY(cudaMalloc(&slot.spec_cr, KKT_BATCH_MAX * sizeof(SpecJob)));
+      KKT_CUDA_TRY(cudaMalloc(&slot.cr_prefix, (KKT_BATCH_MAX + 1) * sizeof(long long)));
+    }
+    KKT_CUDA_TRY(cudaMemcpy(slot.spec_cr, cr.data(), cr.size() * sizeof(SpecJob), cudaMemcpyHostToDevice));
+    KKT_CUDA_TRY(cudaMemcpy(slot.cr_prefix, crp.data(), crp.size() * sizeof(long long), cudaMemcpyHostToDevice));
+  }
   KKT_CUDA_TRY(cudaMemcpy(slot.coarse_prefix, cp.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));
   KKT_CUDA_TRY(cudaMemcpy(slot.sweep_prefix, sp.data(), (nj + 1) * sizeof(long long), cudaMemcpyHostToDevice));
   slot.coarse_total = cp[nj];
@@ -854,12 +903,24 @@ int spectral_batched_launch(const BatchSlot& slot, const double* scale_dev, cuda
   int dev = 0, sms = 0;
   KKT_CUDA_TRY(cudaGetDevice(&dev));
   KKT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  if (slot.coarse_total > 0) {
-    const long long grid = std::min<long long>(slot.coarse_total, static_cast<long long>(sms) * 16);
+  if (slot.coarse_total > 0 || slot.cr_total > 0) {
     ProfScope ps(KKT_K_COARSE, st, slot.coarse_flops, slot.coarse_bytes);
-    coarse_batched<<<static_cast<unsigned>(grid), 128, 0, st>>>(slot.spec, slot.coarse_prefix, slot.njobs,
-                                                                slot.coarse_total, scale_dev);
-    KKT_CUDA_TRY(cudaGetLastError());
+    if (slot.coarse_total > 0) {
+      const long long grid = std::min<long long>(slot.coarse_total, static_cast<long long>(sms) * 16);
+      coarse_batched<<<static_cast<unsigned>(grid), 128, 0, st>>>(slot.spec, slot.coarse_prefix, slot.njobs,
+                                                                  slot.coarse_total, scale_dev);
+      KKT_CUDA_TRY(cudaGetLastError());
+    }
+    if (slot.cr_total > 0) {
+      KKT_CUDA_TRY(cudaFuncSetAttribute(coarse_cr_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(slot.cr_smem)));
+      int per_sm = 0;
+      KKT_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_cr_batched, kCrThreads, slot.cr_smem));
+      const long long grid = std::min<long long>(slot.cr_total, static_cast<long long>(sms) * std::max(per_sm, 1));
+      coarse_cr_batched<<<static_cast<unsigned>(grid), kCrThreads, slot.cr_smem, st>>>(
+          slot.spec_cr, slot.cr_prefix, slot.cr_njobs, slot.cr_total, scale_dev);
+      KKT_CUDA_TRY(cudaGetLastError());
+    }
   }
   if (slot.sweep_total > 0) {
     KKT_CUDA_TRY(cudaFuncSetAttribute(sweep_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -576,7 +576,8 @@ class Batch:
     with nx, ny, Nt, n_sub, T, nu, omega attributes (e.g. workloads.Workload) or tuples."""
 
     def __init__(self, instances, *, coarse="exact", variant="multiplicative", pou="left", restart=30,
-                 jhat_sign=-1, residual_norm="l2", orth="mgs2", basis="physical", Lx=1.0, Ly=1.0):
+                 jhat_sign=-1, residual_norm="l2", orth="mgs2", basis="physical", Lx=1.0, Ly=1.0,
+                 coarse_solve="auto"):
         descs = []
         for w in instances:
             if isinstance(w, tuple):
@@ -585,7 +586,7 @@ class Batch:
                 descs.append(KKTInstance(w.nx, w.ny, w.Nt, w.n_sub, w.T, w.nu, w.omega))
         opt = KKTOptions(PREC["fp64"], COARSE[coarse], VARIANT[variant], POU[pou], restart, jhat_sign,
                          NORM[residual_norm], 1, ORTH[orth], BASIS[basis], LOCAL["rasq"], Lx, Ly,
-                         COARSE_SOLVE["auto"])
+                         COARSE_SOLVE[coarse_solve])
         self.b = kkt_batch_create(descs, opt)
         self.infos = [kkt_batch_get_info(self.b, i) for i in range(len(descs))]
 

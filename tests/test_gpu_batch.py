@@ -106,6 +106,30 @@ def test_batch_tight_solutions_match_the_oracle(kkt, small_case, basis):
         assert rel(host(res.xs[i]), exact) < TOL, SMALL[i].name
 
 
+# the paper's mesh (15 x 15 interior points) with 5 steps per subdomain: the batched waves run the
+# cyclic-reduction coarse solve for these instances (and Thomas when told to)
+PAPER_LIKE = [workloads.Workload(f"p{Nt}", nx=16, ny=16, Nt=Nt, n_sub=Nt // 5, omega=om, target="sine-series",
+                                 seed=30 + q)
+              for q, (Nt, om) in enumerate([(100, 1e-2), (400, 1e-4), (1600, 1e-3), (3200, 1e-4)])]
+
+
+def test_batch_cyclic_coarse_solve_on_paper_like_instances(kkt):
+    ps, fs = zip(*[rhs(w) for w in PAPER_LIKE])
+    fs = [dev(f) for f in fs]
+    out = {}
+    for solver in ("auto", "thomas"):
+        b = kkt.Batch(PAPER_LIKE, coarse_solve=solver)
+        b.set_single_threshold(0)
+        out[solver] = b.solve(fs, tol=1e-12, maxit=420)
+        assert out[solver].status == kkt.KKT_OK
+        b.close()
+    for i, w in enumerate(PAPER_LIKE):
+        assert out["auto"].iterations[i] == out["thomas"].iterations[i], w.name
+        exact = spectral.kkt_exact_solve(ps[i], host(fs[i]))
+        assert rel(host(out["auto"].xs[i]), exact) < TOL, w.name
+        assert rel(host(out["thomas"].xs[i]), exact) < TOL, w.name
+
+
 def test_batch_waves_give_the_same_results(kkt, small_case):
     ps, fs = small_case
     one = kkt.Batch(SMALL).solve(fs, tol=1e-8, maxit=420)
