@@ -216,9 +216,8 @@ __device__ void dst_tile_body(const DstLaunch& L, long long bid, double* smem) {
 // reading all of it, so in == out is allowed.
 constexpr int kLaneMaxM = 31;
 
-__global__ void __launch_bounds__(kThreads) dst_lane_kernel(DstLaunch L, long long lines) {
-  const long long t = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= lines) return;
+__device__ void dst_lane_body(const DstLaunch& L, long long t) {
+  if (t >= L.lines) return;
   long long base;
   long long stride;
   if (L.mode == 0) {
@@ -255,6 +254,10 @@ __global__ void __launch_bounds__(kThreads) dst_lane_kernel(DstLaunch L, long lo
   }
 }
 
+__global__ void __launch_bounds__(kThreads) dst_lane_kernel(DstLaunch L) {
+  dst_lane_body(L, static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x);
+}
+
 __global__ void __launch_bounds__(kThreads) dst_tile_kernel(DstLaunch L) {
   extern __shared__ double smem[];
   dst_tile_body(L, blockIdx.x, smem);
@@ -270,8 +273,12 @@ __global__ void __launch_bounds__(kThreads) dst_tile_batched(const DstLaunch* __
   batch_prefix_load(sp, prefix, nl);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int k = batch_find(sp, nl, t);
-    dst_tile_body(Ls[k], t - sp[k], smem);
-    __syncthreads();
+    if (Ls[k].lane) {   // an item is kThreads lines, one per thread
+      dst_lane_body(Ls[k], (t - sp[k]) * kThreads + threadIdx.x);
+    } else {
+      dst_tile_body(Ls[k], t - sp[k], smem);
+      __syncthreads();
+    }
   }
 }
 
@@ -285,7 +292,7 @@ size_t smem_bytes(int n, int tl) {
 }
 
 DstLaunch make_launch(const DstPlan& p, const double* in, double* out, int mode, long long total_lines, int cols,
-                      long long slice, int tile_lines) {
+                      long long slice, int tile_lines, long long nslices) {
   DstLaunch L;
   L.in = in;
   L.out = out;
@@ -303,25 +310,28 @@ DstLaunch make_launch(const DstPlan& p, const double* in, double* out, int mode,
   L.tw = p.d_tw;
   L.post = p.d_post;
   L.sintab = p.d_sin;
+  L.lane = p.lane_direct && L.M <= kLaneMaxM;
+  L.lines = mode == 0 ? total_lines : nslices * cols;
   return L;
 }
 
 long long launch_tiles(const DstLaunch& L, long long nslices) {
+  if (L.lane) return (L.lines + kThreads - 1) / kThreads;
   return L.mode == 0 ? (L.total_lines + L.tile_lines - 1) / L.tile_lines : nslices * L.tiles_per_slice;
 }
 
 int launch_lines(const DstPlan& p, const double* in, double* out, int mode, long long total_lines,
                  int cols, long long slice, long long nslices, cudaStream_t st) {
-  const DstLaunch L = make_launch(p, in, out, mode, total_lines, cols, slice, p.tile_lines);
-  if (p.lane_direct && L.M <= kLaneMaxM) {
-    const long long lines = mode == 0 ? total_lines : nslices * cols;
+  const DstLaunch L = make_launch(p, in, out, mode, total_lines, cols, slice, p.tile_lines, nslices);
+  if (L.lane) {
+    const long long lines = L.lines;
     if (lines <= 0) return KKT_OK;
-    const long long grid = (lines + kThreads - 1) / kThreads;
+    const long long grid = launch_tiles(L, nslices);
     if (grid > 2147483647LL) return set_error(KKT_ERR_UNSUPPORTED, "DST grid too large");
     // the same algorithmic count as the FFT path (the work the transform needs), not the
     // direct sum's M FMAs per output
     ProfScope ps(KKT_K_DST, st, lines * 2.5 * L.M * std::log2(2.0 * p.n), lines * L.M * 16.0);
-    dst_lane_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(L, lines);
+    dst_lane_kernel<<<static_cast<unsigned>(grid), kThreads, 0, st>>>(L);
     KKT_CUDA_TRY(cudaGetLastError());
     return KKT_OK;
   }
@@ -399,8 +409,8 @@ int dst_batched_prepare(BatchSlot& slot, int first_pass, const DstJob* jobs, int
       const kkt_handle* h = jobs[k].h;
       const Geometry& g = h->g;
       L[k] = rows ? make_launch(h->dst_x, jobs[k].in, jobs[k].out, 0, static_cast<long long>(g.Nt) * g.My, g.Mx, 0,
-                                tile_lines)
-                  : make_launch(h->dst_y, jobs[k].out, jobs[k].out, 1, 0, g.Mx, g.N, tile_lines);
+                                tile_lines, 0)
+                  : make_launch(h->dst_y, jobs[k].out, jobs[k].out, 1, 0, g.Mx, g.N, tile_lines, g.Nt);
       prefix[k + 1] = prefix[k] + launch_tiles(L[k], g.Nt);
       sm = std::max(sm, smem_bytes(L[k].n, L[k].tile_lines));
       const double lines = rows ? static_cast<double>(g.Nt) * g.My : static_cast<double>(g.Nt) * g.Mx;

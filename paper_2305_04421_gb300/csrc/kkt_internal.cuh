@@ -260,6 +260,8 @@ struct DstLaunch {
   const double2* tw;
   const double2* post;
   const double* sintab;
+  int lane;                 // one thread per line (lines of at most 31 points), no tiles
+  long long lines;          // lines of the launch (rows: total_lines; columns: slices x cols)
 };
 
 // Per-instance parameters of the spectral kernels (modes, decomposition, coarse buffers).
