@@ -1,5 +1,9 @@
 // Process-wide launch counters and optional CUDA-event timing of every kernel launch,
-// exported as kkt_profile_enable / kkt_profile_read.
+// exported as kkt_profile_enable / kkt_profile_read. Every launch scope is also an NVTX range
+// named after its kernel class (header-only NVTX v3: a no-op unless a tool is attached), so an
+// ncu or nsys capture can be filtered by phase.
+#include <nvtx3/nvToolsExt.h>
+
 #include <mutex>
 #include <vector>
 
@@ -53,9 +57,13 @@ void drain_locked() {
   g_pending.clear();
 }
 
+const char* const kClassNames[KKT_K_COUNT] = {"kkt.dst",    "kkt.coarse", "kkt.sweep",  "kkt.matvec", "kkt.multidot",
+                                               "kkt.update", "kkt.axpy",   "kkt.reduce", "kkt.graph"};
+
 }  // namespace
 
 void prof_begin(int cls, cudaStream_t st) {
+  nvtxRangePushA(kClassNames[cls]);
   if (t_cap) {   // being captured into a graph: count the launch for every replay instead
     t_cap->launches[cls] += 1;
     return;
@@ -68,6 +76,7 @@ void prof_begin(int cls, cudaStream_t st) {
 }
 
 void prof_end(int cls, cudaStream_t st, double flops, double bytes) {
+  nvtxRangePop();
   if (t_cap) {
     t_cap->flops += flops;
     t_cap->bytes += bytes;
