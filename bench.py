@@ -495,7 +495,7 @@ def measure_batched(kkt_mod, dev) -> dict:
 
 
 def measure_learned(kkt_mod, dev) -> dict:
-    """Learned-vs-plain judge on the 256 x 256, Nt = 2048, N_D = 256 workload (m = 8): the
+    """Learned-vs-plain comparison on the 256 x 256, Nt = 2048, N_D = 256 workload (m = 8): the
     network (in 2 N_D + 2 -> 512 -> 512 -> 2 N_D, ReLU) is trained on the GPU on exact coarse
     solves of modes k, l < 32 with (nu, omega) drawn log-uniform from [0.1, 10] x [1e-6, 1e-2],
     then every form solves the same seeded right-hand side to 1e-8 from x_0 = 0: one-level RASQ,

@@ -1,7 +1,7 @@
-"""Guard bands around every buffer an entry point touches (compute-sanitizer is closed on this
-pool, so out-of-range writes are caught this way): each vector is a view into a larger device
-allocation whose margins hold a sentinel bit pattern, and after the call the margins must be
-untouched and the inputs unchanged. Sizes are odd and ragged (tails in every kernel's tiling),
+"""Guard bands around every buffer an entry point touches, a check for out-of-range writes
+that needs no memory-checking tool: each vector is a view into a larger device allocation whose
+margins hold a sentinel bit pattern, and after the call the margins must be untouched and the
+inputs unchanged. Sizes are odd and ragged (tails in every kernel's tiling),
 both coarse solvers and both transform methods run, and so do the reduced-precision forms
 and the batched form.
 """
