@@ -272,9 +272,10 @@ int kkt_solve_zero_guess(kkt_handle* h, const double* f, double* x, double tol, 
 
 /* out = Q in for every time slice: the orthonormal 2D DST-I along x then y (Q^2 = I), which
  * diagonalises the 5-point Laplacian of Eq 2. Blocks: in [n][j][i], out [n][l][k] (k the x mode,
- * fastest). FP64 precision: FFT-based, in == out allowed. BF16 / TF32 precision (square grids):
- * the two tensor-core GEMMs with Q, operands rounded to BF16 (the intermediate too) or TF32,
- * FP32 accumulation; in and out must not overlap. */
+ * fastest). FP64 precision: a half-length FFT per line for power-of-two interval counts, the
+ * direct sum otherwise or for short lines (kkt_set_dst_method); in == out allowed. BF16 / TF32
+ * precision (square grids): the two tensor-core GEMMs with Q, operands rounded to BF16 (the
+ * intermediate too) or TF32, FP32 accumulation; in and out must not overlap. */
 int kkt_dst2d(kkt_handle* h, const double* in, double* out, void* stream);
 
 /* y = S-hat x = Jhat M_u^{-1} Jhat^T x (Eq 7), blocks. */
