@@ -44,17 +44,21 @@ __device__ __forceinline__ double2 cmul(double2 v, double2 w) {
   return make_double2(fma(v.x, w.x, -v.y * w.y), fma(v.x, w.y, v.y * w.x));
 }
 
-// One warp, one line x[0..n-2] (x[j-1] holds the j-th point), in place. buf: n/2 double2.
+// One line x[0..n-2] (x[j-1] holds the j-th point), in place, on G lanes of a warp (lane `sub`
+// of the group); the warp's 32 / G groups transform 32 / G lines side by side, each with its own
+// buf (n/2 double2, padded). G is about P / 4, so every lane has a radix-4 butterfly in each pass
+// of a short line (one line per warp from 256 intervals up).
 // FP64 is the bound on this part (2 DFMA-pipe instructions per clock per SM), so the line is
 // arranged to spend as few FP64 instructions as possible: the orthonormal scale is folded into
 // the pre-processing weights (y_j = w+_j x_j + w-_j x_n-j), stages 1 and 2 of the FFT (twiddles
 // 1 and -i) are one radix-4 pass of additions only, later stages go two at a time as radix-4
 // passes (3 complex products per 4 points instead of 4), and R_0 / 2 is taken out of the
 // prefix sum once per lane instead of per output.
-__device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int lane) {
+template <int G>
+__device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int sub) {
   const int n = L.n, P = n >> 1, logp = L.logn - 1;
   const double2* pw = reinterpret_cast<const double2*>(L.pre);   // c (sin + 1/2), c (sin - 1/2)
-  for (int j = lane; j < n; j += 32) {
+  for (int j = sub; j < n; j += G) {
     double yj = 0.0;
     if (j > 0) {
       const double a = x[j - 1], b = x[n - j - 1];
@@ -67,7 +71,7 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
   int s = 1;
   if (logp >= 2) {
     // stages 1 and 2: pairs (0,1), (2,3) with twiddle 1, then (0,2) with 1 and (1,3) with -i
-    for (int b = lane; b < (P >> 2); b += 32) {
+    for (int b = sub; b < (P >> 2); b += G) {
       const int i0 = 4 * b;
       const double2 a0 = buf[pidx(i0)], a1 = buf[pidx(i0 + 1)], a2 = buf[pidx(i0 + 2)], a3 = buf[pidx(i0 + 3)];
       const double2 b0 = make_double2(a0.x + a1.x, a0.y + a1.y), b1 = make_double2(a0.x - a1.x, a0.y - a1.y);
@@ -85,7 +89,7 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
   // (p0 + p2) +- (p1 + p3) and (p0 - p2) -+ i (p1 - p3); tw[m] = exp(-2 pi i m / P)
   for (; s + 1 <= logp; s += 2) {
     const int half = 1 << (s - 1), tsh = logp - s - 1;
-    for (int b = lane; b < (P >> 2); b += 32) {
+    for (int b = sub; b < (P >> 2); b += G) {
       const int k = b & (half - 1);
       const int i0 = ((b >> (s - 1)) << (s + 1)) + k;
       const double2 p0 = buf[pidx(i0)];
@@ -103,7 +107,7 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
   }
   if (s == logp) {   // one radix-2 stage left
     const int half = 1 << (s - 1);
-    for (int b = lane; b < (P >> 1); b += 32) {
+    for (int b = sub; b < (P >> 1); b += G) {
       const int k = b & (half - 1);
       const int i0 = ((b >> (s - 1)) << s) + k;
       const int i1 = i0 + half;
@@ -115,8 +119,8 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
     __syncwarp();
   }
   // Unpack Y_k (times 2) from the half-length FFT; even outputs directly, odd ones by a scan.
-  const int chunk = P >= 32 ? P / 32 : 1;
-  const int k0 = lane * chunk;
+  const int chunk = P >= G ? P / G : 1;
+  const int k0 = sub * chunk;
   const bool active = k0 < P;
   double total = 0.0;
   if (active) {
@@ -134,15 +138,16 @@ __device__ void dst_line_fft(double* x, double2* buf, const DstLaunch& L, int la
       x[2 * k] = total;
     }
   }
-  double incl = total;
-  for (int o = 1; o < 32; o <<= 1) {
-    const double v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
+  double incl = total;   // inclusive scan over the G lanes of this line
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) {
+    const double v = __shfl_up_sync(0xffffffffu, incl, o, G);
+    if (sub >= o) incl += v;
   }
-  const double prev = __shfl_up_sync(0xffffffffu, incl, 1);
+  const double prev = __shfl_up_sync(0xffffffffu, incl, 1, G);
   // S_2k+1 = R_0 / 2 + R_1 + ... + R_k: the exclusive prefix of the lanes before, less R_0 / 2
   // (R_0 = 2 (Z_0.x + Z_0.y) in the times-2 convention)
-  const double corr = (lane == 0 ? 0.0 : prev) - (buf[0].x + buf[0].y);   // (pidx(0) = 0)
+  const double corr = (sub == 0 ? 0.0 : prev) - (buf[0].x + buf[0].y);   // (pidx(0) = 0)
   if (active)
     for (int t = 0; t < chunk; ++t) x[2 * (k0 + t)] += corr;
   __syncwarp();
@@ -166,12 +171,33 @@ __device__ void dst_line_direct(double* x, double* tmp, const DstLaunch& L, int 
   __syncwarp();
 }
 
+// Lanes per line of the FFT path: about P / 4 (one radix-4 butterfly per lane and pass), at
+// most 32, and at least 32 / tile_lines so that a warp's lines stay inside the tile (tile_lines
+// is then a multiple of the lines per warp).
+__host__ __device__ inline int fft_group_for(int n, int tile_lines) {
+  int g = (n >> 1) / 4;
+  if (g < 1) g = 1;
+  if (g > 32) g = 32;
+  const int gmin = 32 / tile_lines;
+  return g < gmin ? gmin : g;
+}
+
+// A warp's 32 / G lines side by side. Groups whose line index passes nl work on the tile's
+// unused rows (below tile_lines) and their results are never stored.
+template <int G>
+__device__ void fft_lines(const DstLaunch& L, double* tile, double* fbase, int nl, int warp, int lane) {
+  constexpr int LW = 32 / G;
+  const int grp = lane / G, sub = lane % G;
+  double2* fbuf = reinterpret_cast<double2*>(fbase + (warp * LW + grp) * fft_buf_words(L.n));
+  for (int l0 = warp * LW; l0 < nl; l0 += kWarps * LW) dst_line_fft<G>(tile + (l0 + grp) * L.ldt, fbuf, L, sub);
+}
+
 // One tile of lines: load, transform, store. `bid` is the tile index within the launch.
 __device__ void dst_tile_body(const DstLaunch& L, long long bid, double* smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double* tile = smem;
   const int tile_words = (L.tile_lines * L.ldt + 1) & ~1;
-  double2* fbuf = reinterpret_cast<double2*>(smem + tile_words + warp * fft_buf_words(L.n));
+  double* fbase = smem + tile_words;   // FFT buffers: kWarps x (32 / G) lines
 
   long long base = 0;
   int nl = 0;
@@ -190,11 +216,18 @@ __device__ void dst_tile_body(const DstLaunch& L, long long bid, double* smem) {
       for (int l = lane; l < nl; l += 32) tile[l * L.ldt + e] = L.in[base + static_cast<long long>(e) * L.cols + l];
   }
   __syncthreads();
-  for (int l = warp; l < nl; l += kWarps) {
-    if (L.logn >= 2)
-      dst_line_fft(tile + l * L.ldt, fbuf, L, lane);
-    else
-      dst_line_direct(tile + l * L.ldt, reinterpret_cast<double*>(fbuf), L, lane);
+  if (L.logn >= 2) {
+    switch (L.fft_group) {
+      case 32: fft_lines<32>(L, tile, fbase, nl, warp, lane); break;
+      case 16: fft_lines<16>(L, tile, fbase, nl, warp, lane); break;
+      case 8: fft_lines<8>(L, tile, fbase, nl, warp, lane); break;
+      case 4: fft_lines<4>(L, tile, fbase, nl, warp, lane); break;
+      case 2: fft_lines<2>(L, tile, fbase, nl, warp, lane); break;
+      default: fft_lines<1>(L, tile, fbase, nl, warp, lane); break;
+    }
+  } else {
+    double* tmp = fbase + warp * fft_buf_words(L.n);
+    for (int l = warp; l < nl; l += kWarps) dst_line_direct(tile + l * L.ldt, tmp, L, lane);
   }
   __syncthreads();
   if (L.mode == 0) {
@@ -292,7 +325,8 @@ size_t smem_bytes(int n, int tl) {
   const int M = n - 1;
   const int ldt = M | 1;
   const size_t tile_words = (static_cast<size_t>(tl) * ldt + 1) & ~static_cast<size_t>(1);
-  return (tile_words + static_cast<size_t>(kWarps) * fft_buf_words(n)) * sizeof(double);
+  const int lines_per_warp = 32 / fft_group_for(n, tl);   // (the direct path uses one buffer per warp)
+  return (tile_words + static_cast<size_t>(kWarps) * lines_per_warp * fft_buf_words(n)) * sizeof(double);
 }
 
 DstLaunch make_launch(const DstPlan& p, const double* in, double* out, int mode, long long total_lines, int cols,
@@ -316,6 +350,7 @@ DstLaunch make_launch(const DstPlan& p, const double* in, double* out, int mode,
   L.sintab = p.d_sin;
   L.lane = p.lane_direct && L.M <= kLaneMaxM;
   L.lines = mode == 0 ? total_lines : nslices * cols;
+  L.fft_group = fft_group_for(p.n, L.tile_lines);
   return L;
 }
 

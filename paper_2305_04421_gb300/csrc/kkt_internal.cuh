@@ -261,6 +261,7 @@ struct DstLaunch {
   const double2* post;
   const double* sintab;
   int lane;                 // one thread per line (lines of at most 31 points), no tiles
+  int fft_group;            // FFT path: lanes per line (32 / fft_group lines per warp)
   long long lines;          // lines of the launch (rows: total_lines; columns: slices x cols)
 };
 
