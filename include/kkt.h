@@ -247,14 +247,16 @@ enum kkt_staging {
   /* every host buffer through cudaMemcpyAsync (the copy engine) */
   KKT_STAGING_COPY_ENGINE = 1
 };
+/* Takes effect at the next kkt_solve; KKT_ERR_INVALID_ARG for another value. */
 int kkt_set_staging(kkt_handle* h, int mode);
 
 /* How the FP64 sine transforms are computed (kkt_dst2d and every FP64 preconditioner apply). */
 enum kkt_dst_method {
   /* chosen per direction at kkt_create by timing the candidates (the default) */
   KKT_DST_AUTO = 0,
-  /* tiles of lines in shared memory, one warp per line: the half-length FFT when the number
-   * of intervals is a power of two (>= 4), else the direct sum over the line */
+  /* tiles of lines in shared memory: the half-length FFT when the number of intervals is a
+   * power of two (>= 4), on about P / 4 lanes per line (one warp per line from 256 intervals
+   * up, several short lines per warp below); else the direct sum, one warp per line */
   KKT_DST_TILES = 1,
   /* one thread per line, the direct sum: lines of at most 31 points (n <= 32) */
   KKT_DST_LANE = 2
