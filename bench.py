@@ -230,6 +230,11 @@ def run_reference(args):
 # (profiles/ncu_fp64_kernels_256x256_nt96.md), whose traffic grows in proportion to the
 # elements processed. Kernels not listed report traffic null.
 TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgs2_step_kernel": 0.998, "dst_tile_kernel": 0.947}
+# FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, of peak sustained, active SMs) from the
+# --set full captures of the small case (profiles/ncu_fp64_kernels_256x256_nt96.md): context for
+# an "alu" roofline whose achieved figure counts algorithmic FLOPs, not issued instructions.
+FP64_PIPE_BUSY = {"dst_tile_kernel": [0.78, 0.82], "mgs2_step_kernel": [0.86, 0.87],
+                  "sweep_kernel": [0.85, 0.85], "matvec_kernel": [0.83, 0.83]}
 
 
 def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -> dict:
@@ -268,6 +273,8 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -
         out = {"kernel": kname, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                "peak_source": f"{peak_kind} HBM copy"}
     bytes_per_launch = e["bytes"] / max(e["timed"], 1)
+    if kname in FP64_PIPE_BUSY and alu_kind == "alu":
+        out["fp64_pipe_busy_ncu"] = FP64_PIPE_BUSY[kname]
     ratio = TRAFFIC_RATIO.get(kname)
     out.update({"traffic": bytes_per_launch * ratio if ratio else None,
                 "traffic_source": ("ncu dram bytes / algorithmic bytes of the same kernel, times this launch's "
