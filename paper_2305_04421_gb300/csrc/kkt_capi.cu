@@ -210,8 +210,11 @@ int configure(kkt_handle* h) {
     KKT_TRY(spectral_coarse_factor(h, true, h->coarse_f_pad, nullptr));
   } else if (h->coarse_f_pad) {
     cudaFree(h->coarse_f_pad);
+  cudaFree(h->cr_factors);
     h->coarse_f_pad = nullptr;
   }
+  // the cyclic reduction's factors (only when that is the FP64 path's coarse solve)
+  KKT_TRY(spectral_cr_factor(h));
   KKT_CUDA_TRY(cudaDeviceSynchronize());
   // sweep storage: shared memory when a subdomain's nodes fit (32 threads x max_len doubles
   // within 200 KB), else a global scratch sized for every mode

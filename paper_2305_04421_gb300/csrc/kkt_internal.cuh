@@ -129,6 +129,8 @@ struct kkt_handle {
   double* coarse_w = nullptr;  // [n_sub][2][modes] eliminated coarse right-hand sides
   double* coarse_f = nullptr;  // [n_sub][3][N] block-Thomas factors D_s^{-1} (per configuration)
   double* coarse_f_pad = nullptr;  // the same over the padded modes of the mixed forms
+  double* cr_factors = nullptr;    // cyclic-reduction factors, slot-major [slots(n_sub)][N] (FP64 path)
+  size_t cr_factor_bytes = 0;
   double* vscratch = nullptr;  // sweep storage when a subdomain is too long for shared memory
   // Krylov workspace (allocated at the first solve)
   int kry_restart = 0;
@@ -209,6 +211,9 @@ int mlp_dims(const kkt_mlp* m, int* d_in, int* width, int* d_out);
 int mlp_make_input(const double* c, const double* feat, long long S, int nc, float* X, cudaStream_t st);
 const kkt_mlp_config& mlp_config(const kkt_mlp* m);
 // per-mode block-Thomas factors of the coarse operator (depend on mu and the decomposition only)
+// Computes (or frees) the cyclic reduction's factors for the handle's options: stored when the
+// FP64 path's coarse solve is the cyclic reduction and they take at most 2 GB.
+int spectral_cr_factor(kkt_handle* h);
 int spectral_coarse_factor(const kkt_handle* h, bool padded, double* cf, cudaStream_t st);
 // reduced-precision forms: FP32 spectral input (padded modes), output BF16 (bf16 != 0) or FP32
 // (yhat_lo non-null: also the lo part, yhat + yhat_lo = the FP32 result)
@@ -287,6 +292,8 @@ struct SpecParams {
   int multiplicative;  // subtract S-hat x_0 before the local solves
   int ras;             // local solves with R_s S-hat R_s^T (Eq 9) instead of RASQ's (Eq 13)
   int cyclic;          // coarse solve by cyclic reduction (else block Thomas)
+  const double* crf;   // the cyclic reduction's stored factors (nullptr: eliminate in every solve)
+  int cr_mpc;          // modes per CTA of the cyclic-reduction solve
 };
 SpecParams make_spec_params(const kkt_handle* h);
 

@@ -400,6 +400,231 @@ __global__ void __launch_bounds__(kCrThreads) coarse_cr_kernel(const TI* __restr
   coarse_cr_body<TI>(rhat, in_scale, p, mpc, blockIdx.x, cc, cr_sm);
 }
 
+// The cyclic reduction with its factors computed once per configuration. The matrices of every
+// level depend only on mu and the decomposition, so coarse_cr_factor_kernel runs the forward
+// elimination on them alone and stores, per mode (slot-major: F[slot * N + q]):
+//   per block s (slots 11 s ..): D_s^-1 (3), P_s = D_s^-1 U_left^T (4), Q_s = D_s^-1 U_s (4)
+//     for the block's own level (U_left the coupling of its left neighbour there);
+//   per level l and kept block j = 2 e 2^l (slots 11 n + 8 (off_l + e) ..): A = U_o1^T D_o1^-1
+//     and B = U_j D_o2^-1, with off_l the kept blocks of the levels below.
+// A solve (coarse_crf_body) then moves only the right-hand side: c_j -= A c_o1 + B c_o2 on the
+// way down, x_o = D_o^-1 c_o - P x_left - Q x_right on the way up: about 20 FMAs per block
+// against about 80 with the elimination, and 2 doubles per block in shared memory.
+__host__ __device__ inline long long cr_kept_total(int n) {
+  long long K = 0;
+  for (int st = 1; st < n; st *= 2) K += ((n + st - 1) / st + 1) / 2;
+  return K;
+}
+__host__ __device__ inline long long cr_factor_slots(int n) { return 11LL * n + 8LL * cr_kept_total(n); }
+
+__global__ void __launch_bounds__(kCrThreads) coarse_cr_factor_kernel(SpecParams p, int mpc, double* __restrict__ F) {
+  extern __shared__ __align__(16) double cr_sm[];
+  const int n = p.n_sub;
+  const int m = threadIdx.x % mpc, w = threadIdx.x / mpc, W = blockDim.x / mpc;
+  const long long N = p.N;
+  const long long q = static_cast<long long>(blockIdx.x) * mpc + m;
+  const bool active = q < N;
+  double* const Fs = cr_sm + static_cast<long long>(m) * n;
+  const long long fs = static_cast<long long>(mpc) * n;
+  double *D00 = Fs, *D01 = Fs + fs, *D11 = Fs + 2 * fs;
+  double *U00 = Fs + 3 * fs, *U01 = Fs + 4 * fs, *U10 = Fs + 5 * fs, *U11 = Fs + 6 * fs;
+  const double mu = active ? mode_mu(p, q) : 1.0, mu2 = mu * mu;
+  for (int s = w; s < n; s += W) {
+    if (!active) continue;
+    const double* M = p.mom + 9 * s;
+    D00[s] = fma(mu2, M[0], M[3]) - mu * M[6];
+    D01[s] = fma(mu2, M[1], M[4]) - mu * M[7];
+    D11[s] = fma(mu2, M[2], M[5]) - mu * M[8];
+    double a1 = 0.0, b1 = 0.0, g = 0.0;
+    if (s + 1 < n) {
+      a1 = __ldg(p.phi + __ldg(p.olast + s) - 1);
+      b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
+      g = -mu;
+    }
+    U00[s] = g;
+    U01[s] = g * b1;
+    U10[s] = g * a1;
+    U11[s] = g * a1 * b1;
+  }
+  __syncthreads();
+  long long off = 0;   // kept blocks of the levels below
+  for (int st = 1; st < n; st *= 2) {
+    const int cnt = (n + st - 1) / st;
+    for (int e = w; 2 * e + 1 < cnt; e += W) {   // eliminated blocks: D^-1, P, Q
+      if (!active) continue;
+      const int k = 2 * e + 1, o = k * st, left = o - st;
+      double i00, i01, i11;
+      sym_inv(D00[o], D01[o], D11[o], i00, i01, i11);
+      const double l00 = U00[left], l01 = U01[left], l10 = U10[left], l11 = U11[left];
+      double q00 = 0, q01 = 0, q10 = 0, q11 = 0;
+      if (k + 1 < cnt) {
+        q00 = i00 * U00[o] + i01 * U10[o];
+        q01 = i00 * U01[o] + i01 * U11[o];
+        q10 = i01 * U00[o] + i11 * U10[o];
+        q11 = i01 * U01[o] + i11 * U11[o];
+      }
+      double* B = F + 11LL * o * N + q;
+      B[0] = i00;
+      B[N] = i01;
+      B[2 * N] = i11;
+      B[3 * N] = i00 * l00 + i01 * l01;   // P = D^-1 U_left^T
+      B[4 * N] = i00 * l10 + i01 * l11;
+      B[5 * N] = i01 * l00 + i11 * l01;
+      B[6 * N] = i01 * l10 + i11 * l11;
+      B[7 * N] = q00;
+      B[8 * N] = q01;
+      B[9 * N] = q10;
+      B[10 * N] = q11;
+      D00[o] = i00;
+      D01[o] = i01;
+      D11[o] = i11;
+    }
+    __syncthreads();
+    for (int e = w; 2 * e < cnt; e += W) {   // kept blocks: A, B, and the Schur update
+      if (!active) continue;
+      const int k = 2 * e, j = k * st;
+      double d00 = D00[j], d01 = D01[j], d11 = D11[j];
+      double a00 = 0, a01 = 0, a10 = 0, a11 = 0, b00 = 0, b01 = 0, b10 = 0, b11 = 0;
+      if (k >= 1) {   // A = U_o1^T D_o1^-1; D_j -= A U_o1
+        const int o = j - st;
+        const double i00 = D00[o], i01 = D01[o], i11 = D11[o];
+        const double u00 = U00[o], u01 = U01[o], u10 = U10[o], u11 = U11[o];
+        a00 = u00 * i00 + u10 * i01;
+        a01 = u00 * i01 + u10 * i11;
+        a10 = u01 * i00 + u11 * i01;
+        a11 = u01 * i01 + u11 * i11;
+        d00 -= a00 * u00 + a01 * u10;
+        d01 -= a00 * u01 + a01 * u11;
+        d11 -= a10 * u01 + a11 * u11;
+      }
+      if (k + 1 < cnt) {   // B = U_j D_o2^-1; D_j -= B U_j^T; U_j <- -B U_o2
+        const int o = j + st;
+        const double i00 = D00[o], i01 = D01[o], i11 = D11[o];
+        const double u00 = U00[j], u01 = U01[j], u10 = U10[j], u11 = U11[j];
+        b00 = u00 * i00 + u01 * i01;
+        b01 = u00 * i01 + u01 * i11;
+        b10 = u10 * i00 + u11 * i01;
+        b11 = u10 * i01 + u11 * i11;
+        d00 -= b00 * u00 + b01 * u01;
+        d01 -= b00 * u10 + b01 * u11;
+        d11 -= b10 * u10 + b11 * u11;
+        const double v00 = U00[o], v01 = U01[o], v10 = U10[o], v11 = U11[o];
+        U00[j] = -(b00 * v00 + b01 * v10);
+        U01[j] = -(b00 * v01 + b01 * v11);
+        U10[j] = -(b10 * v00 + b11 * v10);
+        U11[j] = -(b10 * v01 + b11 * v11);
+      }
+      D00[j] = d00;
+      D01[j] = d01;
+      D11[j] = d11;
+      double* A = F + (11LL * n + 8 * (off + e)) * N + q;
+      A[0] = a00;
+      A[N] = a01;
+      A[2 * N] = a10;
+      A[3 * N] = a11;
+      A[4 * N] = b00;
+      A[5 * N] = b01;
+      A[6 * N] = b10;
+      A[7 * N] = b11;
+    }
+    __syncthreads();
+    off += (cnt + 1) / 2;
+  }
+  if (active && w == 0) {   // the last block
+    double i00, i01, i11;
+    sym_inv(D00[0], D01[0], D11[0], i00, i01, i11);
+    F[q] = i00;
+    F[N + q] = i01;
+    F[2 * N + q] = i11;
+  }
+}
+
+// A solve with the stored factors: R_0 r, the right-hand side down the levels, back up, c' = h x.
+// Shared memory: c (2 doubles per block and mode, overwritten by x).
+template <typename TI>
+__device__ void coarse_crf_body(const TI* __restrict__ rhat, double in_scale, const SpecParams& p, int mpc,
+                                long long group, double* __restrict__ cc, double* __restrict__ cr_sm) {
+  const int n = p.n_sub;
+  const int m = threadIdx.x % mpc, w = threadIdx.x / mpc, W = blockDim.x / mpc;
+  const long long N = p.N;
+  const long long q = group * mpc + m;
+  const bool active = q < N;
+  double* const C0 = cr_sm + static_cast<long long>(m) * n;
+  double* const C1 = C0 + static_cast<long long>(mpc) * n;
+  const double* __restrict__ F = p.crf;
+  for (int s = w; s < n; s += W) {
+    if (!active) continue;
+    double c0, c1;
+    restrict_sub<TI>(rhat, in_scale, p, q, s, c0, c1);
+    C0[s] = c0;
+    C1[s] = c1;
+  }
+  __syncthreads();
+  long long off = 0;
+  int top = 1;
+  for (int st = 1; st < n; st *= 2) {
+    const int cnt = (n + st - 1) / st;
+    for (int e = w; 2 * e < cnt; e += W) {
+      if (!active) continue;
+      const int k = 2 * e, j = k * st;
+      const double* A = F + (11LL * n + 8 * (off + e)) * N + q;
+      double c0 = C0[j], c1 = C1[j];
+      if (k >= 1) {
+        const double y0 = C0[j - st], y1 = C1[j - st];
+        c0 -= A[0] * y0 + A[N] * y1;
+        c1 -= A[2 * N] * y0 + A[3 * N] * y1;
+      }
+      if (k + 1 < cnt) {
+        const double y0 = C0[j + st], y1 = C1[j + st];
+        c0 -= A[4 * N] * y0 + A[5 * N] * y1;
+        c1 -= A[6 * N] * y0 + A[7 * N] * y1;
+      }
+      C0[j] = c0;
+      C1[j] = c1;
+    }
+    __syncthreads();
+    off += (cnt + 1) / 2;
+    top = 2 * st;
+  }
+  if (active && w == 0) {
+    const double c0 = C0[0], c1 = C1[0];
+    C0[0] = F[q] * c0 + F[N + q] * c1;
+    C1[0] = F[N + q] * c0 + F[2 * N + q] * c1;
+  }
+  __syncthreads();
+  for (int st = top / 2; st >= 1; st /= 2) {
+    const int cnt = (n + st - 1) / st;
+    for (int e = w; 2 * e + 1 < cnt; e += W) {
+      if (!active) continue;
+      const int k = 2 * e + 1, o = k * st;
+      const double* B = F + 11LL * o * N + q;
+      const double c0 = C0[o], c1 = C1[o], xl0 = C0[o - st], xl1 = C1[o - st];
+      double x0 = B[0] * c0 + B[N] * c1 - (B[3 * N] * xl0 + B[4 * N] * xl1);
+      double x1 = B[N] * c0 + B[2 * N] * c1 - (B[5 * N] * xl0 + B[6 * N] * xl1);
+      if (k + 1 < cnt) {
+        const double xr0 = C0[o + st], xr1 = C1[o + st];
+        x0 -= B[7 * N] * xr0 + B[8 * N] * xr1;
+        x1 -= B[9 * N] * xr0 + B[10 * N] * xr1;
+      }
+      C0[o] = x0;
+      C1[o] = x1;
+    }
+    __syncthreads();
+  }
+  for (int s = w; s < n; s += W) {
+    if (!active) continue;
+    cc[(2LL * s) * N + q] = p.h * C0[s];
+    cc[(2LL * s + 1) * N + q] = p.h * C1[s];
+  }
+}
+
+template <typename TI>
+__global__ void __launch_bounds__(kCrThreads) coarse_crf_kernel(const TI* __restrict__ rhat, double in_scale,
+                                                                 SpecParams p, int mpc, double* __restrict__ cc) {
+  extern __shared__ __align__(16) double cr_sm[];
+  coarse_crf_body<TI>(rhat, in_scale, p, mpc, blockIdx.x, cc, cr_sm);
+}
+
 // Learned coarse correction of one mode: the network's direction d, scaled by the Galerkin
 // condition alpha = d^T c / d^T G d on the mode's coarse operator G = h S_0(mu), is kept when
 // its coarse residual satisfies ||c - alpha G d||^2 <= ||c||^2 / 4, else the exact solve's
@@ -640,8 +865,9 @@ __global__ void coarse_batched(const SpecJob* __restrict__ jobs, const long long
   }
 }
 
-// Batched cyclic-reduction coarse solves: item = a group of cr_modes_per_cta(N_D) modes of one
-// instance (FP64); the dynamic shared memory fits the largest group of the launch.
+// Batched cyclic-reduction coarse solves: item = a group of cr_mpc modes of one instance (FP64),
+// with stored factors or the elimination in the solve; the dynamic shared memory fits the
+// largest group of the launch.
 __global__ void __launch_bounds__(kCrThreads) coarse_cr_batched(const SpecJob* __restrict__ jobs,
                                                                  const long long* __restrict__ prefix, int nj,
                                                                  long long total, const double* __restrict__ scale_dev) {
@@ -651,8 +877,11 @@ __global__ void __launch_bounds__(kCrThreads) coarse_cr_batched(const SpecJob* _
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int k = batch_find(sp, nj, t);
     const SpecJob& J = jobs[k];
-    coarse_cr_body<double>(J.rhat, J.scale_base * scale_dev[J.scale_index], J.p, cr_modes_per_cta(J.p.n_sub),
-                           t - sp[k], J.cc, cr_sm);
+    const double scale = J.scale_base * scale_dev[J.scale_index];
+    if (J.p.crf)
+      coarse_crf_body<double>(J.rhat, scale, J.p, J.p.cr_mpc, t - sp[k], J.cc, cr_sm);
+    else
+      coarse_cr_body<double>(J.rhat, scale, J.p, J.p.cr_mpc, t - sp[k], J.cc, cr_sm);
     __syncthreads();   // the next item reuses the shared memory
   }
 }
@@ -683,6 +912,22 @@ __global__ void prolong_kernel(SpecParams p, const double* __restrict__ cc, doub
   const int o = __ldg(p.owner + n - 1);
   xhat[static_cast<long long>(n - 1) * p.N + q] =
       cc[(2LL * o) * p.N + q] + cc[(2LL * o + 1) * p.N + q] * __ldg(p.phi + n - 1);
+}
+
+// Modes per CTA of the factored solve (2 doubles per block and mode in shared memory): up to 32,
+// within 96 KB, and few enough that the modes still make two CTAs per SM.
+int crf_modes_per_cta(int n_sub, long long N) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  const size_t per_mode = 2 * static_cast<size_t>(n_sub) * sizeof(double);
+  int mpc = 32;
+  while (mpc > 1 && (mpc * per_mode > 96 * 1024 || N / mpc < 2LL * sms)) mpc /= 2;
+  return mpc;
 }
 
 bool use_cyclic(const kkt_handle* h, const SpecParams& p) {
@@ -719,12 +964,27 @@ SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixe
   p.multiplicative = h->opt.variant == KKT_MULTIPLICATIVE;
   p.ras = h->opt.local == KKT_LOCAL_RAS;
   p.cyclic = p.two_level && use_cyclic(h, p);
+  p.crf = (!padded && p.cyclic) ? h->cr_factors : nullptr;
+  p.cr_mpc = p.crf ? crf_modes_per_cta(p.n_sub, p.N) : cr_modes_per_cta(p.n_sub);
   return p;
 }
 
 template <typename TI>
 int launch_coarse(const kkt_handle* h, const SpecParams& p, const TI* rhat, double in_scale, cudaStream_t st) {
   const double V = static_cast<double>(p.N) * p.Nt;
+  if (p.cyclic && p.crf) {
+    const int mpc = p.cr_mpc;
+    const size_t smem = 2 * static_cast<size_t>(p.n_sub) * mpc * sizeof(double);
+    KKT_CUDA_TRY(cudaFuncSetAttribute(coarse_crf_kernel<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+    // restriction: 2 flops per node; right-hand side down and back up: about 20 FMAs per block,
+    // reading 19 stored factors per block
+    ProfScope ps(KKT_K_COARSE, st, 2.0 * V + 40.0 * p.n_sub * p.N, V * sizeof(TI) + (16.0 + 152.0) * p.n_sub * p.N);
+    const long long nb = (p.N + mpc - 1) / mpc;
+    coarse_crf_kernel<TI><<<static_cast<unsigned>(nb), kCrThreads, smem, st>>>(rhat, in_scale, p, mpc, h->coarse_c);
+    KKT_CUDA_TRY(cudaGetLastError());
+    return KKT_OK;
+  }
   if (p.cyclic) {
     const int mpc = cr_modes_per_cta(p.n_sub);
     const size_t smem = static_cast<size_t>(kCrFields) * p.n_sub * mpc * sizeof(double);
@@ -845,8 +1105,8 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
     max_len = std::max(max_len, jobs[k].max_len);
     const double V = static_cast<double>(p.N) * p.Nt, visits = static_cast<double>(p.N) * (p.Nt + p.n_sub);
     if (p.two_level) {
-      cf += 2.0 * V + (p.cyclic ? 80.0 : 26.0) * p.n_sub * p.N;
-      cb += 8.0 * V + (p.cyclic ? 16.0 : 12.0 * 8.0) * p.n_sub * p.N;
+      cf += 2.0 * V + (p.cyclic ? (p.crf ? 40.0 : 80.0) : 26.0) * p.n_sub * p.N;
+      cb += 8.0 * V + (p.cyclic ? (p.crf ? 168.0 : 16.0) : 12.0 * 8.0) * p.n_sub * p.N;
     }
     sf += 12.0 * visits;
     sb += 8.0 * visits + 8.0 * V;
@@ -868,10 +1128,11 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
   for (int k = 0; k < nj; ++k) {
     const SpecParams& p = jobs[k].p;
     if (!p.two_level || !p.cyclic) continue;
-    const int mpc = cr_modes_per_cta(p.n_sub);
+    const int mpc = p.cr_mpc;
     cr.push_back(jobs[k]);
     crp.push_back(crp.back() + (p.N + mpc - 1) / mpc);
-    cr_smem = std::max(cr_smem, static_cast<size_t>(kCrFields) * p.n_sub * mpc * sizeof(double));
+    const size_t fields = p.crf ? 2 : kCrFields;
+    cr_smem = std::max(cr_smem, fields * p.n_sub * mpc * sizeof(double));
   }
   slot.cr_njobs = static_cast<int>(cr.size());
   slot.cr_total = crp.back();
@@ -942,6 +1203,40 @@ int spectral_batched_launch(const BatchSlot& slot, const double* scale_dev, cuda
       KKT_TRY(launch(0, slot.sweep_total, slot.sweep_smem));
     }
   }
+  return KKT_OK;
+}
+
+int spectral_cr_factor(kkt_handle* h) {
+  SpecParams p = make_params(h, false);
+  const long long slots = cr_factor_slots(p.n_sub);
+  const double bytes = static_cast<double>(slots) * p.N * sizeof(double);
+  if (!p.cyclic || bytes > 2.0 * 1024 * 1024 * 1024) {
+    if (h->cr_factors) {
+      cudaFree(h->cr_factors);
+      h->bytes -= h->cr_factor_bytes;
+      h->cr_factors = nullptr;
+      h->cr_factor_bytes = 0;
+    }
+    return KKT_OK;
+  }
+  if (h->cr_factor_bytes != static_cast<size_t>(bytes)) {
+    if (h->cr_factors) {
+      cudaFree(h->cr_factors);
+      h->bytes -= h->cr_factor_bytes;
+      h->cr_factors = nullptr;
+      h->cr_factor_bytes = 0;
+    }
+    KKT_CUDA_TRY(cudaMalloc(&h->cr_factors, static_cast<size_t>(bytes)));
+    h->cr_factor_bytes = static_cast<size_t>(bytes);
+    h->bytes += static_cast<size_t>(bytes);
+  }
+  const int mpc = cr_modes_per_cta(p.n_sub);
+  const size_t smem = 7 * static_cast<size_t>(p.n_sub) * mpc * sizeof(double);
+  KKT_CUDA_TRY(cudaFuncSetAttribute(coarse_cr_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  const long long nb = (p.N + mpc - 1) / mpc;
+  coarse_cr_factor_kernel<<<static_cast<unsigned>(nb), kCrThreads, smem, nullptr>>>(p, mpc, h->cr_factors);
+  KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
 
