@@ -1128,8 +1128,12 @@ int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int nj) {
   for (int k = 0; k < nj; ++k) {
     const SpecParams& p = jobs[k].p;
     if (!p.two_level || !p.cyclic) continue;
-    const int mpc = p.cr_mpc;
     cr.push_back(jobs[k]);
+    // the instances share the launch, so pack modes as densely as shared memory allows
+    // (cr_modes_per_cta, within 96 KB for the elimination's 13 doubles per block) rather than
+    // spreading one instance's modes over the SMs
+    const int mpc = cr_modes_per_cta(p.n_sub);
+    cr.back().p.cr_mpc = mpc;
     crp.push_back(crp.back() + (p.N + mpc - 1) / mpc);
     const size_t fields = p.crf ? 2 : kCrFields;
     cr_smem = std::max(cr_smem, fields * p.n_sub * mpc * sizeof(double));
