@@ -689,6 +689,40 @@ def run_study(args):
     return 0
 
 
+def run_coarse_study(args):
+    """kkt_coarse_apply (R_0^T S_0^-1 R_0 r: forward 2D DST, restriction, coarse solve,
+    prolongation, inverse DST) with the two coarse solvers, across mode counts and N_D; device
+    time per call (CUDA events over 20 calls after 3). One JSON line per case."""
+    import torch
+
+    import paper_2305_04421_gb300.kkt as kkt
+
+    torch.cuda.set_device(0)
+    for nx, Nt, nd in [(16, 3200, 640), (16, 800, 160), (16, 400, 80), (16, 100, 20), (32, 1024, 64),
+                       (64, 1024, 64), (96, 1024, 64), (128, 1024, 64), (160, 1024, 64), (256, 1024, 64),
+                       (64, 4096, 820), (128, 2048, 410)]:
+        s = kkt.Solver(nx, nx, Nt, 1.0, 1.0, 1e-4, nd, coarse_solve="thomas")
+        r = torch.randn(s.V, dtype=torch.float64, device="cuda")
+        y = torch.empty_like(r)
+        row = {"nx": nx, "Nt": Nt, "n_sub": nd, "modes": (nx - 1) ** 2}
+        for solver in ("thomas", "cyclic"):
+            s.set_options(coarse_solve=solver)
+            for _ in range(3):
+                s.coarse_apply(r, out=y)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                s.coarse_apply(r, out=y)
+            e1.record()
+            torch.cuda.synchronize()
+            row[solver + "_us"] = e0.elapsed_time(e1) / 20 * 1e3
+        s.close()
+        print(json.dumps(row), flush=True)
+    return 0
+
+
 def run_profile_case(args):
     """A small solve for counter captures, two solves; prints the iteration count. 'grid':
     256 x 256, Nt = 96, N_D = 8 (a KKT vector of 150 MB, above the 126 MB L2), FGMRES(10) to
@@ -862,8 +896,9 @@ def main():
                     help="FGMRES basis of --profile-case")
     ap.add_argument("--precision", choices=["fp64", "bf16", "tf32"], default="fp64",
                     help="preconditioner arithmetic of --profile-case")
-    ap.add_argument("--study", choices=["paper"], default=None,
-                    help="run Section 4's one- vs two-level iteration study instead of the benchmark")
+    ap.add_argument("--study", choices=["paper", "coarse"], default=None,
+                    help="instead of the benchmark: 'paper' runs Section 4's one- vs two-level iteration "
+                         "study, 'coarse' times kkt_coarse_apply with block Thomas and the cyclic reduction")
     ap.add_argument("--no-learned", action="store_true",
                     help="skip the learned-vs-plain coarse comparison on the 256 x 256, Nt = 2048 workload")
     ap.add_argument("--no-batched", action="store_true",
@@ -873,6 +908,8 @@ def main():
     args = ap.parse_args()
     if args.study == "paper":
         return run_study(args)
+    if args.study == "coarse":
+        return run_coarse_study(args)
     if args.profile_case:
         return run_profile_case(args)
     if args.impl == "reference":
