@@ -230,8 +230,9 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
 constexpr int kCrThreads = 256;
 constexpr int kCrFields = 13;
 // AUTO picks cyclic reduction below this many spatial modes (per mode, Thomas is one thread).
-// Measured crossover on GB300: cyclic ahead by 3 % at 9025 modes (N_D = 64), Thomas ahead by 5 %
-// at 16129 modes with N_D = 410 and by 6 % at 65025 modes.
+// Set from the crossover measured on GB300 with the elimination in every solve (cyclic ahead by
+// 3 % at 9025 modes with N_D = 64, Thomas ahead by 5 % at 16129 modes with N_D = 410); with the
+// stored factors the cyclic solve measured at least as fast up to 65025 modes.
 constexpr long long kCyclicBelowModes = 12288;
 
 __device__ __forceinline__ void sym_inv(double d00, double d01, double d11, double& i00, double& i01, double& i11) {
