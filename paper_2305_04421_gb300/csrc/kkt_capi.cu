@@ -210,10 +210,11 @@ int configure(kkt_handle* h) {
     KKT_TRY(spectral_coarse_factor(h, true, h->coarse_f_pad, nullptr));
   } else if (h->coarse_f_pad) {
     cudaFree(h->coarse_f_pad);
-  cudaFree(h->cr_factors);
     h->coarse_f_pad = nullptr;
   }
-  // the cyclic reduction's factors (only when that is the FP64 path's coarse solve)
+  // the cyclic reduction's factors (only when that is the FP64 path's coarse solve). The factor
+  // kernel runs on the legacy default stream; this device-wide sync must stay, so that no solve
+  // on a caller's (non-blocking) stream reads h->cr_factors before they are written.
   KKT_TRY(spectral_cr_factor(h));
   KKT_CUDA_TRY(cudaDeviceSynchronize());
   // sweep storage: shared memory when a subdomain's nodes fit (32 threads x max_len doubles
@@ -482,6 +483,7 @@ void kkt_destroy(kkt_handle* h) {
   cudaFree(h->coarse_w);
   cudaFree(h->coarse_f);
   cudaFree(h->coarse_f_pad);
+  cudaFree(h->cr_factors);
   cudaFree(h->vscratch);
   cudaFree(h->kV);
   cudaFree(h->kZw);

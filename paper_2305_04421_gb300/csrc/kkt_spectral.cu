@@ -1240,6 +1240,8 @@ int spectral_cr_factor(kkt_handle* h) {
   KKT_CUDA_TRY(cudaFuncSetAttribute(coarse_cr_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     static_cast<int>(smem)));
   const long long nb = (p.N + mpc - 1) / mpc;
+  // Legacy default stream: the caller (configure) synchronises the device before any solve can
+  // read these factors on the caller's stream.
   coarse_cr_factor_kernel<<<static_cast<unsigned>(nb), kCrThreads, smem, nullptr>>>(p, mpc, h->cr_factors);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
