@@ -462,3 +462,81 @@ def test_coarse_operator_inverse_reproduces_the_per_mode_coarse_solve():
     r = workloads.random_vector(Nt, 5)
     c = pre.Z.T @ r
     np.testing.assert_allclose(pre.Z @ np.linalg.solve(G, c), pre.coarse(r), rtol=1e-12, atol=1e-12)
+
+
+def test_mlp_forward_matches_hand_computed_network():
+    """A 2-3-3-2 network with hand-picked weights, evaluated by hand:
+    x = (1, 2): a1 = W1 x + b1 = (-1, 1, 2.5), h1 = (0, 1, 2.5); a2 = W2 h1 + b2 = (0.5, 3.5, -3),
+    h2 = (0.5, 3.5, 0); y = W3 h2 + b3 = (7.5, -1.5).
+    x = (-1, 0.5): a1 = (-1.5, -3, 1), h1 = (0, 0, 1); a2 = (0.5, 1, -2), h2 = (0.5, 1, 0);
+    y = (2.5, -1.5).
+    A dropped bias, a ReLU on the output or a transposed weight changes one of the outputs."""
+    from oracle import mlp
+    params = {"W1": np.array([[1.0, -1.0], [2.0, 0.0], [0.0, 1.0]]), "b1": np.array([0.0, -1.0, 0.5]),
+              "W2": np.array([[1.0, 0.0, 0.0], [0.0, 1.0, 1.0], [1.0, -1.0, 0.0]]), "b2": np.array([0.5, 0.0, -2.0]),
+              "W3": np.array([[1.0, 2.0, 3.0], [-1.0, 0.0, 1.0]]), "b3": np.array([0.0, -1.0])}
+    Y, _ = mlp.forward(params, np.array([[1.0, 2.0], [-1.0, 0.5]]))
+    np.testing.assert_array_equal(Y, np.array([[7.5, -1.5], [2.5, -1.5]]))
+
+
+def _coarse_batch(B=5, Nt=24, nd=4, seed=3):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    mus = 1.0 + rng.uniform(0.02, 3.0, B)
+    G = [mlp.coarse_operator(float(m), Nt, nd) for m in mus]
+    C = rng.standard_normal((B, 2 * nd))
+    D = rng.standard_normal((B, 2 * nd))
+    return G, C, D
+
+
+def test_coarse_residual_loss_is_the_least_squares_residual():
+    """Per sample, min over alpha of ||c - alpha G d|| from numpy's least squares, squared and
+    divided by ||c||^2, averaged over the batch; and zero at the exact coarse solve d = G^-1 c."""
+    from oracle import mlp
+    G, C, D = _coarse_batch()
+    want = 0.0
+    for b in range(len(G)):
+        g = (G[b] @ D[b])[:, None]
+        _, res, _, _ = np.linalg.lstsq(g, C[b], rcond=None)
+        want += float(res[0]) / float(C[b] @ C[b])
+    loss, _ = mlp.coarse_residual_loss(D, C, G)
+    np.testing.assert_allclose(loss, want / len(G), rtol=1e-12)
+    exact = np.stack([3.7 * np.linalg.solve(G[b], C[b]) for b in range(len(G))])
+    loss0, grad0 = mlp.coarse_residual_loss(exact, C, G)
+    assert loss0 < 1e-24 and np.abs(grad0).max() < 1e-10
+
+
+def test_coarse_residual_loss_gradient_matches_central_differences():
+    from oracle import mlp
+    G, C, D = _coarse_batch(seed=4)
+    _, g = mlp.coarse_residual_loss(D, C, G)
+    fd = np.zeros_like(D)
+    for idx in np.ndindex(D.shape):
+        old = D[idx]
+        D[idx] = old + 1e-6
+        lp, _ = mlp.coarse_residual_loss(D, C, G)
+        D[idx] = old - 1e-6
+        lm, _ = mlp.coarse_residual_loss(D, C, G)
+        D[idx] = old
+        fd[idx] = (lp - lm) / 2e-6
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-9)
+
+
+def test_coarse_data_restriction_by_brute_force():
+    """c = R_0 r for one mode's time series: per subdomain s with steps lo+1..hi (balanced split,
+    left partition of unity), the sum of r_n and of r_n (-1 + 2 (n - lo) / (hi - lo)); x solves
+    the coarse system."""
+    from oracle import mlp
+    Nt, nd = 30, 7
+    rng = np.random.default_rng(8)
+    r = rng.standard_normal((Nt, 3))
+    mu = np.array([1.05, 1.6, 4.0])
+    C, X = mlp.coarse_data(r, mu, Nt, nd)
+    for b in range(3):
+        for s in range(nd):
+            lo, hi = s * Nt // nd, (s + 1) * Nt // nd
+            c0 = sum(r[n - 1, b] for n in range(lo + 1, hi + 1))
+            c1 = sum(r[n - 1, b] * (-1.0 + 2.0 * (n - lo) / (hi - lo)) for n in range(lo + 1, hi + 1))
+            np.testing.assert_allclose(C[b, 2 * s], c0, rtol=1e-12, atol=1e-12)
+            np.testing.assert_allclose(C[b, 2 * s + 1], c1, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(mlp.coarse_operator(mu[b], Nt, nd) @ X[b], C[b], rtol=1e-10, atol=1e-10)
