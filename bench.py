@@ -194,6 +194,47 @@ def cpu_threads() -> int:
     return os.cpu_count() or 1
 
 
+def oracle_sample_one_thread(omega: float, krylov_dim: int) -> tuple[float | None, str]:
+    """The same oracle sample in a child process with every BLAS/OpenMP pool at one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json, bench; s, _ = bench.oracle_iteration_sample(bench.workload_for(%r), %d); "
+            "print(json.dumps(s))" % (omega, krylov_dim))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600,
+                             cwd=os.path.dirname(os.path.abspath(__file__)))
+        return float(out.stdout.strip().splitlines()[-1]), ""
+    except Exception as e:   # reported, not fatal: the all-core figure stands on its own
+        return None, f"{type(e).__name__}: {e}"
+
+
+def error_vs_exact(w: workloads.Workload, x: np.ndarray, kmax: int = 8) -> dict:
+    """Relative error of a solution x of the sine-series workload against the exact solution on
+    its active modes k, l <= kmax (the right-hand side's modes; the oracle's per-mode banded
+    solve), per block, and the content of x off those modes relative to each block."""
+    from oracle import spectral
+    from oracle.problem import HeatKKT
+
+    p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
+    ut = workloads.make_target(w)
+    fu_hat = spectral.dst2(p.h * ut.reshape(-1), p)
+    lam = spectral.mode_eigenvalues(p)
+    zeros = np.zeros(w.Nt)
+    exact = np.empty((3, w.Nt, kmax, kmax))
+    for l in range(kmax):
+        for k in range(kmax):
+            exact[:, :, l, k] = spectral.kkt_exact_mode_solve(p, lam[l, k], fu_hat[:, l, k], zeros, zeros)
+    out = {"modes": f"k, l <= {kmax}"}
+    errs = []
+    for b, name in enumerate("uzw"):
+        xh = spectral.dst2(x[b * p.V:(b + 1) * p.V], p)
+        err = float(np.linalg.norm(xh[:, :kmax, :kmax] - exact[b]) / np.linalg.norm(exact[b]))
+        xh[:, :kmax, :kmax] = 0.0
+        out[name] = {"rel_error": err, "off_mode_rel": float(np.linalg.norm(xh) / np.linalg.norm(exact[b]))}
+        errs.append(err)
+    out["max_block_rel_error"] = max(errs)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -226,13 +267,12 @@ def run_reference(args):
 # DRAM traffic per algorithmic byte for kernels captured with ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum over the launch, divided by the launch's algorithmic bytes). The paired
 # MGS step and the sine transform come from a single-pass capture of the benchmark workload
-# itself (profiles/ncu_traffic_256x256_nt1024.md); one-pass MGS from the small-case capture
-# (profiles/ncu_fp64_kernels_256x256_nt96.md), whose traffic grows in proportion to the
-# elements processed. Kernels not listed report traffic null.
+# itself; one-pass MGS from a capture of the 256 x 256, Nt = 96 case, whose traffic grows in
+# proportion to the elements processed. Kernels not listed report traffic null.
 TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgs2_step_kernel": 0.998, "dst_tile_kernel": 0.947}
 # FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, of peak sustained, active SMs) from the
-# --set full captures of the small case (profiles/ncu_fp64_kernels_256x256_nt96.md): context for
-# an "alu" roofline whose achieved figure counts algorithmic FLOPs, not issued instructions.
+# --set full captures of the 256 x 256, Nt = 96 case: context for an "alu" roofline whose
+# achieved figure counts algorithmic FLOPs, not issued instructions.
 FP64_PIPE_BUSY = {"dst_tile_kernel": [0.78, 0.82], "mgs2_step_kernel": [0.86, 0.87],
                   "sweep_kernel": [0.85, 0.85], "matvec_kernel": [0.83, 0.83]}
 
@@ -505,10 +545,14 @@ def measure_learned(kkt_mod, dev) -> dict:
     """Learned-vs-plain comparison on the 256 x 256, Nt = 2048, N_D = 256 workload (m = 8): the
     network (in 2 N_D + 2 -> 512 -> 512 -> 2 N_D, ReLU) is trained on the GPU on exact coarse
     solves of modes k, l < 32 with (nu, omega) drawn log-uniform from [0.1, 10] x [1e-6, 1e-2],
-    then every form solves the same seeded right-hand side to 1e-8 from x_0 = 0: one-level RASQ,
-    the exact two-level method, the learned coarse correction, its ablation (no coarse
-    correction on the learned modes), and TF32 transforms with the exact and the learned coarse
-    level. Cases: the workload's own (nu, omega) = (1, 1e-4) and one held-out pair (seed 5)."""
+    first on the squared error to the unit target and then on the coarse residual after the
+    minimal-residual step (the guard's quantity). Every form then solves the same seeded
+    right-hand side to 1e-8 from x_0 = 0: one-level RASQ, the exact two-level method, the learned
+    coarse correction (guarded, exact fallback), the network alone (no guard, no fallback), the
+    ablation (no coarse correction on the learned modes), and TF32 transforms with the exact and
+    the learned coarse level. Cases: the workload's own (nu, omega) = (1, 1e-4) and one held-out
+    pair (seed 5). A second network trained on the squared error alone (the earlier objective)
+    gives the guarded and network-only counts before the residual phase."""
     import torch
 
     w0 = workloads.CFG_LEARNED
@@ -516,49 +560,73 @@ def measure_learned(kkt_mod, dev) -> dict:
     nu_h, om_h = float(10 ** rng.uniform(-1, 1)), float(10 ** rng.uniform(-6, -2))
     cases = [w0, workloads.Workload("held-out", nx=w0.nx, ny=w0.ny, Nt=w0.Nt, n_sub=w0.n_sub, nu=nu_h, omega=om_h,
                                     target=w0.target, seed=5)]
-    net = kkt_mod.Mlp()
-    t0 = time.perf_counter()
-    st = net.train()
-    out = {"workload": f"nx=ny={w0.nx} Nt={w0.Nt} N_D={w0.n_sub}, sine-series targets",
-           "training": {"seconds": time.perf_counter() - t0, "samples": st.samples, "adam_steps": st.steps,
-                        "final_train_loss": st.final_train_loss, "val_loss": st.val_loss,
-                        "val_cosine": st.val_cosine, "modes_learned": f"k, l < {net.cfg.modes}",
-                        "width": net.cfg.width}}
+
+    def train(**over):
+        net = kkt_mod.Mlp(**over)
+        t0 = time.perf_counter()
+        st = net.train()
+        info = {"seconds": time.perf_counter() - t0, "samples": st.samples, "adam_steps": st.steps,
+                "epochs_unit_direction": net.cfg.epochs, "epochs_coarse_residual": net.cfg.resid_epochs,
+                "final_train_loss": st.final_train_loss, "val_loss": st.val_loss, "val_cosine": st.val_cosine,
+                "val_coarse_residual": st.val_resid, "val_within_guard": st.val_within_guard,
+                "modes_learned": f"k, l < {net.cfg.modes}", "width": net.cfg.width}
+        return net, info
+
+    net, info = train()
+    out = {"workload": f"nx=ny={w0.nx} Nt={w0.Nt} N_D={w0.n_sub}, sine-series targets", "training": info}
     forms = [("one_level", "fp64", "none", None), ("exact", "fp64", "exact", None),
-             ("learned", "fp64", "learned", "learned"), ("learned_ablation", "fp64", "learned", "none"),
+             ("learned", "fp64", "learned", "learned"), ("network_only", "fp64", "learned", "network"),
+             ("learned_ablation", "fp64", "learned", "none"),
              ("tf32_exact", "tf32", "exact", None), ("tf32_learned", "tf32", "learned", "learned")]
     stream = torch.cuda.current_stream()
+
+    def solve_form(w, ut, network, prec, coarse, mode):
+        s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=prec)
+        if mode is not None:
+            s.attach_mlp(network, mode)
+        s.set_options(precision=prec, coarse=coarse)
+        f = s.build_rhs(ut)
+        x = torch.zeros_like(f)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = s.solve(f, x, tol=TOL, maxit=MAXIT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        entry = {"iterations": r.iterations, "solve_ms": e0.elapsed_time(e1),
+                 "converged": r.status == kkt_mod.KKT_OK, "rel_residual": r.rel_residual}
+        if mode == "learned":
+            kept, fb = s.learned_stats()
+            entry["learned_corrections_kept"] = kept
+            entry["exact_fallbacks"] = fb
+            entry["kept_fraction"] = kept / max(kept + fb, 1)
+        elif mode == "network":
+            applied, beyond = s.learned_stats()
+            entry["network_corrections_applied"] = applied
+            entry["beyond_guard"] = beyond
+            entry["within_guard_fraction"] = 1.0 - beyond / max(applied, 1)
+        del f, x
+        s.close()
+        torch.cuda.empty_cache()
+        return entry
+
     for w in cases:
         ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
         res_case = {"nu": w.nu, "omega": w.omega}
         for name, prec, coarse, mode in forms:
-            s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision=prec)
-            if mode is not None:
-                s.attach_mlp(net, mode)
-            s.set_options(precision=prec, coarse=coarse)
-            f = s.build_rhs(ut)
-            x = torch.zeros_like(f)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = s.solve(f, x, tol=TOL, maxit=MAXIT)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            entry = {"iterations": r.iterations, "solve_ms": e0.elapsed_time(e1),
-                     "converged": r.status == kkt_mod.KKT_OK, "rel_residual": r.rel_residual}
-            if mode == "learned":
-                kept, fb = s.learned_stats()
-                entry["learned_corrections_kept"] = kept
-                entry["exact_fallbacks"] = fb
-            res_case[name] = entry
-            del f, x
-            s.close()
-            torch.cuda.empty_cache()
+            res_case[name] = solve_form(w, ut, net, prec, coarse, mode)
         base = res_case["exact"]["solve_ms"]
         res_case["time_vs_exact_fp64"] = {k: res_case[k]["solve_ms"] / base for k, *_ in forms}
         out["case_" + ("workload" if w is w0 else "held_out")] = res_case
     net.close()
+    # the same network trained on the unit-direction error alone (no coarse-residual phase)
+    net0, info0 = train(resid_epochs=0)
+    ut = torch.from_numpy(workloads.make_target(w0).ravel()).to(dev)
+    out["unit_direction_only"] = {"training": info0,
+                                  "learned": solve_form(w0, ut, net0, "fp64", "learned", "learned"),
+                                  "network_only": solve_form(w0, ut, net0, "fp64", "learned", "network")}
+    net0.close()
     return out
 
 
@@ -806,6 +874,7 @@ def run_ours(args):
     its = results[-1].iterations
     value = job_value(world, args.steps, ms / 1e3)
     launches = sum(v["launches"] for k, v in prof.items() if k != "graph")   # kernels only
+    x_solution = x.cpu().numpy() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     applies = sum(r.iterations for r in results)
     # end to end through the C ABI with host buffers: the solve from x_0 = 0 (kkt_solve_zero_guess)
     # uploads f and downloads x inside the timed region
@@ -869,9 +938,15 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_learned:
         line["learned"] = measure_learned(kkt, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s, sample = oracle_iteration_sample(w, min(its, 30) // 2 + 1)
+        kdim = min(its, 30) // 2 + 1
+        s, sample = oracle_iteration_sample(w, kdim)
         line["cpu_baseline"] = {"value": 1.0 / (s * its), "unit": "solves/s", "cores": cpu_threads(),
                                 "kind": "oracle", "sample": sample + f"; x {its} iterations"}
+        s1, why = oracle_sample_one_thread(w.omega, kdim)
+        line["cpu_baseline"]["one_thread"] = ({"value": 1.0 / (s1 * its), "unit": "solves/s", "cores": 1}
+                                              if s1 else {"unavailable": why})
+        # the timed solve's answer against the oracle's exact solution on the target's modes
+        line["rel_error_vs_exact"] = error_vs_exact(w, x_solution)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -315,14 +315,22 @@ int kkt_multidot(kkt_handle* h, const double* V, long long stride, int count, co
 int kkt_multidot_noalloc(const double* V, long long stride, int count, const double* w, long long n,
                          double* out, void* stream);
 
+/* Test hook for the reduced-precision forms' failure path, injected from the host: writes the
+ * device flag that a tensor-core transform sets when one of its bounded pipeline waits runs out
+ * (no kernel is made to wait). The next kkt_solve on the handle then returns KKT_ERR_TIMEOUT and
+ * clears the flag. KKT_ERR_INVALID_ARG on an FP64 handle. Synchronous. */
+int kkt_inject_tc_timeout(kkt_handle* h);
+
 /* ---- learned coarse correction (not in the paper) ---------------------------------------
- * A two-hidden-layer ReLU network maps a low sine mode's coarse right-hand side R_0 r
- * (normalised, 2 n_sub values) and the mode's features (log dt nu lambda, log dt/sqrt(omega))
- * to the direction of its coarse correction S_0^{-1} R_0 r; an exact one-dimensional Galerkin
- * step with the mode's coarse operator sets the magnitude, and a residual guard
- * (||c - S_0 x|| <= ||c|| / 2) falls back to the exact coarse solve. Trained on the GPU on
- * coarse solves generated by the method (restriction of seeded residual time series, exact
- * block-Thomas solve) with Adam on the squared error to the unit target. Weights BF16 for
+ * A two-hidden-layer ReLU network maps a low sine mode's coarse right-hand side c = R_0 r
+ * (Eq 14; normalised, 2 n_sub values) and the mode's features (log dt nu lambda,
+ * log dt/sqrt(omega)) to a direction d of its coarse correction S_0^{-1} R_0 r. An exact
+ * one-dimensional minimal-residual step with the mode's coarse operator G = h S_0(mu) sets the
+ * magnitude, alpha = (G d)^T c / ||G d||^2, so the correction alpha d never increases the coarse
+ * residual; a residual guard (||c - alpha G d|| <= ||c|| / 2) falls back to the exact coarse
+ * solve. Trained on the GPU on coarse solves generated by the method (restriction of seeded
+ * residual time series, exact block-Thomas solve) with Adam, first on the squared error to the
+ * unit target, then on the guard's quantity ||c - alpha G d||^2 / ||c||^2. Weights BF16 for
  * inference, FP32 accumulation; FP32 master weights for training. */
 typedef struct kkt_mlp kkt_mlp;
 
@@ -334,17 +342,20 @@ typedef struct kkt_mlp_config {
   int width;     /* hidden width */
   int seed;      /* initialisation and sampling seed */
   int samples;   /* training samples (rounded up to whole (nu, omega) draws of modes^2) */
-  int epochs;
+  int epochs;    /* epochs on the squared error to the unit target */
   int batch;
   double T;
   double nu_lo, nu_hi;        /* nu log-uniform on [nu_lo, nu_hi] */
   double omega_lo, omega_hi;  /* omega log-uniform on [omega_lo, omega_hi] */
-  double lr;                  /* Adam step (x 0.3 for the last third of the epochs) */
+  double lr;                  /* Adam step (x 0.3 for the last third of each phase's epochs) */
+  int resid_epochs;           /* then epochs on the coarse residual after the minimal-residual step */
 } kkt_mlp_config;
 
 typedef struct kkt_mlp_train_stats {
   int samples, steps;
   double final_train_loss, val_loss, val_cosine;   /* val: held-out tenth, BF16 weights */
+  double val_resid;          /* mean of ||c - alpha G d||^2 / ||c||^2 on the held-out samples */
+  double val_within_guard;   /* fraction of them the guard keeps (that ratio <= 1/4) */
 } kkt_mlp_train_stats;
 
 int kkt_mlp_default_config(kkt_mlp_config* cfg);
@@ -363,6 +374,20 @@ int kkt_mlp_forward(kkt_mlp* m, const float* X, float* Y, int batch, int use_bf1
  * NULL; *loss is written after synchronising `stream` when loss != NULL. */
 int kkt_mlp_loss_grad(kkt_mlp* m, const float* X, const float* T, int batch, float* grad, double* loss,
                       void* stream);
+/* The coarse-residual loss: loss = 1/batch sum_b ||c_b - alpha_b G(mu_b) d_b||^2 / ||c_b||^2 with
+ * d_b = net(X_b) (FP32 weights), c_b the first 2 n_sub entries of X_b, alpha_b the
+ * minimal-residual step and G(mu) the coarse operator of a mode with Jhat diagonal mu on the
+ * network's training decomposition (config Nt, n_sub; balanced split, left partition of unity).
+ * mu: device FP64 [batch]. grad and loss as for kkt_mlp_loss_grad. */
+int kkt_mlp_resid_loss_grad(kkt_mlp* m, const float* X, const double* mu, int batch, float* grad, double* loss,
+                            void* stream);
+/* The training pairs the method generates, for checking: per sample b of `count`, the mode's time
+ * series r[n * count + b] (n = 0..Nt-1, device FP64) is restricted, c_b = R_0 r_b [2 n_sub]
+ * (Eq 14), and x_b = G(mu_b)^{-1} c_b by the block-Thomas elimination of the coarse system.
+ * c, x: device FP64 [count][2 n_sub]. Allocates a scratch of 40 n_sub bytes per sample and
+ * synchronises `stream`. */
+int kkt_mlp_coarse_data(kkt_mlp* m, const double* r, const double* mu, long long count, double* c, double* x,
+                        void* stream);
 /* One Adam step (beta 0.9, 0.999, eps 1e-8) on the batch. */
 int kkt_mlp_adam_step(kkt_mlp* m, const float* X, const float* T, int batch, double lr, double* loss,
                       void* stream);
@@ -371,11 +396,14 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream);
 int kkt_mlp_save(const kkt_mlp* m, const char* path);
 kkt_mlp* kkt_mlp_load(const char* path);
 /* Use the network for coarse = KKT_COARSE_LEARNED on this handle (the handle does not own it;
- * keep it alive). mode 0: learned directions with the guard; mode 1: no coarse correction on the
- * learned modes (ablation: what the network adds). Needs 2 n_sub of the handle = the network's
- * output and modes <= min(nx, ny) - 1. */
+ * keep it alive). mode 0: the network's corrections with the guard (exact solve where the guard
+ * rejects); mode 1: no coarse correction on the learned modes (the ablation); mode 2: the
+ * network's corrections always, no guard and no exact fallback (what the network alone gives).
+ * Needs 2 n_sub of the handle = the network's output and modes <= min(nx, ny) - 1. */
 int kkt_attach_mlp(kkt_handle* h, kkt_mlp* m, int mode);
-/* Learned-mode coarse corrections kept and replaced by the exact solve since the last call. */
+/* Learned-mode coarse corrections since the last call: kept (applied) and, in mode 0, replaced
+ * by the exact solve; in mode 2 `fallback` counts the applied corrections the guard would have
+ * rejected. */
 int kkt_learned_stats(kkt_handle* h, long long* kept, long long* fallback, int reset);
 
 /* ---- batched form: many independent instances of uneven sizes ------------------------

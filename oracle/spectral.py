@@ -39,48 +39,57 @@ def dst2(block: np.ndarray, p: HeatKKT) -> np.ndarray:
     return sfft.dstn(X, type=1, axes=(1, 2), norm="ortho")
 
 
-def kkt_exact_solve(p: HeatKKT, f: np.ndarray) -> np.ndarray:
-    """x = K^{-1} f by per-mode banded solves.
+def kkt_exact_mode_solve(p: HeatKKT, lam: float, fu: np.ndarray, fz: np.ndarray, fw: np.ndarray):
+    """The exact solution's time series (u, z, w) on one sine mode with eigenvalue lam, given the
+    right-hand side's time series of that mode (each [Nt]).
 
-    Per mode (mu0 = 1 + dt nu lambda) the unknowns u_n, z_n, w_n obey
+    With mu0 = 1 + dt nu lam the unknowns u_n, z_n, w_n obey
       h u_n + mu0 w_n - w_{n+1}        = fu_n
       omega h z_n - dt w_n             = fz_n
       mu0 u_n - u_{n-1} - dt z_n       = fw_n
     z is eliminated, and (u_1, w_1, u_2, w_2, ...) is solved as a banded system.
     """
+    Nt = p.Nt
+    c = p.dt * p.dt / (p.omega * p.h)
+    nunk = 2 * Nt
+    mu0 = 1.0 + p.dt * p.nu * lam
+    ab = np.zeros((7, nunk))                      # band storage, 3 sub- and 3 super-diagonals
+    rhs = np.empty(nunk)
+
+    def put(row, col, val):
+        ab[3 + row - col, col] = val
+
+    for n in range(Nt):
+        iu, iw = 2 * n, 2 * n + 1
+        put(iu, iu, p.h)
+        put(iu, iw, mu0)
+        if n + 1 < Nt:
+            put(iu, iw + 2, -1.0)
+        rhs[iu] = fu[n]
+        put(iw, iu, mu0)
+        if n > 0:
+            put(iw, iu - 2, -1.0)
+        put(iw, iw, -c)
+        rhs[iw] = fw[n] + p.dt * fz[n] / (p.omega * p.h)
+    sol = sla.solve_banded((3, 3), ab, rhs)
+    U = sol[0::2]
+    W = sol[1::2]
+    Z = (fz + p.dt * W) / (p.omega * p.h)
+    return U, Z, W
+
+
+def kkt_exact_solve(p: HeatKKT, f: np.ndarray) -> np.ndarray:
+    """x = K^{-1} f by per-mode banded solves (kkt_exact_mode_solve on every sine mode)."""
     V, Nt = p.V, p.Nt
     fu = dst2(f[:V], p).reshape(Nt, -1)
     fz = dst2(f[V : 2 * V], p).reshape(Nt, -1)
     fw = dst2(f[2 * V :], p).reshape(Nt, -1)
     lam = mode_eigenvalues(p).ravel()
-    c = p.dt * p.dt / (p.omega * p.h)
-    nunk = 2 * Nt
     U = np.empty((Nt, lam.size))
+    Z = np.empty((Nt, lam.size))
     W = np.empty((Nt, lam.size))
     for q, lq in enumerate(lam):
-        mu0 = 1.0 + p.dt * p.nu * lq
-        ab = np.zeros((7, nunk))                      # band storage, 3 sub- and 3 super-diagonals
-        rhs = np.empty(nunk)
-
-        def put(row, col, val):
-            ab[3 + row - col, col] = val
-
-        for n in range(Nt):
-            iu, iw = 2 * n, 2 * n + 1
-            put(iu, iu, p.h)
-            put(iu, iw, mu0)
-            if n + 1 < Nt:
-                put(iu, iw + 2, -1.0)
-            rhs[iu] = fu[n, q]
-            put(iw, iu, mu0)
-            if n > 0:
-                put(iw, iu - 2, -1.0)
-            put(iw, iw, -c)
-            rhs[iw] = fw[n, q] + p.dt * fz[n, q] / (p.omega * p.h)
-        sol = sla.solve_banded((3, 3), ab, rhs)
-        U[:, q] = sol[0::2]
-        W[:, q] = sol[1::2]
-    Z = (fz + p.dt * W) / (p.omega * p.h)
+        U[:, q], Z[:, q], W[:, q] = kkt_exact_mode_solve(p, lq, fu[:, q], fz[:, q], fw[:, q])
     u = dst2(U, p).ravel()
     z = dst2(Z, p).ravel()
     w = dst2(W, p).ravel()

@@ -645,7 +645,8 @@ int kkt_coarse_apply(kkt_handle* h, const double* r, double* x0, void* stream) {
 int kkt_attach_mlp(kkt_handle* h, kkt_mlp* m, int mode) {
   KKT_TRY(check_handle(h));
   if (!m) return set_error(KKT_ERR_INVALID_ARG, "null network");
-  if (mode != 0 && mode != 1) return set_error(KKT_ERR_INVALID_ARG, "mode must be 0 (learned) or 1 (none)");
+  if (mode < 0 || mode > 2)
+    return set_error(KKT_ERR_INVALID_ARG, "mode must be 0 (learned, guarded), 1 (none) or 2 (network only)");
   int d_in = 0, width = 0, d_out = 0;
   KKT_TRY(mlp_dims(m, &d_in, &width, &d_out));
   const Geometry& g = h->g;
@@ -673,6 +674,13 @@ int kkt_attach_mlp(kkt_handle* h, kkt_mlp* m, int mode) {
   h->mlp_mode = mode;
   h->learn_k = K;
   return KKT_OK;
+}
+
+int kkt_inject_tc_timeout(kkt_handle* h) {
+  KKT_TRY(check_handle(h));
+  if (h->opt.precision == KKT_PREC_FP64 || !h->tc.err)
+    return set_error(KKT_ERR_INVALID_ARG, "the handle has no tensor-core transforms (FP64 precision)");
+  return tc_set_flag(h->tc);
 }
 
 int kkt_learned_stats(kkt_handle* h, long long* kept, long long* fallback, int reset) {

@@ -57,6 +57,36 @@ struct TimeDecomp {
   std::vector<double> P0, P1, P2;
 };
 
+// (G v)_s for one mode's coarse operator G = h S_0(mu) (Eq 14 and the operator after it): the
+// 2 x 2 diagonal block mu^2 P0 + P1 - mu P2 from the subdomain's moments mom[9 s ..] and the
+// couplings E_s = -mu a_s b_{s+1}^T with a_s = (1, phi(last owned node of s)),
+// b_{s+1} = (1, phi(first owned node of s+1)). v holds the pairs (v_{2s}, v_{2s+1}).
+template <typename TV>
+__device__ __forceinline__ void coarse_op_apply_row(const double* __restrict__ mom, const double* __restrict__ phi,
+                                                    const int* __restrict__ ofirst, const int* __restrict__ olast,
+                                                    int n_sub, double mu, double mu2, const TV* v, int s,
+                                                    double& e0, double& e1) {
+  const double* M = mom + 9 * s;
+  const double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
+  const double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
+  const double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
+  const double v0 = static_cast<double>(v[2 * s]), v1 = static_cast<double>(v[2 * s + 1]);
+  e0 = g00 * v0 + g01 * v1;
+  e1 = g01 * v0 + g11 * v1;
+  if (s + 1 < n_sub) {   // E_s v_{s+1}
+    const double a1 = __ldg(phi + __ldg(olast + s) - 1), b1 = __ldg(phi + __ldg(ofirst + s + 1) - 1);
+    const double bv = static_cast<double>(v[2 * s + 2]) + b1 * static_cast<double>(v[2 * s + 3]);
+    e0 -= mu * bv;
+    e1 -= mu * a1 * bv;
+  }
+  if (s > 0) {           // E_{s-1}^T v_{s-1}
+    const double a1 = __ldg(phi + __ldg(olast + s - 1) - 1), b1 = __ldg(phi + __ldg(ofirst + s) - 1);
+    const double av = static_cast<double>(v[2 * s - 2]) + a1 * static_cast<double>(v[2 * s - 1]);
+    e0 -= mu * av;
+    e1 -= mu * b1 * av;
+  }
+}
+
 // Device copy of TimeDecomp (one allocation).
 struct DeviceDecomp {
   int n_sub = 0, max_len = 0, Nt = 0;
@@ -116,7 +146,7 @@ struct kkt_handle {
   long long coarse_modes = 0;  // modes the coarse buffers are sized for
   // learned coarse correction
   kkt_mlp* mlp = nullptr;      // not owned
-  int mlp_mode = 0;            // 0 learned, 1 no coarse on the learned modes
+  int mlp_mode = 0;            // 0 learned with the guard, 1 no coarse on the learned modes, 2 network only
   int learn_k = 0;             // learned modes per direction
   double* learn_c = nullptr;   // [learn_k^2][2 n_sub] restricted right-hand sides
   double* learn_feat = nullptr;  // [learn_k^2][2]
@@ -230,6 +260,7 @@ int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, c
             void* out_lo = nullptr);
 int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStream_t st);   // -> x0
 int tc_check(const TcPlan& t, cudaStream_t st);
+int tc_set_flag(const TcPlan& t);   // host-side write of the timeout flag (kkt_inject_tc_timeout)
 
 // Krylov primitives (deterministic two-stage reductions; results in h->red_out on device)
 int krylov_multidot(kkt_handle* h, const double* V, long long stride, int count, const double* w,

@@ -2,15 +2,17 @@
 // low sine mode's normalised coarse right-hand side R_0 r (Eq 14) and two features of the mode
 // (log dt nu lambda, log dt / sqrt(omega)) to the direction of its coarse correction
 // S_0^{-1} R_0 r. The magnitude along that direction comes from an exact one-dimensional
-// Galerkin step with the mode's coarse operator, so the correction never increases the coarse
-// energy error; a residual guard falls back to the exact coarse solve, which stays the reference
-// the learned correction is measured against.
+// minimal-residual step with the mode's coarse operator, so the correction never increases the
+// coarse residual; a residual guard falls back to the exact coarse solve, which stays the
+// reference the learned correction is measured against.
 // FGMRES admits the resulting preconditioner because it tolerates a variable one.
 //
 // Training runs on the GPU with the kernels of this file: the coarse right-hand sides come
 // from the method's restriction of seeded residual time series, the targets from the method's
-// exact block-Thomas coarse solve, and the network is fitted with Adam on the mean squared
-// error to the unit target. All products are tiled FP32 CUDA-core GEMMs (the network is
+// exact block-Thomas coarse solve. The network is fitted with Adam in two phases: first on the
+// mean squared error to the unit target (a smooth start), then on the quantity the guard tests,
+// the squared relative coarse residual ||c - alpha G d||^2 / ||c||^2 after the minimal-residual
+// step (G = h S_0(mu) of the sample's mode), which weights the error of d by the coarse operator. All products are tiled FP32 CUDA-core GEMMs (the network is
 // about 1.6 MFLOP per mode, far below any tensor-core bound); inference reads BF16 weights
 // and accumulates in FP32.
 #include <cuda_bf16.h>
@@ -256,6 +258,75 @@ __global__ void make_xy_kernel(const double* __restrict__ c, const double* __res
   }
 }
 
+// The decomposition of the training geometry as the coarse-operator helper reads it.
+struct MlpDecomp {
+  int n_sub;
+  const int* ofirst;
+  const int* olast;
+  const double* phi;
+  const double* mom;
+};
+
+// Coarse-residual loss of a batch, one warp per sample b: d = Y row b, c = the first nc entries
+// of X row b (the normalised coarse right-hand side), G = G(mu_b):
+//   g = G d, alpha = g^T c / g^T g, r = c - alpha g, loss_b = r^T r / c^T c,
+//   dY_b = dloss_b/dd / B = -2 alpha G r / (c^T c B).
+// Lanes stride over the subdomains; r is staged in scratch[b][nc] so that every lane can read
+// its neighbours' pairs for G r (after __syncwarp, which orders the warp's memory accesses).
+__global__ void resid_grad_kernel(const float* __restrict__ Y, const float* __restrict__ X, int ldx,
+                                  const double* __restrict__ mu_arr, int B, int nc, MlpDecomp dd,
+                                  double* __restrict__ scratch, float* __restrict__ dY, float invB,
+                                  double* __restrict__ loss) {
+  const int b = static_cast<int>((static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= B) return;   // uniform per warp
+  const float* d = Y + static_cast<long long>(b) * nc;
+  const float* c = X + static_cast<long long>(b) * ldx;
+  double* R = scratch + static_cast<long long>(b) * nc;
+  const double mu = mu_arr[b], mu2 = mu * mu;
+  double gg = 0, gc = 0, cc = 0;
+  for (int s = lane; s < dd.n_sub; s += 32) {
+    double e0, e1;
+    coarse_op_apply_row(dd.mom, dd.phi, dd.ofirst, dd.olast, dd.n_sub, mu, mu2, d, s, e0, e1);
+    const double c0 = c[2 * s], c1 = c[2 * s + 1];
+    gg += e0 * e0 + e1 * e1;
+    gc += e0 * c0 + e1 * c1;
+    cc += c0 * c0 + c1 * c1;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    gg += __shfl_xor_sync(0xffffffffu, gg, o);
+    gc += __shfl_xor_sync(0xffffffffu, gc, o);
+    cc += __shfl_xor_sync(0xffffffffu, cc, o);
+  }
+  if (!(gg > 0.0) || !(cc > 0.0)) {   // d = 0 (or c = 0): loss 1, no gradient
+    if (dY)
+      for (int j = lane; j < nc; j += 32) dY[static_cast<long long>(b) * nc + j] = 0.f;
+    if (lane == 0) loss[b] = 1.0;
+    return;
+  }
+  const double alpha = gc / gg;
+  double rr = 0;
+  for (int s = lane; s < dd.n_sub; s += 32) {
+    double e0, e1;
+    coarse_op_apply_row(dd.mom, dd.phi, dd.ofirst, dd.olast, dd.n_sub, mu, mu2, d, s, e0, e1);
+    const double r0 = c[2 * s] - alpha * e0, r1 = c[2 * s + 1] - alpha * e1;
+    R[2 * s] = r0;
+    R[2 * s + 1] = r1;
+    rr += r0 * r0 + r1 * r1;
+  }
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  if (lane == 0) loss[b] = rr / cc;
+  if (!dY) return;
+  __syncwarp();
+  const double sc = -2.0 * alpha / cc * invB;
+  for (int s = lane; s < dd.n_sub; s += 32) {
+    double e0, e1;
+    coarse_op_apply_row(dd.mom, dd.phi, dd.ofirst, dd.olast, dd.n_sub, mu, mu2, R, s, e0, e1);
+    dY[static_cast<long long>(b) * nc + 2 * s] = static_cast<float>(sc * e0);
+    dY[static_cast<long long>(b) * nc + 2 * s + 1] = static_cast<float>(sc * e1);
+  }
+}
+
 }  // namespace
 }  // namespace kkt
 
@@ -278,6 +349,12 @@ struct kkt_mlp {
   float* dh1 = nullptr;
   double* part = nullptr;
   float lr = 1e-3f;
+  // the training geometry's time decomposition (left partition of unity): owned node ranges
+  // [2 n_sub] and phi [Nt] + moments [9 n_sub]
+  int* dof = nullptr;
+  double* dtab = nullptr;
+  double* rscratch = nullptr;  // coarse-residual loss: r per sample [max_batch][2 n_sub]
+  double* lossv = nullptr;     // per-sample loss [max_batch]
 };
 
 namespace kkt {
@@ -306,6 +383,10 @@ int ensure_batch(kkt_mlp* m, int B) {
   cudaFree(m->dy);
   cudaFree(m->dh2);
   cudaFree(m->dh1);
+  cudaFree(m->rscratch);
+  cudaFree(m->lossv);
+  m->rscratch = nullptr;
+  m->lossv = nullptr;
   const size_t h = static_cast<size_t>(B) * m->H, o = static_cast<size_t>(B) * m->d_out;
   KKT_CUDA_TRY(cudaMalloc(&m->a1, h * 4));
   KKT_CUDA_TRY(cudaMalloc(&m->a2, h * 4));
@@ -313,6 +394,8 @@ int ensure_batch(kkt_mlp* m, int B) {
   KKT_CUDA_TRY(cudaMalloc(&m->dy, o * 4));
   KKT_CUDA_TRY(cudaMalloc(&m->dh2, h * 4));
   KKT_CUDA_TRY(cudaMalloc(&m->dh1, h * 4));
+  KKT_CUDA_TRY(cudaMalloc(&m->rscratch, o * sizeof(double)));
+  KKT_CUDA_TRY(cudaMalloc(&m->lossv, static_cast<size_t>(B) * sizeof(double)));
   m->max_batch = B;
   return KKT_OK;
 }
@@ -338,14 +421,10 @@ int mlp_forward(kkt_mlp* m, const float* X, int B, int use_bf16, cudaStream_t st
   return KKT_OK;
 }
 
-// loss and gradients (FP32 weights) into m->g; returns the loss through *loss (synchronises)
-int mlp_loss_grad(kkt_mlp* m, const float* X, const float* T, int B, double* loss, cudaStream_t st) {
-  KKT_TRY(mlp_forward(m, X, B, 0, st));
+// Back-propagation from m->dy (= dloss/dY of the last forward pass on X) into m->g.
+int mlp_backward(kkt_mlp* m, const float* X, int B, cudaStream_t st) {
   const ParamView P = view(m->p, m), G = view(m->g, m);
-  const long long no = static_cast<long long>(B) * m->d_out, nh = static_cast<long long>(B) * m->H;
-  const unsigned gb = grid_for(no);
-  mse_grad_kernel<<<gb, 256, 0, st>>>(m->y, T, m->dy, no, 1.f / B, m->part);
-  KKT_CUDA_TRY(cudaGetLastError());
+  const long long nh = static_cast<long long>(B) * m->H;
   // layer 3: dW3 = dY^T h2, db3 = colsum dY, dh2 = dY W3 masked
   KKT_TRY((gemm<1, 1, float>(m->d_out, m->H, B, m->dy, m->d_out, m->a2, m->H, nullptr, 0, G.W3, m->H, st)));
   colsum_kernel<<<(m->d_out + 127) / 128, 128, 0, st>>>(m->dy, B, m->d_out, G.b3);
@@ -360,6 +439,17 @@ int mlp_loss_grad(kkt_mlp* m, const float* X, const float* T, int B, double* los
   KKT_TRY((gemm<1, 1, float>(m->H, m->d_in, B, m->dh1, m->H, X, m->d_in, nullptr, 0, G.W1, m->d_in, st)));
   colsum_kernel<<<(m->H + 127) / 128, 128, 0, st>>>(m->dh1, B, m->H, G.b1);
   KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+// loss and gradients (FP32 weights) into m->g; returns the loss through *loss (synchronises)
+int mlp_loss_grad(kkt_mlp* m, const float* X, const float* T, int B, double* loss, cudaStream_t st) {
+  KKT_TRY(mlp_forward(m, X, B, 0, st));
+  const long long no = static_cast<long long>(B) * m->d_out;
+  const unsigned gb = grid_for(no);
+  mse_grad_kernel<<<gb, 256, 0, st>>>(m->y, T, m->dy, no, 1.f / B, m->part);
+  KKT_CUDA_TRY(cudaGetLastError());
+  KKT_TRY(mlp_backward(m, X, B, st));
   if (loss) {
     std::vector<double> part(gb);
     KKT_CUDA_TRY(cudaMemcpyAsync(part.data(), m->part, gb * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -367,6 +457,48 @@ int mlp_loss_grad(kkt_mlp* m, const float* X, const float* T, int B, double* los
     double s = 0;
     for (double v : part) s += v;
     *loss = 0.5 * s / B;
+  }
+  return KKT_OK;
+}
+
+MlpDecomp mlp_decomp(const kkt_mlp* m) {
+  const int ns = m->cfg.n_sub;
+  return MlpDecomp{ns, m->dof, m->dof + ns, m->dtab, m->dtab + m->cfg.Nt};
+}
+
+// Coarse-residual loss of the network output Y for inputs X (rows of d_in, the first 2 n_sub
+// the normalised coarse right-hand side) and per-sample mu; with grad: dY into m->dy. *loss
+// (the batch mean) is written after synchronising st when loss != nullptr; per-sample values
+// stay in m->lossv.
+int mlp_resid_eval(kkt_mlp* m, const float* Y, const float* X, const double* mu, int B, bool grad, double* loss,
+                   cudaStream_t st) {
+  KKT_TRY(ensure_batch(m, B));
+  const int nc = m->d_out;
+  resid_grad_kernel<<<static_cast<unsigned>((32LL * B + 127) / 128), 128, 0, st>>>(
+      Y, X, m->d_in, mu, B, nc, mlp_decomp(m), m->rscratch, grad ? m->dy : nullptr, 1.f / B, m->lossv);
+  KKT_CUDA_TRY(cudaGetLastError());
+  if (loss) {
+    std::vector<double> lv(B);
+    KKT_CUDA_TRY(cudaMemcpyAsync(lv.data(), m->lossv, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KKT_CUDA_TRY(cudaStreamSynchronize(st));
+    double s = 0;
+    for (double v : lv) s += v;
+    *loss = s / B;
+  }
+  return KKT_OK;
+}
+
+int mlp_resid_loss_grad(kkt_mlp* m, const float* X, const double* mu, int B, double* loss, cudaStream_t st) {
+  KKT_TRY(mlp_forward(m, X, B, 0, st));
+  KKT_TRY(mlp_resid_eval(m, m->y, X, mu, B, true, nullptr, st));
+  KKT_TRY(mlp_backward(m, X, B, st));
+  if (loss) {
+    std::vector<double> lv(B);
+    KKT_CUDA_TRY(cudaMemcpyAsync(lv.data(), m->lossv, B * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KKT_CUDA_TRY(cudaStreamSynchronize(st));
+    double s = 0;
+    for (double v : lv) s += v;
+    *loss = s / B;
   }
   return KKT_OK;
 }
@@ -404,6 +536,50 @@ int mlp_make_input(const double* c, const double* feat, long long S, int nc, flo
   return KKT_OK;
 }
 
+// The training geometry's time decomposition (balanced split, left partition of unity, the
+// linear coarse function -1 + 2 (n - lo) / m_s on each subdomain's owned nodes, and the moment
+// matrices of (1, phi) the coarse operator's blocks are built from), uploaded to m->dof / m->dtab.
+int mlp_upload_decomp(kkt_mlp* m) {
+  const kkt_mlp_config& c = m->cfg;
+  std::vector<int> of(2 * c.n_sub);
+  std::vector<double> tab(c.Nt + 9 * c.n_sub, 0.0);
+  for (int s = 0; s < c.n_sub; ++s) {
+    const int lo = static_cast<int>(static_cast<long long>(s) * c.Nt / c.n_sub);
+    const int hi = static_cast<int>(static_cast<long long>(s + 1) * c.Nt / c.n_sub), m_s = hi - lo;
+    of[s] = lo + 1;
+    of[c.n_sub + s] = hi;
+    double p0[3] = {0, 0, 0}, p1[3] = {0, 0, 0}, p2[3] = {0, 0, 0};
+    for (int n = lo + 1; n <= hi; ++n) {
+      const double ph = -1.0 + 2.0 * (n - lo) / m_s;
+      tab[n - 1] = ph;
+      p0[0] += 1;
+      p0[1] += ph;
+      p0[2] += ph * ph;
+      if (n >= 2) {
+        p1[0] += 1;
+        p1[1] += ph;
+        p1[2] += ph * ph;
+      }
+      if (n + 1 <= hi) {
+        const double pn = -1.0 + 2.0 * (n + 1 - lo) / m_s;
+        p2[0] += 2;
+        p2[1] += ph + pn;
+        p2[2] += 2 * ph * pn;
+      }
+    }
+    for (int t = 0; t < 3; ++t) {
+      tab[c.Nt + 9 * s + t] = p0[t];
+      tab[c.Nt + 9 * s + 3 + t] = p1[t];
+      tab[c.Nt + 9 * s + 6 + t] = p2[t];
+    }
+  }
+  KKT_CUDA_TRY(cudaMalloc(&m->dof, of.size() * sizeof(int)));
+  KKT_CUDA_TRY(cudaMalloc(&m->dtab, tab.size() * sizeof(double)));
+  KKT_CUDA_TRY(cudaMemcpy(m->dof, of.data(), of.size() * sizeof(int), cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(m->dtab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return KKT_OK;
+}
+
 }  // namespace kkt
 
 using namespace kkt;
@@ -427,12 +603,13 @@ int kkt_mlp_default_config(kkt_mlp_config* c) {
   c->epochs = 30;
   c->batch = 256;
   c->lr = 1e-3;
+  c->resid_epochs = 30;
   return KKT_OK;
 }
 
 kkt_mlp* kkt_mlp_create(const kkt_mlp_config* cfg) {
   if (!cfg || cfg->n_sub < 1 || cfg->Nt / cfg->n_sub < 2 || cfg->width < 1 || cfg->modes < 1 || cfg->nx < 2 ||
-      cfg->modes > cfg->nx - 1) {
+      cfg->modes > cfg->nx - 1 || cfg->epochs < 0 || cfg->resid_epochs < 0) {
     set_error(KKT_ERR_INVALID_ARG, "invalid network configuration");
     return nullptr;
   }
@@ -463,7 +640,7 @@ kkt_mlp* kkt_mlp_create(const kkt_mlp_config* cfg) {
   for (long long i = 0; i < static_cast<long long>(m->d_out) * m->H; ++i) P.W3[i] = static_cast<float>(nd(rng) * std::sqrt(2.0 / m->H));
   if (cudaMemcpy(m->p, h.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(m->m, 0, n * 4) != cudaSuccess || cudaMemset(m->v, 0, n * 4) != cudaSuccess ||
-      mlp_refresh_bf16(m, nullptr) < 0 || cudaDeviceSynchronize() != cudaSuccess) {
+      mlp_refresh_bf16(m, nullptr) < 0 || mlp_upload_decomp(m) < 0 || cudaDeviceSynchronize() != cudaSuccess) {
     set_error(KKT_ERR_CUDA, "network initialisation failed");
     kkt_mlp_destroy(m);
     return nullptr;
@@ -485,6 +662,10 @@ void kkt_mlp_destroy(kkt_mlp* m) {
   cudaFree(m->dh2);
   cudaFree(m->dh1);
   cudaFree(m->part);
+  cudaFree(m->dof);
+  cudaFree(m->dtab);
+  cudaFree(m->rscratch);
+  cudaFree(m->lossv);
   delete m;
 }
 
@@ -538,6 +719,32 @@ int kkt_mlp_adam_step(kkt_mlp* m, const float* X, const float* T, int batch, dou
   return mlp_refresh_bf16(m, st);
 }
 
+int kkt_mlp_resid_loss_grad(kkt_mlp* m, const float* X, const double* mu, int batch, float* grad, double* loss,
+                            void* stream) {
+  if (!m || !X || !mu || batch < 1) return set_error(KKT_ERR_INVALID_ARG, "invalid gradient arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  KKT_TRY(mlp_resid_loss_grad(m, X, mu, batch, loss, st));
+  if (grad) KKT_CUDA_TRY(cudaMemcpyAsync(grad, m->g, m->nparam * 4, cudaMemcpyDeviceToDevice, st));
+  return KKT_OK;
+}
+
+int kkt_mlp_coarse_data(kkt_mlp* m, const double* r, const double* mu, long long count, double* c, double* x,
+                        void* stream) {
+  if (!m || !r || !mu || !c || !x || count < 1) return set_error(KKT_ERR_INVALID_ARG, "invalid coarse-data arguments");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const kkt_mlp_config& cf = m->cfg;
+  double* w = nullptr;
+  KKT_CUDA_TRY(cudaMalloc(&w, static_cast<size_t>(count) * 5 * cf.n_sub * sizeof(double)));
+  DecompView dv{cf.n_sub, cf.Nt, m->dof, m->dof + cf.n_sub, m->dtab, m->dtab + cf.Nt};
+  coarse_data_kernel<<<static_cast<unsigned>((count + 127) / 128), 128, 0, st>>>(r, mu, count, dv, c, x, w);
+  const cudaError_t e1 = cudaGetLastError();
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  cudaFree(w);
+  KKT_CUDA_TRY(e1);
+  KKT_CUDA_TRY(e2);
+  return KKT_OK;
+}
+
 int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
   if (!m) return set_error(KKT_ERR_INVALID_ARG, "null network");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -546,44 +753,6 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
   const int per = K * K;                           // samples per (nu, omega) draw
   const int draws = std::max(1, (c.samples + per - 1) / per);
   const long long S = static_cast<long long>(draws) * per;
-  // time decomposition of the training geometry (left partition of unity)
-  TimeDecomp td;
-  {
-    std::vector<long long> b(c.n_sub + 1);
-    for (int s = 0; s <= c.n_sub; ++s) b[s] = static_cast<long long>(s) * c.Nt / c.n_sub;
-    td.n_sub = c.n_sub;
-    td.owner.assign(c.Nt, 0);
-    td.phi.assign(c.Nt, 0.0);
-    for (int s = 0; s < c.n_sub; ++s) {
-      const int lo = static_cast<int>(b[s]), hi = static_cast<int>(b[s + 1]), m_s = hi - lo;
-      td.ofirst.push_back(lo + 1);
-      td.olast.push_back(hi);
-      double p0[3] = {0, 0, 0}, p1[3] = {0, 0, 0}, p2[3] = {0, 0, 0};
-      for (int n = lo + 1; n <= hi; ++n) {
-        const double ph = -1.0 + 2.0 * (n - lo) / m_s;
-        td.phi[n - 1] = ph;
-        p0[0] += 1;
-        p0[1] += ph;
-        p0[2] += ph * ph;
-        if (n >= 2) {
-          p1[0] += 1;
-          p1[1] += ph;
-          p1[2] += ph * ph;
-        }
-        if (n + 1 <= hi) {
-          const double pn = -1.0 + 2.0 * (n + 1 - lo) / m_s;
-          p2[0] += 2;
-          p2[1] += ph + pn;
-          p2[2] += 2 * ph * pn;
-        }
-      }
-      for (int t = 0; t < 3; ++t) {
-        td.P0.push_back(p0[t]);
-        td.P1.push_back(p1[t]);
-        td.P2.push_back(p2[t]);
-      }
-    }
-  }
   // seeded samples: (nu, omega) log-uniform, modes k, l < K of the nx grid, residual time series
   std::mt19937_64 rng(static_cast<unsigned long long>(c.seed) * 7919ULL + 17ULL);
   std::uniform_real_distribution<double> uni(0.0, 1.0);
@@ -618,8 +787,6 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
   // device buffers
   double *d_r = nullptr, *d_mu = nullptr, *d_feat = nullptr, *d_c = nullptr, *d_x = nullptr, *d_w = nullptr;
   float *X = nullptr, *Tt = nullptr;
-  int *dof = nullptr;
-  double* dtab = nullptr;
   auto cleanup = [&]() {
     cudaFree(d_r);
     cudaFree(d_mu);
@@ -629,8 +796,6 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
     cudaFree(d_w);
     cudaFree(X);
     cudaFree(Tt);
-    cudaFree(dof);
-    cudaFree(dtab);
   };
   auto fail = [&](const char* what) {
     cudaGetLastError();
@@ -639,27 +804,13 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
   };
   if (cudaMalloc(&d_r, r.size() * 8) || cudaMalloc(&d_mu, S * 8) || cudaMalloc(&d_feat, 2 * S * 8) ||
       cudaMalloc(&d_c, S * nc * 8) || cudaMalloc(&d_x, S * nc * 8) || cudaMalloc(&d_w, S * 5LL * c.n_sub * 8) ||
-      cudaMalloc(&X, S * (nc + 2) * 4) || cudaMalloc(&Tt, S * nc * 4) || cudaMalloc(&dof, 2 * c.n_sub * 4) ||
-      cudaMalloc(&dtab, (c.Nt + 9 * c.n_sub) * 8))
+      cudaMalloc(&X, S * (nc + 2) * 4) || cudaMalloc(&Tt, S * nc * 4))
     return fail("allocation");
-  std::vector<int> of(2 * c.n_sub);
-  std::copy(td.ofirst.begin(), td.ofirst.end(), of.begin());
-  std::copy(td.olast.begin(), td.olast.end(), of.begin() + c.n_sub);
-  std::vector<double> tab(c.Nt + 9 * c.n_sub);
-  std::copy(td.phi.begin(), td.phi.end(), tab.begin());
-  for (int s = 0; s < c.n_sub; ++s)
-    for (int t = 0; t < 3; ++t) {
-      tab[c.Nt + 9 * s + t] = td.P0[3 * s + t];
-      tab[c.Nt + 9 * s + 3 + t] = td.P1[3 * s + t];
-      tab[c.Nt + 9 * s + 6 + t] = td.P2[3 * s + t];
-    }
   if (cudaMemcpy(d_r, r.data(), r.size() * 8, cudaMemcpyHostToDevice) ||
       cudaMemcpy(d_mu, mu.data(), S * 8, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(d_feat, feat.data(), 2 * S * 8, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(dof, of.data(), of.size() * 4, cudaMemcpyHostToDevice) ||
-      cudaMemcpy(dtab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice))
+      cudaMemcpy(d_feat, feat.data(), 2 * S * 8, cudaMemcpyHostToDevice))
     return fail("upload");
-  DecompView dv{c.n_sub, c.Nt, dof, dof + c.n_sub, dtab, dtab + c.Nt};
+  DecompView dv{c.n_sub, c.Nt, m->dof, m->dof + c.n_sub, m->dtab, m->dtab + c.Nt};
   coarse_data_kernel<<<static_cast<unsigned>((S + 127) / 128), 128, 0, st>>>(d_r, d_mu, S, dv, d_c, d_x, d_w);
   make_xy_kernel<<<static_cast<unsigned>((S * 32 + 255) / 256), 256, 0, st>>>(d_c, d_x, d_feat, S, nc, X, Tt);
   if (cudaGetLastError() != cudaSuccess) return fail("sample generation");
@@ -670,13 +821,21 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
   for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<long long>(i) * B;
   double last = 0.0;
   int steps = 0;
-  for (int ep = 0; ep < c.epochs; ++ep) {
+  // phase 1: squared error to the unit target; phase 2: the coarse residual after the
+  // minimal-residual step (the guard's quantity). Each phase steps at lr for its first two
+  // thirds and at 0.3 lr after.
+  const int total = c.epochs + c.resid_epochs;
+  for (int ep = 0; ep < total; ++ep) {
+    const bool resid = ep >= c.epochs;
+    const int e_in = resid ? ep - c.epochs : ep, e_len = resid ? c.resid_epochs : c.epochs;
     std::shuffle(order.begin(), order.end(), rng);
-    const float lr = static_cast<float>(c.lr * (ep < c.epochs * 2 / 3 ? 1.0 : 0.3));
+    const float lr = static_cast<float>(c.lr * (e_in < e_len * 2 / 3 ? 1.0 : 0.3));
     for (size_t bi = 0; bi < order.size(); ++bi) {
       const long long o = order[bi];
       double* lp = (bi + 1 == order.size()) ? &last : nullptr;
-      if (mlp_loss_grad(m, X + o * (nc + 2), Tt + o * nc, B, lp, st) < 0 || mlp_adam(m, lr, st) < 0) {
+      const int rc = resid ? mlp_resid_loss_grad(m, X + o * (nc + 2), d_mu + o, B, lp, st)
+                           : mlp_loss_grad(m, X + o * (nc + 2), Tt + o * nc, B, lp, st);
+      if (rc < 0 || mlp_adam(m, lr, st) < 0) {
         const std::string msg = kkt_last_error();
         cleanup();
         return set_error(KKT_ERR_CUDA, "network training step: " + msg);
@@ -685,14 +844,21 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
     }
   }
   mlp_refresh_bf16(m, st);
-  // validation: mean cosine between prediction and target on the held-out samples (BF16 weights)
+  // validation on the held-out samples with the BF16 weights the preconditioner uses: mean
+  // cosine to the unit target, and the coarse residual after the minimal-residual step (its mean
+  // and the fraction within the guard's bound ||c - alpha G d||^2 <= ||c||^2 / 4)
   const long long nval = S - ntrain;
-  double cos_sum = 0.0, val_loss = 0.0;
+  double cos_sum = 0.0, val_loss = 0.0, res_sum = 0.0;
+  long long within = 0;
   if (nval > 0) {
     std::vector<float> yv(static_cast<size_t>(nval) * nc), tv(static_cast<size_t>(nval) * nc);
-    if (mlp_forward(m, X + ntrain * (nc + 2), static_cast<int>(nval), 1, st) < 0) return fail("validation");
+    std::vector<double> lv(nval);
+    if (mlp_forward(m, X + ntrain * (nc + 2), static_cast<int>(nval), 1, st) < 0 ||
+        mlp_resid_eval(m, m->y, X + ntrain * (nc + 2), d_mu + ntrain, static_cast<int>(nval), false, nullptr, st) < 0)
+      return fail("validation");
     cudaMemcpyAsync(yv.data(), m->y, yv.size() * 4, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(tv.data(), Tt + ntrain * nc, tv.size() * 4, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(lv.data(), m->lossv, lv.size() * 8, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
     for (long long i = 0; i < nval; ++i) {
       double dot = 0, yy = 0, e = 0;
@@ -704,6 +870,8 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
       }
       cos_sum += yy > 0 ? dot / std::sqrt(yy) : 0.0;
       val_loss += 0.5 * e;
+      res_sum += lv[i];
+      within += lv[i] <= 0.25 ? 1 : 0;
     }
   }
   cleanup();
@@ -714,6 +882,8 @@ int kkt_mlp_train(kkt_mlp* m, kkt_mlp_train_stats* stats, void* stream) {
     stats->final_train_loss = last;
     stats->val_loss = nval > 0 ? val_loss / nval : 0.0;
     stats->val_cosine = nval > 0 ? cos_sum / nval : 0.0;
+    stats->val_resid = nval > 0 ? res_sum / nval : 0.0;
+    stats->val_within_guard = nval > 0 ? static_cast<double>(within) / nval : 0.0;
   }
   return KKT_OK;
 }
@@ -724,7 +894,7 @@ int kkt_mlp_save(const kkt_mlp* m, const char* path) {
   KKT_CUDA_TRY(cudaMemcpy(h.data(), m->p, h.size() * 4, cudaMemcpyDeviceToHost));
   FILE* f = std::fopen(path, "wb");
   if (!f) return set_error(KKT_ERR_INVALID_ARG, std::string("cannot open ") + path);
-  const char magic[8] = {'K', 'K', 'T', 'M', 'L', 'P', '0', '1'};
+  const char magic[8] = {'K', 'K', 'T', 'M', 'L', 'P', '0', '2'};
   bool ok = std::fwrite(magic, 1, 8, f) == 8 && std::fwrite(&m->cfg, sizeof(kkt_mlp_config), 1, f) == 1 &&
             std::fwrite(&m->nparam, sizeof(long long), 1, f) == 1 && std::fwrite(h.data(), 4, h.size(), f) == h.size();
   std::fclose(f);
@@ -740,7 +910,7 @@ kkt_mlp* kkt_mlp_load(const char* path) {
   char magic[8];
   kkt_mlp_config cfg;
   long long n = 0;
-  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "KKTMLP01", 8) == 0 &&
+  bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "KKTMLP02", 8) == 0 &&
             std::fread(&cfg, sizeof(cfg), 1, f) == 1 && std::fread(&n, sizeof(n), 1, f) == 1;
   kkt_mlp* m = ok ? kkt_mlp_create(&cfg) : nullptr;
   if (m && n == m->nparam) {

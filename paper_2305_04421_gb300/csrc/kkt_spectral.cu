@@ -626,38 +626,17 @@ __global__ void __launch_bounds__(kCrThreads) coarse_crf_kernel(const TI* __rest
   coarse_crf_body<TI>(rhat, in_scale, p, mpc, blockIdx.x, cc, cr_sm);
 }
 
-// Learned coarse correction of one mode: the network's direction d, scaled by the Galerkin
-// condition alpha = d^T c / d^T G d on the mode's coarse operator G = h S_0(mu), is kept when
-// its coarse residual satisfies ||c - alpha G d||^2 <= ||c||^2 / 4, else the exact solve's
-// result stays. One warp per learned mode: lanes stride over the subdomains (coalesced reads
-// of d and c) and the four sums are reduced with shuffles.
+// Learned coarse correction of one mode: the network's direction d, scaled by the
+// minimal-residual step alpha = (G d)^T c / ||G d||^2 on the mode's coarse operator G = h S_0(mu)
+// (the scale that minimises the coarse residual along d, the quantity training minimises).
+// mode 0: kept when ||c - alpha G d||^2 <= ||c||^2 / 4, else the exact solve's result stays;
+// mode 1: no coarse correction on the learned modes (the ablation); mode 2: always kept (the
+// network alone; counts[1] then tallies the corrections the guard would have rejected). One
+// warp per learned mode: lanes stride over the subdomains (coalesced reads of d and c) and the
+// sums are reduced with shuffles.
 __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
-}
-
-// (G d)_s for the block-tridiagonal G (2 x 2 blocks mu^2 P0 + P1 - mu P2, couplings -mu a b^T)
-__device__ __forceinline__ void coarse_op_row(const SpecParams& p, double mu, double mu2, const float* __restrict__ d,
-                                              int s, double& e0, double& e1) {
-  const double* M = p.mom + 9 * s;
-  const double g00 = fma(mu2, M[0], M[3]) - mu * M[6];
-  const double g01 = fma(mu2, M[1], M[4]) - mu * M[7];
-  const double g11 = fma(mu2, M[2], M[5]) - mu * M[8];
-  const double d0 = d[2 * s], d1 = d[2 * s + 1];
-  e0 = g00 * d0 + g01 * d1;
-  e1 = g01 * d0 + g11 * d1;
-  if (s + 1 < p.n_sub) {   // E_s d_{s+1}, E_s = -mu a_s b_{s+1}^T
-    const double a1 = __ldg(p.phi + __ldg(p.olast + s) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s + 1) - 1);
-    const double bd = d[2 * s + 2] + b1 * d[2 * s + 3];
-    e0 -= mu * bd;
-    e1 -= mu * a1 * bd;
-  }
-  if (s > 0) {             // E_{s-1}^T d_{s-1} = -mu b_s (a_{s-1}^T d_{s-1})
-    const double a1 = __ldg(p.phi + __ldg(p.olast + s - 1) - 1), b1 = __ldg(p.phi + __ldg(p.ofirst + s) - 1);
-    const double ad = d[2 * s - 2] + a1 * d[2 * s - 1];
-    e0 -= mu * ad;
-    e1 -= mu * b1 * ad;
-  }
 }
 
 __global__ void learned_apply_kernel(SpecParams p, const float* __restrict__ y, int mode, double* __restrict__ cc,
@@ -678,31 +657,32 @@ __global__ void learned_apply_kernel(SpecParams p, const float* __restrict__ y, 
   const double mu = mode_mu(p, q), mu2 = mu * mu;
   const float* d = y + static_cast<long long>(w) * 2 * p.n_sub;
   const double* c = p.learn_c + static_cast<long long>(w) * 2 * p.n_sub;
-  double dGd = 0, dc = 0, cc2 = 0;
+  double gg = 0, gc = 0, cc2 = 0;
   for (int s = lane; s < p.n_sub; s += 32) {
     double e0, e1;
-    coarse_op_row(p, mu, mu2, d, s, e0, e1);
-    dGd += d[2 * s] * e0 + d[2 * s + 1] * e1;
-    dc += d[2 * s] * c[2 * s] + d[2 * s + 1] * c[2 * s + 1];
+    coarse_op_apply_row(p.mom, p.phi, p.ofirst, p.olast, p.n_sub, mu, mu2, d, s, e0, e1);
+    gg += e0 * e0 + e1 * e1;
+    gc += e0 * c[2 * s] + e1 * c[2 * s + 1];
     cc2 += c[2 * s] * c[2 * s] + c[2 * s + 1] * c[2 * s + 1];
   }
-  dGd = warp_sum_d(dGd);
-  dc = warp_sum_d(dc);
+  gg = warp_sum_d(gg);
+  gc = warp_sum_d(gc);
   cc2 = warp_sum_d(cc2);
-  if (!(dGd > 0.0)) {
-    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
-    return;
+  const bool degenerate = !(gg > 0.0);
+  const double alpha = degenerate ? 0.0 : gc / gg;
+  double res2 = cc2;
+  if (!degenerate) {
+    res2 = 0;
+    for (int s = lane; s < p.n_sub; s += 32) {
+      double e0, e1;
+      coarse_op_apply_row(p.mom, p.phi, p.ofirst, p.olast, p.n_sub, mu, mu2, d, s, e0, e1);
+      const double r0 = c[2 * s] - alpha * e0, r1 = c[2 * s + 1] - alpha * e1;
+      res2 += r0 * r0 + r1 * r1;
+    }
+    res2 = warp_sum_d(res2);
   }
-  const double alpha = dc / dGd;
-  double res2 = 0;
-  for (int s = lane; s < p.n_sub; s += 32) {
-    double e0, e1;
-    coarse_op_row(p, mu, mu2, d, s, e0, e1);
-    const double r0 = c[2 * s] - alpha * e0, r1 = c[2 * s + 1] - alpha * e1;
-    res2 += r0 * r0 + r1 * r1;
-  }
-  res2 = warp_sum_d(res2);
-  if (res2 > 0.25 * cc2) {
+  const bool guard_ok = !degenerate && res2 <= 0.25 * cc2;
+  if (mode == 0 && !guard_ok) {
     if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
     return;
   }
@@ -710,7 +690,10 @@ __global__ void learned_apply_kernel(SpecParams p, const float* __restrict__ y, 
     cc[(2LL * s) * N + q] = p.h * alpha * d[2 * s];
     cc[(2LL * s + 1) * N + q] = p.h * alpha * d[2 * s + 1];
   }
-  if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(counts), 1ull);
+  if (lane == 0) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(counts), 1ull);
+    if (!guard_ok) atomicAdd(reinterpret_cast<unsigned long long*>(counts + 1), 1ull);
+  }
 }
 
 // x_0 at node n (1-based), given the coarse pairs of the three subdomains around s.

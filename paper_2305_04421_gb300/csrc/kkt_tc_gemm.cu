@@ -803,11 +803,22 @@ int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStre
   return KKT_OK;
 }
 
+// Reads (and clears) the pipeline-timeout flag the transform kernels set when a bounded
+// mbarrier wait ran out; a set flag is reported once as KKT_ERR_TIMEOUT.
 int tc_check(const TcPlan& t, cudaStream_t st) {
   int e = 0;
   KKT_CUDA_TRY(cudaMemcpyAsync(&e, t.err, sizeof(int), cudaMemcpyDeviceToHost, st));
   KKT_CUDA_TRY(cudaStreamSynchronize(st));
-  if (e) return set_error(KKT_ERR_TIMEOUT, "a tensor-core transform timed out waiting on its pipeline");
+  if (e) {
+    KKT_CUDA_TRY(cudaMemsetAsync(t.err, 0, sizeof(int), st));
+    return set_error(KKT_ERR_TIMEOUT, "a tensor-core transform timed out waiting on its pipeline");
+  }
+  return KKT_OK;
+}
+
+int tc_set_flag(const TcPlan& t) {
+  const int one = 1;
+  KKT_CUDA_TRY(cudaMemcpy(t.err, &one, sizeof(int), cudaMemcpyHostToDevice));
   return KKT_OK;
 }
 

@@ -38,6 +38,7 @@ LOCAL = {"rasq": 0, "ras": 1}
 COARSE_SOLVE = {"auto": 0, "thomas": 1, "cyclic": 2}
 STAGING = {"auto": 0, "copy_engine": 1}
 DST_METHOD = {"auto": 0, "tiles": 1, "lane": 2}
+MLP_MODE = {"learned": 0, "none": 1, "network": 2}
 HISTORY_MAX = 1024
 
 
@@ -97,12 +98,14 @@ class KKTMlpConfig(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("Nt", ctypes.c_int), ("n_sub", ctypes.c_int), ("modes", ctypes.c_int),
                 ("width", ctypes.c_int), ("seed", ctypes.c_int), ("samples", ctypes.c_int), ("epochs", ctypes.c_int),
                 ("batch", ctypes.c_int), ("T", ctypes.c_double), ("nu_lo", ctypes.c_double), ("nu_hi", ctypes.c_double),
-                ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double), ("lr", ctypes.c_double)]
+                ("omega_lo", ctypes.c_double), ("omega_hi", ctypes.c_double), ("lr", ctypes.c_double),
+                ("resid_epochs", ctypes.c_int)]
 
 
 class KKTMlpTrainStats(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_int), ("steps", ctypes.c_int), ("final_train_loss", ctypes.c_double),
-                ("val_loss", ctypes.c_double), ("val_cosine", ctypes.c_double)]
+                ("val_loss", ctypes.c_double), ("val_cosine", ctypes.c_double), ("val_resid", ctypes.c_double),
+                ("val_within_guard", ctypes.c_double)]
 
 
 class KKTError(RuntimeError):
@@ -147,11 +150,14 @@ SIGNATURES = [
     ("kkt_mlp_get_params", _I, [_P, _P, ctypes.c_longlong]),
     ("kkt_mlp_forward", _I, [_P, _P, _P, _I, _I, _P]),
     ("kkt_mlp_loss_grad", _I, [_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    ("kkt_mlp_resid_loss_grad", _I, [_P, _P, _P, _I, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    ("kkt_mlp_coarse_data", _I, [_P, _P, _P, ctypes.c_longlong, _P, _P, _P]),
     ("kkt_mlp_adam_step", _I, [_P, _P, _P, _I, _D, ctypes.POINTER(ctypes.c_double), _P]),
     ("kkt_mlp_train", _I, [_P, ctypes.POINTER(KKTMlpTrainStats), _P]),
     ("kkt_mlp_save", _I, [_P, ctypes.c_char_p]),
     ("kkt_mlp_load", _P, [ctypes.c_char_p]),
     ("kkt_attach_mlp", _I, [_P, _P, _I]),
+    ("kkt_inject_tc_timeout", _I, [_P]),
     ("kkt_learned_stats", _I, [_P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _I]),
     ("kkt_batch_create", _P, [_I, ctypes.POINTER(KKTInstance), ctypes.POINTER(KKTOptions)]),
     ("kkt_batch_destroy", None, [_P]),
@@ -405,6 +411,24 @@ class Mlp:
                                                 _stream(stream)))
         return loss.value, g
 
+    def resid_loss_grad(self, X, mu, stream=None):
+        """Coarse-residual loss of net(X) and its parameter gradient; mu: float64 [batch]."""
+        g = torch.empty(self.nparam, dtype=torch.float32, device=X.device)
+        loss = ctypes.c_double()
+        _check(load_library().kkt_mlp_resid_loss_grad(self.m, _fptr(X), _ptr(mu), X.shape[0], _fptr(g),
+                                                      ctypes.byref(loss), _stream(stream)))
+        return loss.value, g
+
+    def coarse_data(self, r, mu, stream=None):
+        """Training pairs: r float64 [Nt][count] time series, mu float64 [count] ->
+        (c = R_0 r, x = G(mu)^-1 c), each float64 [count][2 n_sub]."""
+        count = mu.shape[0]
+        c = torch.empty((count, self._d_out()), dtype=torch.float64, device=r.device)
+        x = torch.empty_like(c)
+        _check(load_library().kkt_mlp_coarse_data(self.m, _ptr(r), _ptr(mu), count, _ptr(c), _ptr(x),
+                                                  _stream(stream)))
+        return c, x
+
     def adam_step(self, X, T, lr, stream=None):
         loss = ctypes.c_double()
         _check(load_library().kkt_mlp_adam_step(self.m, _fptr(X), _fptr(T), X.shape[0], lr, ctypes.byref(loss),
@@ -531,9 +555,11 @@ class Solver:
         return y
 
     def attach_mlp(self, mlp: "Mlp", mode: str = "learned"):
-        """Use `mlp` for coarse='learned' (mode 'learned'), or no coarse correction on the learned
-        modes (mode 'none', the ablation); then switch the options to coarse='learned'."""
-        _check(load_library().kkt_attach_mlp(self.h, mlp.m, 0 if mode == "learned" else 1))
+        """Use `mlp` for coarse='learned': mode 'learned' (the network's corrections, guarded,
+        exact solve where the guard rejects), 'none' (no coarse correction on the learned modes,
+        the ablation) or 'network' (the network's corrections always, no guard or fallback);
+        then switch the options to coarse='learned'."""
+        _check(load_library().kkt_attach_mlp(self.h, mlp.m, MLP_MODE[mode]))
         self._mlp = mlp
 
     def learned_stats(self, reset=False):

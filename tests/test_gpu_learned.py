@@ -83,6 +83,51 @@ def test_forward_gradients_and_adam_match_reference(kkt):
         assert rel(got[k], params[k]) < 1e-5, k
 
 
+def test_coarse_residual_loss_and_gradients_match_reference(kkt):
+    """The guard's quantity as a training loss: ||c - alpha G d||^2 / ||c||^2 with the
+    minimal-residual alpha, per sample mu, on the network's own decomposition (Nt = 16,
+    N_D = 4); loss and every parameter gradient against the FP64 reference."""
+    net = small_net(kkt)
+    nc = 2 * net.cfg.n_sub
+    params = ref.init_params(nc + 2, net.cfg.width, nc, seed=12)
+    rng = np.random.default_rng(21)
+    for k in ("b1", "b2", "b3"):
+        params[k] = 0.1 * rng.standard_normal(params[k].shape)
+    params = {k: v.astype(np.float32).astype(np.float64) for k, v in params.items()}
+    net.set_params(flat(params))
+    B = 29
+    C = rng.standard_normal((B, nc))
+    C /= np.linalg.norm(C, axis=1, keepdims=True)
+    X = np.concatenate([C, rng.standard_normal((B, 2))], axis=1).astype(np.float32)
+    mu = 1.0 + rng.uniform(0.01, 3.0, B)
+    loss, g = net.resid_loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(mu).cuda())
+    Y, cache = ref.forward(params, X.astype(np.float64))
+    G = [ref.coarse_operator(float(m), net.cfg.Nt, net.cfg.n_sub) for m in mu]
+    want, dY = ref.coarse_residual_loss(Y, X[:, :nc].astype(np.float64), G)
+    np.testing.assert_allclose(loss, want, rtol=1e-5)
+    gref = ref.backward_from(params, cache, dY)
+    gg = unflat(g.cpu().numpy(), params)
+    for k in ORDER:
+        assert rel(gg[k], gref[k]) < 1e-4, k
+
+
+def test_training_pairs_match_reference(kkt):
+    """The coarse right-hand sides R_0 r and exact coarse solutions the network is trained on,
+    generated by the GPU's restriction and block-Thomas elimination, against the reference's
+    restriction matrix and dense solve (ragged split: Nt = 30, N_D = 7), element by element."""
+    net = small_net(kkt, nx=16, Nt=30, n_sub=7, modes=4)
+    rng = np.random.default_rng(9)
+    count = 50
+    r = rng.standard_normal((30, count))
+    mu = 1.0 + np.concatenate([rng.uniform(0.005, 0.05, count // 2), rng.uniform(0.05, 6.0, count - count // 2)])
+    c, x = net.coarse_data(torch.from_numpy(r).cuda(), torch.from_numpy(mu).cuda())
+    c, x = c.cpu().numpy(), x.cpu().numpy()
+    C, Xr = ref.coarse_data(r, mu, 30, 7)
+    for b in range(count):
+        np.testing.assert_allclose(c[b], C[b], rtol=0, atol=1e-13 * np.abs(C[b]).max())
+        np.testing.assert_allclose(x[b], Xr[b], rtol=0, atol=1e-10 * np.abs(Xr[b]).max())
+
+
 def test_save_and_load_round_trip(kkt, tmp_path):
     net = small_net(kkt, seed=5)
     path = str(tmp_path / "net.bin")
@@ -98,7 +143,8 @@ def _solve_counts(kkt, w, net):
     fd = torch.from_numpy(f).cuda()
     its = {}
     for name, coarse, mode in [("exact", "exact", None), ("one-level", "none", None),
-                               ("learned", "learned", "learned"), ("without-network", "learned", "none")]:
+                               ("learned", "learned", "learned"), ("without-network", "learned", "none"),
+                               ("network-only", "learned", "network")]:
         s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
         if mode is not None:
             s.attach_mlp(net, mode)
@@ -108,6 +154,8 @@ def _solve_counts(kkt, w, net):
         its[name] = res.iterations
         if name == "learned":
             its["kept"], its["fallback"] = s.learned_stats()
+        if name == "network-only":
+            its["net_applied"], its["net_beyond_guard"] = s.learned_stats()
     return its
 
 
@@ -122,13 +170,17 @@ def trained(kkt):
 
 
 def test_trained_network_reduces_iterations(kkt, trained):
-    """Solve with the exact coarse solve, none, the learned correction, and the learned modes
-    left without coarse correction: the network must beat its own ablation."""
+    """Solve with the exact coarse solve, none, the learned correction (guarded), the network's
+    corrections alone (no guard, no exact fallback), and the learned modes left without coarse
+    correction: the network alone must beat that ablation, so the gain is the network's and not
+    the exact solve's."""
     w, net, st = trained
     assert st.val_cosine > 0.8, st.val_cosine
     its = _solve_counts(kkt, w, net)
     assert its["kept"] > 0
+    assert its["net_applied"] > 0
     assert its["learned"] < its["without-network"], its
+    assert its["network-only"] < its["without-network"], its
     assert its["exact"] <= its["learned"], its
 
 

@@ -162,3 +162,23 @@ def test_mixed_solve_converges_on_a_large_grid(kkt, prec):
     bound = a.iterations + 2 if prec == "tf32" else int(1.5 * a.iterations) + 2
     assert b.iterations <= bound
     assert float(torch.linalg.vector_norm(b.x - a.x) / torch.linalg.vector_norm(a.x)) < 1e-6
+
+
+def test_pipeline_timeout_flag_is_reported_and_cleared(kkt):
+    """The tensor-core transforms' timeout path, injected from the host (the device flag a
+    bounded pipeline wait sets when it runs out; no kernel is made to wait): the next solve
+    returns KKT_ERR_TIMEOUT, and the one after it, with the flag cleared, converges."""
+    w = workloads.Workload("t", nx=32, ny=32, Nt=32, n_sub=4, omega=1e-4)
+    s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, precision="tf32")
+    ut = torch.from_numpy(workloads.make_target(w).ravel()).cuda()
+    f = s.build_rhs(ut)
+    kkt.load_library().kkt_inject_tc_timeout(s.h)
+    with pytest.raises(kkt.KKTError) as ei:
+        s.solve(f, tol=1e-8, maxit=100)
+    assert ei.value.status == kkt.KKT_ERR_TIMEOUT
+    res = s.solve(f, tol=1e-8, maxit=100)
+    assert res.status == kkt.KKT_OK
+    s.close()
+    fp64 = kkt.Solver(8, 8, 8, 1.0, 1.0, 1e-3, 2)
+    assert kkt.load_library().kkt_inject_tc_timeout(fp64.h) == kkt.KKT_ERR_INVALID_ARG
+    fp64.close()

@@ -34,6 +34,21 @@ def rel(a, b):
     return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300)
 
 
+def close(got, want, tol, n_slices):
+    """Norm-wise relative error below tol, and element by element per time slice: each slice's
+    largest error below tol times the larger of that slice's largest value and 1e-3 of the
+    whole output's (so an error confined to a few small entries or slices cannot hide under
+    the norm of the rest)."""
+    got, want = np.asarray(got), np.asarray(want)
+    assert rel(got, want) < tol
+    g = got.reshape(n_slices, -1)
+    w = want.reshape(n_slices, -1)
+    err = np.abs(g - w).max(axis=1)
+    scale = np.maximum(np.abs(w).max(axis=1), 1e-3 * np.abs(w).max())
+    bad = np.nonzero(err > tol * scale)[0]
+    assert bad.size == 0, f"slices {bad[:8]}: error {err[bad[:8]]}, scale {scale[bad[:8]]}"
+
+
 @pytest.fixture(scope="module")
 def kkt():
     if not torch.cuda.is_available():
@@ -84,7 +99,7 @@ def test_dst2d_matches_scipy_dst(kkt, c):
     x = workloads.random_vector(p.V, 3)
     got = host(s.dst2d(dev(x)))
     want = spectral.dst2(x, p).ravel()
-    assert rel(got, want) < 1e-13
+    close(got, want, 1e-13, p.Nt)
     # involution: applying it twice gives the input back; in-place call allowed
     t = dev(x)
     s.dst2d(t, out=t)
@@ -126,7 +141,7 @@ def test_matvec_matches_sparse_kkt(kkt, c):
     s = _solver(kkt, c)
     x = workloads.random_vector(3 * p.V, 5)
     got = host(s.matvec(dev(x)))
-    assert rel(got, problem.assemble_K(p) @ x) < 1e-13
+    close(got, problem.assemble_K(p) @ x, 1e-13, 3 * p.Nt)
 
 
 @pytest.mark.parametrize("c", CASES)
@@ -135,7 +150,7 @@ def test_schur_apply_matches_oracle(kkt, c):
     s = _solver(kkt, c)
     pre = schwarz.schur_preconditioner(p, nd, variant="one-level")
     x = workloads.random_vector(p.V, 6)
-    assert rel(host(s.schur_apply(dev(x))), pre.schur_apply(x)) < 1e-12
+    close(host(s.schur_apply(dev(x))), pre.schur_apply(x), 1e-12, p.Nt)
 
 
 @pytest.mark.parametrize("c", CASES)
@@ -145,7 +160,7 @@ def test_coarse_correction_matches_oracle(kkt, c, pou):
     s = _solver(kkt, c, pou=pou)
     pre = schwarz.schur_preconditioner(p, nd, pou=pou)
     r = workloads.random_vector(p.V, 7)
-    assert rel(host(s.coarse_apply(dev(r))), pre.coarse(r)) < TOL
+    close(host(s.coarse_apply(dev(r))), pre.coarse(r), TOL, p.Nt)
 
 
 @pytest.mark.parametrize("c", CASES)
@@ -158,7 +173,7 @@ def test_schur_preconditioner_matches_oracle(kkt, c, variant, coarse, pou):
     ov = "one-level" if coarse == "none" else variant
     pre = schwarz.schur_preconditioner(p, nd, variant=ov, pou=pou)
     r = workloads.random_vector(p.V, 8)
-    assert rel(host(s.schur_precond_apply(dev(r))), pre.apply(r)) < TOL
+    close(host(s.schur_precond_apply(dev(r))), pre.apply(r), TOL, p.Nt)
 
 
 @pytest.mark.parametrize("c", CASES)
@@ -171,7 +186,7 @@ def test_ras_local_solves_match_oracle(kkt, c, coarse, pou):
     s = _solver(kkt, c, coarse=coarse, pou=pou, local="ras")
     pre = schwarz.schur_preconditioner(p, nd, variant="ras" if coarse == "none" else "ras-multiplicative", pou=pou)
     r = workloads.random_vector(p.V, 18)
-    assert rel(host(s.schur_precond_apply(dev(r))), pre.apply(r)) < TOL
+    close(host(s.schur_precond_apply(dev(r))), pre.apply(r), TOL, p.Nt)
 
 
 def test_ras_local_solves_in_fp64_solves_and_tensor_core_forms(kkt):
@@ -193,7 +208,7 @@ def test_block_preconditioner_matches_oracle(kkt, c):
     s = _solver(kkt, c)
     pre = schwarz.schur_preconditioner(p, nd)
     r = workloads.random_vector(3 * p.V, 9)
-    assert rel(host(s.precond_apply(dev(r))), schwarz.block_preconditioner_apply(p, pre, r)) < TOL
+    close(host(s.precond_apply(dev(r))), schwarz.block_preconditioner_apply(p, pre, r), TOL, 3 * p.Nt)
 
 
 def test_literal_sign_option_matches_oracle(kkt):

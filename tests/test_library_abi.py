@@ -67,6 +67,22 @@ def test_options_struct_matches_the_header():
     assert "KKT_K_COUNT = %d" % len(kkt.KERNEL_CLASSES) in text
 
 
+@pytest.mark.parametrize("cname,pyname", [("kkt_mlp_config", "KKTMlpConfig"),
+                                          ("kkt_mlp_train_stats", "KKTMlpTrainStats"),
+                                          ("kkt_instance", "KKTInstance")])
+def test_network_and_batch_structs_match_the_header(cname, pyname):
+    import re
+    from paper_2305_04421_gb300 import kkt
+    text = open(os.path.join(ROOT, "include", "kkt.h")).read()
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (cname, cname), text, re.S).group(1)
+    fields = []
+    for line in body.splitlines():
+        m = re.match(r"\s*(int|double|long long)\s+([\w, ]+);", line)
+        if m:
+            fields += [f.strip() for f in m.group(2).split(",")]
+    assert [f[0] for f in getattr(kkt, pyname)._fields_] == fields
+
+
 def test_invalid_sizes_rejected_before_any_device_call(lib):
     assert not lib.kkt_create(1, 8, 8, 1.0, 1.0, 1e-3, 2)
     assert b"nx" in lib.kkt_last_error()
