@@ -25,9 +25,11 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 # Relative error of the headline solve against the exact solution on its modes, per block. The
-# solve stops at a 1e-8 weighted relative residual; measured errors are stated in the docstring
-# of the test.
-SOLVE_ERROR_BOUND = 1e-7
+# error tracks the stopping tolerance (measured on GB300, u / z / w: 1.05e-7 / 4.4e-8 / 4.4e-8 at
+# 1e-8; 8.0e-10 / 3.7e-10 / 3.7e-10 at 1e-10; 1.1e-11 / 5.8e-12 / 5.8e-12 at 1e-12), so the 1e-8
+# solve is held to 3e-7 and a 1e-12 solve to the FP64 bar of 1e-10. Off-mode content measured
+# 5e-16 to 7e-16 of each block.
+BOUNDS = {1e-8: 3e-7, 1e-12: 1e-10}
 
 
 @pytest.fixture(scope="module")
@@ -65,19 +67,23 @@ def test_full_size_dst2d_on_full_spectrum_input(kkt, n, Nt, inplace):
 
 
 def test_headline_solve_matches_the_exact_solution_on_its_modes(kkt):
-    """Per block (u, z, w): the relative error on the 64 modes below SOLVE_ERROR_BOUND, and the
-    content off those modes below 1e-12 of the block (rounding)."""
+    """Per block (u, z, w): the relative error on the 64 modes below BOUNDS[tol] for the 1e-8
+    solve the benchmark times and for a 1e-12 solve, and the content off those modes below
+    1e-14 of the block (rounding)."""
     w = workloads.CFG_GPU
     p = HeatKKT(nx=w.nx, ny=w.ny, Nt=w.Nt, nu=w.nu, omega=w.omega)
     ut = workloads.make_target(w)
     kmax = 8
     s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
     f = s.build_rhs(torch.from_numpy(ut.ravel()).cuda())
-    res = s.solve(f, tol=1e-8, maxit=420)
-    assert res.status == kkt.KKT_OK and res.rel_residual <= 1e-8
-    torch.cuda.synchronize()
-    x = res.x.cpu().numpy()
-    del f, res
+    xs = {}
+    for tol in BOUNDS:
+        res = s.solve(f, tol=tol, maxit=420)
+        assert res.status == kkt.KKT_OK and res.rel_residual <= tol
+        torch.cuda.synchronize()
+        xs[tol] = res.x.cpu().numpy()
+        del res
+    del f
     s.close()
     torch.cuda.empty_cache()
     # the oracle's right-hand side on the active modes (f_z = 0 and f_w = 0: u_0 = 0)
@@ -93,10 +99,11 @@ def test_headline_solve_matches_the_exact_solution_on_its_modes(kkt):
         for k in range(kmax):
             U, Z, W = spectral.kkt_exact_mode_solve(p, lam[l, k], fu_hat[:, l, k], zeros, zeros)
             exact[0, :, l, k], exact[1, :, l, k], exact[2, :, l, k] = U, Z, W
-    for b, name in enumerate("uzw"):
-        xh = spectral.dst2(x[b * V:(b + 1) * V], p)
-        act = xh[:, :kmax, :kmax]
-        err = np.linalg.norm(act - exact[b]) / np.linalg.norm(exact[b])
-        assert err < SOLVE_ERROR_BOUND, (name, err)
-        xh[:, :kmax, :kmax] = 0.0
-        assert np.linalg.norm(xh) < 1e-12 * np.linalg.norm(exact[b]), (name, np.linalg.norm(xh) / np.linalg.norm(exact[b]))
+    for tol, x in xs.items():
+        for b, name in enumerate("uzw"):
+            xh = spectral.dst2(x[b * V:(b + 1) * V], p)
+            scale = np.linalg.norm(exact[b])
+            err = np.linalg.norm(xh[:, :kmax, :kmax] - exact[b]) / scale
+            assert err < BOUNDS[tol], (tol, name, err)
+            xh[:, :kmax, :kmax] = 0.0
+            assert np.linalg.norm(xh) < 1e-14 * scale, (tol, name, np.linalg.norm(xh) / scale)
