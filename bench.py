@@ -35,18 +35,68 @@ import workloads  # noqa: E402
 METRIC = "KKT solve time to 1e-8 rel. residual; precond applies/s; HBM GB/s vs peak"
 TOL = 1e-8
 MAXIT = 420
-# Roofline denominators: HBM from the measured copy (MEASURED_PEAKS.json when present, else the
-# recipe's fallback); FP64 from the unit count: 2 DFMA per SM per clock x 152 SMs x 2070 MHz.
+# Roofline denominators: HBM and BF16 from MEASURED_PEAKS.json (the measured copy and cuBLAS
+# BF16 GEMM) when present, else the recipe's fallback; FP64 and FP32 from this run's FMA probe
+# (kkt_probe_fma_rate) and TF32 from this run's cuBLAS TF32 GEMM (probe_peaks). Without a probe
+# the FP64 peak falls back to the unit count: 2 DFMA per SM per clock x 152 SMs x 2070 MHz.
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
+PROBE: dict = {}
 
 
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as fh:
-            return json.load(fh), "measured"
-    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+            peaks, kind = json.load(fh), "measured"
+    else:
+        peaks, kind = {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+    return dict(peaks, **PROBE), kind
+
+
+def probe_peaks(kkt_mod) -> dict:
+    """Measure the compute peaks of this GPU once per run (outside every timed region): FP64 and
+    FP32 FMA loops of the library's probe, and cuBLAS dense GEMMs in TF32 (8192^3, best of 10)
+    and FP64 (4096^3, best of 3), CUDA events. Stored in PROBE for measured_peaks()."""
+    import torch
+
+    if PROBE:
+        return PROBE
+    out = {"fp64_fma_tflops": kkt_mod.kkt_probe_fma_rate("fp64") / 1e12,
+           "fp32_fma_tflops": kkt_mod.kkt_probe_fma_rate("fp32") / 1e12}
+    stream = torch.cuda.current_stream()
+
+    def gemm_rate(dtype, n, reps):
+        a = torch.randn(n, n, dtype=dtype, device="cuda")
+        b = torch.randn(n, n, dtype=dtype, device="cuda")
+        c = torch.empty(n, n, dtype=dtype, device="cuda")
+        torch.matmul(a, b, out=c)
+        best = None
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.matmul(a, b, out=c)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b, c
+        torch.cuda.empty_cache()
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+    tf32_prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        out["tf32_tflops"] = gemm_rate(torch.float32, 8192, 10)
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32_prev
+    out["fp64_gemm_tflops"] = gemm_rate(torch.float64, 4096, 3)
+    out["probe_how"] = ("FP64/FP32: kkt_probe_fma_rate (8 independent FMA chains per thread, 8 CTAs x 256 "
+                        "threads per SM, best of 5); TF32: torch.matmul fp32 8192^3 with TF32 allowed, best of "
+                        "10; FP64 GEMM: torch.matmul fp64 4096^3, best of 3")
+    PROBE.update(out)
+    return PROBE
 
 
 def workload_for(omega: float) -> workloads.Workload:
@@ -283,8 +333,9 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -
     The library sums, for every timed launch, the algorithmic FLOPs and bytes of that launch
     (what the method must compute and move; formulas at each launch site). The binding roof is
     the larger of FLOPs / compute peak and bytes / HBM peak; achieved = work / measured time.
-    Compute peaks: FP64 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived from unit counts); BF16 the
-    measured dense GEMM burst; TF32 the BF16 figure x 1.1/2.25 (nominal dense ratio).
+    Compute peaks: FP64 the probe's measured FMA rate (else 2 DFMA/clk/SM x 152 SMs x 2070 MHz
+    from the unit counts); BF16 the measured dense GEMM burst; TF32 the probe's measured cuBLAS
+    TF32 GEMM (else the BF16 figure x 1.1/2.25, the nominal dense ratio).
     """
     top = max(prof, key=lambda k: prof[k]["ms"])
     e = prof[top]
@@ -292,14 +343,25 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
     if top == "dst" and precision in ("bf16", "tf32"):
         bf = float(peaks.get("bf16_tflops", 1900.0))
-        alu_peak = bf if precision == "bf16" else bf * 1.1 / 2.25
-        alu_kind, alu_src = "tensor", f"{peak_kind} BF16 dense GEMM" + ("" if precision == "bf16" else " x 1.1/2.25 (TF32)")
+        if precision == "bf16":
+            alu_peak, alu_src = bf, f"{peak_kind} BF16 dense GEMM"
+        elif "tf32_tflops" in peaks:
+            alu_peak, alu_src = float(peaks["tf32_tflops"]), "measured cuBLAS TF32 dense GEMM (this run's probe)"
+        else:
+            alu_peak, alu_src = bf * 1.1 / 2.25, f"{peak_kind} BF16 dense GEMM x 1.1/2.25 (TF32)"
+        alu_kind = "tensor"
         kname = "tc_dst_gemm_kernel"
     else:
-        alu_peak = FP64_PEAK_TFLOPS
-        alu_kind, alu_src = "alu", "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)"
+        if "fp64_fma_tflops" in peaks:
+            alu_peak = float(peaks["fp64_fma_tflops"])
+            alu_src = "measured FP64 FMA rate (this run's kkt_probe_fma_rate)"
+        else:
+            alu_peak = FP64_PEAK_TFLOPS
+            alu_src = "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)"
+        alu_kind = "alu"
         kname = {"dst": "dst_tile_kernel", "multidot": "mgs2_step_kernel", "update": "mgs2_step_kernel",
-                 "axpy": "axpy_multi_kernel", "matvec": "matvec_kernel", "sweep": "sweep_kernel",
+                 "axpy": "axpy_multi_kernel" if precision == "fp64" else "scale2_kernel",
+                 "pack": "pack_kernel", "matvec": "matvec_kernel", "sweep": "sweep_kernel",
                  "coarse": "coarse_solve_kernel"}.get(top, top)
     t_alu = e["flops"] / (alu_peak * 1e12)
     t_mem = e["bytes"] / (hbm * 1e9)
@@ -837,6 +899,7 @@ def run_ours(args):
 
     w = workload_for(args.omega)
     dev = torch.device("cuda", local)
+    probe_peaks(kkt)   # compute peaks of this GPU, before (and outside) every timed region
     solver = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
     f = solver.build_rhs(ut)
@@ -922,7 +985,7 @@ def run_ours(args):
             "e2e": {"value": job_value(world, e2e_steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "staging": "copy kernel through the pinned buffers' device mapping",
                     "value_copy_engine": job_value(world, e2e_steps, e2e_ce_s), "host_link_gbs": link},
-            "gpu_launches": launches,
+            "gpu_launches": launches, "peaks_probed": dict(PROBE),
             "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "kernel_launches": {k: v["launches"] for k, v in prof.items()},
             "clocks": clocks}

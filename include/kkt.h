@@ -479,7 +479,8 @@ enum kkt_kernel_class {
   KKT_K_REDUCE = 7,    /* reduction finalisation and norms */
   KKT_K_GRAPH = 8,     /* a replayed CUDA graph (batched form): its kernels are counted in their
                           own classes, its time, flops and bytes here */
-  KKT_K_COUNT = 9
+  KKT_K_PACK = 9,      /* reduced-precision forms: FP64 input split into tensor-core operands */
+  KKT_K_COUNT = 10
 };
 
 typedef struct kkt_kernel_stats {
@@ -495,6 +496,13 @@ typedef struct kkt_kernel_stats {
 int kkt_profile_enable(int on);
 /* Copy the counters (synchronising on the pending timing events) and, if reset != 0, zero them. */
 int kkt_profile_read(kkt_kernel_stats* out, int reset);
+
+/* Peak-rate probe (no counterpart in the paper; the denominator of the FP64 and FP32 rooflines):
+ * a bounded loop of independent fused multiply-adds on 8 CTAs of 256 threads per SM, about 20 ms
+ * per launch, best of 5 timed launches with CUDA events on `stream` after one warm-up.
+ * precision 0: FP64, 1: FP32; *flops_per_s = 2 x FMAs / s. Synchronises `stream`; allocates and
+ * frees a small sink buffer. */
+int kkt_probe_fma_rate(int precision, double* flops_per_s, void* stream);
 
 #ifdef __cplusplus
 }

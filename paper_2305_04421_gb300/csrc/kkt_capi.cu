@@ -599,8 +599,7 @@ int kkt_precond_apply(kkt_handle* h, const double* r, double* y, void* stream) {
   KKT_TRY(check_ptrs({r, y}));
   cudaStream_t st = as_stream(stream);
   const Geometry& g = h->g;
-  KKT_TRY(launch_scale(r, 1.0 / g.h, y, g.V, st));
-  KKT_TRY(launch_scale(r + g.V, 1.0 / (g.omega * g.h), y + g.V, g.V, st));
+  KKT_TRY(launch_scale2(r, 1.0 / g.h, y, r + g.V, 1.0 / (g.omega * g.h), y + g.V, g.V, st));
   return schur_precond_w(h, r + 2 * g.V, 1.0, y + 2 * g.V, st);
 }
 

@@ -225,6 +225,9 @@ int launch_matvec_spectral(const kkt_handle* h, const double* u, double su, cons
                   double ow = 1.0);
 int launch_build_rhs(const kkt_handle* h, const double* ut, const double* u0, double* f, cudaStream_t st);
 int launch_scale(const double* x, double s, double* y, long long n, cudaStream_t st);
+// yu = su xu and yz = sz xz in one launch (n elements each)
+int launch_scale2(const double* xu, double su, double* yu, const double* xz, double sz, double* yz, long long n,
+                  cudaStream_t st);
 int launch_jhat_time(const kkt_handle* h, const double* in, double* out, int dir, double scale,
                      cudaStream_t st);
 

@@ -58,7 +58,8 @@ void drain_locked() {
 }
 
 const char* const kClassNames[KKT_K_COUNT] = {"kkt.dst",    "kkt.coarse", "kkt.sweep",  "kkt.matvec", "kkt.multidot",
-                                               "kkt.update", "kkt.axpy",   "kkt.reduce", "kkt.graph"};
+                                               "kkt.update", "kkt.axpy",   "kkt.reduce", "kkt.graph",
+                                               "kkt.pack"};
 
 }  // namespace
 

@@ -168,15 +168,6 @@ __device__ __forceinline__ float f64_to_f32_rne(double d) {
   return __uint_as_float(sign | (static_cast<unsigned int>(e32) << 23) | static_cast<unsigned int>(m >> 29));
 }
 
-// v rounded to `bits` significant bits (ties to even), in the FP64 bit pattern
-template <int BITS>
-__device__ __forceinline__ double round_bits(double v) {
-  constexpr int drop = 53 - BITS;
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
-  const unsigned long long r = (b + ((1ull << (drop - 1)) - 1) + ((b >> drop) & 1ull)) & ~((1ull << drop) - 1);
-  return __longlong_as_double(static_cast<long long>(r));
-}
-
 // hi + lo split of a value in the operand type
 template <typename TIn>
 struct Split;
@@ -186,26 +177,12 @@ struct Split<__nv_bfloat16> {
     hi = __float2bfloat16_rn(v);
     lo = __float2bfloat16_rn(v - __bfloat162float(hi));
   }
-  // hi = v to 8 significant bits (exact in BF16), lo = v - hi (one exact FP64 subtraction)
-  // rounded to BF16; the conversions in integer arithmetic
-  static __device__ __forceinline__ void make_d(double v, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-    const double h = round_bits<8>(v);
-    hi = __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(f64_to_f32_rne(h)) >> 16));
-    const double l = round_bits<8>(v - h);   // one rounding of the exact remainder
-    lo = __ushort_as_bfloat16(static_cast<unsigned short>(__float_as_uint(f64_to_f32_rne(l)) >> 16));
-  }
 };
 template <>
 struct Split<float> {
   static __device__ __forceinline__ void make(float v, float& hi, float& lo) {
     hi = tf32_round(v);
     lo = v - hi;
-  }
-  // hi = v to 11 significant bits (exact in TF32), lo = v - hi in FP32
-  static __device__ __forceinline__ void make_d(double v, float& hi, float& lo) {
-    const double h = round_bits<11>(v);
-    hi = f64_to_f32_rne(h);
-    lo = f64_to_f32_rne(v - h);
   }
 };
 
@@ -561,26 +538,50 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
 }
 
 // out + out_lo (P x P per slice, zero padded) = scale * in[s][j][i] (valid x valid), split into
-// hi and lo parts of the operand type
-// Grid (P / 256 rounded up, P, slices): no 64-bit index divisions (the compiler builds those
-// from FP64 arithmetic, the scarce pipe here).
+// hi and lo parts of the operand type. No FP64 instruction in the default case (scale = 1): the
+// value is rounded to FP32 by integer operations on its bit pattern (f64_to_f32_rne) and split
+// on the FP32 pipe (Split::make: hi = v rounded to the operand's significand, lo = v - hi, exact
+// in FP32). The FP32 rounding (2^-24 relative) is far below the split's own 2^-16 (BF16) and
+// 2^-22 (TF32). Each thread packs two neighbouring elements of a row (one 4- or 8-byte store per
+// part; P is even). Grid (P / 512 rounded up, P, slices): no 64-bit index divisions (the
+// compiler builds those from FP64 arithmetic, the scarce pipe here).
+template <typename TIn>
+struct Pair;
+template <>
+struct Pair<__nv_bfloat16> {
+  using T = __nv_bfloat162;
+  static __device__ __forceinline__ T make(__nv_bfloat16 a, __nv_bfloat16 b) { return __halves2bfloat162(a, b); }
+};
+template <>
+struct Pair<float> {
+  using T = float2;
+  static __device__ __forceinline__ T make(float a, float b) { return make_float2(a, b); }
+};
+
 template <typename TIn>
 __global__ void pack_kernel(const double* __restrict__ in, double scale, TIn* __restrict__ out,
                             TIn* __restrict__ out_lo, int P, int valid) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int j = blockIdx.y;
   const long long s = blockIdx.z;
   if (i >= P) return;
   const long long t = (s * P + j) * P + i;
-  double v = 0.0;
-  if (i < valid && j < valid) {
-    v = in[(s * valid + j) * valid + i];
-    if (scale != 1.0) v *= scale;   // callers fold their scale downstream where they can
+  float v0 = 0.f, v1 = 0.f;
+  if (j < valid) {
+    const double* row = in + (s * valid + j) * valid;
+    double d0 = i < valid ? row[i] : 0.0, d1 = i + 1 < valid ? row[i + 1] : 0.0;
+    if (scale != 1.0) {   // callers fold their scale downstream where they can
+      d0 *= scale;
+      d1 *= scale;
+    }
+    v0 = f64_to_f32_rne(d0);
+    v1 = f64_to_f32_rne(d1);
   }
-  TIn hi, lo;
-  Split<TIn>::make_d(v, hi, lo);
-  out[t] = hi;
-  out_lo[t] = lo;
+  TIn h0, l0, h1, l1;
+  Split<TIn>::make(v0, h0, l0);
+  Split<TIn>::make(v1, h1, l1);
+  *reinterpret_cast<typename Pair<TIn>::T*>(out + t) = Pair<TIn>::make(h0, h1);
+  *reinterpret_cast<typename Pair<TIn>::T*>(out_lo + t) = Pair<TIn>::make(l0, l1);
 }
 
 using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -791,8 +792,9 @@ int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStre
   const long long total = static_cast<long long>(t.slices) * t.P * t.P;
   const int tb = 256;
   if (t.slices > 65535) return set_error(KKT_ERR_UNSUPPORTED, "too many time slices for the pack grid");
-  const dim3 grid((t.P + tb - 1) / tb, t.P, t.slices);
-  ProfScope ps(KKT_K_AXPY, st, 0.0, 8.0 * t.slices * static_cast<double>(valid) * valid + 2.0 * (t.bf16 ? 2.0 : 4.0) * total);
+  if (t.P % 2) return set_error(KKT_ERR_UNSUPPORTED, "odd padded transform size");
+  const dim3 grid((t.P / 2 + tb - 1) / tb, t.P, t.slices);
+  ProfScope ps(KKT_K_PACK, st, 0.0, 8.0 * t.slices * static_cast<double>(valid) * valid + 2.0 * (t.bf16 ? 2.0 : 4.0) * total);
   if (t.bf16)
     pack_kernel<__nv_bfloat16><<<grid, tb, 0, st>>>(in, scale, static_cast<__nv_bfloat16*>(t.x0),
                                                      static_cast<__nv_bfloat16*>(t.x0_lo), t.P, valid);

@@ -67,7 +67,7 @@ class KKTStats(ctypes.Structure):
 
 # "graph" is a replayed CUDA graph of the batched form: its kernels are counted in their own
 # classes, its device time, flops and bytes under "graph"; it is not itself a kernel launch.
-KERNEL_CLASSES = ["dst", "coarse", "sweep", "matvec", "multidot", "update", "axpy", "reduce", "graph"]
+KERNEL_CLASSES = ["dst", "coarse", "sweep", "matvec", "multidot", "update", "axpy", "reduce", "graph", "pack"]
 _NK = len(KERNEL_CLASSES)
 
 
@@ -169,6 +169,7 @@ SIGNATURES = [
                              ctypes.POINTER(KKTBatchStats), _P]),
     ("kkt_profile_enable", _I, [_I]),
     ("kkt_profile_read", _I, [ctypes.POINTER(KKTKernelStats), _I]),
+    ("kkt_probe_fma_rate", _I, [_I, ctypes.POINTER(ctypes.c_double), _P]),
 ]
 
 _lib = None
@@ -340,6 +341,13 @@ def kkt_profile_read(reset: bool = False) -> dict:
     _check(load_library().kkt_profile_read(ctypes.byref(st), 1 if reset else 0))
     return {name: {"launches": st.launches[i], "timed": st.timed[i], "ms": st.ms[i], "flops": st.flops[i],
                    "bytes": st.bytes[i]} for i, name in enumerate(KERNEL_CLASSES)}
+
+
+def kkt_probe_fma_rate(precision: str, stream=None) -> float:
+    """Measured FMA throughput of this GPU in FLOP/s ('fp64' or 'fp32'; 2 FLOPs per FMA)."""
+    r = ctypes.c_double()
+    _check(load_library().kkt_probe_fma_rate({"fp64": 0, "fp32": 1}[precision], ctypes.byref(r), _stream(stream)))
+    return r.value
 
 
 def _fptr(t):

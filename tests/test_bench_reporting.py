@@ -13,7 +13,8 @@ sys.path.insert(0, ROOT)
 
 def prof(**classes):
     base = {"launches": 0, "timed": 0, "ms": 0.0, "flops": 0.0, "bytes": 0.0}
-    out = {k: dict(base) for k in ("dst", "coarse", "sweep", "matvec", "multidot", "update", "axpy", "reduce")}
+    out = {k: dict(base) for k in ("dst", "coarse", "sweep", "matvec", "multidot", "update", "axpy", "reduce",
+                                   "pack")}
     for k, v in classes.items():
         out[k].update(v)
     return out
@@ -33,6 +34,23 @@ def test_fp64_alu_bound_kernel_reports_against_the_fp64_peak():
     assert r["per_launch_ms"] == pytest.approx(10.0)
     assert r["traffic"] == pytest.approx(1e9 * bench.TRAFFIC_RATIO["dst_tile_kernel"])
     assert r["share_of_step"] == pytest.approx(100.0 / 120.0)
+
+
+def test_probed_peaks_replace_the_derived_ones():
+    """With this run's probe in the peaks, the FP64 kernels report against the measured FMA rate
+    and the TF32 transforms against the measured TF32 GEMM."""
+    import bench
+    p = prof(dst={"launches": 10, "timed": 10, "ms": 100.0, "flops": 50e9, "bytes": 10e9})
+    peaks = {"hbm_gbs": 6800.0, "bf16_tflops": 1800.0, "fp64_fma_tflops": 1.04, "tf32_tflops": 900.0}
+    r = bench.roofline(p, peaks, "measured")
+    assert r["peak"] == pytest.approx(1.04) and "probe" in r["peak_source"]
+    assert r["frac"] == pytest.approx(0.5 / 1.04)
+    p2 = prof(dst={"launches": 2, "timed": 2, "ms": 2.0, "flops": 2e12, "bytes": 1e9})
+    r2 = bench.roofline(p2, peaks, "measured", precision="tf32")
+    assert r2["peak"] == pytest.approx(900.0) and r2["bound"] == "tensor"
+    p3 = prof(pack={"launches": 2, "timed": 2, "ms": 2.0, "flops": 0.0, "bytes": 12e9})
+    r3 = bench.roofline(p3, peaks, "measured", precision="bf16")
+    assert r3["kernel"] == "pack_kernel" and r3["bound"] == "hbm"
 
 
 def test_memory_bound_kernel_reports_against_the_measured_copy_bandwidth():

@@ -79,7 +79,7 @@ def test_bf16_tensor_core_transform_matches_emulation(kkt, n, Nt):
     x = workloads.random_vector(p.V, 40 + n).reshape(Nt, n - 1, n - 1)
     got = host(s.dst2d(dev(x.ravel()))).reshape(Nt, n - 1, n - 1)       # [t][l][k]
     Qh, Ql = split_bf16(dst_matrix(n))
-    xh, xl = split_bf16(x)
+    xh, xl = split_bf16(x.astype(np.float32).astype(np.float64))   # the pack splits the FP32-rounded input
     y1 = (np.einsum("tji,ik->tkj", xh, Qh) + np.einsum("tji,ik->tkj", xh, Ql)
           + np.einsum("tji,ik->tkj", xl, Qh))      # along x -> [t][k][j], accumulated in FP32
     yh, yl = split_f32_bf16(y1)
