@@ -863,6 +863,26 @@ def run_profile_case(args):
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    if args.profile_case == "batched":
+        # two 128 x 128, Nt = 128, N_D = 16 instances (KKT vectors of 48 MB, a 1.5 GB Krylov basis
+        # each) solved one after another and then together through the batched kernels (graphs
+        # off, so that every kernel is a launch of its own)
+        ws = [workloads.Workload(f"profile-batch{q}", nx=128, ny=128, Nt=128, n_sub=16, nu=1.0 + q,
+                                 omega=1e-4, target="sine-series", seed=10 + q) for q in range(2)]
+        fs = []
+        for w in ws:
+            s = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
+            fs.append(s.build_rhs(torch.from_numpy(workloads.make_target(w).ravel()).to(dev)))
+            r = s.solve(fs[-1], tol=1e-8, maxit=200)
+            s.close()
+        b = kkt.Batch(ws)
+        b.set_single_threshold(0)
+        b.set_graphs(False)
+        res = b.solve(fs, [torch.zeros_like(f) for f in fs], tol=1e-8, maxit=200)
+        b.close()
+        print(json.dumps({"profile_case": "2 instances 128x128 Nt=128 N_D=16, single then batched",
+                          "iterations": res.iterations[:2], "status": res.status}))
+        return 0 if res.status == kkt.KKT_OK and r.status == kkt.KKT_OK else 1
     if args.profile_case == "paper":
         # the Eq 16 problem on the 17 x 17 mesh, 5 steps per subdomain: 225 modes, so the coarse
         # solve runs the multilevel (cyclic-reduction) kernel
@@ -1027,9 +1047,10 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=25,
                     help="iterations the reference arm scales its per-iteration sample by")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", nargs="?", const="grid", choices=["grid", "paper"], default=None,
+    ap.add_argument("--profile-case", nargs="?", const="grid", choices=["grid", "paper", "batched"], default=None,
                     help="run only a small solve for counter captures: 'grid' (default) 256 x 256, Nt = 96; "
-                         "'paper' the Section 4 mesh (17 x 17 points) with Nt = 3200, 640 subdomains")
+                         "'paper' the Section 4 mesh (17 x 17 points) with Nt = 3200, 640 subdomains; "
+                         "'batched' two 128 x 128, Nt = 128 instances, single solves then the batched kernels")
     ap.add_argument("--basis", choices=["physical", "spectral"], default="physical",
                     help="FGMRES basis of --profile-case")
     ap.add_argument("--precision", choices=["fp64", "bf16", "tf32"], default="fp64",

@@ -22,6 +22,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr long long kChunk = kThreads * 64;   // elements per work item of the vector kernels
+// Resident blocks per SM the persistent vector kernels are compiled for (their grid is this many
+// blocks per SM, so the whole grid is resident at once: no tail of late-starting blocks).
+constexpr int kBlocksPerSm = 4;
 
 struct Seg {
   const double* V;   // first vector (basis V_0 or a single vector)
@@ -57,9 +60,25 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
+// Two sums over the block at once (one pair of barriers); valid in thread 0.
+__device__ __forceinline__ double2 block_sum2(double a, double b, double2* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) sh[warp] = make_double2(a, b);
+  __syncthreads();
+  double2 t = make_double2(0.0, 0.0);
+  if (warp == 0) {
+    const double2 v = lane < (blockDim.x >> 5) ? sh[lane] : make_double2(0.0, 0.0);
+    t = make_double2(warp_sum(v.x), warp_sum(v.y));
+  }
+  return t;
+}
+
 // part[t][k] = sum over item t's elements of V_k w (k < NV), part[t][NV] = sum w^2
 template <int NV>
-__global__ void __launch_bounds__(kThreads) multidot_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) multidot_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                        int nj, long long total, double* __restrict__ part) {
   __shared__ double sh[32];
   KKT_SEG_TABLE
@@ -86,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) multidot_b(const Seg* __restrict__ s
 
 // w -= sum_k coef[inst][k] V_k over the item; part[t] = sum w^2 (NV = 0: norm only)
 template <int NV>
-__global__ void __launch_bounds__(kThreads) update_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) update_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                      int nj, long long total, const double* __restrict__ coef, int ldc,
                                                      double* __restrict__ part, int want_norm) {
   __shared__ double sh[32];
@@ -115,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) update_b(const Seg* __restrict__ seg
 }
 
 // out = alpha[inst] * x + beta[inst] * y, x = V, y = w of the segment (out = w)
-__global__ void __launch_bounds__(kThreads) axpby_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) axpby_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                     int nj, long long total, const double* __restrict__ ab) {
   KKT_SEG_TABLE
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -131,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) axpby_b(const Seg* __restrict__ segs
 // c = dots[inst][k] * sc[inst][k] (zero: the instance is left as it is); then the partial of
 // <V_k+1, w> (DOTV) or <w, w> over the updated w. V_k = V + k stride of the segment.
 template <bool AXPY, bool DOTV>
-__global__ void __launch_bounds__(kThreads) mgs_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) mgs_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                   int nj, long long total, int k, const double* __restrict__ dots,
                                                   const double* __restrict__ sc, int ld, double* __restrict__ part) {
   __shared__ double sh[32];
@@ -176,10 +195,11 @@ __global__ void __launch_bounds__(kThreads) mgs_b(const Seg* __restrict__ segs, 
 // * sc[inst][k+i]), then partial dots <V_k+NA, w>, <V_k+NA+1, w> (ND of them) or <w, w> when
 // ND = 0, max(ND, 1) columns per item.
 template <int NA, int ND>
-__global__ void __launch_bounds__(kThreads) mgs2_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+__global__ void __launch_bounds__(kThreads, kBlocksPerSm) mgs2_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                    int nj, long long total, int k, const double* __restrict__ dots,
                                                    const double* __restrict__ sc, int ld, double* __restrict__ part) {
   __shared__ double sh[32];
+  __shared__ double2 sh2[32];
   KKT_SEG_TABLE
   constexpr int W = ND > 1 ? 2 : 1;
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
@@ -193,10 +213,60 @@ __global__ void __launch_bounds__(kThreads) mgs2_b(const Seg* __restrict__ segs,
     const double* B1 = B0 + S.stride;
     const long long e0 = (t - sp[q]) * kChunk, e1 = min(e0 + kChunk, S.n);
     double acc0 = 0.0, acc1 = 0.0;
-    for (long long base = e0 + threadIdx.x; base < e1; base += 4 * kThreads) {
-      double wv[4], a0[4], a1[4], b0[4], b1[4];
+    // 16-byte loads and stores when every vector of the step starts 16-byte aligned (item
+    // starts are even: kChunk is); else 8-byte loads
+    const uintptr_t al = reinterpret_cast<uintptr_t>(S.w) | reinterpret_cast<uintptr_t>(A0) |
+                         reinterpret_cast<uintptr_t>(A1) | reinterpret_cast<uintptr_t>(B0) |
+                         reinterpret_cast<uintptr_t>(B1);
+    long long scalar_from = e0;
+    if ((al & 15) == 0) {
+      const long long p0 = e0 / 2, p1 = e1 / 2;   // whole pairs of the item
+      double2* w2 = reinterpret_cast<double2*>(S.w);
+      const double2* a02 = reinterpret_cast<const double2*>(A0);
+      const double2* a12 = reinterpret_cast<const double2*>(A1);
+      const double2* b02 = reinterpret_cast<const double2*>(B0);
+      const double2* b12 = reinterpret_cast<const double2*>(B1);
+      constexpr int RV = NA + ND >= 4 ? 1 : 2;   // 16-byte loads in flight: 5 (or up to 8) per thread
+      for (long long base = p0 + threadIdx.x; base < p1; base += RV * kThreads) {
+        double2 wv[RV], a0[RV], a1[RV], b0[RV], b1[RV];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+        for (int r = 0; r < RV; ++r) {
+          const long long i = base + r * kThreads;
+          const bool in = i < p1;
+          const double2 z = make_double2(0.0, 0.0);
+          wv[r] = in ? w2[i] : z;
+          a0[r] = (in && NA > 0) ? a02[i] : z;
+          a1[r] = (in && NA > 1) ? a12[i] : z;
+          b0[r] = (in && ND > 0) ? b02[i] : z;
+          b1[r] = (in && ND > 1) ? b12[i] : z;
+        }
+#pragma unroll
+        for (int r = 0; r < RV; ++r) {
+          const long long i = base + r * kThreads;
+          if (NA > 0) {
+            wv[r].x = fma(-c0, a0[r].x, wv[r].x);
+            wv[r].y = fma(-c0, a0[r].y, wv[r].y);
+            if (NA > 1) {
+              wv[r].x = fma(-c1, a1[r].x, wv[r].x);
+              wv[r].y = fma(-c1, a1[r].y, wv[r].y);
+            }
+            if (i < p1) w2[i] = wv[r];
+          }
+          if (ND == 0) {
+            acc0 = fma(wv[r].x, wv[r].x, fma(wv[r].y, wv[r].y, acc0));
+          } else {
+            acc0 = fma(b0[r].x, wv[r].x, fma(b0[r].y, wv[r].y, acc0));
+            if (ND > 1) acc1 = fma(b1[r].x, wv[r].x, fma(b1[r].y, wv[r].y, acc1));
+          }
+        }
+      }
+      scalar_from = 2 * p1;   // an odd last element of the vector, if any
+    }
+    constexpr int R = NA + ND >= 4 ? 2 : 4;   // loads in flight per thread within 64 registers
+    for (long long base = scalar_from + threadIdx.x; base < e1; base += R * kThreads) {
+      double wv[R], a0[R], a1[R], b0[R], b1[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
         const long long i = base + r * kThreads;
         const bool in = i < e1;
         wv[r] = in ? S.w[i] : 0.0;
@@ -206,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) mgs2_b(const Seg* __restrict__ segs,
         b1[r] = (in && ND > 1) ? B1[i] : 0.0;
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
+      for (int r = 0; r < R; ++r) {
         const long long i = base + r * kThreads;
         if (NA > 0) {
           wv[r] = fma(-c0, a0[r], wv[r]);
@@ -221,11 +291,15 @@ __global__ void __launch_bounds__(kThreads) mgs2_b(const Seg* __restrict__ segs,
         }
       }
     }
-    const double r0 = block_sum(acc0, sh);
-    if (threadIdx.x == 0) part[t * W] = r0;
     if (ND > 1) {
-      const double r1 = block_sum(acc1, sh);
-      if (threadIdx.x == 0) part[t * W + 1] = r1;
+      const double2 r = block_sum2(acc0, acc1, sh2);
+      if (threadIdx.x == 0) {
+        part[t * W] = r.x;
+        part[t * W + 1] = r.y;
+      }
+    } else {
+      const double r0 = block_sum(acc0, sh);
+      if (threadIdx.x == 0) part[t * W] = r0;
     }
   }
 }
@@ -531,21 +605,46 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   long long graph_launches = 0;
   int rc_all = KKT_OK;
   std::vector<InstState> all(n_inst);
+  // One Krylov arena for the whole call, sized for the largest wave and carved anew for each
+  // wave (every buffer 256-byte aligned): no device allocation between waves.
+  auto carve = [](long long doubles) { return (doubles + 31) / 32 * 32; };
+  auto inst_doubles = [&](int i) {
+    const long long V = b->inst[i]->g.V;
+    return carve((m + 1) * 3 * V) + carve(m * V) + (spectral ? carve(3 * V) : 0);
+  };
+  long long arena_doubles = 0;
+  for (const auto& wave : waves) {
+    long long t = 0;
+    for (int i : wave) t += inst_doubles(i);
+    arena_doubles = std::max(arena_doubles, t);
+  }
+  double* arena = nullptr;
+  if (arena_doubles > 0 && cudaMalloc(&arena, sizeof(double) * static_cast<size_t>(arena_doubles)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(h_tmp);
+    cudaFree(d_small);
+    return set_error(KKT_ERR_OOM, "batched Krylov arena");
+  }
   for (const auto& wave : waves) {
     const int nw = static_cast<int>(wave.size());
-    // per-instance Krylov arenas
+    // per-instance Krylov storage, carved from the arena
     std::vector<double*> Vb(nw, nullptr), Zw(nw, nullptr), Fs(nw, nullptr);
     std::vector<InstState*> S(nw);
     double* part = nullptr;
     long long max_items = 0;
     int rc = KKT_OK;
+    long long cursor = 0;
     for (int k = 0; k < nw && rc == KKT_OK; ++k) {
       kkt_handle* h = b->inst[wave[k]];
       const long long V = h->g.V;
-      if (cudaMalloc(&Vb[k], sizeof(double) * (m + 1) * 3 * V) != cudaSuccess ||
-          cudaMalloc(&Zw[k], sizeof(double) * m * V) != cudaSuccess ||
-          (spectral && cudaMalloc(&Fs[k], sizeof(double) * 3 * V) != cudaSuccess))
-        rc = set_error(KKT_ERR_OOM, "batched Krylov arena");
+      Vb[k] = arena + cursor;
+      cursor += carve((m + 1) * 3 * V);
+      Zw[k] = arena + cursor;
+      cursor += carve(m * V);
+      if (spectral) {
+        Fs[k] = arena + cursor;
+        cursor += carve(3 * V);
+      }
       max_items += (3 * V + kChunk - 1) / kChunk;
       InstState& I = all[wave[k]];
       I.h = h;
@@ -1097,11 +1196,6 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       for (int bl = 0; bl < 3; ++bl)
         if (dst2d(S[k]->h, S[k]->x + bl * V, S[k]->x + bl * V, st) < 0 && rc == KKT_OK) rc = KKT_ERR_CUDA;
     }
-    for (int k = 0; k < nw; ++k) {
-      cudaFree(Vb[k]);
-      cudaFree(Zw[k]);
-      cudaFree(Fs[k]);
-    }
     if (rc != KKT_OK) {
       rc_all = rc;
       break;
@@ -1110,6 +1204,7 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   }
   cudaFreeHost(h_tmp);
   cudaFree(d_small);
+  cudaFree(arena);
   if (rc_all < 0) return rc_all;
   for (int i : solo) {
     all[i].its = solo_its[i];
