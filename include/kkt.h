@@ -120,8 +120,11 @@ enum kkt_basis {
  * block tridiagonal in time: N_D blocks of 2 x 2, symmetric positive definite. Both solvers
  * are exact; they differ in how the work is spread over the GPU. */
 enum kkt_coarse_solve {
-  /* cyclic reduction when the modes alone leave the GPU idle (fewer than 12288 spatial modes)
-   * and one mode's system fits in shared memory, block Thomas otherwise */
+  /* FP64: cyclic reduction when its per-configuration factors (19 doubles per block and mode,
+   * about) take at most 256 MiB and one mode's system fits in shared memory, block Thomas
+   * otherwise (measured: the factored cyclic solve is never slower; above the cap it gains
+   * nothing measurable for its memory). BF16/TF32 (padded modes, no stored factors): cyclic
+   * below 12288 spatial modes. */
   KKT_COARSE_SOLVE_AUTO = 0,
   /* block Thomas elimination, one thread per mode: R_0 r summed node by node, then N_D
    * dependent elimination steps and N_D back-substitution steps. The fewest FLOPs. */
@@ -259,10 +262,18 @@ enum kkt_dst_method {
    * up, several short lines per warp below); else the direct sum, one warp per line */
   KKT_DST_TILES = 1,
   /* one thread per line, the direct sum: lines of at most 31 points (n <= 32) */
-  KKT_DST_LANE = 2
+  KKT_DST_LANE = 2,
+  /* FP64-accurate dense transform on the tcgen05 tensor cores: every line and every column of
+   * the DST matrix is scaled by its own power of two and cut into seven 7-bit digit planes
+   * (exact in BF16); the digit-plane products accumulate exactly in FP32 and are recombined
+   * in 64-bit integers (error-free splitting after Ozaki, Ogita, Oishi and Rump, 2012). Error
+   * about 2^-46 of each output's line scale. Square grids with nx - 1 <= 255; holds digit
+   * planes of 14 bytes and one FP64 buffer per point of a block. */
+  KKT_DST_TENSOR = 3
 };
 /* Re-selects the method (KKT_DST_AUTO re-runs the timing). KKT_ERR_UNSUPPORTED for
- * KKT_DST_LANE when a direction has more than 31 points. */
+ * KKT_DST_LANE when a direction has more than 31 points, and for KKT_DST_TENSOR on a
+ * non-square grid or lines of more than 255 points. */
 int kkt_set_dst_method(kkt_handle* h, int method);
 
 /* kkt_solve from the initial guess x_0 = 0: x is output only (its contents on entry are not

@@ -466,6 +466,7 @@ void kkt_destroy(kkt_handle* h) {
   dst_plan_destroy(h->dst_x);
   dst_plan_destroy(h->dst_y);
   if (h->tc.q) tc_plan_destroy(h->tc);
+  oz_plan_destroy(h->oz);
   cudaFree(h->d_lx_pad);
   cudaFree(h->d_ly_pad);
   cudaFree(h->learn_c);
@@ -712,7 +713,7 @@ int kkt_solve(kkt_handle* h, const double* f, double* x, double tol, int maxit, 
 
 int kkt_set_dst_method(kkt_handle* h, int method) {
   KKT_TRY(check_handle(h));
-  if (method < KKT_DST_AUTO || method > KKT_DST_LANE) return set_error(KKT_ERR_INVALID_ARG, "dst method out of range");
+  if (method < KKT_DST_AUTO || method > KKT_DST_TENSOR) return set_error(KKT_ERR_INVALID_ARG, "dst method out of range");
   return dst_set_method(h, method);
 }
 
@@ -800,6 +801,7 @@ static int solve_impl(kkt_handle* h, const double* f, double* x, double tol, int
     if (status >= 0 && std::isfinite(rel) && fnorm_plain > 0.0 && euclid_residual)
       local.rel_residual_euclid = euclid_residual();
     if (status >= 0 && h->opt.precision != KKT_PREC_FP64 && tc_check(h->tc, st) < 0) status = KKT_ERR_TIMEOUT;
+    if (status >= 0 && h->dst_tensor && oz_check(h->oz, st) < 0) status = KKT_ERR_TIMEOUT;
     if (!dev_x) {
       if (stage_copy(h, x, px, n3, cudaMemcpyDeviceToHost, st) < 0 && status >= 0) status = KKT_ERR_CUDA;
       cudaStreamSynchronize(st);

@@ -499,6 +499,10 @@ void batch_slot_free(BatchSlot& slot) {
   slot = BatchSlot();
 }
 
+// Smallest grid the create-time timing offers the tensor-core transform to (below it the lines
+// are short enough that the FFT and direct-sum tiles are cheap and accurate to rounding).
+constexpr int kTensorMinN = 64;
+
 int dst_autotune(kkt_handle* h) {
   const Geometry& g = h->g;
   KKT_CUDA_TRY(cudaMemset(h->spec, 0, static_cast<size_t>(g.V) * sizeof(double)));
@@ -542,6 +546,35 @@ int dst_autotune(kkt_handle* h) {
       p.lane_direct = ms < best_ms;
     }
   }
+  // square grids with lines of 63..255 points: the tensor-core FP64 transform against the two
+  // tuned passes, both timed as whole 2D transforms
+  h->dst_tensor = false;
+  if (g.nx == g.ny && g.nx >= kTensorMinN && g.nx - 1 <= 255) {
+    auto time_2d = [&]() -> double {
+      dst2d(h, h->spec, h->spec2, nullptr);   // warm-up
+      cudaEventRecord(e0, nullptr);
+      for (int r = 0; r < 2; ++r) dst2d(h, h->spec, h->spec2, nullptr);
+      cudaEventRecord(e1, nullptr);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      return ms;
+    };
+    const double ms_tiles = time_2d();
+    if (!h->oz.qs && oz_plan_create(h->oz, g.nx, g.Nt) == KKT_OK) h->bytes += h->oz.bytes;
+    if (h->oz.qs) {
+      h->dst_tensor = true;
+      const double ms_tensor = time_2d();
+      if (cudaGetLastError() != cudaSuccess || !(ms_tensor < ms_tiles)) {
+        h->dst_tensor = false;
+        h->bytes -= h->oz.bytes;
+        oz_plan_destroy(h->oz);
+      }
+    } else {
+      cudaGetLastError();   // no room for the digit planes: the tiles stay
+      oz_plan_destroy(h->oz);
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   const cudaError_t e = cudaDeviceSynchronize();
@@ -555,12 +588,34 @@ int dst_set_method(kkt_handle* h, int method) {
     if (method == KKT_DST_LANE && p->n - 1 > kLaneMaxM)
       return set_error(KKT_ERR_UNSUPPORTED, "the thread-per-line transform needs lines of at most 31 points");
   }
+  if (method == KKT_DST_TENSOR) {
+    const Geometry& g = h->g;
+    if (g.nx != g.ny || g.nx - 1 > 255)
+      return set_error(KKT_ERR_UNSUPPORTED, "the tensor-core FP64 transform needs a square grid of at most 256 intervals");
+    if (!h->oz.qs) {
+      const int rc = oz_plan_create(h->oz, g.nx, g.Nt);
+      if (rc < 0) {
+        const std::string msg = kkt_last_error();
+        oz_plan_destroy(h->oz);
+        return set_error(rc, msg);
+      }
+      h->bytes += h->oz.bytes;
+    }
+    h->dst_tensor = true;
+    return KKT_OK;
+  }
+  h->dst_tensor = false;
+  if (h->oz.qs) {
+    h->bytes -= h->oz.bytes;
+    oz_plan_destroy(h->oz);
+  }
   if (method == KKT_DST_AUTO) return dst_autotune(h);
   for (DstPlan* p : {&h->dst_x, &h->dst_y}) p->lane_direct = method == KKT_DST_LANE;
   return KKT_OK;
 }
 
 int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st) {
+  if (h->dst_tensor) return oz_dst2d(h->oz, in, out, st);
   const Geometry& g = h->g;
   // rows: Nt * My lines of Mx contiguous points (transform along x)
   KKT_TRY(launch_lines(h->dst_x, in, out, 0, static_cast<long long>(g.Nt) * g.My, g.Mx, 0, 0, st));

@@ -119,6 +119,29 @@ struct TcPlan {
   size_t bytes = 0;
 };
 
+// FP64-accurate sine transform on the tensor cores (square grids, at most 255 points per line):
+// every line and every column of the DST matrix is scaled by its own power of two and cut into
+// kOzDigits signed digits of kOzDigitBits bits, each digit plane exact in BF16; digit-plane
+// products accumulate exactly in FP32 (tcgen05, TMEM) and are recombined in 64-bit integers.
+constexpr int kOzDigits = 7;
+constexpr int kOzDigitBits = 7;
+struct OzPlan {
+  int n = 0;            // intervals per direction (lines of n - 1 points)
+  int M = 0;            // n - 1
+  int P = 0;            // padded line length: 64, 128 or 256
+  int slices = 0;       // time slices (Nt)
+  long long rows = 0;   // lines per pass: slices * M
+  int rows_pad = 0;     // rows rounded up to the 128-row tile
+  void* qs = nullptr;   // digit planes of Q: [kOzDigits][P][P] BF16, row c = output column, K contiguous
+  int* qexp = nullptr;  // per column c: G_c with |Q[k][c]| < 2^G_c
+  void* xs = nullptr;   // digit planes of the pass input: [kOzDigits][rows_pad][P] BF16
+  int* xexp = nullptr;  // per row: E_r with |x| < 2^E_r
+  double* tmp = nullptr;  // first pass output [slices][M][M] (transposed per slice)
+  int* err = nullptr;   // device flag: a pipeline wait timed out
+  CUtensorMap map_q, map_x;
+  size_t bytes = 0;
+};
+
 struct Geometry {
   int nx, ny, Nt, n_sub, Mx, My;
   long long N, V;
@@ -143,6 +166,8 @@ struct kkt_handle {
   double* d_lx_pad = nullptr;  // the same, zero-padded to the tensor-core transform size
   double* d_ly_pad = nullptr;
   kkt::TcPlan tc;              // reduced-precision transforms (allocated when such a precision is set)
+  kkt::OzPlan oz;              // FP64 transforms on the tensor cores (kkt_set_dst_method TENSOR)
+  bool dst_tensor = false;     // FP64 sine transforms by the tensor-core digit-plane GEMMs
   long long coarse_modes = 0;  // modes the coarse buffers are sized for
   // learned coarse correction
   kkt_mlp* mlp = nullptr;      // not owned
@@ -263,6 +288,11 @@ int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, c
             void* out_lo = nullptr);
 int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStream_t st);   // -> x0
 int tc_check(const TcPlan& t, cudaStream_t st);
+// FP64-accurate transforms on the tensor cores (kkt_tc_gemm.cu)
+int oz_plan_create(OzPlan& o, int n, int slices);
+void oz_plan_destroy(OzPlan& o);
+int oz_dst2d(const OzPlan& o, const double* in, double* out, cudaStream_t st);   // both directions
+int oz_check(const OzPlan& o, cudaStream_t st);   // reads and clears the timeout flag
 int tc_set_flag(const TcPlan& t);   // host-side write of the timeout flag (kkt_inject_tc_timeout)
 
 // Krylov primitives (deterministic two-stage reductions; results in h->red_out on device)

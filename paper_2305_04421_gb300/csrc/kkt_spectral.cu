@@ -229,11 +229,16 @@ __global__ void coarse_solve_kernel(const TI* __restrict__ rhat, double in_scale
 // its subdomains and eliminations. Threads past the last mode only join the barriers.
 constexpr int kCrThreads = 256;
 constexpr int kCrFields = 13;
-// AUTO picks cyclic reduction below this many spatial modes (per mode, Thomas is one thread).
-// Set from the crossover measured on GB300 with the elimination in every solve (cyclic ahead by
-// 3 % at 9025 modes with N_D = 64, Thomas ahead by 5 % at 16129 modes with N_D = 410); with the
-// stored factors the cyclic solve measured at least as fast up to 65025 modes.
+// AUTO on the FP64 path: the cyclic reduction with stored factors whenever those factors take at
+// most kCyclicAutoFactorBytes, else block Thomas. Measured on GB300 (kkt_coarse_apply) the stored-
+// factor cyclic solve is never slower than Thomas, from 225 modes (4.7x faster at N_D = 640) up
+// to the benchmark's 65025 modes (equal there, 10.27 against 10.23 ms), and 9 % faster at 16129
+// modes; above the cap the factors cost device memory (632 MB at 65025 modes, N_D = 64) for
+// no measurable gain. The mixed forms' padded modes eliminate in every solve, so there AUTO keeps
+// the crossover measured for that kernel: cyclic below kCyclicBelowModes modes (ahead by 3 % at
+// 9025 modes with N_D = 64, Thomas ahead by 5 % at 16129 modes with N_D = 410).
 constexpr long long kCyclicBelowModes = 12288;
+constexpr double kCyclicAutoFactorBytes = 256.0 * 1024 * 1024;
 
 __device__ __forceinline__ void sym_inv(double d00, double d01, double d11, double& i00, double& i01, double& i11) {
   const double id = 1.0 / (d00 * d11 - d01 * d01);
@@ -914,10 +919,12 @@ int crf_modes_per_cta(int n_sub, long long N) {
   return mpc;
 }
 
-bool use_cyclic(const kkt_handle* h, const SpecParams& p) {
+bool use_cyclic(const kkt_handle* h, const SpecParams& p, bool padded) {
   if (p.learn_k > 0 || cr_modes_per_cta(p.n_sub) == 0) return false;
   if (h->opt.coarse_solve == KKT_COARSE_SOLVE_CYCLIC) return true;
-  return h->opt.coarse_solve == KKT_COARSE_SOLVE_AUTO && p.N < kCyclicBelowModes;
+  if (h->opt.coarse_solve != KKT_COARSE_SOLVE_AUTO) return false;
+  if (padded) return p.N < kCyclicBelowModes;
+  return static_cast<double>(cr_factor_slots(p.n_sub)) * p.N * sizeof(double) <= kCyclicAutoFactorBytes;
 }
 
 SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixed forms' mode grid)
@@ -947,7 +954,7 @@ SpecParams make_params(const kkt_handle* h, bool padded) {  // (padded: the mixe
   p.learn_c = h->learn_c;
   p.multiplicative = h->opt.variant == KKT_MULTIPLICATIVE;
   p.ras = h->opt.local == KKT_LOCAL_RAS;
-  p.cyclic = p.two_level && use_cyclic(h, p);
+  p.cyclic = p.two_level && use_cyclic(h, p, padded);
   p.crf = (!padded && p.cyclic) ? h->cr_factors : nullptr;
   p.cr_mpc = p.crf ? crf_modes_per_cta(p.n_sub, p.N) : cr_modes_per_cta(p.n_sub);
   return p;

@@ -824,4 +824,487 @@ int tc_set_flag(const TcPlan& t) {
   return KKT_OK;
 }
 
+namespace {
+
+// ---- FP64-accurate sine transforms on the tensor cores ---------------------------------
+//
+// The orthonormal DST-I of a line x (n - 1 points) is y_c = sum_k x_k Q[k][c]. Following the
+// error-free splitting of Ozaki, Ogita, Oishi and Rump ("Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its applications",
+// Numer. Algorithms 59, 2012), both operands are cut into digits that the tensor cores multiply
+// exactly:
+//   x = 2^E_r sum_{i=1..7} a_i 2^(-7i),  Q[k][c] = 2^G_c sum_{j=1..7} b_j 2^(-7j),
+// with a_i, b_j signed integers of at most 7 bits (|a| <= 127), E_r the exponent of line r's
+// largest entry and G_c that of column c's. Each digit plane a_i 2^(-7i) is exact in BF16. A
+// product plane sum_k a_i b_j 2^(-7(i+j)) is a multiple of 2^(-7L) (L = i + j) below
+// 127^2 * 256 * 2^(-7L) in magnitude, so up to four products of one level L accumulate exactly
+// in FP32 (4 * 127^2 * 256 < 2^24). Levels L = 2..5 (1, 2, 3 and 4 products) each get their
+// own exact TMEM accumulator and level 6 (5 products) two; levels 7 and 8 (13 products, at
+// most 2^-35 of the result) share one accumulator, which the tensor core's FP32 accumulation
+// rounds (measured: its error grows with the number of accumulation steps like a truncation,
+// which is why level 6 is kept exact), and levels 9 and above (about 2^-46 of the result) are
+// dropped: 28 BF16 products per tile instead of 49. The epilogue turns each accumulator into a
+// 64-bit integer in units of 2^-49 (exact for levels 2..6), sums them, and rounds once to
+// FP64, with integer operations only: y = 2^(E_r + G_c - 49) T.
+//
+// Kernel: persistent and warp-specialised like the reduced-precision transform. Warp 0 lane 0
+// streams the 7 digit planes of a 128-line x 64-K chunk of the input (one shared-memory buffer
+// per plane, each released as soon as the MMAs that read it complete) and the 7 planes of a
+// 64-column x 64-K chunk of Q (two stages) with TMA; warp 1 lane 0 issues the 28 products x 4
+// K-steps per chunk into the seven accumulators (7 x 64 TMEM columns); warps 2-9 recombine
+// and store the tile, transposed per slice as the next pass reads it.
+constexpr int kOzN = 64;                          // output columns per tile
+constexpr int kOzAcc = 7;                         // accumulators: levels 2, 3, 4, 5, 6 (two), 7-8
+
+// Accumulator of the product of digit planes i and j (0-based): level L = i + j + 2.
+__host__ __device__ constexpr int oz_acc(int i, int j) {
+  return i + j < 4 ? i + j : (i + j == 4 ? (i < 3 ? 4 : 5) : 6);
+}
+constexpr int kOzABytes = kTileM * kChunkBytes;   // one digit plane: 128 lines x 64 K (BF16)
+constexpr int kOzBBytes = kOzN * kChunkBytes;     // one digit plane of Q: 64 columns x 64 K
+constexpr int kOzEpiWarps = 8;                    // two per TMEM lane quadrant, 32 columns each
+constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
+constexpr size_t kOzSmem = 1024 + kOzDigits * kOzABytes + 2 * kOzDigits * kOzBBytes + 256;
+
+struct OzParams {
+  int P;              // padded line length (multiple of 64, at most 256)
+  int M;              // points per line
+  long long rows;     // lines
+  int rows_pad;       // lines rounded up to 128
+  const int* xexp;
+  const int* qexp;
+  double* out;        // [slices][M][M]; line r = s M + j, column c -> out[(s M + c) M + j]
+  int* err;
+};
+
+// BF16 bit pattern of sign * d * 2^(-7 level), 0 <= d < 128
+__host__ __device__ inline uint16_t oz_digit_bf16(unsigned d, int level, unsigned sign) {
+  if (d == 0) return 0;
+#ifdef __CUDA_ARCH__
+  const int p = 31 - __clz(static_cast<int>(d));
+#else
+  const int p = 31 - __builtin_clz(d);
+#endif
+  return static_cast<uint16_t>((sign << 15) | (static_cast<unsigned>(p - kOzDigitBits * level + 127) << 7) |
+                               ((d << (7 - p)) & 0x7Fu));
+}
+
+// |v| relative to 2^E with E = emax - 1022 (emax: the largest biased exponent of the line), as
+// a 49-bit fixed-point integer, truncated: floor(|v| 2^(49 - E)) = m >> (emax - e + 4).
+__host__ __device__ inline unsigned long long oz_fixed(unsigned long long bits, int emax) {
+  const int e = static_cast<int>((bits >> 52) & 0x7FF);
+  if (e == 0) return 0;   // zero (subnormals flushed)
+  const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = emax - e + 4;
+  return sh >= 64 ? 0ull : m >> sh;
+}
+
+// The seven digit planes of one value: digit i (1-based) = bits 49 - 7i .. 55 - 7i of F.
+__host__ __device__ inline void oz_split_value(unsigned long long bits, int emax, uint16_t* dig) {
+  const unsigned long long F = oz_fixed(bits, emax);
+  const unsigned sign = static_cast<unsigned>(bits >> 63);
+#pragma unroll
+  for (int i = 1; i <= kOzDigits; ++i)
+    dig[i - 1] = oz_digit_bf16(static_cast<unsigned>((F >> (49 - kOzDigitBits * i)) & 127ull), i, sign);
+}
+
+// One warp per line: the line's largest exponent, then its digit planes (EPL = P / 32
+// consecutive elements per lane, one 4-, 8- or 16-byte store per plane) and E_r. The line is
+// read coalesced (lane l: elements l, l + 32, ...) and regrouped through shared memory (one
+// padding word per 8, so that the regrouping reads conflict at most 2-way).
+template <int EPL>
+__global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict__ in, long long rows, int M, int P,
+                                                       int rows_pad, uint16_t* __restrict__ xs, int* __restrict__ xexp) {
+  __shared__ unsigned long long buf[8][32 * EPL + 4 * EPL];
+  const long long r = (static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5;
+  if (r >= rows) return;   // uniform per warp
+  const double* row = in + r * M;
+  int emax = 0;
+#pragma unroll
+  for (int t = 0; t < EPL; ++t) {
+    const int k = t * 32 + lane;
+    const unsigned long long bits = k < M ? static_cast<unsigned long long>(__double_as_longlong(row[k])) : 0ull;
+    emax = max(emax, static_cast<int>((bits >> 52) & 0x7FF));
+    buf[wb][k + (k >> 3)] = bits;
+  }
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  __syncwarp();
+  unsigned long long b[EPL];
+#pragma unroll
+  for (int t = 0; t < EPL; ++t) {
+    const int k = lane * EPL + t;
+    b[t] = buf[wb][k + (k >> 3)];
+  }
+  uint16_t d[EPL][kOzDigits];
+#pragma unroll
+  for (int t = 0; t < EPL; ++t) oz_split_value(b[t], emax, d[t]);
+#pragma unroll
+  for (int i = 0; i < kOzDigits; ++i) {
+    uint16_t* dst = xs + (static_cast<long long>(i) * rows_pad + r) * P + lane * EPL;
+    if constexpr (EPL == 8) {
+      uint4 v;
+      v.x = d[0][i] | (static_cast<unsigned>(d[1][i]) << 16);
+      v.y = d[2][i] | (static_cast<unsigned>(d[3][i]) << 16);
+      v.z = d[4][i] | (static_cast<unsigned>(d[5][i]) << 16);
+      v.w = d[6][i] | (static_cast<unsigned>(d[7][i]) << 16);
+      *reinterpret_cast<uint4*>(dst) = v;
+    } else if constexpr (EPL == 4) {
+      uint2 v;
+      v.x = d[0][i] | (static_cast<unsigned>(d[1][i]) << 16);
+      v.y = d[2][i] | (static_cast<unsigned>(d[3][i]) << 16);
+      *reinterpret_cast<uint2*>(dst) = v;
+    } else {
+      *reinterpret_cast<unsigned*>(dst) = d[0][i] | (static_cast<unsigned>(d[1][i]) << 16);
+    }
+  }
+  if (lane == 0) xexp[r] = emax ? emax - 1022 : 0;
+}
+
+// The seven accumulators of one output as T in units of 2^-49, then y = 2^k T in FP64. The
+// exact accumulators hold n 2^(-7L) with integer |n| < 2^24 (levels 2..6, L = 2..6), so
+// n = rint(acc 2^(7L)) is exact (a power-of-two product and an FP32 -> int32 conversion); the
+// tail (levels 7 and 8) is rounded to units of 2^-49. T = sum_L n_L 2^(7(7 - L)) + tail by
+// Horner's rule in 64-bit integers (|T| < 2^60), then one int64 -> FP64 rounding, and the
+// exponent k added to the bit pattern.
+__device__ __forceinline__ double oz_combine(const uint32_t* v, int k) {
+  const int n2 = __float2int_rn(__uint_as_float(v[0]) * 0x1p14f);
+  const int n3 = __float2int_rn(__uint_as_float(v[1]) * 0x1p21f);
+  const int n4 = __float2int_rn(__uint_as_float(v[2]) * 0x1p28f);
+  const int n5 = __float2int_rn(__uint_as_float(v[3]) * 0x1p35f);
+  const int n6 = __float2int_rn(__uint_as_float(v[4]) * 0x1p42f) + __float2int_rn(__uint_as_float(v[5]) * 0x1p42f);
+  const int tl = __float2int_rn(__uint_as_float(v[6]) * 0x1p49f);
+  long long T = static_cast<long long>(n2 * 128 + n3);   // < 2^30
+  T = T * 128 + n4;
+  T = T * 128 + n5;
+  T = T * 128 + n6;
+  T = T * 128 + tl;
+  const long long b = __double_as_longlong(__ll2double_rn(T));
+  const long long sgn = b & static_cast<long long>(0x8000000000000000ull);
+  const int e = static_cast<int>((b >> 52) & 0x7FF) + k;
+  long long r = b + (static_cast<long long>(k) << 52);
+  r = e <= 0 ? sgn : r;                              // below the normal range: signed zero
+  r = e >= 2047 ? (sgn | 0x7FF0000000000000ll) : r;  // above it: infinity
+  r = T == 0 ? 0ll : r;
+  return __longlong_as_double(r);
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, OzParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sa = smem;                                   // [7] planes of the input chunk
+  uint8_t* sb = smem + kOzDigits * kOzABytes;           // [2 stages][7] planes of the Q chunk
+  uint64_t* a_full = reinterpret_cast<uint64_t*>(sb + 2 * kOzDigits * kOzBBytes);
+  uint64_t* a_empty = a_full + kOzDigits;
+  uint64_t* b_full = a_empty + kOzDigits;               // [2]
+  uint64_t* b_empty = b_full + 2;                       // [2]
+  uint64_t* t_full = b_empty + 2;
+  uint64_t* t_empty = t_full + 1;
+  uint64_t* done = t_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  constexpr int KCHUNK = kChunkBytes / 2;               // 64 BF16 of K per chunk
+  constexpr int K_STEPS = KCHUNK / 16;                  // 4 MMAs of K = 16 per chunk and product
+  constexpr uint32_t IDESC = instr_desc<__nv_bfloat16, kOzN>();
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nct = p.P / kOzN, nchunks = p.P / KCHUNK;
+  const long long ntiles = static_cast<long long>(p.rows_pad / kTileM) * nct;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kOzDigits; ++i) {
+      mbar_init(a_full + i, 1);
+      mbar_init(a_empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(b_full + i, 1);
+      mbar_init(b_empty + i, 1);
+    }
+    mbar_init(t_full, 1);
+    mbar_init(t_empty, kOzEpiWarps);
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  long long a_loads = 0, b_loads = 0;   // producer: chunks whose plane copies were issued
+  if (warp == 0) {
+    if (lane == 0) {
+      long long g = 0;
+      for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+        const int rt = static_cast<int>(tile / nct), ct = static_cast<int>(tile % nct);
+        for (int c = 0; c < nchunks && !*abort_flag; ++c, ++g) {
+          const int st = static_cast<int>(g & 1);
+          if (g >= 2 && !mbar_wait(b_empty + st, static_cast<uint32_t>(((g >> 1) & 1) ^ 1))) {
+            *abort_flag = 1;
+            break;
+          }
+          mbar_expect_tx(b_full + st, kOzDigits * kOzBBytes);
+          for (int j = 0; j < kOzDigits; ++j)
+            tma_load_2d(sb + (st * kOzDigits + j) * kOzBBytes, &tmQ, c * KCHUNK, j * p.P + ct * kOzN, b_full + st);
+          b_loads = g + 1;
+          for (int i = 0; i < kOzDigits; ++i) {
+            if (g >= 1 && !mbar_wait(a_empty + i, static_cast<uint32_t>((g & 1) ^ 1))) {
+              *abort_flag = 1;
+              break;
+            }
+            mbar_expect_tx(a_full + i, kOzABytes);
+            tma_load_2d(sa + i * kOzABytes, &tmX, c * KCHUNK, i * p.rows_pad + rt * kTileM, a_full + i);
+          }
+          if (*abort_flag) break;
+          a_loads = g + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      long long g = 0;
+      int lt = 0;
+      for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++lt) {
+        if (lt >= 1 && !mbar_wait(t_empty, static_cast<uint32_t>((lt & 1) ^ 1))) {
+          *abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        uint32_t fresh = (1u << kOzAcc) - 1;   // accumulators not yet written in this tile
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int st = static_cast<int>(g & 1);
+          if (!mbar_wait(b_full + st, static_cast<uint32_t>((g >> 1) & 1))) {
+            *abort_flag = 1;
+            break;
+          }
+          const uint8_t* sbs = sb + st * kOzDigits * kOzBBytes;
+#pragma unroll
+          for (int i = 0; i < kOzDigits; ++i) {
+            if (!mbar_wait(a_full + i, static_cast<uint32_t>(g & 1))) {
+              *abort_flag = 1;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t da = smem_desc(sa + i * kOzABytes);
+#pragma unroll
+            for (int j = 0; j + i < kOzDigits; ++j) {
+              const int acc = oz_acc(i, j);
+              const uint64_t db = smem_desc(sbs + j * kOzBBytes);
+              const uint32_t tacc = tmem + static_cast<uint32_t>(acc * kOzN);
+              const uint32_t first = (fresh >> acc) & 1u;
+#pragma unroll
+              for (int kk = 0; kk < K_STEPS; ++kk)
+                MmaKind<__nv_bfloat16>::mma(tacc, da + 2ull * kk, db + 2ull * kk, IDESC, (first && kk == 0) ? 0u : 1u);
+              fresh &= ~(1u << acc);
+            }
+            // plane i of this chunk is free once these MMAs complete
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(smem_u32(a_empty + i)) : "memory");
+          }
+          if (*abort_flag) break;
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       ::"r"(smem_u32(b_empty + st)) : "memory");
+        }
+        if (*abort_flag) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(t_full)) : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(done)) : "memory");
+    }
+  } else {
+    // epilogue warps 2..9: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the tile's lines) and
+    // the 32 columns (w - 2) / 4 of the tile's 64
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    int lt = 0;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+      if (*abort_flag) break;
+      if (!mbar_wait(t_full, static_cast<uint32_t>(lt & 1))) {
+        *abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int rt = static_cast<int>(tile / nct), ct = static_cast<int>(tile % nct);
+      const long long r = static_cast<long long>(rt) * kTileM + quad * 32 + lane;
+      const bool row_ok = r < p.rows;
+      const unsigned ru = static_cast<unsigned>(row_ok ? r : 0);
+      const unsigned sl = ru / static_cast<unsigned>(p.M), jj = ru - sl * static_cast<unsigned>(p.M);
+      const int er = row_ok ? p.xexp[r] : 0;
+      double* obase = p.out + static_cast<long long>(sl) * p.M * p.M + jj;
+      const uint32_t tbase = tmem + (static_cast<uint32_t>(quad * 32) << 16);
+#pragma unroll 1
+      for (int c0 = half * 32; c0 < half * 32 + 32; c0 += 16) {
+        // the 16 columns' exponents G_c - 49, one per lane, broadcast by shuffles below
+        const int cl = ct * kOzN + c0 + (lane & 15);
+        const int gl = (cl < p.P ? __ldg(p.qexp + cl) : 0) - 49;
+        uint32_t v[kOzAcc][16];
+#pragma unroll
+        for (int a = 0; a < kOzAcc; ++a)
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
+                "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
+              : "r"(tbase + static_cast<uint32_t>(a * kOzN + c0)));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+          const int c = ct * kOzN + c0 + t;
+          const int k = er + __shfl_sync(0xffffffffu, gl, t);
+          uint32_t w[kOzAcc];
+#pragma unroll
+          for (int a = 0; a < kOzAcc; ++a) w[a] = v[a][t];
+          if (row_ok && c < p.M) obase[static_cast<long long>(c) * p.M] = oz_combine(w, k);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(t_empty)) : "memory");
+    }
+  }
+  __syncwarp();
+  if (!mbar_wait(done, 0)) *abort_flag = 1;
+  __syncthreads();
+  if (*abort_flag) {
+    if (threadIdx.x == 0) atomicExch(p.err, 1);
+    // let this CTA's copies land before its shared memory is released: the last load of every
+    // input plane and of the last two Q stages
+    if (warp == 0 && lane == 0) {
+      if (a_loads > 0)
+        for (int i = 0; i < kOzDigits; ++i) mbar_wait(a_full + i, static_cast<uint32_t>((a_loads - 1) & 1));
+      for (long long k = b_loads > 2 ? b_loads - 2 : 0; k < b_loads; ++k)
+        mbar_wait(b_full + static_cast<int>(k & 1), static_cast<uint32_t>((k >> 1) & 1));
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
+int oz_split(const OzPlan& o, const double* in, cudaStream_t st) {
+  const long long threads = o.rows * 32;
+  const unsigned grid = static_cast<unsigned>((threads + 255) / 256);
+  ProfScope ps(KKT_K_DST, st, 0.0, 8.0 * o.rows * o.M + 2.0 * kOzDigits * static_cast<double>(o.rows) * o.P);
+  uint16_t* xs = static_cast<uint16_t*>(o.xs);
+  if (o.P == 256) oz_split_kernel<8><<<grid, 256, 0, st>>>(in, o.rows, o.M, o.P, o.rows_pad, xs, o.xexp);
+  else if (o.P == 128) oz_split_kernel<4><<<grid, 256, 0, st>>>(in, o.rows, o.M, o.P, o.rows_pad, xs, o.xexp);
+  else oz_split_kernel<2><<<grid, 256, 0, st>>>(in, o.rows, o.M, o.P, o.rows_pad, xs, o.xexp);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int oz_gemm(const OzPlan& o, double* out, cudaStream_t st) {
+  static bool attr = false;
+  if (!attr) {
+    KKT_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(kOzSmem)));
+    attr = true;
+  }
+  int dev = 0, sms = 0;
+  KKT_CUDA_TRY(cudaGetDevice(&dev));
+  KKT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long ntiles = static_cast<long long>(o.rows_pad / kTileM) * (o.P / kOzN);
+  const unsigned grid = static_cast<unsigned>(std::min<long long>(ntiles, sms));
+  OzParams p{o.P, o.M, o.rows, o.rows_pad, o.xexp, o.qexp, out, o.err};
+  // 28 BF16 digit-plane products per tile (2 rows_pad P^2 FLOP each); digit planes in, FP64 out
+  ProfScope ps(KKT_K_DST, st, 28.0 * 2.0 * o.rows_pad * static_cast<double>(o.P) * o.P,
+               2.0 * kOzDigits * static_cast<double>(o.rows_pad) * o.P + 8.0 * static_cast<double>(o.rows) * o.M);
+  oz_gemm_kernel<<<grid, kOzThreads, kOzSmem, st>>>(o.map_x, o.map_q, p);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+}  // namespace
+
+int oz_plan_create(OzPlan& o, int n, int slices) {
+  o = OzPlan();
+  if (n < 2 || n - 1 > 255) return set_error(KKT_ERR_UNSUPPORTED, "tensor-core FP64 transform: lines of 1..255 points");
+  o.n = n;
+  o.M = n - 1;
+  o.P = o.M <= 64 ? 64 : (o.M <= 128 ? 128 : 256);
+  o.slices = slices;
+  o.rows = static_cast<long long>(slices) * o.M;
+  if ((o.rows + kTileM - 1) / kTileM * kTileM * kOzDigits > 0x7FFFFFFFLL)
+    return set_error(KKT_ERR_UNSUPPORTED, "tensor-core FP64 transform: too many lines");
+  o.rows_pad = static_cast<int>((o.rows + kTileM - 1) / kTileM * kTileM);
+  const int P = o.P, M = o.M;
+  // Q's digit planes and column exponents (host, integer arithmetic on the FP64 entries)
+  std::vector<uint16_t> qs(static_cast<size_t>(kOzDigits) * P * P, 0);
+  std::vector<int> qexp(P, 0);
+  const double pi = 3.14159265358979323846, scale = std::sqrt(2.0 / n);
+  std::vector<double> col(M);
+  for (int c = 0; c < M; ++c) {
+    int emax = 0;
+    for (int k = 0; k < M; ++k) {
+      col[k] = scale * std::sin(pi * (k + 1.0) * (c + 1.0) / n);
+      unsigned long long b;
+      std::memcpy(&b, &col[k], 8);
+      emax = std::max(emax, static_cast<int>((b >> 52) & 0x7FF));
+    }
+    qexp[c] = emax ? emax - 1022 : 0;
+    for (int k = 0; k < M; ++k) {
+      unsigned long long b;
+      std::memcpy(&b, &col[k], 8);
+      uint16_t d[kOzDigits];
+      oz_split_value(b, emax, d);
+      for (int j = 0; j < kOzDigits; ++j) qs[(static_cast<size_t>(j) * P + c) * P + k] = d[j];
+    }
+  }
+  const size_t qbytes = qs.size() * 2, xbytes = static_cast<size_t>(kOzDigits) * o.rows_pad * P * 2;
+  KKT_CUDA_TRY(cudaMalloc(&o.qs, qbytes));
+  KKT_CUDA_TRY(cudaMalloc(&o.qexp, P * sizeof(int)));
+  KKT_CUDA_TRY(cudaMalloc(&o.xs, xbytes));
+  KKT_CUDA_TRY(cudaMalloc(&o.xexp, o.rows_pad * sizeof(int)));
+  KKT_CUDA_TRY(cudaMalloc(&o.tmp, static_cast<size_t>(o.rows) * M * sizeof(double)));
+  KKT_CUDA_TRY(cudaMalloc(&o.err, sizeof(int)));
+  KKT_CUDA_TRY(cudaMemcpy(o.qs, qs.data(), qbytes, cudaMemcpyHostToDevice));
+  KKT_CUDA_TRY(cudaMemcpy(o.qexp, qexp.data(), P * sizeof(int), cudaMemcpyHostToDevice));
+  // padding lines and columns stay zero: the split writes only lines < rows and columns < P
+  KKT_CUDA_TRY(cudaMemset(o.xs, 0, xbytes));
+  KKT_CUDA_TRY(cudaMemset(o.xexp, 0, o.rows_pad * sizeof(int)));
+  KKT_CUDA_TRY(cudaMemset(o.err, 0, sizeof(int)));
+  o.bytes = qbytes + xbytes + P * sizeof(int) + o.rows_pad * sizeof(int) + o.rows * M * sizeof(double) + sizeof(int);
+  KKT_TRY(make_map(&o.map_x, o.xs, 2, static_cast<long long>(kOzDigits) * o.rows_pad, P, kTileM));
+  KKT_TRY(make_map(&o.map_q, o.qs, 2, static_cast<long long>(kOzDigits) * P, P, kOzN));
+  return KKT_OK;
+}
+
+void oz_plan_destroy(OzPlan& o) {
+  cudaFree(o.qs);
+  cudaFree(o.qexp);
+  cudaFree(o.xs);
+  cudaFree(o.xexp);
+  cudaFree(o.tmp);
+  cudaFree(o.err);
+  o = OzPlan();
+}
+
+// Both directions: along x (lines = rows of each slice) into tmp, transposed per slice, then
+// along the lines of tmp (the columns of the input) into out, transposed back: out = the 2D
+// transform in the input's [slice][y][x] layout. in and out may be the same array.
+int oz_dst2d(const OzPlan& o, const double* in, double* out, cudaStream_t st) {
+  KKT_TRY(oz_split(o, in, st));
+  KKT_TRY(oz_gemm(o, o.tmp, st));
+  KKT_TRY(oz_split(o, o.tmp, st));
+  return oz_gemm(o, out, st);
+}
+
+int oz_check(const OzPlan& o, cudaStream_t st) {
+  if (!o.err) return KKT_OK;
+  int e = 0;
+  KKT_CUDA_TRY(cudaMemcpyAsync(&e, o.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  KKT_CUDA_TRY(cudaStreamSynchronize(st));
+  if (e) {
+    KKT_CUDA_TRY(cudaMemsetAsync(o.err, 0, sizeof(int), st));
+    return set_error(KKT_ERR_TIMEOUT, "a tensor-core FP64 transform timed out waiting on its pipeline");
+  }
+  return KKT_OK;
+}
+
 }  // namespace kkt

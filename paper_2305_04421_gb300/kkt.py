@@ -37,7 +37,7 @@ BASIS = {"physical": 0, "spectral": 1}
 LOCAL = {"rasq": 0, "ras": 1}
 COARSE_SOLVE = {"auto": 0, "thomas": 1, "cyclic": 2}
 STAGING = {"auto": 0, "copy_engine": 1}
-DST_METHOD = {"auto": 0, "tiles": 1, "lane": 2}
+DST_METHOD = {"auto": 0, "tiles": 1, "lane": 2, "tensor": 3}
 MLP_MODE = {"learned": 0, "none": 1, "network": 2}
 HISTORY_MAX = 1024
 
@@ -500,8 +500,9 @@ class Solver:
         self.info = kkt_get_info(self.h)
 
     def set_dst_method(self, method="auto"):
-        """FP64 sine transforms: 'auto' (timed at create), 'tiles' (warp per line) or 'lane'
-        (thread per line; lines of at most 31 points)."""
+        """FP64 sine transforms: 'auto' (timed at create), 'tiles' (warp per line), 'lane'
+        (thread per line; lines of at most 31 points) or 'tensor' (FP64-accurate digit-plane
+        GEMMs on the tensor cores; square grids of at most 256 intervals)."""
         _check(load_library().kkt_set_dst_method(self.h, DST_METHOD[method]))
 
     def set_staging(self, mode="auto"):

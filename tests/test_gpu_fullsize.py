@@ -4,7 +4,8 @@
   lines and the mixed workload's 511-point FP64 reference) on full-spectrum random input,
   out of place and in place, against SciPy's orthonormal DST-I: 1e-13 norm-wise, and per time
   slice element by element (each slice's largest error below 1e-13 of that slice's largest
-  value).
+  value); the tensor-core FP64 transform to its own stated bound (TENSOR_DST_TOL), at the
+  benchmark size and at other padded lengths, inside the preconditioner and in a tight solve.
 * The headline solve (256 x 256, Nt = 1024, N_D = 64, omega = 1e-4, sine-series target on the
   modes k, l <= 8, 1e-8 weighted relative residual from x_0 = 0) against the exact solution.
   The right-hand side lives on those 64 sine modes, so the exact solution does too: the
@@ -50,19 +51,80 @@ def slicewise_close(got, want, tol, n_slices):
     assert bad.size == 0, f"slices {bad[:8]}: error {err[bad[:8]]} vs scale {scale[bad[:8]]}"
 
 
-@pytest.mark.parametrize("n,Nt", [(256, 3), (512, 2)])
+# The tensor-core FP64 transform (seven 7-bit digits per operand, levels 9 and above dropped,
+# levels 7-8 accumulated with the tensor core's rounding) carries about 2^-46 of each line's
+# scale per output; measured 3e-14 (n = 16) to 6e-14 (n = 256) norm-wise against SciPy.
+TENSOR_DST_TOL = 2e-13
+
+
+@pytest.mark.parametrize("n,Nt,method", [(256, 3, "tiles"), (512, 2, "tiles"), (256, 3, "tensor")])
 @pytest.mark.parametrize("inplace", [False, True])
-def test_full_size_dst2d_on_full_spectrum_input(kkt, n, Nt, inplace):
+def test_full_size_dst2d_on_full_spectrum_input(kkt, n, Nt, method, inplace):
     p = HeatKKT(nx=n, ny=n, Nt=Nt)
     s = kkt.Solver(n, n, Nt, 1.0, 1.0, 1e-4, 1)
+    s.set_dst_method(method)
+    tol = 1e-13 if method == "tiles" else TENSOR_DST_TOL
     x = workloads.random_vector(p.V, 40 + n + Nt)
     t = torch.from_numpy(x).cuda()
     y = s.dst2d(t, out=t) if inplace else s.dst2d(t)
     torch.cuda.synchronize()
     got = y.cpu().numpy()
     want = spectral.dst2(x, p).ravel()
-    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-13
-    slicewise_close(got, want, 1e-13, Nt)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < tol
+    slicewise_close(got, want, tol, Nt)
+    s.close()
+
+
+@pytest.mark.parametrize("n,Nt", [(64, 5), (100, 3), (128, 4), (200, 2)])
+def test_tensor_dst2d_matches_scipy(kkt, n, Nt):
+    """Padded line lengths 64, 128 and 256, power-of-two and other interval counts, ragged
+    last 128-line tiles; out of place and in place."""
+    p = HeatKKT(nx=n, ny=n, Nt=Nt)
+    s = kkt.Solver(n, n, Nt, 1.0, 1.0, 1e-4, 1)
+    s.set_dst_method("tensor")
+    x = workloads.random_vector(p.V, 70 + n)
+    want = spectral.dst2(x, p).ravel()
+    got = s.dst2d(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < TENSOR_DST_TOL
+    slicewise_close(got, want, TENSOR_DST_TOL, Nt)
+    t = torch.from_numpy(x).cuda()
+    s.dst2d(t, out=t)
+    s.dst2d(t, out=t)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(t.cpu().numpy() - x) / np.linalg.norm(x) < 2 * TENSOR_DST_TOL   # involution
+    s.close()
+
+
+def test_tensor_dst_rejected_where_it_does_not_apply(kkt):
+    for shape in ((64, 32), (512, 512)):
+        s = kkt.Solver(shape[0], shape[1], 4, 1.0, 1.0, 1e-4, 2)
+        with pytest.raises(kkt.KKTError) as e:
+            s.set_dst_method("tensor")
+        assert e.value.status == kkt.KKT_ERR_UNSUPPORTED
+        s.close()
+
+
+@pytest.mark.parametrize("n,Nt,nd", [(64, 40, 8), (128, 24, 6)])
+def test_tensor_dst_preconditioner_and_solve_match_oracle(kkt, n, Nt, nd):
+    """The two-level Schur preconditioner with the tensor-core transforms against the oracle
+    (1e-10, per time slice as well), and a 1e-12 solve against the exact per-mode solution."""
+    from oracle import schwarz
+    w = workloads.Workload("t", nx=n, ny=n, Nt=Nt, n_sub=nd, omega=1e-4, target="sine-series", seed=3)
+    p = HeatKKT(nx=n, ny=n, Nt=Nt, nu=w.nu, omega=w.omega)
+    s = kkt.Solver(n, n, Nt, w.T, w.nu, w.omega, nd)
+    s.set_dst_method("tensor")
+    pre = schwarz.schur_preconditioner(p, nd)
+    r = workloads.random_vector(p.V, 19)
+    got = s.schur_precond_apply(torch.from_numpy(r).cuda()).cpu().numpy()
+    want = pre.apply(r)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-10
+    slicewise_close(got, want, 1e-10, Nt)
+    f = problem.assemble_rhs(p, workloads.make_target(w), None)
+    res = s.solve(torch.from_numpy(f).cuda(), tol=1e-12, maxit=420)
+    assert res.status == kkt.KKT_OK
+    exact = spectral.kkt_exact_solve(p, f)
+    x = res.x.cpu().numpy()
+    assert np.linalg.norm(x - exact) / np.linalg.norm(exact) < 1e-10
     s.close()
 
 
