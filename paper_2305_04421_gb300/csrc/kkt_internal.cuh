@@ -121,10 +121,11 @@ struct TcPlan {
 
 // FP64-accurate sine transform on the tensor cores (square grids, at most 255 points per line):
 // every line and every column of the DST matrix is scaled by its own power of two and cut into
-// kOzDigits signed digits of kOzDigitBits bits, each digit plane exact in BF16; digit-plane
-// products accumulate exactly in FP32 (tcgen05, TMEM) and are recombined in 64-bit integers.
-constexpr int kOzDigits = 7;
-constexpr int kOzDigitBits = 7;
+// kOzDigits balanced signed digits of kOzDigitBits bits, each digit plane exact in BF16;
+// digit-plane products accumulate exactly in FP32 (tcgen05, TMEM) and are recombined in 64-bit
+// integers.
+constexpr int kOzDigits = 6;
+constexpr int kOzDigitBits = 8;
 struct OzPlan {
   int n = 0;            // intervals per direction (lines of n - 1 points)
   int M = 0;            // n - 1

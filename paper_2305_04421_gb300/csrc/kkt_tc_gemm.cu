@@ -833,38 +833,41 @@ namespace {
 // multiplication by using fast routines of matrix multiplication and its applications",
 // Numer. Algorithms 59, 2012), both operands are cut into digits that the tensor cores multiply
 // exactly:
-//   x = 2^E_r sum_{i=1..7} a_i 2^(-7i),  Q[k][c] = 2^G_c sum_{j=1..7} b_j 2^(-7j),
-// with a_i, b_j signed integers of at most 7 bits (|a| <= 127), E_r the exponent of line r's
-// largest entry and G_c that of column c's. Each digit plane a_i 2^(-7i) is exact in BF16. A
-// product plane sum_k a_i b_j 2^(-7(i+j)) is a multiple of 2^(-7L) (L = i + j) below
-// 127^2 * 256 * 2^(-7L) in magnitude, so up to four products of one level L accumulate exactly
-// in FP32 (4 * 127^2 * 256 < 2^24). Levels L = 2..5 (1, 2, 3 and 4 products) each get their
-// own exact TMEM accumulator and level 6 (5 products) two; levels 7 and 8 (13 products, at
-// most 2^-35 of the result) share one accumulator, which the tensor core's FP32 accumulation
-// rounds (measured: its error grows with the number of accumulation steps like a truncation,
-// which is why level 6 is kept exact), and levels 9 and above (about 2^-46 of the result) are
-// dropped: 28 BF16 products per tile instead of 49. The epilogue turns each accumulator into a
-// 64-bit integer in units of 2^-49 (exact for levels 2..6), sums them, and rounds once to
-// FP64, with integer operations only: y = 2^(E_r + G_c - 49) T.
+//   x = 2^E_r sum_{i=1..6} a_i 2^(-8i),  Q[k][c] = 2^G_c sum_{j=1..6} b_j 2^(-8j),
+// with E_r one above the exponent of line r's largest entry (so |x| < 2^(E_r - 1)), G_c the same
+// for column c, and a_i, b_j balanced signed digits: the base-256 digits, less 128, of the
+// 48-bit fixed-point value plus 128 in every digit position, so |a_i| <= 128 (the leading digit
+// reaches 128 only at the top of its range). Each digit plane a_i 2^(-8i) is exact in BF16. A
+// product plane sum_k a_i b_j 2^(-8(i+j)) is a multiple of 2^(-8L) (L = i + j) of magnitude
+// at most 2^14 * 256 * 2^(-8L), so up to four products of one level accumulate exactly in FP32
+// (4 * 2^22 = 2^24). Levels L = 2..5 (1, 2, 3 and 4 products) each get their own exact TMEM
+// accumulator; levels 6 and 7 (11 products, at most 2^-32 of the result) share one accumulator,
+// which the tensor core's FP32 accumulation rounds (measured: its error grows with the number
+// of accumulation steps like a truncation, 2^-49 of the result here), and levels 8 and above
+// (about 2^-46 of the result) are dropped: 21 BF16 products per tile instead of 36. The
+// epilogue turns the five accumulators into one 64-bit integer in units of 2^-48 (exact for
+// levels 2..5) and rounds it once to FP64: y = 2^(E_r + G_c - 48) T.
 //
 // Kernel: persistent and warp-specialised like the reduced-precision transform. Warp 0 lane 0
-// streams the 7 digit planes of a 128-line x 64-K chunk of the input (one shared-memory buffer
-// per plane, each released as soon as the MMAs that read it complete) and the 7 planes of a
-// 64-column x 64-K chunk of Q (two stages) with TMA; warp 1 lane 0 issues the 28 products x 4
-// K-steps per chunk into the seven accumulators (7 x 64 TMEM columns); warps 2-9 recombine
-// and store the tile, transposed per slice as the next pass reads it.
+// streams the 6 digit planes of a 128-line x 64-K chunk of the input (one shared-memory buffer
+// per plane, each released as soon as the MMAs that read it complete) and the 6 planes of a
+// 64-column x 64-K chunk of Q (two stages) with TMA; warp 1 lane 0 issues the 21 products x 4
+// K-steps per chunk into the five accumulators (5 x 64 TMEM columns); warps 2-9 fold the
+// accumulators into 64-bit integers, release them to the next tile's MMAs, then round and
+// store the tile, transposed per slice as the next pass reads it.
 constexpr int kOzN = 64;                          // output columns per tile
-constexpr int kOzAcc = 7;                         // accumulators: levels 2, 3, 4, 5, 6 (two), 7-8
+constexpr int kOzAcc = 5;                         // accumulators: levels 2, 3, 4, 5 and 6-7
+constexpr int kOzProducts = kOzDigits * (kOzDigits + 1) / 2;
 
 // Accumulator of the product of digit planes i and j (0-based): level L = i + j + 2.
-__host__ __device__ constexpr int oz_acc(int i, int j) {
-  return i + j < 4 ? i + j : (i + j == 4 ? (i < 3 ? 4 : 5) : 6);
-}
+__host__ __device__ constexpr int oz_acc(int i, int j) { return i + j < 4 ? i + j : 4; }
+
 constexpr int kOzABytes = kTileM * kChunkBytes;   // one digit plane: 128 lines x 64 K (BF16)
 constexpr int kOzBBytes = kOzN * kChunkBytes;     // one digit plane of Q: 64 columns x 64 K
 constexpr int kOzEpiWarps = 8;                    // two per TMEM lane quadrant, 32 columns each
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
 constexpr size_t kOzSmem = 1024 + kOzDigits * kOzABytes + 2 * kOzDigits * kOzBBytes + 256;
+constexpr unsigned long long kOzBias = 0x808080808080ull;   // 128 in each of the six digit positions
 
 struct OzParams {
   int P;              // padded line length (multiple of 64, at most 256)
@@ -877,35 +880,46 @@ struct OzParams {
   int* err;
 };
 
-// BF16 bit pattern of sign * d * 2^(-7 level), 0 <= d < 128
-__host__ __device__ inline uint16_t oz_digit_bf16(unsigned d, int level, unsigned sign) {
-  if (d == 0) return 0;
-#ifdef __CUDA_ARCH__
-  const int p = 31 - __clz(static_cast<int>(d));
-#else
-  const int p = 31 - __builtin_clz(d);
-#endif
-  return static_cast<uint16_t>((sign << 15) | (static_cast<unsigned>(p - kOzDigitBits * level + 127) << 7) |
-                               ((d << (7 - p)) & 0x7Fu));
-}
-
-// |v| relative to 2^E with E = emax - 1022 (emax: the largest biased exponent of the line), as
-// a 49-bit fixed-point integer, truncated: floor(|v| 2^(49 - E)) = m >> (emax - e + 4).
+// |v| 2^(48 - E) truncated to an integer, E = emax - 1021 (emax: the line's largest biased
+// exponent): m >> (emax - e + 6), below 2^47.
 __host__ __device__ inline unsigned long long oz_fixed(unsigned long long bits, int emax) {
   const int e = static_cast<int>((bits >> 52) & 0x7FF);
   if (e == 0) return 0;   // zero (subnormals flushed)
   const unsigned long long m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = emax - e + 4;
+  const int sh = emax - e + 6;
   return sh >= 64 ? 0ull : m >> sh;
 }
 
-// The seven digit planes of one value: digit i (1-based) = bits 49 - 7i .. 55 - 7i of F.
-__host__ __device__ inline void oz_split_value(unsigned long long bits, int emax, uint16_t* dig) {
+// The biased fixed-point value U = 128 in each digit position + sign * F (0 < U < 2^48 + 2^40).
+__host__ __device__ inline unsigned long long oz_biased(unsigned long long bits, int emax) {
   const unsigned long long F = oz_fixed(bits, emax);
-  const unsigned sign = static_cast<unsigned>(bits >> 63);
-#pragma unroll
-  for (int i = 1; i <= kOzDigits; ++i)
-    dig[i - 1] = oz_digit_bf16(static_cast<unsigned>((F >> (49 - kOzDigitBits * i)) & 127ull), i, sign);
+  return (bits >> 63) ? kOzBias - F : kOzBias + F;
+}
+
+// Balanced digit i (1-based) of U: -128..127 (the leading one up to 128).
+__host__ __device__ inline int oz_digit(unsigned long long U, int i) {
+  return i == 1 ? static_cast<int>(U >> 40) - 128
+                : static_cast<int>((U >> (48 - kOzDigitBits * i)) & 255ull) - 128;
+}
+
+// BF16 bit pattern of d 2^(-8 level), |d| <= 128 (host side: the digit planes of Q)
+inline uint16_t oz_digit_bf16(int d, int level) {
+  if (d == 0) return 0;
+  const unsigned a = static_cast<unsigned>(d < 0 ? -d : d), sign = d < 0 ? 1u : 0u;
+  const int p = 31 - __builtin_clz(a);
+  return static_cast<uint16_t>((sign << 15) | (static_cast<unsigned>(p - kOzDigitBits * level + 127) << 7) |
+                               ((a << (7 - p)) & 0x7Fu));
+}
+
+// FP32 bit pattern of d 2^(-8i) (|d| <= 128, i = 1..6) in two FP32 operations: the float with
+// exponent 23 - 8i and fraction bits |d| is 2^(23-8i) + |d| 2^(-8i), and subtracting 2^(23-8i)
+// leaves |d| 2^(-8i) exactly. Its upper 16 bits are the BF16 digit (at most 8 significant bits:
+// no rounding).
+__device__ __forceinline__ uint32_t oz_digit_f32(int d, int i) {
+  const uint32_t base = static_cast<uint32_t>(150 - kOzDigitBits * i) << 23;
+  const unsigned a = static_cast<unsigned>(d < 0 ? -d : d);
+  const float v = __uint_as_float(base | a) - __uint_as_float(base);
+  return __float_as_uint(v) | (d < 0 ? 0x80000000u : 0u);
 }
 
 // One warp per line: the line's largest exponent, then its digit planes (EPL = P / 32
@@ -936,49 +950,47 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict_
     const int k = lane * EPL + t;
     b[t] = buf[wb][k + (k >> 3)];
   }
-  uint16_t d[EPL][kOzDigits];
+  unsigned long long U[EPL];
 #pragma unroll
-  for (int t = 0; t < EPL; ++t) oz_split_value(b[t], emax, d[t]);
+  for (int t = 0; t < EPL; ++t) U[t] = oz_biased(b[t], emax);
 #pragma unroll
-  for (int i = 0; i < kOzDigits; ++i) {
-    uint16_t* dst = xs + (static_cast<long long>(i) * rows_pad + r) * P + lane * EPL;
+  for (int i = 1; i <= kOzDigits; ++i) {
+    uint32_t w[EPL / 2];
+#pragma unroll
+    for (int t = 0; t < EPL; t += 2)   // upper halves of two FP32 patterns: two BF16 digits in one word
+      w[t / 2] = __byte_perm(oz_digit_f32(oz_digit(U[t], i), i), oz_digit_f32(oz_digit(U[t + 1], i), i), 0x7632);
+    uint16_t* dst = xs + (static_cast<long long>(i - 1) * rows_pad + r) * P + lane * EPL;
     if constexpr (EPL == 8) {
-      uint4 v;
-      v.x = d[0][i] | (static_cast<unsigned>(d[1][i]) << 16);
-      v.y = d[2][i] | (static_cast<unsigned>(d[3][i]) << 16);
-      v.z = d[4][i] | (static_cast<unsigned>(d[5][i]) << 16);
-      v.w = d[6][i] | (static_cast<unsigned>(d[7][i]) << 16);
-      *reinterpret_cast<uint4*>(dst) = v;
+      *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
     } else if constexpr (EPL == 4) {
-      uint2 v;
-      v.x = d[0][i] | (static_cast<unsigned>(d[1][i]) << 16);
-      v.y = d[2][i] | (static_cast<unsigned>(d[3][i]) << 16);
-      *reinterpret_cast<uint2*>(dst) = v;
+      *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
     } else {
-      *reinterpret_cast<unsigned*>(dst) = d[0][i] | (static_cast<unsigned>(d[1][i]) << 16);
+      *reinterpret_cast<unsigned*>(dst) = w[0];
     }
   }
-  if (lane == 0) xexp[r] = emax ? emax - 1022 : 0;
+  if (lane == 0) xexp[r] = emax ? emax - 1021 : 0;
 }
 
-// The seven accumulators of one output as T in units of 2^-49, then y = 2^k T in FP64. The
-// exact accumulators hold n 2^(-7L) with integer |n| < 2^24 (levels 2..6, L = 2..6), so
-// n = rint(acc 2^(7L)) is exact (a power-of-two product and an FP32 -> int32 conversion); the
-// tail (levels 7 and 8) is rounded to units of 2^-49. T = sum_L n_L 2^(7(7 - L)) + tail by
-// Horner's rule in 64-bit integers (|T| < 2^60), then one int64 -> FP64 rounding, and the
-// exponent k added to the bit pattern.
-__device__ __forceinline__ double oz_combine(const uint32_t* v, int k) {
-  const int n2 = __float2int_rn(__uint_as_float(v[0]) * 0x1p14f);
-  const int n3 = __float2int_rn(__uint_as_float(v[1]) * 0x1p21f);
-  const int n4 = __float2int_rn(__uint_as_float(v[2]) * 0x1p28f);
-  const int n5 = __float2int_rn(__uint_as_float(v[3]) * 0x1p35f);
-  const int n6 = __float2int_rn(__uint_as_float(v[4]) * 0x1p42f) + __float2int_rn(__uint_as_float(v[5]) * 0x1p42f);
-  const int tl = __float2int_rn(__uint_as_float(v[6]) * 0x1p49f);
-  long long T = static_cast<long long>(n2 * 128 + n3);   // < 2^30
-  T = T * 128 + n4;
-  T = T * 128 + n5;
-  T = T * 128 + n6;
-  T = T * 128 + tl;
+// The five accumulators of one output as T in units of 2^-48. The exact accumulators hold
+// n 2^(-8L) with integer |n| <= 2^24 (levels L = 2..5), so n = rint(acc 2^(8L)) is exact (a
+// power-of-two product and an FP32 -> int32 conversion); the tail (levels 6 and 7) is rounded
+// to units of 2^-48. T = sum_L n_L 2^(8(6 - L)) + tail by Horner's rule in 64-bit integers
+// (|T| < 2^55).
+__device__ __forceinline__ long long oz_fixed_sum(const uint32_t* v) {
+  const int n2 = __float2int_rn(__uint_as_float(v[0]) * 0x1p16f);
+  const int n3 = __float2int_rn(__uint_as_float(v[1]) * 0x1p24f);
+  const int n4 = __float2int_rn(__uint_as_float(v[2]) * 0x1p32f);
+  const int n5 = __float2int_rn(__uint_as_float(v[3]) * 0x1p40f);
+  const int tl = __float2int_rn(__uint_as_float(v[4]) * 0x1p48f);
+  long long T = static_cast<long long>(n2) * 256 + n3;
+  T = T * 256 + n4;
+  T = T * 256 + n5;
+  return T * 256 + tl;
+}
+
+// y = T 2^k rounded once to FP64 (one int64 -> FP64 conversion, then the exponent added to the
+// bit pattern; zero, and results outside the normal range, handled branch-free).
+__device__ __forceinline__ double oz_to_double(long long T, int k) {
   const long long b = __double_as_longlong(__ll2double_rn(T));
   const long long sgn = b & static_cast<long long>(0x8000000000000000ull);
   const int e = static_cast<int>((b >> 52) & 0x7FF) + k;
@@ -1138,34 +1150,41 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int er = row_ok ? p.xexp[r] : 0;
       double* obase = p.out + static_cast<long long>(sl) * p.M * p.M + jj;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(quad * 32) << 16);
-#pragma unroll 1
-      for (int c0 = half * 32; c0 < half * 32 + 32; c0 += 16) {
-        // the 16 columns' exponents G_c - 49, one per lane, broadcast by shuffles below
-        const int cl = ct * kOzN + c0 + (lane & 15);
-        const int gl = (cl < p.P ? __ldg(p.qexp + cl) : 0) - 49;
-        uint32_t v[kOzAcc][16];
+      // phase 1: the warp's 32 columns as 64-bit integers T (units of 2^-48), read 8 columns
+      // of all five accumulators at a time
+      long long T[32];
+#pragma unroll
+      for (int g8 = 0; g8 < 4; ++g8) {
+        const int c0 = half * 32 + g8 * 8;
+        uint32_t v[kOzAcc][8];
 #pragma unroll
         for (int a = 0; a < kOzAcc; ++a)
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-              : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
-                "=r"(v[a][6]), "=r"(v[a][7]), "=r"(v[a][8]), "=r"(v[a][9]), "=r"(v[a][10]), "=r"(v[a][11]),
-                "=r"(v[a][12]), "=r"(v[a][13]), "=r"(v[a][14]), "=r"(v[a][15])
-              : "r"(tbase + static_cast<uint32_t>(a * kOzN + c0)));
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
+                         "=r"(v[a][6]), "=r"(v[a][7])
+                       : "r"(tbase + static_cast<uint32_t>(a * kOzN + c0)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-          const int c = ct * kOzN + c0 + t;
-          const int k = er + __shfl_sync(0xffffffffu, gl, t);
+        for (int t = 0; t < 8; ++t) {
           uint32_t w[kOzAcc];
 #pragma unroll
           for (int a = 0; a < kOzAcc; ++a) w[a] = v[a][t];
-          if (row_ok && c < p.M) obase[static_cast<long long>(c) * p.M] = oz_combine(w, k);
+          T[g8 * 8 + t] = oz_fixed_sum(w);
         }
       }
+      // the accumulators are free for the next tile's MMAs
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(t_empty)) : "memory");
+      // phase 2: round to FP64 with the line's and the columns' exponents, store transposed
+      const int cl = ct * kOzN + half * 32 + lane;
+      const int gl = (cl < p.P ? __ldg(p.qexp + cl) : 0) - 48;
+#pragma unroll
+      for (int t = 0; t < 32; ++t) {
+        const int c = ct * kOzN + half * 32 + t;
+        const int k = er + __shfl_sync(0xffffffffu, gl, t);
+        if (row_ok && c < p.M) obase[static_cast<long long>(c) * p.M] = oz_to_double(T[t], k);
+      }
     }
   }
   __syncwarp();
@@ -1212,8 +1231,8 @@ int oz_gemm(const OzPlan& o, double* out, cudaStream_t st) {
   const long long ntiles = static_cast<long long>(o.rows_pad / kTileM) * (o.P / kOzN);
   const unsigned grid = static_cast<unsigned>(std::min<long long>(ntiles, sms));
   OzParams p{o.P, o.M, o.rows, o.rows_pad, o.xexp, o.qexp, out, o.err};
-  // 28 BF16 digit-plane products per tile (2 rows_pad P^2 FLOP each); digit planes in, FP64 out
-  ProfScope ps(KKT_K_DST, st, 28.0 * 2.0 * o.rows_pad * static_cast<double>(o.P) * o.P,
+  // kOzProducts BF16 digit-plane products per tile (2 rows_pad P^2 FLOP each); planes in, FP64 out
+  ProfScope ps(KKT_K_DST, st, kOzProducts * 2.0 * o.rows_pad * static_cast<double>(o.P) * o.P,
                2.0 * kOzDigits * static_cast<double>(o.rows_pad) * o.P + 8.0 * static_cast<double>(o.rows) * o.M);
   oz_gemm_kernel<<<grid, kOzThreads, kOzSmem, st>>>(o.map_x, o.map_q, p);
   KKT_CUDA_TRY(cudaGetLastError());
@@ -1247,13 +1266,13 @@ int oz_plan_create(OzPlan& o, int n, int slices) {
       std::memcpy(&b, &col[k], 8);
       emax = std::max(emax, static_cast<int>((b >> 52) & 0x7FF));
     }
-    qexp[c] = emax ? emax - 1022 : 0;
+    qexp[c] = emax ? emax - 1021 : 0;
     for (int k = 0; k < M; ++k) {
       unsigned long long b;
       std::memcpy(&b, &col[k], 8);
-      uint16_t d[kOzDigits];
-      oz_split_value(b, emax, d);
-      for (int j = 0; j < kOzDigits; ++j) qs[(static_cast<size_t>(j) * P + c) * P + k] = d[j];
+      const unsigned long long U = oz_biased(b, emax);
+      for (int j = 0; j < kOzDigits; ++j)
+        qs[(static_cast<size_t>(j) * P + c) * P + k] = oz_digit_bf16(oz_digit(U, j + 1), j + 1);
     }
   }
   const size_t qbytes = qs.size() * 2, xbytes = static_cast<size_t>(kOzDigits) * o.rows_pad * P * 2;
