@@ -255,7 +255,9 @@ int kkt_set_staging(kkt_handle* h, int mode);
 
 /* How the FP64 sine transforms are computed (kkt_dst2d and every FP64 preconditioner apply). */
 enum kkt_dst_method {
-  /* chosen per direction at kkt_create by timing the candidates (the default) */
+  /* chosen at kkt_create by timing the candidates (the default): the tile height or the
+   * thread-per-line transform per direction, then, on square grids of 64 to 256 intervals, the
+   * tensor-core transform against those as a whole 2D transform */
   KKT_DST_AUTO = 0,
   /* tiles of lines in shared memory: the half-length FFT when the number of intervals is a
    * power of two (>= 4), on about P / 4 lanes per line (one warp per line from 256 intervals
@@ -286,7 +288,8 @@ int kkt_solve_zero_guess(kkt_handle* h, const double* f, double* x, double tol, 
 /* out = Q in for every time slice: the orthonormal 2D DST-I along x then y (Q^2 = I), which
  * diagonalises the 5-point Laplacian of Eq 2. Blocks: in [n][j][i], out [n][l][k] (k the x mode,
  * fastest). FP64 precision: a half-length FFT per line for power-of-two interval counts, the
- * direct sum otherwise or for short lines (kkt_set_dst_method); in == out allowed. BF16 / TF32
+ * direct sum otherwise or for short lines, or the FP64-accurate digit-plane GEMMs on the tensor
+ * cores (kkt_set_dst_method; chosen at create where they time faster); in == out allowed. BF16 / TF32
  * precision (square grids): the two tensor-core GEMMs with Q, operands rounded to BF16 (the
  * intermediate too) or TF32, FP32 accumulation; in and out must not overlap. */
 int kkt_dst2d(kkt_handle* h, const double* in, double* out, void* stream);

@@ -96,6 +96,17 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
   return d;
 }
 
+// The same descriptor for 64-byte K rows with 64B swizzle: 8-row atoms 512 B apart.
+__device__ __forceinline__ uint64_t smem_desc64(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = (addr & 0x3FFFFull) >> 4;       // start address, bits [0,14)
+  d |= 1ull << 16;                             // leading byte offset (unused for swizzled K-major)
+  d |= (512ull >> 4) << 32;                    // stride byte offset: 8 rows x 64 B
+  d |= 1ull << 46;                             // descriptor version
+  d |= 4ull << 61;                             // swizzle: 64B
+  return d;
+}
+
 template <typename TIn>
 struct MmaKind;
 
@@ -601,18 +612,20 @@ int get_encode(EncodeFn* fn) {
   return KKT_OK;
 }
 
-// 2D tensor map over rows x P (K contiguous), box = (128 bytes of K) x box_rows, 128B swizzle.
-int make_map(CUtensorMap* map, const void* base, int elem_bytes, long long rows, int P, int box_rows) {
+// 2D tensor map over rows x P (K contiguous), box = (chunk_bytes of K) x box_rows, swizzled over
+// the box's rows: 128B swizzle for 128-byte chunks, 64B swizzle for 64-byte chunks.
+int make_map(CUtensorMap* map, const void* base, int elem_bytes, long long rows, int P, int box_rows,
+             int chunk_bytes = kChunkBytes) {
   EncodeFn enc = nullptr;
   KKT_TRY(get_encode(&enc));
   const cuuint64_t dims[2] = {static_cast<cuuint64_t>(P), static_cast<cuuint64_t>(rows)};
   const cuuint64_t strides[1] = {static_cast<cuuint64_t>(P) * elem_bytes};
-  const cuuint32_t box[2] = {static_cast<cuuint32_t>(kChunkBytes / elem_bytes), static_cast<cuuint32_t>(box_rows)};
+  const cuuint32_t box[2] = {static_cast<cuuint32_t>(chunk_bytes / elem_bytes), static_cast<cuuint32_t>(box_rows)};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = enc(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                         chunk_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(KKT_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(static_cast<int>(r)));
   return KKT_OK;
 }
@@ -849,10 +862,10 @@ namespace {
 // levels 2..5) and rounds it once to FP64: y = 2^(E_r + G_c - 48) T.
 //
 // Kernel: persistent and warp-specialised like the reduced-precision transform. Warp 0 lane 0
-// streams the 6 digit planes of a 128-line x 64-K chunk of the input (one shared-memory buffer
-// per plane, each released as soon as the MMAs that read it complete) and the 6 planes of a
-// 64-column x 64-K chunk of Q (two stages) with TMA; warp 1 lane 0 issues the 21 products x 4
-// K-steps per chunk into the five accumulators (5 x 64 TMEM columns); warps 2-9 fold the
+// streams, with TMA, the 6 digit planes of a 128-line x 32-K chunk of the input and the 6
+// planes of the matching 64-column x 32-K chunk of Q (64-byte rows, 64B swizzle) through a
+// 3-stage shared-memory ring; warp 1 lane 0 issues the 21 products x 2 K-steps per chunk into
+// the five accumulators (5 x 64 TMEM columns); warps 2-9 fold the
 // accumulators into 64-bit integers, release them to the next tile's MMAs, then round and
 // store the tile, transposed per slice as the next pass reads it.
 constexpr int kOzN = 64;                          // output columns per tile
@@ -862,11 +875,14 @@ constexpr int kOzProducts = kOzDigits * (kOzDigits + 1) / 2;
 // Accumulator of the product of digit planes i and j (0-based): level L = i + j + 2.
 __host__ __device__ constexpr int oz_acc(int i, int j) { return i + j < 4 ? i + j : 4; }
 
-constexpr int kOzABytes = kTileM * kChunkBytes;   // one digit plane: 128 lines x 64 K (BF16)
-constexpr int kOzBBytes = kOzN * kChunkBytes;     // one digit plane of Q: 64 columns x 64 K
+constexpr int kOzChunkBytes = 64;                 // K bytes per chunk row (32 BF16, 64B swizzle)
+constexpr int kOzABytes = kTileM * kOzChunkBytes; // one digit plane: 128 lines x 32 K
+constexpr int kOzBBytes = kOzN * kOzChunkBytes;   // one digit plane of Q: 64 columns x 32 K
+constexpr int kOzStageBytes = kOzDigits * (kOzABytes + kOzBBytes);   // 72 KB: every plane of a chunk
+constexpr int kOzStages = 3;
 constexpr int kOzEpiWarps = 8;                    // two per TMEM lane quadrant, 32 columns each
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
-constexpr size_t kOzSmem = 1024 + kOzDigits * kOzABytes + 2 * kOzDigits * kOzBBytes + 256;
+constexpr size_t kOzSmem = 1024 + kOzStages * kOzStageBytes + 256;
 constexpr unsigned long long kOzBias = 0x808080808080ull;   // 128 in each of the six digit positions
 
 struct OzParams {
@@ -971,23 +987,6 @@ __global__ void __launch_bounds__(256) oz_split_kernel(const double* __restrict_
   if (lane == 0) xexp[r] = emax ? emax - 1021 : 0;
 }
 
-// The five accumulators of one output as T in units of 2^-48. The exact accumulators hold
-// n 2^(-8L) with integer |n| <= 2^24 (levels L = 2..5), so n = rint(acc 2^(8L)) is exact (a
-// power-of-two product and an FP32 -> int32 conversion); the tail (levels 6 and 7) is rounded
-// to units of 2^-48. T = sum_L n_L 2^(8(6 - L)) + tail by Horner's rule in 64-bit integers
-// (|T| < 2^55).
-__device__ __forceinline__ long long oz_fixed_sum(const uint32_t* v) {
-  const int n2 = __float2int_rn(__uint_as_float(v[0]) * 0x1p16f);
-  const int n3 = __float2int_rn(__uint_as_float(v[1]) * 0x1p24f);
-  const int n4 = __float2int_rn(__uint_as_float(v[2]) * 0x1p32f);
-  const int n5 = __float2int_rn(__uint_as_float(v[3]) * 0x1p40f);
-  const int tl = __float2int_rn(__uint_as_float(v[4]) * 0x1p48f);
-  long long T = static_cast<long long>(n2) * 256 + n3;
-  T = T * 256 + n4;
-  T = T * 256 + n5;
-  return T * 256 + tl;
-}
-
 // y = T 2^k rounded once to FP64 (one int64 -> FP64 conversion, then the exponent added to the
 // bit pattern; zero, and results outside the normal range, handled branch-free).
 __device__ __forceinline__ double oz_to_double(long long T, int k) {
@@ -1005,19 +1004,16 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, OzParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sa = smem;                                   // [7] planes of the input chunk
-  uint8_t* sb = smem + kOzDigits * kOzABytes;           // [2 stages][7] planes of the Q chunk
-  uint64_t* a_full = reinterpret_cast<uint64_t*>(sb + 2 * kOzDigits * kOzBBytes);
-  uint64_t* a_empty = a_full + kOzDigits;
-  uint64_t* b_full = a_empty + kOzDigits;               // [2]
-  uint64_t* b_empty = b_full + 2;                       // [2]
-  uint64_t* t_full = b_empty + 2;
-  uint64_t* t_empty = t_full + 1;
-  uint64_t* done = t_empty + 1;
+  // stage st: planes A_0..A_5 (kOzABytes each), then B_0..B_5 (kOzBBytes each)
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStageBytes);
+  uint64_t* empty = full + kOzStages;
+  uint64_t* t_full = empty + kOzStages;
+  uint64_t* t_empty = t_full + 1;          // [kOzAcc]: accumulator a drained by the epilogue
+  uint64_t* done = t_empty + kOzAcc;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  constexpr int KCHUNK = kChunkBytes / 2;               // 64 BF16 of K per chunk
-  constexpr int K_STEPS = KCHUNK / 16;                  // 4 MMAs of K = 16 per chunk and product
+  constexpr int KCHUNK = kOzChunkBytes / 2;             // 32 BF16 of K per chunk
+  constexpr int K_STEPS = KCHUNK / 16;                  // 2 MMAs of K = 16 per chunk and product
   constexpr uint32_t IDESC = instr_desc<__nv_bfloat16, kOzN>();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1025,16 +1021,12 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   const long long ntiles = static_cast<long long>(p.rows_pad / kTileM) * nct;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kOzDigits; ++i) {
-      mbar_init(a_full + i, 1);
-      mbar_init(a_empty + i, 1);
-    }
-    for (int i = 0; i < 2; ++i) {
-      mbar_init(b_full + i, 1);
-      mbar_init(b_empty + i, 1);
+    for (int i = 0; i < kOzStages; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
     }
     mbar_init(t_full, 1);
-    mbar_init(t_empty, kOzEpiWarps);
+    for (int a = 0; a < kOzAcc; ++a) mbar_init(t_empty + a, kOzEpiWarps);
     mbar_init(done, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1049,32 +1041,26 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  long long a_loads = 0, b_loads = 0;   // producer: chunks whose plane copies were issued
+  long long issued = 0;   // producer: chunks whose copies were issued
   if (warp == 0) {
     if (lane == 0) {
       long long g = 0;
       for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
         const int rt = static_cast<int>(tile / nct), ct = static_cast<int>(tile % nct);
-        for (int c = 0; c < nchunks && !*abort_flag; ++c, ++g) {
-          const int st = static_cast<int>(g & 1);
-          if (g >= 2 && !mbar_wait(b_empty + st, static_cast<uint32_t>(((g >> 1) & 1) ^ 1))) {
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int st = static_cast<int>(g % kOzStages);
+          if (g >= kOzStages && !mbar_wait(empty + st, static_cast<uint32_t>(((g / kOzStages) & 1) ^ 1))) {
             *abort_flag = 1;
             break;
           }
-          mbar_expect_tx(b_full + st, kOzDigits * kOzBBytes);
-          for (int j = 0; j < kOzDigits; ++j)
-            tma_load_2d(sb + (st * kOzDigits + j) * kOzBBytes, &tmQ, c * KCHUNK, j * p.P + ct * kOzN, b_full + st);
-          b_loads = g + 1;
-          for (int i = 0; i < kOzDigits; ++i) {
-            if (g >= 1 && !mbar_wait(a_empty + i, static_cast<uint32_t>((g & 1) ^ 1))) {
-              *abort_flag = 1;
-              break;
-            }
-            mbar_expect_tx(a_full + i, kOzABytes);
-            tma_load_2d(sa + i * kOzABytes, &tmX, c * KCHUNK, i * p.rows_pad + rt * kTileM, a_full + i);
-          }
           if (*abort_flag) break;
-          a_loads = g + 1;
+          uint8_t* sst = smem + st * kOzStageBytes;
+          mbar_expect_tx(full + st, kOzStageBytes);
+          for (int i = 0; i < kOzDigits; ++i)
+            tma_load_2d(sst + i * kOzABytes, &tmX, c * KCHUNK, i * p.rows_pad + rt * kTileM, full + st);
+          for (int j = 0; j < kOzDigits; ++j)
+            tma_load_2d(sst + kOzDigits * kOzABytes + j * kOzBBytes, &tmQ, c * KCHUNK, j * p.P + ct * kOzN, full + st);
+          issued = g + 1;
         }
       }
     }
@@ -1083,45 +1069,57 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       long long g = 0;
       int lt = 0;
       for (long long tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x, ++lt) {
-        if (lt >= 1 && !mbar_wait(t_empty, static_cast<uint32_t>((lt & 1) ^ 1))) {
-          *abort_flag = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        uint32_t fresh = (1u << kOzAcc) - 1;   // accumulators not yet written in this tile
         for (int c = 0; c < nchunks; ++c, ++g) {
-          const int st = static_cast<int>(g & 1);
-          if (!mbar_wait(b_full + st, static_cast<uint32_t>((g >> 1) & 1))) {
+          const int st = static_cast<int>(g % kOzStages);
+          if (!mbar_wait(full + st, static_cast<uint32_t>((g / kOzStages) & 1))) {
             *abort_flag = 1;
             break;
           }
-          const uint8_t* sbs = sb + st * kOzDigits * kOzBBytes;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint8_t* sst = smem + st * kOzStageBytes;
+          const uint8_t* sbq = sst + kOzDigits * kOzABytes;
+          if (c == 0) {
+            // the tile's first chunk, level by level: accumulator a is overwritten only after
+            // the epilogue has drained it from the previous tile (its own barrier), so these
+            // MMAs overlap the previous tile's epilogue
 #pragma unroll
-          for (int i = 0; i < kOzDigits; ++i) {
-            if (!mbar_wait(a_full + i, static_cast<uint32_t>(g & 1))) {
-              *abort_flag = 1;
-              break;
+            for (int a = 0; a < kOzAcc; ++a) {
+              if (lt >= 1 && !mbar_wait(t_empty + a, static_cast<uint32_t>((lt & 1) ^ 1))) {
+                *abort_flag = 1;
+                break;
+              }
+              asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+              const uint32_t tacc = tmem + static_cast<uint32_t>(a * kOzN);
+              bool first = true;
+#pragma unroll
+              for (int i = 0; i < kOzDigits; ++i)
+#pragma unroll
+                for (int j = 0; j + i < kOzDigits; ++j) {
+                  if (oz_acc(i, j) != a) continue;
+                  const uint64_t da = smem_desc64(sst + i * kOzABytes), db = smem_desc64(sbq + j * kOzBBytes);
+#pragma unroll
+                  for (int kk = 0; kk < K_STEPS; ++kk)
+                    MmaKind<__nv_bfloat16>::mma(tacc, da + 2ull * kk, db + 2ull * kk, IDESC, (first && kk == 0) ? 0u : 1u);
+                  first = false;
+                }
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint64_t da = smem_desc(sa + i * kOzABytes);
+            if (*abort_flag) break;
+          } else {
 #pragma unroll
-            for (int j = 0; j + i < kOzDigits; ++j) {
-              const int acc = oz_acc(i, j);
-              const uint64_t db = smem_desc(sbs + j * kOzBBytes);
-              const uint32_t tacc = tmem + static_cast<uint32_t>(acc * kOzN);
-              const uint32_t first = (fresh >> acc) & 1u;
+            for (int i = 0; i < kOzDigits; ++i) {
+              const uint64_t da = smem_desc64(sst + i * kOzABytes);
 #pragma unroll
-              for (int kk = 0; kk < K_STEPS; ++kk)
-                MmaKind<__nv_bfloat16>::mma(tacc, da + 2ull * kk, db + 2ull * kk, IDESC, (first && kk == 0) ? 0u : 1u);
-              fresh &= ~(1u << acc);
+              for (int j = 0; j + i < kOzDigits; ++j) {
+                const uint64_t db = smem_desc64(sbq + j * kOzBBytes);
+                const uint32_t tacc = tmem + static_cast<uint32_t>(oz_acc(i, j) * kOzN);
+#pragma unroll
+                for (int kk = 0; kk < K_STEPS; ++kk) MmaKind<__nv_bfloat16>::mma(tacc, da + 2ull * kk, db + 2ull * kk, IDESC, 1u);
+              }
             }
-            // plane i of this chunk is free once these MMAs complete
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(smem_u32(a_empty + i)) : "memory");
           }
-          if (*abort_flag) break;
+          // this stage is free once its MMAs complete
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                       ::"r"(smem_u32(b_empty + st)) : "memory");
+                       ::"r"(smem_u32(empty + st)) : "memory");
         }
         if (*abort_flag) break;
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -1150,32 +1148,33 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int er = row_ok ? p.xexp[r] : 0;
       double* obase = p.out + static_cast<long long>(sl) * p.M * p.M + jj;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(quad * 32) << 16);
-      // phase 1: the warp's 32 columns as 64-bit integers T (units of 2^-48), read 8 columns
-      // of all five accumulators at a time
+      // phase 1: the warp's 32 columns as 64-bit integers T in units of 2^-48, one accumulator
+      // at a time, each released to the next tile's MMAs as soon as it is folded in. The exact
+      // accumulators hold n 2^(-8L) with integer |n| <= 2^24 (levels L = 2..5), so
+      // n = rint(acc 2^(8L)) is exact (a power-of-two product and an FP32 -> int32 conversion);
+      // the tail (levels 6 and 7) is rounded to units of 2^-48. Horner's rule from level 2 on,
+      // T = 256 T + n, gives T = sum_L n_L 2^(8(6 - L)) + tail (|T| < 2^55).
       long long T[32];
 #pragma unroll
-      for (int g8 = 0; g8 < 4; ++g8) {
-        const int c0 = half * 32 + g8 * 8;
-        uint32_t v[kOzAcc][8];
+      for (int t = 0; t < 32; ++t) T[t] = 0;
 #pragma unroll
-        for (int a = 0; a < kOzAcc; ++a)
+      for (int a = 0; a < kOzAcc; ++a) {
+        const float scale = a == 0 ? 0x1p16f : a == 1 ? 0x1p24f : a == 2 ? 0x1p32f : a == 3 ? 0x1p40f : 0x1p48f;
+#pragma unroll
+        for (int g8 = 0; g8 < 4; ++g8) {
+          uint32_t v[8];
           asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                       : "=r"(v[a][0]), "=r"(v[a][1]), "=r"(v[a][2]), "=r"(v[a][3]), "=r"(v[a][4]), "=r"(v[a][5]),
-                         "=r"(v[a][6]), "=r"(v[a][7])
-                       : "r"(tbase + static_cast<uint32_t>(a * kOzN + c0)));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                       : "r"(tbase + static_cast<uint32_t>(a * kOzN + half * 32 + g8 * 8)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          uint32_t w[kOzAcc];
-#pragma unroll
-          for (int a = 0; a < kOzAcc; ++a) w[a] = v[a][t];
-          T[g8 * 8 + t] = oz_fixed_sum(w);
+          for (int t = 0; t < 8; ++t)
+            T[g8 * 8 + t] = T[g8 * 8 + t] * 256 + __float2int_rn(__uint_as_float(v[t]) * scale);
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(t_empty + a)) : "memory");
       }
-      // the accumulators are free for the next tile's MMAs
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(t_empty)) : "memory");
       // phase 2: round to FP64 with the line's and the columns' exponents, store transposed
       const int cl = ct * kOzN + half * 32 + lane;
       const int gl = (cl < p.P ? __ldg(p.qexp + cl) : 0) - 48;
@@ -1192,13 +1191,11 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   __syncthreads();
   if (*abort_flag) {
     if (threadIdx.x == 0) atomicExch(p.err, 1);
-    // let this CTA's copies land before its shared memory is released: the last load of every
-    // input plane and of the last two Q stages
+    // let this CTA's copies land before its shared memory is released (only the last
+    // kOzStages issued chunks can still be in flight)
     if (warp == 0 && lane == 0) {
-      if (a_loads > 0)
-        for (int i = 0; i < kOzDigits; ++i) mbar_wait(a_full + i, static_cast<uint32_t>((a_loads - 1) & 1));
-      for (long long k = b_loads > 2 ? b_loads - 2 : 0; k < b_loads; ++k)
-        mbar_wait(b_full + static_cast<int>(k & 1), static_cast<uint32_t>((k >> 1) & 1));
+      for (long long c = issued > kOzStages ? issued - kOzStages : 0; c < issued; ++c)
+        mbar_wait(full + static_cast<int>(c % kOzStages), static_cast<uint32_t>((c / kOzStages) & 1));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1289,8 +1286,8 @@ int oz_plan_create(OzPlan& o, int n, int slices) {
   KKT_CUDA_TRY(cudaMemset(o.xexp, 0, o.rows_pad * sizeof(int)));
   KKT_CUDA_TRY(cudaMemset(o.err, 0, sizeof(int)));
   o.bytes = qbytes + xbytes + P * sizeof(int) + o.rows_pad * sizeof(int) + o.rows * M * sizeof(double) + sizeof(int);
-  KKT_TRY(make_map(&o.map_x, o.xs, 2, static_cast<long long>(kOzDigits) * o.rows_pad, P, kTileM));
-  KKT_TRY(make_map(&o.map_q, o.qs, 2, static_cast<long long>(kOzDigits) * P, P, kOzN));
+  KKT_TRY(make_map(&o.map_x, o.xs, 2, static_cast<long long>(kOzDigits) * o.rows_pad, P, kTileM, kOzChunkBytes));
+  KKT_TRY(make_map(&o.map_q, o.qs, 2, static_cast<long long>(kOzDigits) * P, P, kOzN, kOzChunkBytes));
   return KKT_OK;
 }
 
