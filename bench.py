@@ -921,6 +921,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     probe_peaks(kkt)   # compute peaks of this GPU, before (and outside) every timed region
     solver = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
+    if args.dst_method != "auto":
+        solver.set_dst_method(args.dst_method)   # (under a profiler the create-time timing can pick another)
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
     f = solver.build_rhs(ut)
     x = torch.zeros_like(f)
@@ -1005,7 +1007,7 @@ def run_ours(args):
             "e2e": {"value": job_value(world, e2e_steps, e2e_s), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                     "d2h_bytes_per_step": nbytes, "staging": "copy kernel through the pinned buffers' device mapping",
                     "value_copy_engine": job_value(world, e2e_steps, e2e_ce_s), "host_link_gbs": link},
-            "gpu_launches": launches, "peaks_probed": dict(PROBE),
+            "gpu_launches": launches, "peaks_probed": dict(PROBE), "dst_method": solver.dst_method(),
             "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "kernel_launches": {k: v["launches"] for k, v in prof.items()},
             "clocks": clocks}
@@ -1062,6 +1064,8 @@ def main():
                     help="skip the learned-vs-plain coarse comparison on the 256 x 256, Nt = 2048 workload")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-instance batched vs one-after-another comparison")
+    ap.add_argument("--dst-method", choices=["auto", "tiles", "lane", "tensor"], default="auto",
+                    help="FP64 sine transforms of the benchmark solve (default: the create-time timing's choice)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64/BF16/TF32 time-to-solution comparison on the 512 x 512 workload")
     args = ap.parse_args()

@@ -277,6 +277,9 @@ enum kkt_dst_method {
  * KKT_DST_LANE when a direction has more than 31 points, and for KKT_DST_TENSOR on a
  * non-square grid or lines of more than 255 points. */
 int kkt_set_dst_method(kkt_handle* h, int method);
+/* The FP64 transform method in use (after KKT_DST_AUTO's timing): KKT_DST_TENSOR, KKT_DST_LANE
+ * when at least one direction runs thread-per-line, else KKT_DST_TILES. */
+int kkt_get_dst_method(const kkt_handle* h, int* method);
 
 /* kkt_solve from the initial guess x_0 = 0: x is output only (its contents on entry are not
  * read, and a host x is not uploaded). Otherwise identical, including the iterates. */

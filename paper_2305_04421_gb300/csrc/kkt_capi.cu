@@ -333,7 +333,7 @@ int schur_precond_w(kkt_handle* h, const double* rw, double scale, double* yw, c
   const bool sp = h->opt.tc_split != 0;
   const int mid = sp ? 3 : (t.bf16 ? 0 : 1);
   const int valid = h->g.nx - 1;
-  KKT_TRY(tc_pack(t, rw, 1.0, valid, st));                         // hi (+ lo) parts, unscaled
+  KKT_TRY(tc_pack(t, rw, valid, st));                              // hi (+ lo) parts, unscaled
   KKT_TRY(tc_gemm(t, 0, mid, t.x1, valid, st, sp, t.x1_lo));        // along x: [n][j][i] -> [n][k][j]
   KKT_TRY(tc_gemm(t, 1, 1, t.rhat, valid, st, sp));                 // along y: -> [n][l][k], FP32
   KKT_TRY(spectral_schur_precond_mixed(h, t.rhat, scale, t.yin, sp ? t.yin_lo : nullptr, t.bf16, st));
@@ -613,7 +613,7 @@ int kkt_dst2d(kkt_handle* h, const double* in, double* out, void* stream) {
   const TcPlan& t = h->tc;
   const int valid = h->g.nx - 1;
   const bool sp = h->opt.tc_split != 0;
-  KKT_TRY(tc_pack(t, in, 1.0, valid, st));
+  KKT_TRY(tc_pack(t, in, valid, st));
   KKT_TRY(tc_gemm(t, 0, sp ? 3 : (t.bf16 ? 0 : 1), t.x1, valid, st, sp, t.x1_lo));
   return tc_gemm(t, 1, 2, out, valid, st, sp);
 }
@@ -715,6 +715,14 @@ int kkt_set_dst_method(kkt_handle* h, int method) {
   KKT_TRY(check_handle(h));
   if (method < KKT_DST_AUTO || method > KKT_DST_TENSOR) return set_error(KKT_ERR_INVALID_ARG, "dst method out of range");
   return dst_set_method(h, method);
+}
+
+int kkt_get_dst_method(const kkt_handle* h, int* method) {
+  KKT_TRY(check_handle(h));
+  if (!method) return set_error(KKT_ERR_INVALID_ARG, "null method");
+  *method = h->dst_tensor ? KKT_DST_TENSOR
+                          : ((h->dst_x.lane_direct || h->dst_y.lane_direct) ? KKT_DST_LANE : KKT_DST_TILES);
+  return KKT_OK;
 }
 
 int kkt_set_staging(kkt_handle* h, int mode) {

@@ -287,7 +287,7 @@ void tc_plan_destroy(TcPlan& t);
 // valid, 3 hi + lo pair (out, out_lo); split: the input and Q as hi + lo parts (3 products)
 int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, cudaStream_t st, bool split = false,
             void* out_lo = nullptr);
-int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStream_t st);   // -> x0
+int tc_pack(const TcPlan& t, const double* in, int valid, cudaStream_t st);   // -> x0 (+ x0_lo)
 int tc_check(const TcPlan& t, cudaStream_t st);
 // FP64-accurate transforms on the tensor cores (kkt_tc_gemm.cu)
 int oz_plan_create(OzPlan& o, int n, int slices);

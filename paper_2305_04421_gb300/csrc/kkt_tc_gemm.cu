@@ -158,25 +158,29 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// FP64 -> FP32 conversion in integer arithmetic. On this part the FP64 pipe (2 instructions
-// per clock per SM) also executes F2F conversions, so the pack builds the bit patterns with
-// integer operations instead. Values below FP32's normal range are
-// flushed to zero, values above it become infinities, NaNs stay NaNs.
+// FP64 -> FP32 conversion in integer arithmetic on the two 32-bit halves of the bit pattern. On
+// this part the FP64 pipe (2 instructions per clock per SM) also executes F2F conversions, and a
+// version on 64-bit integers still kept that pipe 78 % busy under ncu, so the rounding uses
+// 32-bit operations only: the top 23 fraction bits come from the high word and the top 3 bits of
+// the low word, the other 29 bits of the low word decide the rounding (to nearest, ties to
+// even). Values below FP32's normal range are flushed to zero, values above it become
+// infinities, NaNs stay NaNs.
 __device__ __forceinline__ float f64_to_f32_rne(double d) {
-  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
-  const unsigned int sign = static_cast<unsigned int>(b >> 32) & 0x80000000u;
-  const int e = static_cast<int>((b >> 52) & 0x7ff);
-  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | (m ? 0x00400000u : 0u));
+  const unsigned hi = static_cast<unsigned>(__double2hiint(d)), lo = static_cast<unsigned>(__double2loint(d));
+  const unsigned sign = hi & 0x80000000u;
+  const int e = static_cast<int>((hi >> 20) & 0x7ffu);
+  unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  const unsigned rest = lo & 0x1FFFFFFFu;
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | ((m | rest) ? 0x00400000u : 0u));
   int e32 = e - 1023 + 127;
   if (e32 <= 0) return __uint_as_float(sign);
-  m += 0x0FFFFFFFull + ((m >> 29) & 1ull);   // round the 52-bit fraction to 23 bits, ties to even
-  if (m >> 52) {
+  m += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+  if (m >> 23) {
     m = 0;
     ++e32;
   }
   if (e32 >= 255) return __uint_as_float(sign | 0x7f800000u);
-  return __uint_as_float(sign | (static_cast<unsigned int>(e32) << 23) | static_cast<unsigned int>(m >> 29));
+  return __uint_as_float(sign | (static_cast<unsigned>(e32) << 23) | m);
 }
 
 // hi + lo split of a value in the operand type
@@ -548,8 +552,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TILE_N));
 }
 
-// out + out_lo (P x P per slice, zero padded) = scale * in[s][j][i] (valid x valid), split into
-// hi and lo parts of the operand type. No FP64 instruction in the default case (scale = 1): the
+// out + out_lo (P x P per slice, zero padded) = in[s][j][i] (valid x valid), split into hi and
+// lo parts of the operand type (callers fold any scale downstream). No FP64 instruction: the
 // value is rounded to FP32 by integer operations on its bit pattern (f64_to_f32_rne) and split
 // on the FP32 pipe (Split::make: hi = v rounded to the operand's significand, lo = v - hi, exact
 // in FP32). The FP32 rounding (2^-24 relative) is far below the split's own 2^-16 (BF16) and
@@ -570,8 +574,8 @@ struct Pair<float> {
 };
 
 template <typename TIn>
-__global__ void pack_kernel(const double* __restrict__ in, double scale, TIn* __restrict__ out,
-                            TIn* __restrict__ out_lo, int P, int valid) {
+__global__ void pack_kernel(const double* __restrict__ in, TIn* __restrict__ out, TIn* __restrict__ out_lo, int P,
+                            int valid) {
   const int i = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int j = blockIdx.y;
   const long long s = blockIdx.z;
@@ -580,11 +584,7 @@ __global__ void pack_kernel(const double* __restrict__ in, double scale, TIn* __
   float v0 = 0.f, v1 = 0.f;
   if (j < valid) {
     const double* row = in + (s * valid + j) * valid;
-    double d0 = i < valid ? row[i] : 0.0, d1 = i + 1 < valid ? row[i + 1] : 0.0;
-    if (scale != 1.0) {   // callers fold their scale downstream where they can
-      d0 *= scale;
-      d1 *= scale;
-    }
+    const double d0 = i < valid ? row[i] : 0.0, d1 = i + 1 < valid ? row[i + 1] : 0.0;
     v0 = f64_to_f32_rne(d0);
     v1 = f64_to_f32_rne(d1);
   }
@@ -801,7 +801,7 @@ int tc_gemm(const TcPlan& t, int which_in, int out_mode, void* out, int valid, c
   return set_error(KKT_ERR_UNSUPPORTED, "tensor-core transform: unsupported output mode");
 }
 
-int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStream_t st) {
+int tc_pack(const TcPlan& t, const double* in, int valid, cudaStream_t st) {
   const long long total = static_cast<long long>(t.slices) * t.P * t.P;
   const int tb = 256;
   if (t.slices > 65535) return set_error(KKT_ERR_UNSUPPORTED, "too many time slices for the pack grid");
@@ -809,10 +809,10 @@ int tc_pack(const TcPlan& t, const double* in, double scale, int valid, cudaStre
   const dim3 grid((t.P / 2 + tb - 1) / tb, t.P, t.slices);
   ProfScope ps(KKT_K_PACK, st, 0.0, 8.0 * t.slices * static_cast<double>(valid) * valid + 2.0 * (t.bf16 ? 2.0 : 4.0) * total);
   if (t.bf16)
-    pack_kernel<__nv_bfloat16><<<grid, tb, 0, st>>>(in, scale, static_cast<__nv_bfloat16*>(t.x0),
+    pack_kernel<__nv_bfloat16><<<grid, tb, 0, st>>>(in, static_cast<__nv_bfloat16*>(t.x0),
                                                      static_cast<__nv_bfloat16*>(t.x0_lo), t.P, valid);
   else
-    pack_kernel<float><<<grid, tb, 0, st>>>(in, scale, static_cast<float*>(t.x0), static_cast<float*>(t.x0_lo), t.P,
+    pack_kernel<float><<<grid, tb, 0, st>>>(in, static_cast<float*>(t.x0), static_cast<float*>(t.x0_lo), t.P,
                                             valid);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;

@@ -135,6 +135,7 @@ SIGNATURES = [
     ("kkt_solve_zero_guess", _I, [_P, _P, _P, _D, _I, ctypes.POINTER(KKTStats), _P]),
     ("kkt_set_staging", _I, [_P, _I]),
     ("kkt_set_dst_method", _I, [_P, _I]),
+    ("kkt_get_dst_method", _I, [_P, ctypes.POINTER(ctypes.c_int)]),
     ("kkt_dst2d", _I, [_P, _P, _P, _P]),
     ("kkt_schur_apply", _I, [_P, _P, _P, _P]),
     ("kkt_schur_precond_apply", _I, [_P, _P, _P, _P]),
@@ -504,6 +505,12 @@ class Solver:
         (thread per line; lines of at most 31 points) or 'tensor' (FP64-accurate digit-plane
         GEMMs on the tensor cores; square grids of at most 256 intervals)."""
         _check(load_library().kkt_set_dst_method(self.h, DST_METHOD[method]))
+
+    def dst_method(self) -> str:
+        """The FP64 transform method in use: 'tiles', 'lane' or 'tensor'."""
+        m = ctypes.c_int()
+        _check(load_library().kkt_get_dst_method(self.h, ctypes.byref(m)))
+        return {v: k for k, v in DST_METHOD.items()}[m.value]
 
     def set_staging(self, mode="auto"):
         """How solve() moves host vectors: 'auto' (pinned buffers by a copy kernel, pageable by
