@@ -863,6 +863,20 @@ def run_profile_case(args):
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    if args.profile_case == "tensor":
+        # the tensor-core FP64 transform alone: 256 x 256, Nt = 64 (16,320 lines of 255 points,
+        # 50 MB of digit planes), three 2D transforms of a seeded random block
+        n, Nt = 256, 64
+        s = kkt.Solver(n, n, Nt, 1.0, 1.0, 1e-4, 1)
+        s.set_dst_method("tensor")
+        x = torch.from_numpy(workloads.random_vector((n - 1) ** 2 * Nt, 1)).to(dev)
+        for _ in range(3):
+            y = s.dst2d(x)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "tensor-core FP64 2D transform 256x256 Nt=64",
+                          "finite": bool(torch.isfinite(y).all())}))
+        s.close()
+        return 0
     if args.profile_case == "batched":
         # two 128 x 128, Nt = 128, N_D = 16 instances (KKT vectors of 48 MB, a 1.5 GB Krylov basis
         # each) solved one after another and then together through the batched kernels (graphs
@@ -1049,10 +1063,12 @@ def main():
     ap.add_argument("--ref-iterations", type=int, default=25,
                     help="iterations the reference arm scales its per-iteration sample by")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-case", nargs="?", const="grid", choices=["grid", "paper", "batched"], default=None,
+    ap.add_argument("--profile-case", nargs="?", const="grid", choices=["grid", "paper", "batched", "tensor"],
+                    default=None,
                     help="run only a small solve for counter captures: 'grid' (default) 256 x 256, Nt = 96; "
                          "'paper' the Section 4 mesh (17 x 17 points) with Nt = 3200, 640 subdomains; "
-                         "'batched' two 128 x 128, Nt = 128 instances, single solves then the batched kernels")
+                         "'batched' two 128 x 128, Nt = 128 instances, single solves then the batched kernels; "
+                         "'tensor' three tensor-core FP64 2D transforms at 256 x 256, Nt = 64")
     ap.add_argument("--basis", choices=["physical", "spectral"], default="physical",
                     help="FGMRES basis of --profile-case")
     ap.add_argument("--precision", choices=["fp64", "bf16", "tf32"], default="fp64",
