@@ -105,12 +105,21 @@ def workload_for(omega: float) -> workloads.Workload:
                               target=w.target, seed=w.seed)
 
 
-def describe(w: workloads.Workload) -> dict:
+ORTH_TEXT = {
+    0: "modified Gram-Schmidt",
+    1: "classical Gram-Schmidt with one conditional repeat",
+    2: "modified Gram-Schmidt over pairs of basis vectors",
+    3: "modified Gram-Schmidt over blocks of four basis vectors",
+    4: "modified Gram-Schmidt over blocks of eight basis vectors",
+}
+
+
+def describe(w: workloads.Workload, orth: int = 2) -> dict:
     return {"workload": f"plain FP64 KKT solve nx=ny={w.nx} Nt={w.Nt} N_D={w.n_sub} nu={w.nu} omega={w.omega:g}",
             "nx": w.nx, "ny": w.ny, "Nt": w.Nt, "n_sub": w.n_sub, "nu": w.nu, "omega": w.omega,
             "unknowns": 3 * w.V, "tol": TOL, "restart": 30, "coarse": "exact two-level, multiplicative",
             "residual_norm": "discrete L2 pair (u, z rows weighted h^-1/2, state rows h^1/2)",
-            "orthogonalisation": "modified Gram-Schmidt over pairs of basis vectors",
+            "orthogonalisation": ORTH_TEXT[orth],
             "l2": "inputs larger than L2 (KKT vector 1.6 GB, Krylov basis ~66 GB)"}
 
 
@@ -301,7 +310,8 @@ def run_reference(args):
     value = 1.0 / solve_s
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": describe(w), "impl": "reference",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(w, kkt.kkt_get_options(solver.h).orth), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": sample + f"; x {iters} iterations (the GPU solve's count on this "
                                                 f"workload)"},
@@ -319,15 +329,14 @@ def run_reference(args):
 # MGS step and the sine transform come from a single-pass capture of the benchmark workload
 # itself; one-pass MGS from a capture of the 256 x 256, Nt = 96 case, whose traffic grows in
 # proportion to the elements processed. Kernels not listed report traffic null.
-TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgs2_step_kernel": 0.998, "dst_tile_kernel": 0.947}
+TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "dst_tile_kernel": 0.947}
 # FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, of peak sustained, active SMs) from the
 # --set full captures of the 256 x 256, Nt = 96 case: context for an "alu" roofline whose
 # achieved figure counts algorithmic FLOPs, not issued instructions.
-FP64_PIPE_BUSY = {"dst_tile_kernel": [0.78, 0.82], "mgs2_step_kernel": [0.86, 0.87],
-                  "sweep_kernel": [0.85, 0.85], "matvec_kernel": [0.83, 0.83]}
+FP64_PIPE_BUSY = {"dst_tile_kernel": [0.78, 0.82], "sweep_kernel": [0.85, 0.85], "matvec_kernel": [0.83, 0.83]}
 
 
-def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -> dict:
+def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64", orth: int = 2) -> dict:
     """Roofline of the kernel class with the largest device time in the timed region.
 
     The library sums, for every timed launch, the algorithmic FLOPs and bytes of that launch
@@ -359,7 +368,8 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64") -
             alu_peak = FP64_PEAK_TFLOPS
             alu_src = "derived: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (FP64)"
         alu_kind = "alu"
-        kname = {"dst": "dst_tile_kernel", "multidot": "mgs2_step_kernel", "update": "mgs2_step_kernel",
+        gs = {0: "mgs_step_kernel", 1: "update_norm_kernel"}.get(orth, "mgsb_step_kernel")
+        kname = {"dst": "dst_tile_kernel", "multidot": gs if orth != 1 else "multidot_kernel", "update": gs,
                  "axpy": "axpy_multi_kernel" if precision == "fp64" else "scale2_kernel",
                  "pack": "pack_kernel", "matvec": "matvec_kernel", "sweep": "sweep_kernel",
                  "coarse": "coarse_solve_kernel"}.get(top, top)
@@ -486,6 +496,7 @@ def measure_variants(kkt_mod, dev, w: workloads.Workload, physical_ms: float, st
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
     out = {}
     for name, opts in (("spectral_basis", {"basis": "spectral"}), ("mgs", {"orth": "mgs"}), ("cgs2", {"orth": "cgs2"}),
+                       ("mgs2", {"orth": "mgs2"}), ("mgs4", {"orth": "mgs4"}), ("mgs8", {"orth": "mgs8"}),
                        ("ras_local_solves", {"local": "ras"}), ("coarse_cyclic", {"coarse_solve": "cyclic"})):
         s = kkt_mod.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub, **opts)
         f = s.build_rhs(ut)
@@ -934,7 +945,8 @@ def run_ours(args):
     w = workload_for(args.omega)
     dev = torch.device("cuda", local)
     probe_peaks(kkt)   # compute peaks of this GPU, before (and outside) every timed region
-    solver = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub)
+    solver = kkt.Solver(w.nx, w.ny, w.Nt, w.T, w.nu, w.omega, w.n_sub,
+                        **({"orth": args.orth} if args.orth else {}))
     if args.dst_method != "auto":
         solver.set_dst_method(args.dst_method)   # (under a profiler the create-time timing can pick another)
     ut = torch.from_numpy(workloads.make_target(w).ravel()).to(dev)
@@ -1014,7 +1026,8 @@ def run_ours(args):
     apply_stats = time_applies(kkt, solver, w.V, 10, dev)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": describe(w),
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(w, kkt.kkt_get_options(solver.h).orth),
             "iterations": its, "converged": ok, "rel_residual": results[-1].rel_residual,
             "rel_residual_euclid": results[-1].rel_residual_euclid,
             "precond_applies_per_s": apply_stats["applies_per_s"], "precond_apply": apply_stats,
@@ -1025,7 +1038,7 @@ def run_ours(args):
             "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "kernel_launches": {k: v["launches"] for k, v in prof.items()},
             "clocks": clocks}
-    line["roofline"] = roofline(prof, peaks, peak_kind)
+    line["roofline"] = roofline(prof, peaks, peak_kind, orth=kkt.kkt_get_options(solver.h).orth)
     solver.close()
     del f, x, f_host, x_host
     torch.cuda.empty_cache()
@@ -1080,6 +1093,8 @@ def main():
                     help="skip the learned-vs-plain coarse comparison on the 256 x 256, Nt = 2048 workload")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the 64-instance batched vs one-after-another comparison")
+    ap.add_argument("--orth", choices=["mgs", "cgs2", "mgs2", "mgs4", "mgs8"], default=None,
+                    help="orthogonalisation of the timed solve (default: the library's)")
     ap.add_argument("--dst-method", choices=["auto", "tiles", "lane", "tensor"], default="auto",
                     help="FP64 sine transforms of the benchmark solve (default: the create-time timing's choice)")
     ap.add_argument("--no-forms", action="store_true",

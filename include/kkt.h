@@ -88,7 +88,13 @@ enum kkt_orth {
    * subtracted in one pass that also takes the next pair's dots. 3 vector passes per basis
    * vector instead of 4, the same FMA count; equals MGS up to the pair's orthogonality error.
    * The default. */
-  KKT_ORTH_MGS2 = 2
+  KKT_ORTH_MGS2 = 2,
+  /* the same over blocks of four basis vectors (block MGS with the block's dots taken on one
+   * w): 2.5 vector passes per basis vector, but each pass streams 9 vectors at once, which the
+   * DRAM serves more slowly: no faster than pairs on GB300 */
+  KKT_ORTH_MGS4 = 3,
+  /* the same over blocks of eight: 2.25 vector passes per basis vector, 17 streams per pass */
+  KKT_ORTH_MGS8 = 4
 };
 
 /* Local solves of the one-level part. */

@@ -460,6 +460,10 @@ kkt_batch* kkt_batch_create(int count, const kkt_instance* desc, const kkt_optio
   kkt_options o;
   kkt_default_options(&o);
   if (opt) o = *opt;
+  if (o.orth == KKT_ORTH_MGS4 || o.orth == KKT_ORTH_MGS8) {
+    set_error(KKT_ERR_UNSUPPORTED, "the batched form orthogonalises with MGS, paired MGS or CGS2");
+    return nullptr;
+  }
   if (o.precision != KKT_PREC_FP64 || o.coarse == KKT_COARSE_LEARNED) {
     set_error(KKT_ERR_UNSUPPORTED, "the batched form runs the FP64 exact or one-level preconditioner");
     return nullptr;

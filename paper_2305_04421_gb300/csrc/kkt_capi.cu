@@ -512,8 +512,7 @@ int kkt_set_options(kkt_handle* h, const kkt_options* opt) {
   if (opt->residual_norm != KKT_NORM_L2 && opt->residual_norm != KKT_NORM_EUCLIDEAN)
     return set_error(KKT_ERR_INVALID_ARG, "residual_norm out of range");
   if (opt->tc_split != 0 && opt->tc_split != 1) return set_error(KKT_ERR_INVALID_ARG, "tc_split must be 0 or 1");
-  if (opt->orth != KKT_ORTH_MGS && opt->orth != KKT_ORTH_CGS2 && opt->orth != KKT_ORTH_MGS2)
-    return set_error(KKT_ERR_INVALID_ARG, "orth out of range");
+  if (opt->orth < KKT_ORTH_MGS || opt->orth > KKT_ORTH_MGS8) return set_error(KKT_ERR_INVALID_ARG, "orth out of range");
   if (opt->local != KKT_LOCAL_RASQ && opt->local != KKT_LOCAL_RAS) return set_error(KKT_ERR_INVALID_ARG, "local out of range");
   if (opt->basis != KKT_BASIS_PHYSICAL && opt->basis != KKT_BASIS_SPECTRAL)
     return set_error(KKT_ERR_INVALID_ARG, "basis out of range");
@@ -891,22 +890,22 @@ static int solve_impl(kkt_handle* h, const double* f, double* x, double tol, int
                      dw));
       for (int k = 0; k <= j; ++k) Hs(k, j) = 0.0;
       double wnorm2 = 0.0;
-      if (h->opt.orth == KKT_ORTH_MGS2) {
-        // MGS over pairs of basis vectors: both dots of a pair are taken on the same w (the
-        // vectors of a pair are orthogonal to working accuracy), the pair is subtracted in one
-        // pass that also takes the next pair's dots: 3 vector passes per basis vector
-        auto vec = [&](int i) -> const double* { return Vb + static_cast<size_t>(i) * n3; };
-        const int nd0 = std::min(2, j + 1);
-        KKT_TRY(krylov_mgs2_step(h, 0, nullptr, nullptr, nullptr, 0.0, 0.0, nd0, vec(0), nd0 > 1 ? vec(1) : nullptr, W,
-                                 n3, h->red_out, st));
+      const int bs = orth_block(h->opt.orth);
+      if (bs > 1) {
+        // MGS over blocks of bs basis vectors: every dot of a block is taken on the same w (the
+        // vectors of a block are orthogonal to working accuracy), and the block is subtracted
+        // in one pass that also takes the next block's dots: 2 + 2 / bs vector passes per
+        // basis vector
+        const double* V0 = Vb;
+        double sc[8];
+        KKT_TRY(krylov_mgsb_step(h, bs, 0, nullptr, nullptr, nullptr, std::min(bs, j + 1), V0, n3, W, n3, h->red_out,
+                                 st));
         for (int k = 0; k <= j;) {
-          const int na = std::min(2, j + 1 - k);
-          const int nd = std::min(2, j + 1 - (k + na));
-          const double s0 = 1.0 / (eta[k] * eta[k]);
-          const double s1 = na > 1 ? 1.0 / (eta[k + 1] * eta[k + 1]) : 0.0;
-          KKT_TRY(krylov_mgs2_step(h, na, vec(k), na > 1 ? vec(k + 1) : nullptr, h->red_out + k, s0, s1, nd,
-                                   nd > 0 ? vec(k + na) : nullptr, nd > 1 ? vec(k + na + 1) : nullptr, W, n3,
-                                   h->red_out + k + na, st));
+          const int na = std::min(bs, j + 1 - k);
+          const int nd = std::min(bs, j + 1 - (k + na));
+          for (int a = 0; a < na; ++a) sc[a] = 1.0 / (eta[k + a] * eta[k + a]);
+          KKT_TRY(krylov_mgsb_step(h, bs, na, V0 + static_cast<size_t>(k) * n3, h->red_out + k, sc, nd,
+                                   V0 + static_cast<size_t>(k + na) * n3, n3, W, n3, h->red_out + k + na, st));
           k += na;
         }
         KKT_TRY(fetch(j + 2));

@@ -308,11 +308,15 @@ int krylov_norm2(kkt_handle* h, const double* x, long long n, cudaStream_t st); 
 // <Vn, w> (Vn non-null) or <w, w> (Vn null), reduced deterministically.
 int krylov_mgs_step(kkt_handle* h, const double* Vk, const double* dot, double s, const double* Vn, double* w,
                     long long n, double* out, cudaStream_t st);
-// Paired MGS step: w -= sum_{i < na} (dot[i] s_i) A_i, then out[0..nd) = <B_i, w> (nd > 0) or
-// out[0] = <w, w> (nd = 0); na, nd in 0..2.
-int krylov_mgs2_step(kkt_handle* h, int na, const double* A0, const double* A1, const double* dot, double s0,
-                     double s1, int nd, const double* B0, const double* B1, double* w, long long n, double* out,
-                     cudaStream_t st);
+// Basis vectors per block of the blocked MGS orthogonalisations (1: plain MGS or CGS2).
+inline int orth_block(int orth) {
+  return orth == KKT_ORTH_MGS2 ? 2 : orth == KKT_ORTH_MGS4 ? 4 : orth == KKT_ORTH_MGS8 ? 8 : 1;
+}
+// Blocked MGS step (block size bs = 2, 4 or 8): w -= sum_{a < na} (dot[a] s[a]) A_a with
+// A_a = A + a stride, then out[0..nd) = <B_d, w> with B_d = Bv + d stride (nd > 0) or
+// out[0] = <w, w> (nd = 0); na, nd in 0..bs.
+int krylov_mgsb_step(kkt_handle* h, int bs, int na, const double* A, const double* dot, const double* s, int nd,
+                     const double* Bv, long long stride, double* w, long long n, double* out, cudaStream_t st);
 int krylov_partial_capacity();
 
 // ---- batched forms: several instances per launch ---------------------------------------

@@ -170,69 +170,80 @@ __global__ void __launch_bounds__(kRedThreads) mgs_step_kernel(const double* __r
   if (threadIdx.x == 0) part[blockIdx.x] = t;
 }
 
-// Paired MGS step (blocks of two basis vectors): w -= c0 A0 + c1 A1 (NA of them, c_i =
-// dot[i] * s_i), then the partial dots <B0, w>, <B1, w> over the updated w (ND of them), or
-// <w, w> when ND = 0. part holds max(ND, 1) columns per block.
-template <int NA, int ND>
-__global__ void __launch_bounds__(kRedThreads) mgs2_step_kernel(const double* __restrict__ A0,
-                                                                const double* __restrict__ A1,
-                                                                const double* __restrict__ dot, double s0, double s1,
-                                                                const double* __restrict__ B0,
-                                                                const double* __restrict__ B1, double* __restrict__ w,
-                                                                long long n, double* __restrict__ part, bool vec2) {
+// Blocked MGS step (blocks of BS basis vectors; BS = 2, 4 or 8): w -= sum_{a < na} c_a A_a
+// (c_a = dot[a] * s_a, A_a = A + a stride), then the partial dots <B_d, w> (B_d = Bv + d stride,
+// d < nd) over the updated w, or <w, w> when NORM (nd = 0). part holds max(nd, 1) columns per
+// block. The counts are uniform over the grid, so the loads and FMAs of the unrolled loops are
+// predicated, not branched.
+template <int BS>
+struct MgsScale {
+  double s[BS];
+};
+
+template <int BS, bool NORM>
+__global__ void __launch_bounds__(kRedThreads) mgsb_step_kernel(const double* __restrict__ A,
+                                                                const double* __restrict__ Bv, long long stride,
+                                                                int na, int nd, const double* __restrict__ dot,
+                                                                MgsScale<BS> sc, double* __restrict__ w, long long n,
+                                                                double* __restrict__ part, bool vec2) {
   __shared__ double sh[32];
-  const double c0 = NA > 0 ? dot[0] * s0 : 0.0;
-  const double c1 = NA > 1 ? dot[1] * s1 : 0.0;
-  double acc0 = 0.0, acc1 = 0.0;
+  double c[BS], acc[BS];
+#pragma unroll
+  for (int a = 0; a < BS; ++a) {
+    c[a] = a < na ? dot[a] * sc.s[a] : 0.0;
+    acc[a] = 0.0;
+  }
   const long long gs = static_cast<long long>(gridDim.x) * blockDim.x;
   const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long np = pair_count(n, vec2);
+  const double2 z2 = make_double2(0.0, 0.0);
   for (long long i = tid; i < np; i += gs) {
     double2 wi = reinterpret_cast<const double2*>(w)[i];
-    if (NA > 0) {
-      const double2 a = reinterpret_cast<const double2*>(A0)[i];
-      double2 b = make_double2(0.0, 0.0);
-      if (NA > 1) b = reinterpret_cast<const double2*>(A1)[i];
-      wi.x = fma(-c0, a.x, wi.x);
-      wi.y = fma(-c0, a.y, wi.y);
-      if (NA > 1) {
-        wi.x = fma(-c1, b.x, wi.x);
-        wi.y = fma(-c1, b.y, wi.y);
-      }
+    double2 av[BS], bv[BS];
+#pragma unroll
+    for (int a = 0; a < BS; ++a) av[a] = a < na ? reinterpret_cast<const double2*>(A + a * stride)[i] : z2;
+#pragma unroll
+    for (int d = 0; d < BS; ++d) bv[d] = (!NORM && d < nd) ? reinterpret_cast<const double2*>(Bv + d * stride)[i] : z2;
+    if (na > 0) {
+#pragma unroll
+      for (int a = 0; a < BS; ++a)
+        if (a < na) {
+          wi.x = fma(-c[a], av[a].x, wi.x);
+          wi.y = fma(-c[a], av[a].y, wi.y);
+        }
       reinterpret_cast<double2*>(w)[i] = wi;
     }
-    if (ND == 0) {
-      acc0 = fma(wi.x, wi.x, fma(wi.y, wi.y, acc0));
+    if (NORM) {
+      acc[0] = fma(wi.x, wi.x, fma(wi.y, wi.y, acc[0]));
     } else {
-      const double2 u = reinterpret_cast<const double2*>(B0)[i];
-      acc0 = fma(u.x, wi.x, fma(u.y, wi.y, acc0));
-      if (ND > 1) {
-        const double2 v = reinterpret_cast<const double2*>(B1)[i];
-        acc1 = fma(v.x, wi.x, fma(v.y, wi.y, acc1));
-      }
+#pragma unroll
+      for (int d = 0; d < BS; ++d)
+        if (d < nd) acc[d] = fma(bv[d].x, wi.x, fma(bv[d].y, wi.y, acc[d]));
     }
   }
   for (long long i = 2 * np + tid; i < n; i += gs) {
     double wi = w[i];
-    if (NA > 0) {
-      wi = fma(-c0, A0[i], wi);
-      if (NA > 1) wi = fma(-c1, A1[i], wi);
+    if (na > 0) {
+#pragma unroll
+      for (int a = 0; a < BS; ++a)
+        if (a < na) wi = fma(-c[a], A[a * stride + i], wi);
       w[i] = wi;
     }
-    if (ND == 0) {
-      acc0 = fma(wi, wi, acc0);
+    if (NORM) {
+      acc[0] = fma(wi, wi, acc[0]);
     } else {
-      acc0 = fma(B0[i], wi, acc0);
-      if (ND > 1) acc1 = fma(B1[i], wi, acc1);
+#pragma unroll
+      for (int d = 0; d < BS; ++d)
+        if (d < nd) acc[d] = fma(Bv[d * stride + i], wi, acc[d]);
     }
   }
-  constexpr int W = ND > 1 ? 2 : 1;
-  const double t0 = block_sum(acc0, sh);
-  if (threadIdx.x == 0) part[static_cast<long long>(blockIdx.x) * W] = t0;
-  if (ND > 1) {
-    const double t1 = block_sum(acc1, sh);
-    if (threadIdx.x == 0) part[static_cast<long long>(blockIdx.x) * W + 1] = t1;
-  }
+  const int width = NORM ? 1 : nd;
+#pragma unroll
+  for (int d = 0; d < BS; ++d)
+    if (d < width) {
+      const double t = block_sum(acc[d], sh);
+      if (threadIdx.x == 0) part[static_cast<long long>(blockIdx.x) * width + d] = t;
+    }
 }
 
 __global__ void norm_kernel(const double* __restrict__ x, long long n, double* __restrict__ part) {
@@ -408,30 +419,42 @@ int krylov_mgs_step(kkt_handle* h, const double* Vk, const double* dot, double s
   return KKT_OK;
 }
 
-int krylov_mgs2_step(kkt_handle* h, int na, const double* A0, const double* A1, const double* dot, double s0,
-                     double s1, int nd, const double* B0, const double* B1, double* w, long long n, double* out,
-                     cudaStream_t st) {
-  if (na < 0 || na > 2 || nd < 0 || nd > 2 || (na == 0 && nd == 0))
-    return set_error(KKT_ERR_INVALID_ARG, "paired MGS step: bad vector counts");
+namespace {
+template <int BS>
+int launch_mgsb(int nb, const double* A, const double* Bv, long long stride, int na, int nd, const double* dot,
+                const double* s, double* w, long long n, double* part, bool vec2, cudaStream_t st) {
+  MgsScale<BS> sc{};
+  for (int a = 0; a < na; ++a) sc.s[a] = s[a];
+  if (nd == 0)
+    mgsb_step_kernel<BS, true><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+  else
+    mgsb_step_kernel<BS, false><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+}  // namespace
+
+int krylov_mgsb_step(kkt_handle* h, int bs, int na, const double* A, const double* dot, const double* s, int nd,
+                     const double* Bv, long long stride, double* w, long long n, double* out, cudaStream_t st) {
+  if ((bs != 2 && bs != 4 && bs != 8) || na < 0 || na > bs || nd < 0 || nd > bs || (na == 0 && nd == 0) ||
+      (na > 0 && (!A || !dot || !s)) || (nd > 0 && !Bv) || ((na > 1 || nd > 1) && stride < n))
+    return set_error(KKT_ERR_INVALID_ARG, "blocked MGS step: bad block size, vector counts or pointers");
   const int nb = grid_blocks();
-  bool vec2 = reinterpret_cast<uintptr_t>(w) % 16 == 0;
-  for (const double* p : {A0, A1, B0, B1})
-    if (p && reinterpret_cast<uintptr_t>(p) % 16) vec2 = false;
+  bool vec2 = reinterpret_cast<uintptr_t>(w) % 16 == 0 && stride % 2 == 0;
+  if (na > 0 && reinterpret_cast<uintptr_t>(A) % 16) vec2 = false;
+  if (nd > 0 && reinterpret_cast<uintptr_t>(Bv) % 16) vec2 = false;
   {
     // per element: na + max(nd, 1) FMA; reads na + nd vectors and w, writes w when na > 0
     const double fl = 2.0 * n * (na + (nd > 0 ? nd : 1));
     const double by = 8.0 * n * (na + nd + 1 + (na > 0 ? 1 : 0));
     ProfScope ps(na > 0 ? KKT_K_UPDATE : KKT_K_MULTIDOT, st, fl, by);
-#define KKT_MGS2(NA_, ND_)                                                                                     \
-  if (na == NA_ && nd == ND_)                                                                                 \
-    mgs2_step_kernel<NA_, ND_><<<nb, kRedThreads, 0, st>>>(A0, A1, dot, s0, s1, B0, B1, w, n, h->red, vec2);
-    KKT_MGS2(0, 1) KKT_MGS2(0, 2) KKT_MGS2(1, 0) KKT_MGS2(1, 1) KKT_MGS2(1, 2) KKT_MGS2(2, 0) KKT_MGS2(2, 1)
-    KKT_MGS2(2, 2)
-#undef KKT_MGS2
-    KKT_CUDA_TRY(cudaGetLastError());
+    const int rc = bs == 2   ? launch_mgsb<2>(nb, A, Bv, stride, na, nd, dot, s, w, n, h->red, vec2, st)
+                   : bs == 4 ? launch_mgsb<4>(nb, A, Bv, stride, na, nd, dot, s, w, n, h->red, vec2, st)
+                             : launch_mgsb<8>(nb, A, Bv, stride, na, nd, dot, s, w, n, h->red, vec2, st);
+    KKT_TRY(rc);
   }
   {
-    const int width = nd > 1 ? 2 : 1;
+    const int width = nd > 0 ? nd : 1;
     ProfScope ps(KKT_K_REDUCE, st);
     finalize_kernel<<<width, 32, 0, st>>>(h->red, nb, width, out);
   }

@@ -32,7 +32,7 @@ COARSE = {"exact": 0, "none": 1, "learned": 2}
 VARIANT = {"multiplicative": 0, "additive": 1}
 POU = {"left": 0, "right": 1}
 NORM = {"l2": 0, "euclidean": 1}
-ORTH = {"mgs": 0, "cgs2": 1, "mgs2": 2}
+ORTH = {"mgs": 0, "cgs2": 1, "mgs2": 2, "mgs4": 3, "mgs8": 4}
 BASIS = {"physical": 0, "spectral": 1}
 LOCAL = {"rasq": 0, "ras": 1}
 COARSE_SOLVE = {"auto": 0, "thomas": 1, "cyclic": 2}

@@ -57,10 +57,14 @@ def test_memory_bound_kernel_reports_against_the_measured_copy_bandwidth():
     import bench
     p = prof(update={"launches": 4, "timed": 4, "ms": 10.0, "flops": 1e9, "bytes": 60e9})
     r = bench.roofline(p, {"hbm_gbs": 6000.0}, "measured")
-    assert r["kernel"] == "mgs2_step_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert r["kernel"] == "mgsb_step_kernel" and r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert r["achieved"] == pytest.approx(60e9 / 0.01 / 1e9)
     assert r["peak"] == 6000.0 and r["frac"] == pytest.approx(1.0)
-    assert r["traffic"] == pytest.approx(15e9 * bench.TRAFFIC_RATIO["mgs2_step_kernel"])
+    ratio = bench.TRAFFIC_RATIO.get("mgsb_step_kernel")
+    assert r["traffic"] == (pytest.approx(15e9 * ratio) if ratio else None)
+    r0 = bench.roofline(p, {"hbm_gbs": 6000.0}, "measured", orth=0)
+    assert r0["kernel"] == "mgs_step_kernel"
+    assert r0["traffic"] == pytest.approx(15e9 * bench.TRAFFIC_RATIO["mgs_step_kernel"])
 
 
 def test_tensor_core_transform_reports_against_its_own_dtype_peak():

@@ -175,6 +175,12 @@ def test_batch_rejects_unsupported_options(kkt):
         kkt.kkt_batch_create([(32, 32, 64, 4, 1.0, 1.0, 1e-4)], opt)
     with pytest.raises(kkt.KKTError):
         kkt.kkt_batch_create([(32, 32, 64, 0, 1.0, 1.0, 1e-4)])   # n_sub 0
+    for orth in ("mgs4", "mgs8"):   # the batched kernels orthogonalise pairs at most
+        kkt.load_library().kkt_default_options(opt)
+        opt.orth = kkt.ORTH[orth]
+        with pytest.raises(kkt.KKTError) as e:
+            kkt.kkt_batch_create([(32, 32, 64, 4, 1.0, 1.0, 1e-4)], opt)
+        assert e.value.status == kkt.KKT_ERR_UNSUPPORTED
 
 
 def test_batch_replays_count_their_kernels(kkt, small_case):

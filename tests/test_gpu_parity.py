@@ -265,7 +265,7 @@ def test_solve_small_configuration_matches_oracle_and_exact(kkt, norm):
     assert rel(host(tight.x), exact) < TOL
 
 
-@pytest.mark.parametrize("orth", ["mgs", "cgs2", "mgs2"])
+@pytest.mark.parametrize("orth", ["mgs", "cgs2", "mgs2", "mgs4", "mgs8"])
 @pytest.mark.parametrize("k", [1, 5, 12, 30])
 def test_fixed_iteration_residuals_match_oracle(kkt, k, orth):
     """After the same k Arnoldi steps (one cycle), GPU and oracle agree on every residual
@@ -290,7 +290,7 @@ def test_fixed_iteration_residuals_match_oracle(kkt, k, orth):
         assert rel(x, ref.x) < TOL       # one step: x = y_1 z_1, well conditioned
 
 
-@pytest.mark.parametrize("orth", ["mgs", "cgs2", "mgs2"])
+@pytest.mark.parametrize("orth", ["mgs", "cgs2", "mgs2", "mgs4", "mgs8"])
 def test_spectral_basis_solve_matches_oracle(kkt, orth):
     """FGMRES on sine-mode coefficients (transforms only at entry and exit): the same residual
     history as the oracle's physical-space FGMRES after 12 steps, the oracle's iteration count
@@ -322,7 +322,7 @@ def test_spectral_basis_solve_matches_oracle(kkt, orth):
     assert rel(x0.numpy(), exact) < TOL
 
 
-@pytest.mark.parametrize("orth", ["mgs", "cgs2", "mgs2"])
+@pytest.mark.parametrize("orth", ["mgs", "cgs2", "mgs2", "mgs4", "mgs8"])
 def test_restarted_fgmres_matches_oracle(kkt, orth):
     """FGMRES(5): several restart cycles; the oracle's FGMRES(5) takes the same iteration count
     within 1, and a 1e-12 solve reaches the exact solution."""
