@@ -480,6 +480,13 @@ int kkt_batch_set_graphs(kkt_batch* b, int on);
  * before the batched waves of the others. Default 2^20 (measured: batching gains 2.6x below
  * about 5e5 unknowns per block and loses above about 1e6); 0 batches every instance. */
 int kkt_batch_set_single_threshold(kkt_batch* b, long long points);
+/* The FP64 transform method of every instance, as kkt_set_dst_method sets it for one handle
+ * (default: each instance's own create-time timing). In the batched waves, an instance whose
+ * transforms run on the tensor cores and whose GEMM passes have at least one tile per SM is
+ * transformed alone (one kkt_dst2d each, inside the step's graph); the others share the line-tile
+ * launches. Returns the first instance's error (KKT_ERR_UNSUPPORTED for KKT_DST_TENSOR on an
+ * instance it does not apply to); instances before it keep the new method. */
+int kkt_batch_set_dst_method(kkt_batch* b, int method);
 /* Solve K_i x_i = f_i for every instance. f, x: host arrays of count DEVICE pointers, 3 V_i
  * doubles each; x_i holds the initial guess on entry. Synchronises `stream`. Returns KKT_OK
  * when every instance converged, KKT_NOT_CONVERGED if some stopped at maxit, else the most

@@ -25,6 +25,9 @@ constexpr long long kChunk = kThreads * 64;   // elements per work item of the v
 // Resident blocks per SM the persistent vector kernels are compiled for (their grid is this many
 // blocks per SM, so the whole grid is resident at once: no tail of late-starting blocks).
 constexpr int kBlocksPerSm = 4;
+// The multi-vector kernels with many vectors need more than 64 registers a thread: compiled (and
+// launched) for 2 blocks per SM above 8 vectors and 1 above 20, so they do not spill.
+constexpr int blocks_per_sm(int nv) { return nv > 20 ? 1 : nv > 8 ? 2 : kBlocksPerSm; }
 
 struct Seg {
   const double* V;   // first vector (basis V_0 or a single vector)
@@ -78,7 +81,7 @@ __device__ __forceinline__ double2 block_sum2(double a, double b, double2* sh) {
 
 // part[t][k] = sum over item t's elements of V_k w (k < NV), part[t][NV] = sum w^2
 template <int NV>
-__global__ void __launch_bounds__(kThreads, kBlocksPerSm) multidot_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+__global__ void __launch_bounds__(kThreads, blocks_per_sm(NV)) multidot_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                        int nj, long long total, double* __restrict__ part) {
   __shared__ double sh[32];
   KKT_SEG_TABLE
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm) multidot_b(const Seg* 
 
 // w -= sum_k coef[inst][k] V_k over the item; part[t] = sum w^2 (NV = 0: norm only)
 template <int NV>
-__global__ void __launch_bounds__(kThreads, kBlocksPerSm) update_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
+__global__ void __launch_bounds__(kThreads, blocks_per_sm(NV)) update_b(const Seg* __restrict__ segs, const long long* __restrict__ prefix,
                                                      int nj, long long total, const double* __restrict__ coef, int ldc,
                                                      double* __restrict__ part, int want_norm) {
   __shared__ double sh[32];
@@ -354,18 +357,19 @@ int dispatch(int count, A... a) {
   }
 }
 
-int persistent_grid() {
+int persistent_grid(int per_sm = kBlocksPerSm) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return std::max(sms, 1) * 4;
+  return std::max(sms, 1) * per_sm;
 }
 
 template <int NV>
 struct MultidotB {
   static int go(const Seg* s, const long long* p, int nj, long long tot, double* part, double flops, cudaStream_t st) {
     ProfScope ps(KKT_K_MULTIDOT, st, flops * (NV + 1), 8.0 * flops / 2 * (NV + 1));
-    multidot_b<NV><<<static_cast<unsigned>(std::min<long long>(tot, persistent_grid())), kThreads, 0, st>>>(s, p, nj, tot, part);
+    multidot_b<NV><<<static_cast<unsigned>(std::min<long long>(tot, persistent_grid(blocks_per_sm(NV)))), kThreads, 0,
+                     st>>>(s, p, nj, tot, part);
     KKT_CUDA_TRY(cudaGetLastError());
     return KKT_OK;
   }
@@ -376,7 +380,7 @@ struct UpdateB {
   static int go(const Seg* s, const long long* p, int nj, long long tot, const double* coef, int ldc, double* part,
                 int want_norm, double flops, cudaStream_t st) {
     ProfScope ps(NV > 0 ? KKT_K_UPDATE : KKT_K_REDUCE, st, flops * (NV + 1), 8.0 * flops / 2 * (NV > 0 ? NV + 2 : 1));
-    update_b<NV><<<static_cast<unsigned>(std::min<long long>(tot, persistent_grid())), kThreads, 0, st>>>(
+    update_b<NV><<<static_cast<unsigned>(std::min<long long>(tot, persistent_grid(blocks_per_sm(NV)))), kThreads, 0, st>>>(
         s, p, nj, tot, coef, ldc, part, want_norm);
     KKT_CUDA_TRY(cudaGetLastError());
     return KKT_OK;
@@ -494,6 +498,15 @@ void kkt_batch_destroy(kkt_batch* b) {
 int kkt_batch_set_graphs(kkt_batch* b, int on) {
   if (!b) return set_error(KKT_ERR_INVALID_ARG, "null batch");
   b->use_graphs = on != 0;
+  return KKT_OK;
+}
+
+int kkt_batch_set_dst_method(kkt_batch* b, int method) {
+  if (!b) return set_error(KKT_ERR_INVALID_ARG, "null batch");
+  for (size_t i = 0; i < b->inst.size(); ++i) {
+    const int rc = kkt_set_dst_method(b->inst[i], method);
+    if (rc < 0) return set_error(rc, std::string("instance ") + std::to_string(i) + ": " + kkt_last_error());
+  }
   return KKT_OK;
 }
 
@@ -743,7 +756,9 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
     auto prepare_slot = [&](BatchSlot& sl, int j, const std::vector<int>& mem) -> int {
       sl.sweep_tb = b->tuned_sweep_tb > 0 ? b->tuned_sweep_tb : 128;
       const int nm = static_cast<int>(mem.size());
-      std::vector<DstJob> fwd(nm), inv(nm);
+      std::vector<DstJob> fwd, inv;
+      sl.oz_jobs[0].clear();
+      sl.oz_jobs[1].clear();
       std::vector<SpecJob> sj(nm);
       std::vector<MatvecJob> mj(nm);
       for (int q = 0; q < nm; ++q) {
@@ -754,8 +769,9 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         const long long V = g.V;
         double* Vj = Vb[k] + static_cast<size_t>(j) * 3 * V;
         double* Zj = Zw[k] + static_cast<size_t>(j) * V;
-        fwd[q] = DstJob{h, Vj + 2 * V, h->spec};
-        inv[q] = DstJob{h, h->spec2, Zj};
+        const bool alone = dst_tensor_fills_gpu(h);
+        (alone ? sl.oz_jobs[0] : fwd).push_back(DstJob{h, Vj + 2 * V, h->spec});
+        (alone ? sl.oz_jobs[1] : inv).push_back(DstJob{h, h->spec2, Zj});
         SpecJob& J = sj[q];
         J.p = make_spec_params(h);
         J.rhat = spectral ? Vj + 2 * V : h->spec;   // the spectral basis needs no transforms
@@ -769,8 +785,8 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       }
       const int tl = b->tuned_tile_lines;
       if (!spectral) {
-        KKT_TRY(dst_batched_prepare(sl, 0, fwd.data(), nm, tl));
-        KKT_TRY(dst_batched_prepare(sl, 2, inv.data(), nm, tl));
+        KKT_TRY(dst_batched_prepare(sl, 0, fwd.data(), static_cast<int>(fwd.size()), tl));
+        KKT_TRY(dst_batched_prepare(sl, 2, inv.data(), static_cast<int>(inv.size()), tl));
       }
       KKT_TRY(spectral_batched_prepare(sl, sj.data(), nm));
       KKT_TRY(matvec_batched_prepare(sl, mj.data(), nm));
@@ -783,9 +799,11 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
       }
       KKT_TRY(dst_batched_launch(sl, 0, s2));
       KKT_TRY(dst_batched_launch(sl, 1, s2));
+      for (const DstJob& d : sl.oz_jobs[0]) KKT_TRY(oz_dst2d(d.h->oz, d.in, d.out, s2));
       KKT_TRY(spectral_batched_launch(sl, d_scale, s2));
       KKT_TRY(dst_batched_launch(sl, 2, s2));
       KKT_TRY(dst_batched_launch(sl, 3, s2));
+      for (const DstJob& d : sl.oz_jobs[1]) KKT_TRY(oz_dst2d(d.h->oz, d.in, d.out, s2));
       KKT_TRY(matvec_batched_launch(sl, d_scale, s2));
       return KKT_OK;
     };
@@ -835,8 +853,13 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
         b->tuned_sweep_tb = cand_tb[a];
         b->tune_ms_sweep[a] = 1e30;
         // (the first candidate also runs the forward transform once, so the sweeps read data)
-        if (prepare_slot(slots[0], 0, everyone) == KKT_OK &&
-            (a > 0 || (dst_batched_launch(slots[0], 0, st) == KKT_OK && dst_batched_launch(slots[0], 1, st) == KKT_OK)))
+        auto forward = [&]() -> int {
+          KKT_TRY(dst_batched_launch(slots[0], 0, st));
+          KKT_TRY(dst_batched_launch(slots[0], 1, st));
+          for (const DstJob& d : slots[0].oz_jobs[0]) KKT_TRY(oz_dst2d(d.h->oz, d.in, d.out, st));
+          return KKT_OK;
+        };
+        if (prepare_slot(slots[0], 0, everyone) == KKT_OK && (a > 0 || forward() == KKT_OK))
           b->tune_ms_sweep[a] = time_it([&] { return spectral_batched_launch(slots[0], d_scale, st); });
         batch_slot_free(slots[0]);
         if (b->tune_ms_sweep[a] < b->tune_ms_sweep[best_tb]) best_tb = a;
@@ -1210,6 +1233,11 @@ int kkt_batch_solve(kkt_batch* b, const double* const* f, double* const* x, doub
   cudaFree(d_small);
   cudaFree(arena);
   if (rc_all < 0) return rc_all;
+  // a tensor-core transform that gave up waiting on its pipeline fails its instance
+  std::vector<char> is_solo(n_inst, 0);
+  for (int i : solo) is_solo[i] = 1;
+  for (int i = 0; i < n_inst; ++i)
+    if (!is_solo[i] && b->inst[i]->dst_tensor && oz_check(b->inst[i]->oz, st) < 0) all[i].status = KKT_ERR_TIMEOUT;
   for (int i : solo) {
     all[i].its = solo_its[i];
     all[i].status = solo_status[i];

@@ -431,8 +431,16 @@ void dst_plan_destroy(DstPlan& p) {
 // Batched 2D DST over several instances: one launch for all row passes, one for all column
 // passes; tables filled once per slot (outside any graph capture), launches read them.
 int dst_batched_prepare(BatchSlot& slot, int first_pass, const DstJob* jobs, int njobs, int tile_lines) {
-  if (njobs < 1 || njobs > KKT_BATCH_MAX) return set_error(KKT_ERR_INVALID_ARG, "batched jobs out of range");
-  slot.njobs = njobs;
+  if (njobs < 0 || njobs > KKT_BATCH_MAX) return set_error(KKT_ERR_INVALID_ARG, "batched jobs out of range");
+  slot.dst_njobs = njobs;
+  if (njobs == 0) {   // every instance of the slot transforms on its own
+    for (int pass = first_pass; pass < first_pass + 2; ++pass) {
+      slot.dst_total[pass] = 0;
+      slot.dst_smem[pass] = 0;
+      slot.dst_flops[pass] = slot.dst_bytes[pass] = 0.0;
+    }
+    return KKT_OK;
+  }
   if (!slot.dst) {
     // capacity for the largest batch, so a slot can be refilled with any job count
     KKT_CUDA_TRY(cudaMalloc(&slot.dst, 4 * static_cast<size_t>(KKT_BATCH_MAX) * sizeof(DstLaunch)));
@@ -481,7 +489,7 @@ int dst_batched_launch(const BatchSlot& slot, int pass, cudaStream_t st) {
   ProfScope ps(KKT_K_DST, st, slot.dst_flops[pass], slot.dst_bytes[pass]);
   dst_tile_batched<<<static_cast<unsigned>(grid), kThreads, sm, st>>>(
       slot.dst + static_cast<size_t>(pass) * KKT_BATCH_MAX, slot.dst_prefix + static_cast<size_t>(pass) * (KKT_BATCH_MAX + 1),
-      slot.njobs, total);
+      slot.dst_njobs, total);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
@@ -612,6 +620,14 @@ int dst_set_method(kkt_handle* h, int method) {
   if (method == KKT_DST_AUTO) return dst_autotune(h);
   for (DstPlan* p : {&h->dst_x, &h->dst_y}) p->lane_direct = method == KKT_DST_LANE;
   return KKT_OK;
+}
+
+bool dst_tensor_fills_gpu(const kkt_handle* h) {
+  if (!h->dst_tensor || !h->oz.qs) return false;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return false;
+  return oz_tiles(h->oz) >= sms;
 }
 
 int dst2d(const kkt_handle* h, const double* in, double* out, cudaStream_t st) {

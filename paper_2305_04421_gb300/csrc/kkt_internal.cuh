@@ -294,6 +294,7 @@ int oz_plan_create(OzPlan& o, int n, int slices);
 void oz_plan_destroy(OzPlan& o);
 int oz_dst2d(const OzPlan& o, const double* in, double* out, cudaStream_t st);   // both directions
 int oz_check(const OzPlan& o, cudaStream_t st);   // reads and clears the timeout flag
+long long oz_tiles(const OzPlan& o);               // output tiles of one GEMM pass
 int tc_set_flag(const TcPlan& t);   // host-side write of the timeout flag (kkt_inject_tc_timeout)
 
 // Krylov primitives (deterministic two-stage reductions; results in h->red_out on device)
@@ -401,9 +402,17 @@ int launch_axpby(double alpha, const double* x, double beta, const double* y, do
                  cudaStream_t st);
 
 // Device tables of one batched phase sequence (the launches of one captured graph).
+struct DstJob {
+  const kkt_handle* h;
+  const double* in;
+  double* out;
+};
+
 struct BatchSlot {
   int njobs = 0;
-  // DST: [pass 0 fwd rows, 1 fwd cols, 2 inv rows, 3 inv cols] x njobs
+  // DST: [pass 0 fwd rows, 1 fwd cols, 2 inv rows, 3 inv cols] x dst_njobs (the instances whose
+  // transforms run as line tiles; the others are in oz_jobs)
+  int dst_njobs = 0;
   DstLaunch* dst = nullptr;
   long long* dst_prefix = nullptr;    // [4][njobs + 1]
   long long dst_total[4] = {0, 0, 0, 0};
@@ -430,6 +439,9 @@ struct BatchSlot {
   long long* mv_prefix = nullptr;
   long long mv_total = 0;
   double mv_V = 0;
+  // instances large enough to fill the GPU alone whose transforms run on the tensor cores:
+  // one 2D transform each, [0] forward, [1] inverse
+  std::vector<DstJob> oz_jobs[2];
 };
 
 // Item lookup of the batched persistent kernels: item t belongs to job k with
@@ -448,16 +460,13 @@ __device__ __forceinline__ int batch_find(const long long* sp, int nj, long long
   return lo;
 }
 
-struct DstJob {
-  const kkt_handle* h;
-  const double* in;
-  double* out;
-};
-
 // Fill the DST tables of `slot` for passes `first_pass`, first_pass + 1 (forward rows/cols or
 // inverse rows/cols) from jobs (synchronous copies); launch one pass from the tables.
 int dst_batched_prepare(BatchSlot& slot, int first_pass, const DstJob* jobs, int njobs, int tile_lines);
 int dst_batched_launch(const BatchSlot& slot, int pass, cudaStream_t st);
+// True when the instance's 2D transforms run on the tensor cores and one of its GEMM passes has
+// at least one tile per SM (a batch then transforms it alone rather than in the line tables).
+bool dst_tensor_fills_gpu(const kkt_handle* h);
 // spectral coarse + sweeps for all jobs of the slot (FP64), scale_dev: per-instance 1/eta
 int spectral_batched_prepare(BatchSlot& slot, const SpecJob* jobs, int njobs);
 int spectral_batched_launch(const BatchSlot& slot, const double* scale_dev, cudaStream_t st);

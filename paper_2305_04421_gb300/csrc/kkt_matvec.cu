@@ -182,7 +182,7 @@ __global__ void matvec_batched(const MatvecJob* __restrict__ jobs, const long lo
   batch_prefix_load(sp, prefix, nj);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int k = batch_find(sp, nj, t);
-    const MatvecJob& J = jobs[k];
+    const MatvecJob J = jobs[k];   // (a register copy: the stores below cannot alias it)
     const double e = scale_dev[J.scale_index];
     const long long idx0 = (t - sp[k]) * kMvItem;
     const long long idx1 = idx0 + kMvItem < J.V ? idx0 + kMvItem : J.V;

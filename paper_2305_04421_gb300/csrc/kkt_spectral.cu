@@ -707,10 +707,13 @@ __device__ __forceinline__ TC coarse_value(const SpecParams& p, int n, int s, co
   if (n < 1 || n > p.Nt) return TC(0);
   const int o = __ldg(p.owner + n - 1) - s + 1;        // 0, 1, 2 for s-1, s, s+1
   if (o < 0 || o > 2) return TC(0);                     // cannot happen when every m_s >= 2
+  // selects, not c3[2 * o]: a runtime index would put c3 in local memory
+  const TC c0 = o == 0 ? c3[0] : (o == 1 ? c3[2] : c3[4]);
+  const TC c1 = o == 0 ? c3[1] : (o == 1 ? c3[3] : c3[5]);
   // FP32 sweeps read phi in FP32: an FP64 load and conversion per node would run on the
   // FP64 pipe, which the reduced-precision forms keep for the coarse solve
-  if constexpr (sizeof(TC) == 4) return c3[2 * o] + c3[2 * o + 1] * __ldg(p.phi_f + n - 1);
-  return c3[2 * o] + c3[2 * o + 1] * static_cast<TC>(__ldg(p.phi + n - 1));
+  if constexpr (sizeof(TC) == 4) return c0 + c1 * __ldg(p.phi_f + n - 1);
+  return c0 + c1 * static_cast<TC>(__ldg(p.phi + n - 1));
 }
 
 template <typename TI, typename TC, typename TO>
@@ -847,7 +850,7 @@ __global__ void coarse_batched(const SpecJob* __restrict__ jobs, const long long
   batch_prefix_load(sp, prefix, nj);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int k = batch_find(sp, nj, t);
-    const SpecJob& J = jobs[k];
+    const SpecJob J = jobs[k];   // (a register copy: the stores below cannot alias it)
     const long long q = (t - sp[k]) * blockDim.x + threadIdx.x;
     if (q < J.p.N && J.p.two_level)
       coarse_body<double>(J.rhat, J.scale_base * scale_dev[J.scale_index], J.p, J.cc, J.cy, q);
@@ -865,7 +868,7 @@ __global__ void __launch_bounds__(kCrThreads) coarse_cr_batched(const SpecJob* _
   batch_prefix_load(sp, prefix, nj);
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int k = batch_find(sp, nj, t);
-    const SpecJob& J = jobs[k];
+    const SpecJob J = jobs[k];   // (a register copy: the stores below cannot alias it)
     const double scale = J.scale_base * scale_dev[J.scale_index];
     if (J.p.crf)
       coarse_crf_body<double>(J.rhat, scale, J.p, J.p.cr_mpc, t - sp[k], J.cc, cr_sm);
@@ -883,7 +886,7 @@ __global__ void sweep_batched(const SpecJob* __restrict__ jobs, const long long*
   batch_prefix_load(sp, prefix, nj);
   for (long long t = t_begin + blockIdx.x; t < t_end; t += gridDim.x) {
     const int k = batch_find(sp, nj, t);
-    const SpecJob& J = jobs[k];
+    const SpecJob J = jobs[k];   // (a register copy: the stores below cannot alias it)
     const long long local = t - sp[k];
     const long long mblocks = (J.p.N + blockDim.x - 1) / blockDim.x;
     const int s = static_cast<int>(local / mblocks);

@@ -1311,6 +1311,8 @@ int oz_dst2d(const OzPlan& o, const double* in, double* out, cudaStream_t st) {
   return oz_gemm(o, out, st);
 }
 
+long long oz_tiles(const OzPlan& o) { return static_cast<long long>(o.rows_pad / kTileM) * (o.P / kOzN); }
+
 int oz_check(const OzPlan& o, cudaStream_t st) {
   if (!o.err) return KKT_OK;
   int e = 0;

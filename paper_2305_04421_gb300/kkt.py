@@ -166,6 +166,7 @@ SIGNATURES = [
     ("kkt_batch_set_memory_limit", _I, [_P, ctypes.c_longlong]),
     ("kkt_batch_set_graphs", _I, [_P, _I]),
     ("kkt_batch_set_single_threshold", _I, [_P, ctypes.c_longlong]),
+    ("kkt_batch_set_dst_method", _I, [_P, _I]),
     ("kkt_batch_solve", _I, [_P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), _D, _I,
                              ctypes.POINTER(KKTBatchStats), _P]),
     ("kkt_profile_enable", _I, [_I]),
@@ -638,6 +639,10 @@ class Batch:
     def set_single_threshold(self, points: int) -> None:
         """Instances with at least `points` unknowns per block are solved one by one (0: none)."""
         _check(load_library().kkt_batch_set_single_threshold(self.b, int(points)))
+
+    def set_dst_method(self, method="auto") -> None:
+        """Every instance's FP64 transform method ('auto', 'tiles', 'lane' or 'tensor')."""
+        _check(load_library().kkt_batch_set_dst_method(self.b, DST_METHOD[method]))
 
     def set_graphs(self, on: bool) -> None:
         """Replay the per-step preconditioner + matvec phase as CUDA graphs (default) or not."""
