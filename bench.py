@@ -325,18 +325,21 @@ def run_reference(args):
 # ---------------------------------------------------------------------------------------------
 
 # DRAM traffic per algorithmic byte for kernels captured with ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum over the launch, divided by the launch's algorithmic bytes). The paired
-# MGS step and the sine transform come from a single-pass capture of the benchmark workload
-# itself; one-pass MGS from a capture of the 256 x 256, Nt = 96 case, whose traffic grows in
-# proportion to the elements processed. Kernels not listed report traffic null.
-TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "dst_tile_kernel": 0.947}
+# dram__bytes_write.sum over the launch, divided by the launch's algorithmic bytes). The blocked
+# (paired) MGS step, the FFT sine transform and the tensor-core transform GEMM come from
+# single-pass captures of the benchmark workload itself; one-pass MGS from a capture of the
+# 256 x 256, Nt = 96 case, whose traffic grows in proportion to the elements processed. Kernels
+# not listed report traffic null.
+TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgsb_step_kernel": 0.997, "dst_tile_kernel": 0.947,
+                 "oz_gemm_kernel": 0.968}
 # FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, of peak sustained, active SMs) from the
 # --set full captures of the 256 x 256, Nt = 96 case: context for an "alu" roofline whose
 # achieved figure counts algorithmic FLOPs, not issued instructions.
 FP64_PIPE_BUSY = {"dst_tile_kernel": [0.78, 0.82], "sweep_kernel": [0.85, 0.85], "matvec_kernel": [0.83, 0.83]}
 
 
-def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64", orth: int = 2) -> dict:
+def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64", orth: int = 2,
+             dst_method: str = "tiles") -> dict:
     """Roofline of the kernel class with the largest device time in the timed region.
 
     The library sums, for every timed launch, the algorithmic FLOPs and bytes of that launch
@@ -350,16 +353,18 @@ def roofline(prof: dict, peaks: dict, peak_kind: str, precision: str = "fp64", o
     e = prof[top]
     sec = e["ms"] / 1e3
     hbm = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS))
-    if top == "dst" and precision in ("bf16", "tf32"):
+    if top == "dst" and (precision in ("bf16", "tf32") or dst_method == "tensor"):
         bf = float(peaks.get("bf16_tflops", 1900.0))
-        if precision == "bf16":
+        if precision == "fp64":   # FP64 transforms as BF16 digit-plane products on the tensor cores
+            alu_peak, alu_src = bf, f"{peak_kind} BF16 dense GEMM (digit-plane products)"
+        elif precision == "bf16":
             alu_peak, alu_src = bf, f"{peak_kind} BF16 dense GEMM"
         elif "tf32_tflops" in peaks:
             alu_peak, alu_src = float(peaks["tf32_tflops"]), "measured cuBLAS TF32 dense GEMM (this run's probe)"
         else:
             alu_peak, alu_src = bf * 1.1 / 2.25, f"{peak_kind} BF16 dense GEMM x 1.1/2.25 (TF32)"
         alu_kind = "tensor"
-        kname = "tc_dst_gemm_kernel"
+        kname = "oz_gemm_kernel" if precision == "fp64" else "tc_dst_gemm_kernel"
     else:
         if "fp64_fma_tflops" in peaks:
             alu_peak = float(peaks["fp64_fma_tflops"])
@@ -1038,7 +1043,8 @@ def run_ours(args):
             "kernel_ms": {k: round(v["ms"], 3) for k, v in prof.items()},
             "kernel_launches": {k: v["launches"] for k, v in prof.items()},
             "clocks": clocks}
-    line["roofline"] = roofline(prof, peaks, peak_kind, orth=kkt.kkt_get_options(solver.h).orth)
+    line["roofline"] = roofline(prof, peaks, peak_kind, orth=kkt.kkt_get_options(solver.h).orth,
+                                dst_method=solver.dst_method())
     solver.close()
     del f, x, f_host, x_host
     torch.cuda.empty_cache()

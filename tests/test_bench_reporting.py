@@ -78,6 +78,10 @@ def test_tensor_core_transform_reports_against_its_own_dtype_peak():
     assert r_tf32["peak"] == pytest.approx(1800.0 * 1.1 / 2.25)
     assert r_bf16["achieved"] == pytest.approx(1000.0)
     assert r_bf16["traffic"] is None   # no ncu ratio for the GEMM kernel
+    r_oz = bench.roofline(p, peaks, "measured", dst_method="tensor")   # FP64 digit-plane products
+    assert r_oz["kernel"] == "oz_gemm_kernel" and r_oz["bound"] == "tensor"
+    assert r_oz["peak"] == pytest.approx(1800.0)
+    assert r_oz["traffic"] == pytest.approx(0.5e9 * bench.TRAFFIC_RATIO["oz_gemm_kernel"])
 
 
 def test_clock_sampler_parses_and_flags_throttle_reasons(tmp_path):
