@@ -130,6 +130,7 @@ struct OzPlan {
   int n = 0;            // intervals per direction (lines of n - 1 points)
   int M = 0;            // n - 1
   int P = 0;            // padded line length: 64, 128 or 256
+  int N = 0;            // output columns per GEMM tile: 64, or 96 when P = 256
   int slices = 0;       // time slices (Nt)
   long long rows = 0;   // lines per pass: slices * M
   int rows_pad = 0;     // rows rounded up to the 128-row tile

@@ -863,12 +863,16 @@ namespace {
 //
 // Kernel: persistent and warp-specialised like the reduced-precision transform. Warp 0 lane 0
 // streams, with TMA, the 6 digit planes of a 128-line x 32-K chunk of the input and the 6
-// planes of the matching 64-column x 32-K chunk of Q (64-byte rows, 64B swizzle) through a
-// 3-stage shared-memory ring; warp 1 lane 0 issues the 21 products x 2 K-steps per chunk into
-// the five accumulators (5 x 64 TMEM columns); warps 2-9 fold the
-// accumulators into 64-bit integers, release them to the next tile's MMAs, then round and
-// store the tile, transposed per slice as the next pass reads it.
-constexpr int kOzN = 64;                          // output columns per tile
+// planes of the matching N-column x 32-K chunk of Q (64-byte rows, 64B swizzle) through a
+// shared-memory ring; warp 1 lane 0 issues the 21 products x 2 K-steps per chunk into the five
+// accumulators (5 x N TMEM columns); warps 2-9 fold the accumulators into 64-bit integers,
+// release them to the next tile's MMAs, then round and store the tile, transposed per slice as
+// the next pass reads it. N is 96 for 256-point padding (five accumulators take 480 of the 512
+// TMEM columns; three tiles cover 288 columns, the last 32 discarded) and 64 otherwise: the
+// wider tile does 1.5x the work per MMA instruction and re-reads each line's planes three
+// times instead of four (measured: 0.64 against 0.77 ms per GEMM pass at 256 x 256, Nt = 1024).
+constexpr int kOzN = 64;                          // output columns per tile (P = 64, 128)
+constexpr int kOzNWide = 96;                      // the same for P = 256 (three tiles of 96 cover 288)
 constexpr int kOzAcc = 5;                         // accumulators: levels 2, 3, 4, 5 and 6-7
 constexpr int kOzProducts = kOzDigits * (kOzDigits + 1) / 2;
 
@@ -877,12 +881,19 @@ __host__ __device__ constexpr int oz_acc(int i, int j) { return i + j < 4 ? i + 
 
 constexpr int kOzChunkBytes = 64;                 // K bytes per chunk row (32 BF16, 64B swizzle)
 constexpr int kOzABytes = kTileM * kOzChunkBytes; // one digit plane: 128 lines x 32 K
-constexpr int kOzBBytes = kOzN * kOzChunkBytes;   // one digit plane of Q: 64 columns x 32 K
-constexpr int kOzStageBytes = kOzDigits * (kOzABytes + kOzBBytes);   // 72 KB: every plane of a chunk
-constexpr int kOzStages = 3;
-constexpr int kOzEpiWarps = 8;                    // two per TMEM lane quadrant, 32 columns each
+constexpr int kOzEpiWarps = 8;                    // two per TMEM lane quadrant, N / 2 columns each
 constexpr int kOzThreads = 64 + 32 * kOzEpiWarps;
-constexpr size_t kOzSmem = 1024 + kOzStages * kOzStageBytes + 256;
+// Per tile width N: one digit plane of Q is N columns x 32 K; a stage holds every plane of a
+// chunk (72 KB at N = 64, 84 KB at N = 96), three stages at N = 64 and two at N = 96.
+template <int N>
+struct OzTile {
+  static constexpr int kBBytes = N * kOzChunkBytes;
+  static constexpr int kStageBytes = kOzDigits * (kOzABytes + kBBytes);
+  static constexpr int kStages = N == kOzN ? 3 : 2;
+  static constexpr size_t kSmem = 1024 + kStages * kStageBytes + 256;
+  static_assert(kOzAcc * N <= 512, "TMEM: five accumulators of N columns");
+  static_assert(kSmem <= 227 * 1024, "shared memory");
+};
 constexpr unsigned long long kOzBias = 0x808080808080ull;   // 128 in each of the six digit positions
 
 struct OzParams {
@@ -1000,8 +1011,11 @@ __device__ __forceinline__ double oz_to_double(long long T, int k) {
   return __longlong_as_double(r);
 }
 
+template <int N>
 __global__ void __launch_bounds__(kOzThreads, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, OzParams p) {
+  constexpr int kOzBBytes = OzTile<N>::kBBytes, kOzStageBytes = OzTile<N>::kStageBytes;
+  constexpr int kOzStages = OzTile<N>::kStages, HALF = N / 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   // stage st: planes A_0..A_5 (kOzABytes each), then B_0..B_5 (kOzBBytes each)
@@ -1014,10 +1028,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   constexpr int KCHUNK = kOzChunkBytes / 2;             // 32 BF16 of K per chunk
   constexpr int K_STEPS = KCHUNK / 16;                  // 2 MMAs of K = 16 per chunk and product
-  constexpr uint32_t IDESC = instr_desc<__nv_bfloat16, kOzN>();
+  constexpr uint32_t IDESC = instr_desc<__nv_bfloat16, N>();
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nct = p.P / kOzN, nchunks = p.P / KCHUNK;
+  const int nct = (p.P + N - 1) / N, nchunks = p.P / KCHUNK;
   const long long ntiles = static_cast<long long>(p.rows_pad / kTileM) * nct;
 
   if (threadIdx.x == 0) {
@@ -1059,7 +1073,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
           for (int i = 0; i < kOzDigits; ++i)
             tma_load_2d(sst + i * kOzABytes, &tmX, c * KCHUNK, i * p.rows_pad + rt * kTileM, full + st);
           for (int j = 0; j < kOzDigits; ++j)
-            tma_load_2d(sst + kOzDigits * kOzABytes + j * kOzBBytes, &tmQ, c * KCHUNK, j * p.P + ct * kOzN, full + st);
+            tma_load_2d(sst + kOzDigits * kOzABytes + j * kOzBBytes, &tmQ, c * KCHUNK, j * p.P + ct * N, full + st);
           issued = g + 1;
         }
       }
@@ -1089,7 +1103,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
                 break;
               }
               asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-              const uint32_t tacc = tmem + static_cast<uint32_t>(a * kOzN);
+              const uint32_t tacc = tmem + static_cast<uint32_t>(a * N);
               bool first = true;
 #pragma unroll
               for (int i = 0; i < kOzDigits; ++i)
@@ -1111,7 +1125,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
 #pragma unroll
               for (int j = 0; j + i < kOzDigits; ++j) {
                 const uint64_t db = smem_desc64(sbq + j * kOzBBytes);
-                const uint32_t tacc = tmem + static_cast<uint32_t>(oz_acc(i, j) * kOzN);
+                const uint32_t tacc = tmem + static_cast<uint32_t>(oz_acc(i, j) * N);
 #pragma unroll
                 for (int kk = 0; kk < K_STEPS; ++kk) MmaKind<__nv_bfloat16>::mma(tacc, da + 2ull * kk, db + 2ull * kk, IDESC, 1u);
               }
@@ -1130,7 +1144,7 @@ __global__ void __launch_bounds__(kOzThreads, 1)
     }
   } else {
     // epilogue warps 2..9: warp w reads TMEM lanes 32 (w % 4) .. + 31 (the tile's lines) and
-    // the 32 columns (w - 2) / 4 of the tile's 64
+    // the half (w - 2) / 4 of the tile's N columns
     const int quad = warp & 3, half = (warp - 2) >> 2;
     int lt = 0;
     for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
@@ -1148,24 +1162,24 @@ __global__ void __launch_bounds__(kOzThreads, 1)
       const int er = row_ok ? p.xexp[r] : 0;
       double* obase = p.out + static_cast<long long>(sl) * p.M * p.M + jj;
       const uint32_t tbase = tmem + (static_cast<uint32_t>(quad * 32) << 16);
-      // phase 1: the warp's 32 columns as 64-bit integers T in units of 2^-48, one accumulator
+      // phase 1: the warp's N / 2 columns as 64-bit integers T in units of 2^-48, one accumulator
       // at a time, each released to the next tile's MMAs as soon as it is folded in. The exact
       // accumulators hold n 2^(-8L) with integer |n| <= 2^24 (levels L = 2..5), so
       // n = rint(acc 2^(8L)) is exact (a power-of-two product and an FP32 -> int32 conversion);
       // the tail (levels 6 and 7) is rounded to units of 2^-48. Horner's rule from level 2 on,
       // T = 256 T + n, gives T = sum_L n_L 2^(8(6 - L)) + tail (|T| < 2^55).
-      long long T[32];
+      long long T[HALF];
 #pragma unroll
-      for (int t = 0; t < 32; ++t) T[t] = 0;
+      for (int t = 0; t < HALF; ++t) T[t] = 0;
 #pragma unroll
       for (int a = 0; a < kOzAcc; ++a) {
         const float scale = a == 0 ? 0x1p16f : a == 1 ? 0x1p24f : a == 2 ? 0x1p32f : a == 3 ? 0x1p40f : 0x1p48f;
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {
+        for (int g8 = 0; g8 < HALF / 8; ++g8) {
           uint32_t v[8];
           asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-                       : "r"(tbase + static_cast<uint32_t>(a * kOzN + half * 32 + g8 * 8)));
+                       : "r"(tbase + static_cast<uint32_t>(a * N + half * HALF + g8 * 8)));
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
           for (int t = 0; t < 8; ++t)
@@ -1176,13 +1190,10 @@ __global__ void __launch_bounds__(kOzThreads, 1)
         if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(t_empty + a)) : "memory");
       }
       // phase 2: round to FP64 with the line's and the columns' exponents, store transposed
-      const int cl = ct * kOzN + half * 32 + lane;
-      const int gl = (cl < p.P ? __ldg(p.qexp + cl) : 0) - 48;
 #pragma unroll
-      for (int t = 0; t < 32; ++t) {
-        const int c = ct * kOzN + half * 32 + t;
-        const int k = er + __shfl_sync(0xffffffffu, gl, t);
-        if (row_ok && c < p.M) obase[static_cast<long long>(c) * p.M] = oz_to_double(T[t], k);
+      for (int t = 0; t < HALF; ++t) {
+        const int c = ct * N + half * HALF + t;   // (the same column in every lane: a broadcast load)
+        if (row_ok && c < p.M) obase[static_cast<long long>(c) * p.M] = oz_to_double(T[t], er + __ldg(p.qexp + c) - 48);
       }
     }
   }
@@ -1215,25 +1226,30 @@ int oz_split(const OzPlan& o, const double* in, cudaStream_t st) {
   return KKT_OK;
 }
 
-int oz_gemm(const OzPlan& o, double* out, cudaStream_t st) {
+template <int N>
+int oz_gemm_launch(const OzPlan& o, double* out, unsigned grid, cudaStream_t st) {
   static bool attr = false;
   if (!attr) {
-    KKT_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(kOzSmem)));
+    KKT_CUDA_TRY(cudaFuncSetAttribute(oz_gemm_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(OzTile<N>::kSmem)));
     attr = true;
   }
+  OzParams p{o.P, o.M, o.rows, o.rows_pad, o.xexp, o.qexp, out, o.err};
+  oz_gemm_kernel<N><<<grid, kOzThreads, OzTile<N>::kSmem, st>>>(o.map_x, o.map_q, p);
+  KKT_CUDA_TRY(cudaGetLastError());
+  return KKT_OK;
+}
+
+int oz_gemm(const OzPlan& o, double* out, cudaStream_t st) {
   int dev = 0, sms = 0;
   KKT_CUDA_TRY(cudaGetDevice(&dev));
   KKT_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const long long ntiles = static_cast<long long>(o.rows_pad / kTileM) * (o.P / kOzN);
+  const long long ntiles = oz_tiles(o);
   const unsigned grid = static_cast<unsigned>(std::min<long long>(ntiles, sms));
-  OzParams p{o.P, o.M, o.rows, o.rows_pad, o.xexp, o.qexp, out, o.err};
   // kOzProducts BF16 digit-plane products per tile (2 rows_pad P^2 FLOP each); planes in, FP64 out
   ProfScope ps(KKT_K_DST, st, kOzProducts * 2.0 * o.rows_pad * static_cast<double>(o.P) * o.P,
                2.0 * kOzDigits * static_cast<double>(o.rows_pad) * o.P + 8.0 * static_cast<double>(o.rows) * o.M);
-  oz_gemm_kernel<<<grid, kOzThreads, kOzSmem, st>>>(o.map_x, o.map_q, p);
-  KKT_CUDA_TRY(cudaGetLastError());
-  return KKT_OK;
+  return o.N == kOzNWide ? oz_gemm_launch<kOzNWide>(o, out, grid, st) : oz_gemm_launch<kOzN>(o, out, grid, st);
 }
 
 }  // namespace
@@ -1244,6 +1260,7 @@ int oz_plan_create(OzPlan& o, int n, int slices) {
   o.n = n;
   o.M = n - 1;
   o.P = o.M <= 64 ? 64 : (o.M <= 128 ? 128 : 256);
+  o.N = o.P == 256 ? kOzNWide : kOzN;
   o.slices = slices;
   o.rows = static_cast<long long>(slices) * o.M;
   if ((o.rows + kTileM - 1) / kTileM * kTileM * kOzDigits > 0x7FFFFFFFLL)
@@ -1287,7 +1304,7 @@ int oz_plan_create(OzPlan& o, int n, int slices) {
   KKT_CUDA_TRY(cudaMemset(o.err, 0, sizeof(int)));
   o.bytes = qbytes + xbytes + P * sizeof(int) + o.rows_pad * sizeof(int) + o.rows * M * sizeof(double) + sizeof(int);
   KKT_TRY(make_map(&o.map_x, o.xs, 2, static_cast<long long>(kOzDigits) * o.rows_pad, P, kTileM, kOzChunkBytes));
-  KKT_TRY(make_map(&o.map_q, o.qs, 2, static_cast<long long>(kOzDigits) * P, P, kOzN, kOzChunkBytes));
+  KKT_TRY(make_map(&o.map_q, o.qs, 2, static_cast<long long>(kOzDigits) * P, P, o.N, kOzChunkBytes));
   return KKT_OK;
 }
 
@@ -1311,7 +1328,7 @@ int oz_dst2d(const OzPlan& o, const double* in, double* out, cudaStream_t st) {
   return oz_gemm(o, out, st);
 }
 
-long long oz_tiles(const OzPlan& o) { return static_cast<long long>(o.rows_pad / kTileM) * (o.P / kOzN); }
+long long oz_tiles(const OzPlan& o) { return static_cast<long long>(o.rows_pad / kTileM) * ((o.P + o.N - 1) / o.N); }
 
 int oz_check(const OzPlan& o, cudaStream_t st) {
   if (!o.err) return KKT_OK;
