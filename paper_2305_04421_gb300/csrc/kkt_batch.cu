@@ -205,6 +205,10 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm) mgs2_b(const Seg* __re
   __shared__ double2 sh2[32];
   KKT_SEG_TABLE
   constexpr int W = ND > 1 ? 2 : 1;
+  // the partial dots run on across this block's consecutive items of one instance and are
+  // reduced over the block once, at its last item of that instance (the other items' slots get
+  // zero): no barrier, and no drain of the loads in flight, between items of one instance
+  double acc0 = 0.0, acc1 = 0.0;
   for (long long t = blockIdx.x; t < total; t += gridDim.x) {
     const int q = batch_find(sp, nj, t);
     const Seg S = ss[q];
@@ -215,7 +219,6 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm) mgs2_b(const Seg* __re
     const double* B0 = S.V + (k + NA) * S.stride;
     const double* B1 = B0 + S.stride;
     const long long e0 = (t - sp[q]) * kChunk, e1 = min(e0 + kChunk, S.n);
-    double acc0 = 0.0, acc1 = 0.0;
     // 16-byte loads and stores when every vector of the step starts 16-byte aligned (item
     // starts are even: kChunk is); else 8-byte loads
     const uintptr_t al = reinterpret_cast<uintptr_t>(S.w) | reinterpret_cast<uintptr_t>(A0) |
@@ -294,6 +297,14 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm) mgs2_b(const Seg* __re
         }
       }
     }
+    const long long tn = t + gridDim.x;
+    if (tn < total && tn < sp[q + 1]) {   // this block's next item is of the same instance
+      if (threadIdx.x == 0) {
+        part[t * W] = 0.0;
+        if (ND > 1) part[t * W + 1] = 0.0;
+      }
+      continue;
+    }
     if (ND > 1) {
       const double2 r = block_sum2(acc0, acc1, sh2);
       if (threadIdx.x == 0) {
@@ -304,6 +315,8 @@ __global__ void __launch_bounds__(kThreads, kBlocksPerSm) mgs2_b(const Seg* __re
       const double r0 = block_sum(acc0, sh);
       if (threadIdx.x == 0) part[t * W] = r0;
     }
+    acc0 = 0.0;
+    acc1 = 0.0;
   }
 }
 
