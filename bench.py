@@ -330,7 +330,8 @@ def run_reference(args):
 # single-pass captures of the benchmark workload itself; one-pass MGS from a capture of the
 # 256 x 256, Nt = 96 case, whose traffic grows in proportion to the elements processed. Kernels
 # not listed report traffic null.
-TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgsb_step_kernel": 0.997, "dst_tile_kernel": 0.947}
+TRAFFIC_RATIO = {"mgs_step_kernel": 0.952, "mgsb_step_kernel": 0.997, "dst_tile_kernel": 0.947,
+                 "oz_gemm_kernel": 0.969}
 # FP64 pipe busy fraction (sm__pipe_fp64_cycles_active, of peak sustained, active SMs) from the
 # --set full captures of the 256 x 256, Nt = 96 case: context for an "alu" roofline whose
 # achieved figure counts algorithmic FLOPs, not issued instructions.
