@@ -180,7 +180,7 @@ struct MgsScale {
   double s[BS];
 };
 
-template <int BS, bool NORM>
+template <int BS, bool NORM, int U>
 __global__ void __launch_bounds__(kRedThreads) mgsb_step_kernel(const double* __restrict__ A,
                                                                 const double* __restrict__ Bv, long long stride,
                                                                 int na, int nd, const double* __restrict__ dot,
@@ -197,28 +197,41 @@ __global__ void __launch_bounds__(kRedThreads) mgsb_step_kernel(const double* __
   const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long np = pair_count(n, vec2);
   const double2 z2 = make_double2(0.0, 0.0);
-  for (long long i = tid; i < np; i += gs) {
-    double2 wi = reinterpret_cast<const double2*>(w)[i];
-    double2 av[BS], bv[BS];
+  // U grid strides per trip, their loads issued together (U = 2 for the steps that stream at most
+  // three vectors, whose single stride keeps too few loads in flight); the accumulation order
+  // is that of U = 1, and an element past the end loads zeros and adds nothing
+  for (long long i0 = tid; i0 < np; i0 += U * gs) {
+    double2 wi[U], av[U][BS], bv[U][BS];
 #pragma unroll
-    for (int a = 0; a < BS; ++a) av[a] = a < na ? reinterpret_cast<const double2*>(A + a * stride)[i] : z2;
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * gs;
+      const bool in = U == 1 || i < np;
+      wi[u] = in ? reinterpret_cast<const double2*>(w)[i] : z2;
 #pragma unroll
-    for (int d = 0; d < BS; ++d) bv[d] = (!NORM && d < nd) ? reinterpret_cast<const double2*>(Bv + d * stride)[i] : z2;
-    if (na > 0) {
-#pragma unroll
-      for (int a = 0; a < BS; ++a)
-        if (a < na) {
-          wi.x = fma(-c[a], av[a].x, wi.x);
-          wi.y = fma(-c[a], av[a].y, wi.y);
-        }
-      reinterpret_cast<double2*>(w)[i] = wi;
-    }
-    if (NORM) {
-      acc[0] = fma(wi.x, wi.x, fma(wi.y, wi.y, acc[0]));
-    } else {
+      for (int a = 0; a < BS; ++a) av[u][a] = (in && a < na) ? reinterpret_cast<const double2*>(A + a * stride)[i] : z2;
 #pragma unroll
       for (int d = 0; d < BS; ++d)
-        if (d < nd) acc[d] = fma(bv[d].x, wi.x, fma(bv[d].y, wi.y, acc[d]));
+        bv[u][d] = (in && !NORM && d < nd) ? reinterpret_cast<const double2*>(Bv + d * stride)[i] : z2;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * gs;
+      if (na > 0) {
+#pragma unroll
+        for (int a = 0; a < BS; ++a)
+          if (a < na) {
+            wi[u].x = fma(-c[a], av[u][a].x, wi[u].x);
+            wi[u].y = fma(-c[a], av[u][a].y, wi[u].y);
+          }
+        if (U == 1 || i < np) reinterpret_cast<double2*>(w)[i] = wi[u];
+      }
+      if (NORM) {
+        acc[0] = fma(wi[u].x, wi[u].x, fma(wi[u].y, wi[u].y, acc[0]));
+      } else {
+#pragma unroll
+        for (int d = 0; d < BS; ++d)
+          if (d < nd) acc[d] = fma(bv[u][d].x, wi[u].x, fma(bv[u][d].y, wi[u].y, acc[d]));
+      }
     }
   }
   for (long long i = 2 * np + tid; i < n; i += gs) {
@@ -425,10 +438,16 @@ int launch_mgsb(int nb, const double* A, const double* Bv, long long stride, int
                 const double* s, double* w, long long n, double* part, bool vec2, cudaStream_t st) {
   MgsScale<BS> sc{};
   for (int a = 0; a < na; ++a) sc.s[a] = s[a];
-  if (nd == 0)
-    mgsb_step_kernel<BS, true><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+  constexpr int UN = BS == 2 ? 2 : 1;          // (pairs only: their narrow steps)
+  const bool narrow = BS == 2 && na + nd <= 2;   // at most two vectors besides w
+  if (nd == 0 && narrow)
+    mgsb_step_kernel<BS, true, UN><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+  else if (nd == 0)
+    mgsb_step_kernel<BS, true, 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+  else if (narrow)
+    mgsb_step_kernel<BS, false, UN><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
   else
-    mgsb_step_kernel<BS, false><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+    mgsb_step_kernel<BS, false, 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
