@@ -105,6 +105,7 @@ def workload_for(omega: float) -> workloads.Workload:
                               target=w.target, seed=w.seed)
 
 
+ORTH_CODE = {"mgs": 0, "cgs2": 1, "mgs2": 2, "mgs4": 3, "mgs8": 4}   # the library's enum kkt_orth
 ORTH_TEXT = {
     0: "modified Gram-Schmidt",
     1: "classical Gram-Schmidt with one conditional repeat",
@@ -311,7 +312,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": solve_s * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": describe(w, kkt.kkt_get_options(solver.h).orth), "impl": "reference",
+            "config": describe(w, ORTH_CODE[args.orth or "mgs2"]), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": sample + f"; x {iters} iterations (the GPU solve's count on this "
                                                 f"workload)"},

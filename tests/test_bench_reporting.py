@@ -107,3 +107,25 @@ def test_clock_sampler_parses_and_flags_throttle_reasons(tmp_path):
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0 and out["samples"] == 3
     assert out["reasons"] == ["sw_power_cap"]
     assert not csv.exists()
+
+
+def test_reference_arm_prints_one_complete_line(monkeypatch, capsys):
+    """The reference arm's JSON line (the oracle's time per iteration stubbed out: the real
+    sample takes tens of seconds) carries the keys the GPU arm's line has, the same config and
+    metric, and a cpu_baseline describing itself."""
+    import argparse
+    import json
+    import bench
+    monkeypatch.setattr(bench, "oracle_iteration_sample", lambda w, kdim: (0.5, "stub sample"))
+    args = argparse.Namespace(gpus=1, steps=2, warmup=1, omega=1e-4, ref_iterations=25, orth=None)
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] == 1.0 / (0.5 * 25) and line["unit"] == "solves/s"
+    assert line["config"] == bench.describe(bench.workload_for(1e-4), 2)
+    assert line["config"]["orthogonalisation"] == bench.ORTH_TEXT[2]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    args.orth = "mgs"
+    assert bench.run_reference(args) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["config"]["orthogonalisation"] == bench.ORTH_TEXT[0]
