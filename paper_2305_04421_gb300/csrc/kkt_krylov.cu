@@ -180,8 +180,9 @@ struct MgsScale {
   double s[BS];
 };
 
+// (Pairs are compiled for four resident blocks per SM, the launch's whole grid.)
 template <int BS, bool NORM, int U>
-__global__ void __launch_bounds__(kRedThreads) mgsb_step_kernel(const double* __restrict__ A,
+__global__ void __launch_bounds__(kRedThreads, BS == 2 ? 4 : 1) mgsb_step_kernel(const double* __restrict__ A,
                                                                 const double* __restrict__ Bv, long long stride,
                                                                 int na, int nd, const double* __restrict__ dot,
                                                                 MgsScale<BS> sc, double* __restrict__ w, long long n,
@@ -197,9 +198,9 @@ __global__ void __launch_bounds__(kRedThreads) mgsb_step_kernel(const double* __
   const long long tid = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
   const long long np = pair_count(n, vec2);
   const double2 z2 = make_double2(0.0, 0.0);
-  // U grid strides per trip, their loads issued together (U = 2 for the steps that stream at most
-  // three vectors, whose single stride keeps too few loads in flight); the accumulation order
-  // is that of U = 1, and an element past the end loads zeros and adds nothing
+  // U grid strides per trip, their loads issued together (U = 2 or 4 for the steps that stream
+  // few vectors, whose single stride keeps too few loads in flight); the accumulation order is
+  // that of U = 1, and an element past the end loads zeros and adds nothing
   for (long long i0 = tid; i0 < np; i0 += U * gs) {
     double2 wi[U], av[U][BS], bv[U][BS];
 #pragma unroll
@@ -438,16 +439,18 @@ int launch_mgsb(int nb, const double* A, const double* Bv, long long stride, int
                 const double* s, double* w, long long n, double* part, bool vec2, cudaStream_t st) {
   MgsScale<BS> sc{};
   for (int a = 0; a < na; ++a) sc.s[a] = s[a];
-  constexpr int UN = BS == 2 ? 2 : 1;          // (pairs only: their narrow steps)
-  const bool narrow = BS == 2 && na + nd <= 2;   // at most two vectors besides w
-  if (nd == 0 && narrow)
-    mgsb_step_kernel<BS, true, UN><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
-  else if (nd == 0)
-    mgsb_step_kernel<BS, true, 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
-  else if (narrow)
-    mgsb_step_kernel<BS, false, UN><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
-  else
-    mgsb_step_kernel<BS, false, 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+  // grid strides per trip for pairs: 4 when one vector besides w is streamed, 2 up to three
+  constexpr bool P2 = BS == 2;
+  const int u = !P2 ? 1 : (na + nd <= 1 ? 4 : (na + nd <= 3 ? 2 : 1));
+  if (nd == 0) {
+    if (u == 4) mgsb_step_kernel<BS, true, P2 ? 4 : 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+    else if (u == 2) mgsb_step_kernel<BS, true, P2 ? 2 : 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+    else mgsb_step_kernel<BS, true, 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+  } else {
+    if (u == 4) mgsb_step_kernel<BS, false, P2 ? 4 : 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+    else if (u == 2) mgsb_step_kernel<BS, false, P2 ? 2 : 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+    else mgsb_step_kernel<BS, false, 1><<<nb, kRedThreads, 0, st>>>(A, Bv, stride, na, nd, dot, sc, w, n, part, vec2);
+  }
   KKT_CUDA_TRY(cudaGetLastError());
   return KKT_OK;
 }
