@@ -98,3 +98,25 @@ def test_product_package_does_not_import_the_oracle():
             if fn.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", txt, re.M), fn
+
+
+def test_binding_enum_maps_match_the_header():
+    """Every name-to-value map of the binding equals the header's enum of the same kind, value for
+    value and complete (a reordered or missing entry would pass wrong options silently)."""
+    import paper_2305_04421_gb300.kkt as kkt
+    text = open(os.path.join(ROOT, "include", "kkt.h")).read()
+
+    def enum(name):
+        body = re.search(r"enum %s \{(.*?)\};" % name, text, re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        return {m.group(1): int(m.group(2)) for m in re.finditer(r"(KKT_\w+)\s*=\s*(-?\d+)", body)}
+
+    cases = [("kkt_precision", "KKT_PREC_", kkt.PREC), ("kkt_coarse", "KKT_COARSE_", kkt.COARSE),
+             ("kkt_variant", "KKT_", kkt.VARIANT), ("kkt_residual_norm", "KKT_NORM_", kkt.NORM),
+             ("kkt_orth", "KKT_ORTH_", kkt.ORTH), ("kkt_basis", "KKT_BASIS_", kkt.BASIS),
+             ("kkt_local", "KKT_LOCAL_", kkt.LOCAL), ("kkt_coarse_solve", "KKT_COARSE_SOLVE_", kkt.COARSE_SOLVE),
+             ("kkt_pou", "KKT_POU_", kkt.POU), ("kkt_staging", "KKT_STAGING_", kkt.STAGING),
+             ("kkt_dst_method", "KKT_DST_", kkt.DST_METHOD)]
+    for cname, prefix, pymap in cases:
+        want = {k[len(prefix):].lower(): v for k, v in enum(cname).items()}
+        assert want == pymap, (cname, want, pymap)
